@@ -1,0 +1,106 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin fails.
+
+Each case swaps one oracle function for a subtly wrong copy -- a dropped term, a
+wrong sign, a transposed operand, an off-by-one index -- and runs the pin that is
+meant to catch it.
+"""
+import numpy as np
+import pytest
+
+import test_oracle_pins as pins
+from oracle import clean, geometry, gmm, imaging, operator, pswf
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_uvw_sign_error_is_caught(monkeypatch):
+    orig = geometry.uvw
+
+    def bad(*a, **k):
+        out = orig(*a, **k)
+        out[..., 1] *= -1.0                       # v with the wrong sign
+        return out
+    monkeypatch.setattr(geometry, "uvw", bad)
+    _fails(pins.test_uvw_closed_form_pole_source)
+
+
+def test_uvw_swapped_axes_is_caught(monkeypatch):
+    orig = geometry.local_xyz
+
+    def bad(enu, lat):
+        out = orig(enu, lat)
+        return out[:, [1, 0, 2]]                  # X and Y transposed
+    monkeypatch.setattr(geometry, "local_xyz", bad)
+    _fails(pins.test_local_xyz_equator_and_pole)
+
+
+def test_mirror_without_conjugate_is_caught(monkeypatch):
+    def bad(rec, G, ker, weights=None):
+        h = (ker.W - 1) // 2
+        taps = np.arange(-h, h + 1)
+        Z = np.zeros((G, G), np.complex128)
+        for i in np.nonzero(rec["w"] > 0)[0]:
+            wk = np.outer(ker.kernel(taps + rec["fv"][i]), ker.kernel(taps + rec["fu"][i]))
+            ku, kv, V = rec["ku"][i], rec["kv"][i], rec["vis"][i]
+            Z[kv - h:kv + h + 1, ku - h:ku + h + 1] += wk * (V + 1j)
+            Z[np.ix_(G - kv - taps, G - ku - taps)] += wk * (V + 1j)   # conj dropped
+        return Z
+    monkeypatch.setattr(imaging, "grid", bad)
+    _fails(pins.test_grid_hermitian_visibility_part)
+
+
+def test_missing_grid_correction_is_caught(monkeypatch):
+    orig = pswf.Spheroidal.grid_correction
+
+    def bad(self, G):
+        return np.ones(G)                        # dropped term: no correction
+    monkeypatch.setattr(pswf.Spheroidal, "grid_correction", bad)
+    _fails(pins.test_gridded_image_matches_direct_dft, 32, 7, 102)
+
+
+def test_kernel_table_off_by_one_is_caught(monkeypatch):
+    orig = pswf.Spheroidal.kernel
+
+    def bad(self, dist):
+        return orig(self, np.abs(np.asarray(dist, float)) + 1.0 / self.OS)
+    monkeypatch.setattr(pswf.Spheroidal, "kernel", bad)
+    _fails(pins.test_kernel_table_interpolation_error)
+
+
+def test_transposed_beam_shift_in_clean_is_caught(monkeypatch):
+    def bad(D, Bm, gain, thr, cap, peak_mode=0):
+        R = np.array(D, float)
+        N = R.shape[0]
+        pos, flux = [], []
+        val, p = clean.peak(R, peak_mode)
+        while val > thr and len(pos) < cap:
+            f = gain * val
+            py, px = divmod(p, N)
+            R -= f * Bm[N - px:2 * N - px, N - py:2 * N - py]      # row/column swapped
+            pos.append(p)
+            flux.append(f)
+            val, p = clean.peak(R, peak_mode)
+        return R, np.asarray(pos), np.asarray(flux)
+    monkeypatch.setattr(clean, "hogbom", bad)
+    _fails(pins.test_hogbom_isolated_point_source_closed_form)
+
+
+def test_adjoint_without_conjugate_phase_is_caught(monkeypatch):
+    orig = operator.adjoint
+
+    def bad(y, rec, N, G, ker, K=None):
+        return orig(np.conj(y), rec, N, G, ker, K)                 # grids conj(y): wrong adjoint
+    monkeypatch.setattr(operator, "adjoint", bad)
+    _fails(pins.test_operator_dot_product_adjoint)
+
+
+def test_gmm_unweighted_variance_is_caught(monkeypatch):
+    orig = gmm.em
+
+    def bad(h, x, width, K=3, max_iter=1000, tol=1e-12):
+        return orig(np.where(h > 0, 1.0, 0.0), x, width, K, max_iter, tol)   # counts dropped
+    monkeypatch.setattr(gmm, "em", bad)
+    _fails(pins.test_gmm_recovers_known_mixture)
