@@ -1,0 +1,208 @@
+/*
+ * muser.h -- C ABI of the B300 (sm_103a) MUSER imaging library (libmuser.so).
+ *
+ * The calls follow the imaging problem of Mei et al., "GPU-Based High-Performance
+ * Imaging for Mingantu Spectral RadioHeliograph": visibilities and (u, v, w) in,
+ * dirty map, dirty beam and CLEANed images out (Algorithm 1: dirty_image,
+ * pre_clean, improved_clean), batched over (frame, channel) instances.
+ *
+ * Conventions shared by every call
+ *  - Pointers named in the argument list are DEVICE pointers owned by the caller,
+ *    except where a comment says "host".  The library never frees them and never
+ *    allocates device memory: scratch comes from a caller buffer `ws` of at least
+ *    muser_workspace_size(...) bytes, aligned to 256 bytes.
+ *  - Complex values are interleaved float pairs (re, im) ("complex64").
+ *    Images and grids are row-major: row = v / m / y, column = u / l / x.
+ *  - Instance i = frame * n_chan + chan.  Batches of records are CSR: records of
+ *    instance i are rec[vis_off[i] .. vis_off[i+1]).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns MUSER_OK or an error code before or at launch time; a
+ *    thread-local message is available from muser_last_error().  Calls that return
+ *    an error launch nothing that writes caller memory.
+ *  - Per-instance problems are not errors: they are OR-ed as MUSER_ST_* bits into a
+ *    device int32 status[B] array, which the caller zeroes before the first call of
+ *    a batch (muser_image zeroes it itself).
+ *  - No kernel traps or asserts; device-side waits are bounded.
+ */
+#ifndef MUSER_H
+#define MUSER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MUSER_API __attribute__((visibility("default")))
+#else
+#define MUSER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *muser_stream_t;   /* = cudaStream_t */
+
+/* return codes */
+enum {
+  MUSER_OK = 0,
+  MUSER_ERR_ARG = 1,          /* invalid argument (size, pointer, alignment, config) */
+  MUSER_ERR_CUDA = 2,         /* a CUDA launch or runtime call failed */
+  MUSER_ERR_TIMEOUT = 3,      /* a bounded device-side wait gave up */
+  MUSER_ERR_UNSUPPORTED = 4,  /* valid but not implemented for these sizes */
+  MUSER_ERR_WORKSPACE = 5     /* workspace missing, too small or misaligned */
+};
+
+/* per-instance status bits */
+enum {
+  MUSER_ST_ALL_FLAGGED = 1,     /* nothing was gridded: dirty map/beam are zero, no CLEAN */
+  MUSER_ST_NONFINITE = 2,       /* a NaN/Inf visibility was dropped */
+  MUSER_ST_DROPPED = 4,         /* a visibility fell outside the uv grid and was dropped */
+  MUSER_ST_GMM_DEGENERATE = 8,  /* a mixture component has weight < 1e-4 */
+  MUSER_ST_ITER_CAP = 16,       /* CLEAN stopped at max_iter with the peak still above thr */
+  MUSER_ST_BEAM_FIT = 32        /* the beam main lobe did not fit the fitting window */
+};
+
+enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1 };
+
+enum {
+  MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
+  MUSER_CALL_RESTORE = 5, MUSER_CALL_IMAGE = 6, MUSER_CALL_DEGRID = 7, MUSER_CALL_CHI2 = 8
+};
+
+/* Imaging parameters (host struct, passed by pointer). */
+typedef struct muser_config {
+  int32_t N;            /* image side, power of two, 16..1024 (Table 2 sizes 256..1024) */
+  int32_t G;            /* uv-grid side: 4N for imaging (beam of 2N, Sec. 3.2.1), 2N for degrid */
+  int32_t W;            /* spheroidal support in cells, odd, 3..9 (7 in every workload) */
+  int32_t os;           /* kernel table samples per cell, 16..4096 (1024) */
+  int32_t weight_mode;  /* 0 natural, 1 uniform (Alg. 1 weighting mode) */
+  int32_t peak_mode;    /* CLEAN peak: 0 largest signed value, 1 largest |value| */
+  int32_t thr_mode;     /* CLEAN threshold: 0 fixed thr[] (or -inf), 1 GMM sky level mu_a (Sec. 4.3) */
+  int32_t max_iter;     /* CLEAN iteration cap (>= 0) */
+  float gain;           /* CLEAN loop gain, (0, 1]; 0.1 in the paper (Sec. 4.3) */
+  int32_t gmm_bins;     /* histogram ranges for the GMM, 2..4096; 2000 in the paper (Sec. 4.1) */
+  double lat_rad;       /* array latitude (Sec. 3.2.2) */
+  int32_t batch_chunk;  /* muser_image: instances per internal chunk (0 = whole batch) */
+  int32_t reserved[7];  /* must be zero */
+} muser_config_t;
+
+/* One gridding record per visibility, 24 bytes (written by muser_uvw).
+ * (ku, kv) is the nearest uv cell of the +uv sample, (fu, fv) = k - g in [-1/2, 1/2]
+ * its offset from the exact grid coordinate g, vis the phase-corrected visibility and
+ * w its weight (0 = not imaged: flagged, non-finite or off-grid; ku = kv = -1 then). */
+typedef struct muser_vis_record {
+  float vis_re, vis_im;
+  float fu, fv;
+  int16_t ku, kv;
+  float w;
+} muser_vis_record_t;
+
+MUSER_API const char *muser_version(void);
+MUSER_API const char *muser_last_error(void);
+
+/* Pixel size rule (host only).  Sec. 3.2.1 / Table 2: three pixels per resolution
+ * element lambda / B_max; reading for a fixed image side: never smaller than
+ * fov_min / N.  freq_hz[n_chan] and cell_rad_out[n_chan] are HOST arrays. */
+MUSER_API int muser_pixel_size(const double *freq_hz, int n_chan, double bmax_m, int N, double fov_min_rad,
+                     double *cell_rad_out);
+
+/* Bytes of workspace a call needs (0 for none; SIZE_MAX on invalid arguments).
+ * B = instances (for MUSER_CALL_IMAGE: the chunk size actually used is
+ * min(B, cfg->batch_chunk or B)); n_vis_total = records over the batch (IMAGE:
+ * baselines per instance; DEGRID and CHI2: records). */
+MUSER_API size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser_config_t *cfg);
+
+/* (u, v, w) and gridding records, FP64 geometry (Sec. 3.2.2; Alg. 1 input).
+ *  ant_enu[n_ant][3]  antenna east/north/up (m);  bl_pairs[n_bl][2] antenna indices i < j
+ *  ha[n_frame], dec[n_frame]  phase-centre hour angle and declination (rad)
+ *  freq_hz[n_chan], cell_rad[n_chan]  channel frequency and pixel size (rad)
+ *  vis[n_frame][n_chan][n_bl] complex64;  flags[...] uint8 (nonzero = flagged, NULL = none)
+ *  dlm[n_frame*n_chan][2] phase-centre shift (rad, NULL = none): V' = V exp(+2 pi i (u dl + v dm))
+ *    (Sec. 4.2 step 3: phase correction by the disk offset)
+ *  rec_out[n_frame*n_chan*n_bl]; uvw_out[...][3] f64 wavelengths (NULL = not written)
+ *  status[n_frame*n_chan] (NULL = not written)
+ * (u, v, w) = R(H, dec) (X_j - X_i) nu / c (Thompson, Moran & Swenson eq. 4.1) with X the local
+ * equatorial frame at cfg->lat_rad; g = u G cell + G/2; k = floor(g + 1/2).  A record is
+ * kept when both samples (+uv at k, -uv at G - k) have all W taps inside the grid. */
+MUSER_API int muser_uvw(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+              const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+              const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+              muser_vis_record_t *rec_out, double *uvw_out, int32_t *status, muser_stream_t stream);
+
+/* Convolutional gridding with the truncated spheroidal kernel (Sec. 3.2.3; Alg. 1
+ * "calculating the weight and gridding").  Z[B][G][G] complex64 receives, for every
+ * kept record, w C(t+fu) C(s+fv) (V + i) at cell (kv+s, ku+t) and w C C (conj V + i)
+ * at (G-kv-s, G-ku-t): Re carries the Hermitian visibility grid, Im the sampling grid
+ * (one inverse FFT then yields dirty map and dirty beam).  Records are counting-sorted
+ * by grid band in `ws`; each block owns a band of rows in shared memory and writes it
+ * once (no global atomics).  vis_off[B+1] int64 device CSR offsets. */
+MUSER_API int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int64_t n_vis_total,
+               const muser_config_t *cfg, float *Z, void *ws, size_t ws_bytes, int32_t *status,
+               muser_stream_t stream);
+
+/* Inverse FFT of the grids to dirty map and dirty beam with grid correction
+ * (Alg. 1 dirty_image; Sec. 3.2.1 beam twice the image).  Z[B][G][G] (read only),
+ * dirty[B][N][N] = Re I / (gc gc) over the central N x N, beam[B][2N][2N] = Im I / (gc gc)
+ * over the central 2N x 2N, both divided by the beam centre so beam[N][N] = 1.
+ * I = centred unnormalised inverse DFT; gc = grid correction of the spheroidal kernel. */
+MUSER_API int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam, void *ws,
+                size_t ws_bytes, int32_t *status, muser_stream_t stream);
+
+/* Sky and disk brightness by a Gaussian mixture on the gmm_bins-range histogram of each
+ * dirty map (Sec. 4.1; Alg. 1 pre_clean): mu_a[B] = sky (lowest mean), mu_b[B] = disk. */
+MUSER_API int muser_gmm(const float *dirty, int B, const muser_config_t *cfg, float *mu_a, float *mu_b, void *ws,
+              size_t ws_bytes, int32_t *status, muser_stream_t stream);
+
+/* Hogbom CLEAN (Alg. 1 improved_clean loop; Sec. 4.3).  residual[B][N][N]: in = dirty map,
+ * out = residual; beam[B][2N][2N].  Per instance: p = argmax (ties: lowest row-major index);
+ * while R[p] > thr and it < max_iter: f = gain R[p]; comp_pos[b][it] = p, comp_flux[b][it] = f;
+ * R[q] -= f beam[q - p + (N, N)] for all q; re-find p.  thr[B] (NULL: -inf for thr_mode 0,
+ * the GMM sky level mu_a for thr_mode 1).  n_comp[B] = components written.
+ * Instances with MUSER_ST_ALL_FLAGGED get n_comp = 0. */
+MUSER_API int muser_clean(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr,
+                int32_t *comp_pos, float *comp_flux, int32_t *n_comp, void *ws, size_t ws_bytes,
+                int32_t *status, muser_stream_t stream);
+
+/* Clean beam and restored image (Alg. 1: dirty_image returns the clean beam).  The clean
+ * beam is the Gaussian whose half-maximum ellipse has the second moments of the 4-connected
+ * beam main lobe >= 1/2 (pixels counted as unit squares): Sigma = (2 / ln 2) M.
+ * beam_params[B][3] = (Sxx, Sxy, Syy) pixel^2; clean_img = residual + sum_c f_c exp(-q'Sigma^-1 q/2),
+ * truncated where the Gaussian is below 1e-7. */
+MUSER_API int muser_restore(const float *residual, const float *beam, const int32_t *comp_pos, const float *comp_flux,
+                  const int32_t *n_comp, int B, const muser_config_t *cfg, float *clean_img,
+                  float *beam_params, void *ws, size_t ws_bytes, int32_t *status, muser_stream_t stream);
+
+/* The whole hot path for a batch (Alg. 1 without the w-term step): muser_uvw ->
+ * muser_grid -> muser_dirty -> [muser_gmm if thr_mode 1] -> muser_clean -> muser_restore,
+ * in chunks of cfg->batch_chunk instances.  Arguments as for muser_uvw, plus outputs
+ * clean_img[B][N][N], residual[B][N][N], comp_pos/comp_flux[B][max_iter], n_comp[B],
+ * thr_out[B] (threshold used, NULL = not written), beam_params[B][3] (NULL = not written).
+ * status[B] is zeroed by the call. */
+MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+                const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+                const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+                float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
+                float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
+                muser_stream_t stream);
+
+/* Degridding measurement operator and its adjoint (the transpose of Alg. 1's gridding +
+ * inverse FFT), for gradient-based imaging of one real sky image img[N][N], cfg->G = 2N:
+ *  FORWARD:  vis[k] = (1/K^2) sum_taps C C X[kv+s][ku+t],  X = centred forward DFT of the
+ *            zero-padded img / (gc gc); vis = 0 for records with w = 0.  img read, vis written.
+ *  ADJOINT:  img = Re (1/K^2) (1/(gc gc)) crop_N( centred inverse DFT( grid of vis ) ), the
+ *            exact adjoint of FORWARD restricted to real images.  vis read, img written.
+ * K = integral of the kernel.  rec[n_vis] from muser_uvw with the same cfg. */
+MUSER_API int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,
+                 const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream);
+
+/* Chi-square of predicted visibilities and its gradient seed:
+ *  loss[0] = sum_k w_k |pred_k - obs_k|^2 / sigma^2,  resid[k] = 2 w_k (pred_k - obs_k) / sigma^2
+ * (complex64 pred, obs, resid; resid may be NULL).  The gradient of the loss with respect to
+ * the sky image is muser_degrid(ADJOINT) of resid. */
+MUSER_API int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *rec, int64_t n_vis,
+               float inv_sigma2, float *resid, float *loss, void *ws, size_t ws_bytes, muser_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUSER_H */

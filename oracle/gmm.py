@@ -42,16 +42,16 @@ def histogram(D, bins: int = 2000):
     return h, x, lo, width
 
 
-def _normal(x, mu, var):
-    return np.exp(-0.5 * (x - mu) ** 2 / var) / np.sqrt(2 * math.pi * var)
-
-
 def em(h, x, width, K: int = 3, max_iter: int = 1000, tol: float = 1e-12):
     """Weighted EM for a K-component 1-D Gaussian mixture on histogram (x_b, h_b).
 
-    E step: r_bk = pi_k N(x_b | mu_k, var_k) / sum_j pi_j N(x_b | mu_j, var_j).
+    E step: r_bk = pi_k N(x_b | mu_k, var_k) / sum_j pi_j N(x_b | mu_j, var_j), evaluated
+            from log densities relative to the largest one so that bins far from every
+            component keep their responsibilities instead of underflowing to 0/0;
+            logL = sum_b h_b log sum_k pi_k N(x_b | mu_k, var_k) for the current parameters.
     M step: n_k = sum_b h_b r_bk; mu_k = sum_b h_b r_bk x_b / n_k;
-            var_k = max(sum_b h_b r_bk (x_b - mu_k)^2 / n_k, width^2); pi_k = n_k / sum h.
+            var_k = max(sum_b h_b r_bk (x_b - mu_k)^2 / n_k, width^2) with the new mu_k;
+            pi_k = n_k / sum h.
     Returns (mu, var, pi, n_iter, logL), components in ascending order of mean.
     """
     total = h.sum()
@@ -64,12 +64,16 @@ def em(h, x, width, K: int = 3, max_iter: int = 1000, tol: float = 1e-12):
     floor = width ** 2
     logL_old = None
     it = 0
+    logL = 0.0
     for it in range(1, max_iter + 1):
-        p = pi[None, :] * _normal(x[:, None], mu[None, :], var[None, :])
-        s = p.sum(1)
-        s_safe = np.where(s > 0, s, 1.0)
-        logL = float((h * np.log(np.where(s > 0, s, 1e-300))).sum())
-        r = p / s_safe[:, None]
+        with np.errstate(divide="ignore"):
+            lp = np.log(pi)[None, :] - 0.5 * (x[:, None] - mu[None, :]) ** 2 / var[None, :] \
+                - 0.5 * np.log(2 * math.pi * var)[None, :]
+        m = lp.max(1)
+        e = np.exp(lp - m[:, None])
+        s = e.sum(1)
+        logL = float((h * (m + np.log(s))).sum())
+        r = e / s[:, None]
         nk = (h[:, None] * r).sum(0)
         nk_safe = np.where(nk > 0, nk, 1.0)
         mu = np.where(nk > 0, (h[:, None] * r * x[:, None]).sum(0) / nk_safe, mu)

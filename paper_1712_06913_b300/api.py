@@ -1,0 +1,277 @@
+"""PyTorch-facing wrappers of the libmuser C ABI: argument marshalling only.
+
+Tensors supply device memory and the current CUDA stream; every computation runs in
+the library's kernels.  Each wrapper allocates its outputs and the workspace the call
+asks for with torch, then passes raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import CALL_CHI2, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
+
+RECORD_FLOATS = 6          # 24-byte record viewed as float32[6]
+
+
+@dataclasses.dataclass
+class Config:
+    """Mirror of muser_config_t."""
+    N: int
+    G: int
+    W: int = 7
+    os: int = 1024
+    weight_mode: int = 0
+    peak_mode: int = 0
+    thr_mode: int = 0
+    max_iter: int = 200
+    gain: float = 0.1
+    gmm_bins: int = 2000
+    lat_rad: float = 0.0
+    batch_chunk: int = 0
+
+    def c(self) -> _lib.Config:
+        return _lib.Config(self.N, self.G, self.W, self.os, self.weight_mode, self.peak_mode, self.thr_mode,
+                           self.max_iter, self.gain, self.gmm_bins, self.lat_rad, self.batch_chunk)
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to("cuda").contiguous()
+
+
+def workspace_size(call_id, B, n_vis, cfg: Config) -> int:
+    c = cfg.c() if cfg is not None else None
+    n = _lib.load().muser_workspace_size(call_id, B, n_vis, ctypes.byref(c) if c is not None else None)
+    if n == ctypes.c_size_t(-1).value:
+        raise _lib.MuserError(_lib.MUSER_ERR_ARG, "invalid workspace query: " + _lib.load().muser_last_error().decode())
+    return n
+
+
+class Workspace:
+    """A reusable 256-byte aligned device workspace."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes):
+        if nbytes == 0:
+            return None, 0
+        if self.buf is None or self.buf.numel() < nbytes + 256:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        off = (-self.buf.data_ptr()) % 256
+        return ctypes.c_void_p(self.buf.data_ptr() + off), self.buf.numel() - off
+
+
+_default_ws = Workspace()
+
+
+def pixel_size(freq_hz, bmax_m, N, fov_min_rad):
+    """Host rule of Table 2 (three pixels per resolution element, floored at fov_min / N)."""
+    f = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    out = np.empty_like(f)
+    check(_lib.load().muser_pixel_size(f.ctypes.data_as(ctypes.c_void_p), len(f), float(bmax_m), int(N),
+                                       float(fov_min_rad), out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def uvw(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None, want_uvw=False, status=None):
+    """Records [F*C*nb, 6] float32 (24-byte muser_vis_record_t), optional uvw [F*C*nb, 3] f64."""
+    ant = _dev(ant_enu, torch.float64)
+    pr = _dev(pairs, torch.int32)
+    ha_t, dec_t = _dev(ha, torch.float64), _dev(dec, torch.float64)
+    fr, ce = _dev(freq, torch.float64), _dev(cell, torch.float64)
+    V = _dev(vis, torch.complex64)
+    F, C, nb = len(ha_t), len(fr), pr.shape[0]
+    fl = _dev(flags, torch.uint8) if flags is not None else None
+    dl = _dev(dlm, torch.float64) if dlm is not None else None
+    rec = torch.empty((F * C * nb, RECORD_FLOATS), dtype=torch.float32, device="cuda")
+    uv = torch.empty((F * C * nb, 3), dtype=torch.float64, device="cuda") if want_uvw else None
+    st = status if status is not None else torch.zeros(F * C, dtype=torch.int32, device="cuda")
+    c = cfg.c()
+    check(_lib.load().muser_uvw(_p(ant), ant.shape[0], _p(pr), nb, _p(ha_t), _p(dec_t), F, _p(fr), _p(ce), C,
+                                _p(V), _p(fl), _p(dl), ctypes.byref(c), _p(rec), _p(uv), _p(st), _stream()))
+    return rec, uv, st
+
+
+def record_fields(rec: torch.Tensor):
+    """Split [n, 6] float32 records into (vis complex64, fu, fv, ku, kv, w)."""
+    vis = torch.complex(rec[:, 0], rec[:, 1])
+    k = rec[:, 4].contiguous().view(torch.int16)
+    return vis, rec[:, 2], rec[:, 3], k[0::2].to(torch.int64), k[1::2].to(torch.int64), rec[:, 5]
+
+
+def grid(rec, vis_off, cfg: Config, status=None, ws: Workspace = None):
+    """uv grids Z [B, G, G] complex64 from CSR records."""
+    vo = _dev(vis_off, torch.int64)
+    B = vo.numel() - 1
+    n = int(vo[-1].item()) if B > 0 else 0
+    Z = torch.empty((B, cfg.G, cfg.G), dtype=torch.complex64, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_GRID, B, n, cfg))
+    check(_lib.load().muser_grid(_p(rec), _p(vo), B, n, ctypes.byref(c), _p(Z), w, wb, _p(st), _stream()))
+    return Z, st
+
+
+def dirty(Z, cfg: Config, status=None, ws: Workspace = None):
+    """(dirty [B, N, N], beam [B, 2N, 2N], status) from grids."""
+    B = Z.shape[0]
+    N = cfg.N
+    D = torch.empty((B, N, N), dtype=torch.float32, device="cuda")
+    Bm = torch.empty((B, 2 * N, 2 * N), dtype=torch.float32, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_DIRTY, B, 0, cfg))
+    check(_lib.load().muser_dirty(_p(Z.contiguous()), B, ctypes.byref(c), _p(D), _p(Bm), w, wb, _p(st), _stream()))
+    return D, Bm, st
+
+
+def gmm(D, cfg: Config, status=None):
+    B = D.shape[0]
+    mu_a = torch.empty(B, dtype=torch.float32, device="cuda")
+    mu_b = torch.empty(B, dtype=torch.float32, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    c = cfg.c()
+    check(_lib.load().muser_gmm(_p(D.contiguous()), B, ctypes.byref(c), _p(mu_a), _p(mu_b), None, 0, _p(st),
+                                _stream()))
+    return mu_a, mu_b, st
+
+
+def clean(D, Bm, cfg: Config, thr=None, status=None, ws: Workspace = None):
+    """Hogbom CLEAN: (residual, comp_pos [B, cap], comp_flux, n_comp, status).  D is not modified."""
+    B = D.shape[0]
+    R = D.clone()
+    cap = cfg.max_iter
+    pos = torch.zeros((B, max(cap, 1)), dtype=torch.int32, device="cuda")
+    flux = torch.zeros((B, max(cap, 1)), dtype=torch.float32, device="cuda")
+    nc = torch.empty(B, dtype=torch.int32, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    th = _dev(thr, torch.float32) if thr is not None else None
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_CLEAN, B, 0, cfg))
+    check(_lib.load().muser_clean(_p(R), _p(Bm.contiguous()), B, ctypes.byref(c), _p(th), _p(pos), _p(flux), _p(nc),
+                                  w, wb, _p(st), _stream()))
+    return R, pos[:, :cap], flux[:, :cap], nc, st
+
+
+def restore(R, Bm, pos, flux, n_comp, cfg: Config, status=None):
+    B = R.shape[0]
+    out = torch.empty_like(R)
+    params = torch.empty((B, 3), dtype=torch.float32, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    cap = cfg.max_iter
+    pos_c = torch.zeros((B, max(cap, 1)), dtype=torch.int32, device="cuda")
+    flux_c = torch.zeros((B, max(cap, 1)), dtype=torch.float32, device="cuda")
+    pos_c[:, :cap] = pos
+    flux_c[:, :cap] = flux
+    c = cfg.c()
+    check(_lib.load().muser_restore(_p(R.contiguous()), _p(Bm.contiguous()), _p(pos_c), _p(flux_c), _p(n_comp), B,
+                                    ctypes.byref(c), _p(out), _p(params), None, 0, _p(st), _stream()))
+    return out, params, st
+
+
+@dataclasses.dataclass
+class ImageResult:
+    clean: torch.Tensor
+    residual: torch.Tensor
+    comp_pos: torch.Tensor
+    comp_flux: torch.Tensor
+    n_comp: torch.Tensor
+    thr: torch.Tensor
+    beam_params: torch.Tensor
+    status: torch.Tensor
+
+
+class Imager:
+    """Device-resident inputs and outputs for repeated muser_image calls on one batch shape."""
+
+    def __init__(self, ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None):
+        self.cfg = cfg
+        self.ant = _dev(ant_enu, torch.float64)
+        self.pairs = _dev(pairs, torch.int32)
+        self.ha, self.dec = _dev(ha, torch.float64), _dev(dec, torch.float64)
+        self.freq, self.cell = _dev(freq, torch.float64), _dev(cell, torch.float64)
+        self.vis = _dev(vis, torch.complex64)
+        self.flags = _dev(flags, torch.uint8) if flags is not None else None
+        self.dlm = _dev(dlm, torch.float64) if dlm is not None else None
+        self.F, self.C, self.nb = len(self.ha), len(self.freq), self.pairs.shape[0]
+        B, N, cap = self.F * self.C, cfg.N, cfg.max_iter
+        self.B = B
+        dev = "cuda"
+        self.out = ImageResult(
+            clean=torch.empty((B, N, N), dtype=torch.float32, device=dev),
+            residual=torch.empty((B, N, N), dtype=torch.float32, device=dev),
+            comp_pos=torch.zeros((B, max(cap, 1)), dtype=torch.int32, device=dev),
+            comp_flux=torch.zeros((B, max(cap, 1)), dtype=torch.float32, device=dev),
+            n_comp=torch.empty(B, dtype=torch.int32, device=dev),
+            thr=torch.empty(B, dtype=torch.float32, device=dev),
+            beam_params=torch.empty((B, 3), dtype=torch.float32, device=dev),
+            status=torch.empty(B, dtype=torch.int32, device=dev))
+        self.ws = Workspace()
+        self.ws_bytes = workspace_size(CALL_IMAGE, B, self.nb, cfg)
+        self.c = cfg.c()
+
+    def run(self, vis=None):
+        """Launch the whole batch on the current stream (no host synchronisation)."""
+        V = self.vis if vis is None else vis
+        o = self.out
+        w, wb = self.ws.get(self.ws_bytes)
+        check(_lib.load().muser_image(
+            _p(self.ant), self.ant.shape[0], _p(self.pairs), self.nb, _p(self.ha), _p(self.dec), self.F,
+            _p(self.freq), _p(self.cell), self.C, _p(V), _p(self.flags), _p(self.dlm), ctypes.byref(self.c),
+            _p(o.clean), _p(o.residual), _p(o.comp_pos), _p(o.comp_flux), _p(o.n_comp), _p(o.thr),
+            _p(o.beam_params), w, wb, _p(o.status), _stream()))
+        return o
+
+
+def image(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None):
+    """Whole hot path for a batch; returns an ImageResult with comp arrays cut to max_iter."""
+    im = Imager(ant_enu, pairs, ha, dec, freq, cell, vis, cfg, flags, dlm)
+    o = im.run()
+    cap = cfg.max_iter
+    return dataclasses.replace(o, comp_pos=o.comp_pos[:, :cap], comp_flux=o.comp_flux[:, :cap])
+
+
+def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None):
+    """FORWARD: img [N, N] f32 -> vis [n] complex64.  ADJOINT: vis -> img (real part of A^H vis)."""
+    n = rec.shape[0]
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_DEGRID, 1, n, cfg))
+    if direction == _lib.FORWARD:
+        img = img.contiguous()
+        out = torch.empty(n, dtype=torch.complex64, device="cuda")
+        check(_lib.load().muser_degrid(0, _p(img), _p(rec), n, _p(out), ctypes.byref(c), w, wb, _stream()))
+        return out
+    vis = vis.contiguous()
+    out = torch.empty((cfg.N, cfg.N), dtype=torch.float32, device="cuda")
+    check(_lib.load().muser_degrid(1, _p(out), _p(rec), n, _p(vis), ctypes.byref(c), w, wb, _stream()))
+    return out
+
+
+def chi2(pred, obs, rec, inv_sigma2: float, want_resid=True, ws: Workspace = None):
+    n = rec.shape[0]
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    resid = torch.empty(n, dtype=torch.complex64, device="cuda") if want_resid else None
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_CHI2, 1, n, None))
+    check(_lib.load().muser_chi2(_p(pred.contiguous()), _p(obs.contiguous()), _p(rec), n, float(inv_sigma2), _p(resid),
+                                 _p(loss), w, wb, _stream()))
+    return loss[0], resid

@@ -1,0 +1,404 @@
+// C ABI of libmuser: argument checks, workspace layout and launch sequencing.
+// Every entry point is asynchronous on the caller's stream, allocates nothing and
+// performs no host synchronisation, so a batch can be captured in a CUDA graph.
+#include <math.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace muser {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(MUSER_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return MUSER_OK;
+}
+
+namespace {
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+enum Mode { IMAGING, DEGRID };
+
+int check_cfg(const muser_config_t *cfg, Mode mode) {
+  if (!cfg) return fail(MUSER_ERR_ARG, "cfg is NULL");
+  const int N = cfg->N, G = cfg->G;
+  if (!is_pow2(N) || N < 16 || N > 1024) return fail(MUSER_ERR_ARG, "N must be a power of two in [16, 1024]");
+  if (mode == IMAGING && G != 4 * N) return fail(MUSER_ERR_ARG, "imaging needs G = 4 N");
+  if (mode == DEGRID && G != 2 * N) return fail(MUSER_ERR_ARG, "degridding needs G = 2 N");
+  if (G < 64 || G > 4096) return fail(MUSER_ERR_UNSUPPORTED, "G must be in [64, 4096]");
+  if (cfg->W < 3 || cfg->W > 9 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "W must be odd in [3, 9]");
+  if (cfg->os < 16 || cfg->os > 4096) return fail(MUSER_ERR_ARG, "os must be in [16, 4096]");
+  if (cfg->weight_mode != 0) return fail(MUSER_ERR_UNSUPPORTED, "only natural weighting (weight_mode 0) is implemented");
+  if (cfg->peak_mode != 0 && cfg->peak_mode != 1) return fail(MUSER_ERR_ARG, "peak_mode must be 0 or 1");
+  if (cfg->thr_mode != 0 && cfg->thr_mode != 1) return fail(MUSER_ERR_ARG, "thr_mode must be 0 or 1");
+  if (cfg->max_iter < 0) return fail(MUSER_ERR_ARG, "max_iter must be >= 0");
+  if (!(cfg->gain > 0.f && cfg->gain <= 1.f)) return fail(MUSER_ERR_ARG, "gain must be in (0, 1]");
+  if (cfg->gmm_bins < 2 || cfg->gmm_bins > 4096) return fail(MUSER_ERR_ARG, "gmm_bins must be in [2, 4096]");
+  if (cfg->batch_chunk < 0) return fail(MUSER_ERR_ARG, "batch_chunk must be >= 0");
+  for (int i = 0; i < 7; i++)
+    if (cfg->reserved[i] != 0) return fail(MUSER_ERR_ARG, "reserved fields must be zero");
+  return MUSER_OK;
+}
+
+// ----------------------------------------------------------------------- workspace layouts
+template <class A>
+struct GridWs {
+  float *tab;
+  int32_t *bin_off, *entries;
+  void carve(A &a, int B, int64_t n_vis, const muser_config_t &c, bool mirror) {
+    const int rows = grid_band_rows(c.G), nb = c.G / rows;
+    tab = (float *)a.template take<float>(table_len(c.W, c.os));
+    bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (nb + 1));
+    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) * grid_bands_per_sample(c.W, rows));
+  }
+};
+
+template <class A>
+struct DirtyWs {
+  float *gc;
+  float2 *tw, *T;
+  float *partial;
+  void carve(A &a, int B, const muser_config_t &c) {
+    const int G = c.G;
+    gc = (float *)a.template take<float>(G);
+    tw = (float2 *)a.template take<float2>(G);
+    T = (float2 *)a.template take<float2>((size_t)B * (G / 2) * G);
+    partial = (float *)a.template take<float>((size_t)B * (G / dirty_strip_width(G)));
+  }
+};
+
+template <class A>
+struct ImageWs {
+  Rec *rec;
+  float2 *Z;
+  float *beam, *mu_a, *mu_b, *params;
+  GridWs<A> g;
+  DirtyWs<A> d;
+  void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
+    rec = (Rec *)a.template take<Rec>((size_t)Bc * n_bl);
+    g.carve(a, Bc, (int64_t)Bc * n_bl, c, true);
+    Z = (float2 *)a.template take<float2>((size_t)Bc * c.G * c.G);
+    d.carve(a, Bc, c);
+    beam = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N);
+    mu_a = (float *)a.template take<float>(Bc);
+    mu_b = (float *)a.template take<float>(Bc);
+    params = (float *)a.template take<float>((size_t)Bc * 3);
+  }
+};
+
+template <class A>
+struct DegridWs {
+  float *tab, *gc;
+  float2 *tw, *T, *X;
+  int32_t *bin_off, *entries;
+  void carve(A &a, int64_t n_vis, const muser_config_t &c) {
+    const int G = c.G, rows = grid_band_rows(G), nb = G / rows;
+    tab = (float *)a.template take<float>(table_len(c.W, c.os));
+    gc = (float *)a.template take<float>(G);
+    tw = (float2 *)a.template take<float2>(G);
+    T = (float2 *)a.template take<float2>((size_t)(G / 2) * G);
+    X = (float2 *)a.template take<float2>((size_t)G * G);
+    bin_off = (int32_t *)a.template take<int32_t>(nb + 1);
+    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * grid_bands_per_sample(c.W, rows));
+  }
+};
+
+// Size-only arena with the same interface as Arena.
+struct SizeArena {
+  size_t off = 0;
+  template <class T>
+  T *take(size_t n) {
+    off += align_up(n * sizeof(T));
+    return nullptr;
+  }
+};
+
+int chunk_of(int B, const muser_config_t &c) { return (c.batch_chunk > 0 && c.batch_chunk < B) ? c.batch_chunk : B; }
+
+int check_ws(void *ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return MUSER_OK;
+  if (!ws) return fail(MUSER_ERR_WORKSPACE, "workspace is NULL");
+  if (!aligned(ws, 256)) return fail(MUSER_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(MUSER_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes, got " +
+                                         std::to_string(ws_bytes));
+  return MUSER_OK;
+}
+
+__global__ void k_fill(float *p, int n, float v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+__global__ void k_copy(float *dst, const float *src, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+#define MUSER_TRY(x)             \
+  do {                           \
+    int _rc = (x);               \
+    if (_rc != MUSER_OK) return _rc; \
+  } while (0)
+
+}  // namespace
+}  // namespace muser
+
+using namespace muser;
+
+extern "C" {
+
+const char *muser_version(void) { return "muser-b300 0.1 (sm_103a)"; }
+
+const char *muser_last_error(void) { return g_last_error.c_str(); }
+
+int muser_pixel_size(const double *freq_hz, int n_chan, double bmax_m, int N, double fov_min_rad,
+                     double *cell_rad_out) {
+  if (!freq_hz || !cell_rad_out || n_chan < 0 || N <= 0 || !(bmax_m > 0) || !(fov_min_rad >= 0))
+    return fail(MUSER_ERR_ARG, "muser_pixel_size: invalid argument");
+  for (int c = 0; c < n_chan; c++) {
+    if (!(freq_hz[c] > 0)) return fail(MUSER_ERR_ARG, "muser_pixel_size: frequency must be > 0");
+    const double res = 299792458.0 / freq_hz[c] / bmax_m;
+    cell_rad_out[c] = fmax(res / 3.0, fov_min_rad / N);
+  }
+  return MUSER_OK;
+}
+
+size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser_config_t *cfg) {
+  if (B < 0 || n_vis_total < 0) return SIZE_MAX;
+  if (call_id == MUSER_CALL_CHI2) return align_up(sizeof(float) * chi2_blocks(n_vis_total));
+  if (!cfg) return SIZE_MAX;
+  const Mode mode = call_id == MUSER_CALL_DEGRID ? DEGRID : IMAGING;
+  if (check_cfg(cfg, mode) != MUSER_OK) return SIZE_MAX;
+  SizeArena a;
+  switch (call_id) {
+    case MUSER_CALL_GRID: { GridWs<SizeArena> w; w.carve(a, B, n_vis_total, *cfg, true); break; }
+    case MUSER_CALL_DIRTY: { DirtyWs<SizeArena> w; w.carve(a, B, *cfg); break; }
+    case MUSER_CALL_GMM: break;
+    case MUSER_CALL_CLEAN: a.take<float>(2 * (size_t)B); break;
+    case MUSER_CALL_RESTORE: break;
+    case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
+    case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
+    default: return SIZE_MAX;
+  }
+  return a.off;
+}
+
+int muser_uvw(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+              const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+              const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+              muser_vis_record_t *rec_out, double *uvw_out, int32_t *status, muser_stream_t stream) {
+  if (!cfg) return fail(MUSER_ERR_ARG, "cfg is NULL");
+  if (cfg->G < 8 || cfg->G > 32767 || cfg->W < 3 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "invalid G or W");
+  if (n_ant < 2 || n_bl < 0 || n_frame < 0 || n_chan < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  const int64_t n_inst = (int64_t)n_frame * n_chan;
+  if (n_inst * n_bl == 0) return MUSER_OK;
+  if (!ant_enu || !bl_pairs || !ha || !dec || !freq_hz || !cell_rad || !vis || !rec_out)
+    return fail(MUSER_ERR_ARG, "muser_uvw: required pointer is NULL");
+  if (n_inst > INT32_MAX) return fail(MUSER_ERR_ARG, "too many instances");
+  if (!aligned(vis, 8) || !aligned(rec_out, 8)) return fail(MUSER_ERR_ARG, "vis and rec_out must be 8-byte aligned");
+  launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, 0,
+             (int)n_inst, cfg->G, cfg->W, cfg->lat_rad, (Rec *)rec_out, uvw_out, status, (cudaStream_t)stream);
+  return check_launch("muser_uvw");
+}
+
+int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int64_t n_vis_total,
+               const muser_config_t *cfg, float *Z, void *ws, size_t ws_bytes, int32_t *status,
+               muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0 || n_vis_total < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (!rec || !vis_off || !Z) return fail(MUSER_ERR_ARG, "muser_grid: required pointer is NULL");
+  if (!aligned(Z, 16)) return fail(MUSER_ERR_ARG, "Z must be 16-byte aligned");
+  if (n_vis_total >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "at most 2^30 records per call");
+  const size_t need = muser_workspace_size(MUSER_CALL_GRID, B, n_vis_total, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  GridWs<Arena> w;
+  w.carve(a, B, n_vis_total, *cfg, true);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_pswf_table(w.tab, cfg->W, cfg->os, nullptr, 0, s);
+  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, cfg->W, cfg->os, w.tab, true, nullptr, (float2 *)Z, w.bin_off,
+              w.entries, status, s);
+  return check_launch("muser_grid");
+}
+
+int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam, void *ws,
+                size_t ws_bytes, int32_t *status, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (!Z || !dirty || !beam) return fail(MUSER_ERR_ARG, "muser_dirty: required pointer is NULL");
+  if (!aligned(Z, 16)) return fail(MUSER_ERR_ARG, "Z must be 16-byte aligned");
+  const size_t need = muser_workspace_size(MUSER_CALL_DIRTY, B, 0, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  DirtyWs<Arena> w;
+  w.carve(a, B, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_pswf_table(nullptr, cfg->W, cfg->os, w.gc, cfg->G, s);    // grid correction only
+  fft::launch_twiddles(w.tw, cfg->G, s);
+  launch_dirty((const float2 *)Z, B, cfg->N, cfg->G, w.tw, w.gc, w.T, w.partial, dirty, beam, status, s);
+  return check_launch("muser_dirty");
+}
+
+int muser_gmm(const float *dirty, int B, const muser_config_t *cfg, float *mu_a, float *mu_b, void *ws,
+              size_t ws_bytes, int32_t *status, muser_stream_t stream) {
+  (void)ws;
+  (void)ws_bytes;
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (!dirty || !mu_a || !mu_b) return fail(MUSER_ERR_ARG, "muser_gmm: required pointer is NULL");
+  launch_gmm(dirty, B, cfg->N, cfg->gmm_bins, mu_a, mu_b, status, (cudaStream_t)stream);
+  return check_launch("muser_gmm");
+}
+
+int muser_clean(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr,
+                int32_t *comp_pos, float *comp_flux, int32_t *n_comp, void *ws, size_t ws_bytes, int32_t *status,
+                muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (!residual || !beam || !n_comp || (cfg->max_iter > 0 && (!comp_pos || !comp_flux)))
+    return fail(MUSER_ERR_ARG, "muser_clean: required pointer is NULL");
+  if (!aligned(residual, 16)) return fail(MUSER_ERR_ARG, "residual must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float *t = thr;
+  if (!thr && cfg->thr_mode == 1) {
+    const size_t need = muser_workspace_size(MUSER_CALL_CLEAN, B, 0, cfg);
+    MUSER_TRY(check_ws(ws, ws_bytes, need));
+    Arena a(ws, ws_bytes);
+    float *mu = a.take<float>(2 * (size_t)B);
+    launch_gmm(residual, B, cfg->N, cfg->gmm_bins, mu, mu + B, status, s);
+    t = mu;
+  }
+  launch_hogbom(residual, beam, B, cfg->N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux, n_comp,
+                status, s);
+  return check_launch("muser_clean");
+}
+
+int muser_restore(const float *residual, const float *beam, const int32_t *comp_pos, const float *comp_flux,
+                  const int32_t *n_comp, int B, const muser_config_t *cfg, float *clean_img, float *beam_params,
+                  void *ws, size_t ws_bytes, int32_t *status, muser_stream_t stream) {
+  (void)ws;
+  (void)ws_bytes;
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (!residual || !beam || !n_comp || !clean_img || !beam_params || (cfg->max_iter > 0 && (!comp_pos || !comp_flux)))
+    return fail(MUSER_ERR_ARG, "muser_restore: required pointer is NULL");
+  launch_restore(residual, beam, comp_pos, comp_flux, n_comp, B, cfg->N, cfg->max_iter, clean_img, beam_params, status,
+                 (cudaStream_t)stream);
+  return check_launch("muser_restore");
+}
+
+int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+                const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+                const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+                float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
+                float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
+                muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (n_ant < 2 || n_bl < 0 || n_frame < 0 || n_chan < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  const int64_t B64 = (int64_t)n_frame * n_chan;
+  if (B64 > INT32_MAX) return fail(MUSER_ERR_ARG, "too many instances");
+  const int B = (int)B64;
+  if (B == 0) return MUSER_OK;
+  if (n_bl == 0) return fail(MUSER_ERR_ARG, "n_bl must be > 0");
+  if (!ant_enu || !bl_pairs || !ha || !dec || !freq_hz || !cell_rad || !vis || !clean_img || !residual || !n_comp ||
+      !status || (cfg->max_iter > 0 && (!comp_pos || !comp_flux)))
+    return fail(MUSER_ERR_ARG, "muser_image: required pointer is NULL");
+  if (!aligned(vis, 8) || !aligned(residual, 16)) return fail(MUSER_ERR_ARG, "vis / residual misaligned");
+  const int Bc = chunk_of(B, *cfg);
+  if ((int64_t)Bc * n_bl >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "chunk too large: lower batch_chunk");
+  const size_t need = muser_workspace_size(MUSER_CALL_IMAGE, B, n_bl, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  ImageWs<Arena> w;
+  w.carve(a, Bc, n_bl, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = cfg->N, G = cfg->G, cap = cfg->max_iter;
+  cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
+  launch_pswf_table(w.g.tab, cfg->W, cfg->os, w.d.gc, G, s);
+  fft::launch_twiddles(w.d.tw, G, s);
+  for (int c0 = 0; c0 < B; c0 += Bc) {
+    const int n = B - c0 < Bc ? B - c0 : Bc;
+    int32_t *st = status + c0;
+    float *R = residual + (size_t)c0 * N * N;
+    launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, c0, n, G,
+               cfg->W, cfg->lat_rad, w.rec, nullptr, status, s);
+    launch_grid(w.rec, nullptr, n_bl, n, G, cfg->W, cfg->os, w.g.tab, true, nullptr, w.Z, w.g.bin_off, w.g.entries, st,
+                s);
+    launch_dirty(w.Z, n, N, G, w.d.tw, w.d.gc, w.d.T, w.d.partial, R, w.beam, st, s);
+    const float *thr = nullptr;
+    if (cfg->thr_mode == 1) {
+      launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a, w.mu_b, st, s);
+      thr = w.mu_a;
+      if (thr_out) k_copy<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, w.mu_a, n);
+    } else if (thr_out) {
+      k_fill<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, n, -INFINITY);
+    }
+    launch_hogbom(R, w.beam, n, N, thr, cfg->gain, cap, cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+                  comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, st, s);
+    launch_restore(R, w.beam, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+                   comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, n, N, cap,
+                   clean_img + (size_t)c0 * N * N, beam_params ? beam_params + (size_t)c0 * 3 : w.params, st, s);
+    MUSER_TRY(check_launch("muser_image"));
+  }
+  return MUSER_OK;
+}
+
+int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,
+                 const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, DEGRID));
+  if (direction != MUSER_FORWARD && direction != MUSER_ADJOINT) return fail(MUSER_ERR_ARG, "direction");
+  if (n_vis < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (n_vis >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "at most 2^30 records per call");
+  if (!img || (n_vis > 0 && (!rec || !vis))) return fail(MUSER_ERR_ARG, "muser_degrid: required pointer is NULL");
+  if (!aligned(vis, 8)) return fail(MUSER_ERR_ARG, "vis must be 8-byte aligned");
+  const size_t need = muser_workspace_size(MUSER_CALL_DEGRID, 1, n_vis, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  DegridWs<Arena> w;
+  w.carve(a, n_vis, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Pswf &P = pswf_coefficients(cfg->W);
+  const float K2 = (float)(P.K * P.K);
+  launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
+  fft::launch_twiddles(w.tw, cfg->G, s);
+  if (direction == MUSER_FORWARD)
+    launch_degrid_forward(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T,
+                          w.X, (float2 *)vis, s);
+  else
+    launch_degrid_adjoint((const float2 *)vis, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw,
+                          w.gc, K2, w.bin_off, w.entries, w.X, w.T, img, s);
+  return check_launch("muser_degrid");
+}
+
+int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2,
+               float *resid, float *loss, void *ws, size_t ws_bytes, muser_stream_t stream) {
+  if (n_vis < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (!loss || (n_vis > 0 && (!pred || !obs || !rec))) return fail(MUSER_ERR_ARG, "muser_chi2: required pointer is NULL");
+  const size_t need = muser_workspace_size(MUSER_CALL_CHI2, 1, n_vis, nullptr);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  const int nb = chi2_blocks(n_vis);
+  launch_chi2((const float2 *)pred, (const float2 *)obs, (const Rec *)rec, n_vis, inv_sigma2, (float2 *)resid,
+              (float *)ws, nb, loss, (cudaStream_t)stream);
+  return check_launch("muser_chi2");
+}
+
+}  // extern "C"

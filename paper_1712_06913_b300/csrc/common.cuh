@@ -1,0 +1,135 @@
+// Shared device-side definitions of libmuser (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/muser.h"
+
+namespace muser {
+
+// 24-byte gridding record, identical layout to muser_vis_record_t.
+struct __align__(8) Rec {
+  float2 v;
+  float fu, fv;
+  short ku, kv;
+  float w;
+};
+static_assert(sizeof(Rec) == 24, "record must be 24 bytes");
+static_assert(sizeof(muser_vis_record_t) == 24, "public record must be 24 bytes");
+
+constexpr int kMaxLegendre = 32;   // even Legendre terms of the spheroidal expansion
+
+// Spheroidal function coefficients (computed on the host, see setup.cu).
+struct Pswf {
+  double d[kMaxLegendre];  // psi0 = sum_i d[i] sqrt((4i+1)/2) P_{2i}
+  int n;
+  double psi00;            // psi0(0)
+  double K;                // integral of the normalised kernel over its support
+};
+
+const Pswf &pswf_coefficients(int W);   // cached per support width
+
+// ---------------------------------------------------------------- error reporting
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int check_launch(const char *what);
+
+// ---------------------------------------------------------------- small device helpers
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Kernel value C(d) from the table tab[j] = C(j / os), linear interpolation; |d| <= W/2.
+__device__ __forceinline__ float kernel_lookup(const float *__restrict__ tab, int ntab, float os, float d) {
+  float pos = fabsf(d) * os;
+  int i = (int)floorf(pos);
+  float t = pos - (float)i;
+  if (i > ntab - 2) return 0.f;
+  float a = __ldg(tab + i), b = __ldg(tab + i + 1);
+  return a * (1.f - t) + b * t;
+}
+
+// A record may be gridded only if all W taps of both samples lie inside the grid.
+__device__ __forceinline__ bool record_ok(const Rec &R, int G, int h) {
+  return R.w > 0.f && R.ku >= h + 1 && R.ku <= G - h - 1 && R.kv >= h + 1 && R.kv <= G - h - 1;
+}
+
+// Pixel-size independent sizes of the spheroidal kernel table.
+inline int table_len(int W, int os) { return (W * os) / 2 + 2; }
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Simple bump allocator over a caller workspace.
+struct Arena {
+  char *base;
+  size_t cap, off = 0;
+  bool ok = true;
+  Arena(void *b, size_t c) : base((char *)b), cap(c) {}
+  template <class T>
+  T *take(size_t n) {
+    size_t bytes = align_up(n * sizeof(T));
+    if (off + bytes > cap) { ok = false; return nullptr; }
+    T *p = (T *)(base + off);
+    off += bytes;
+    return p;
+  }
+};
+// Size-only twin of Arena.
+struct Sizer {
+  size_t off = 0;
+  template <class T>
+  void take(size_t n) { off += align_up(n * sizeof(T)); }
+};
+
+// ---------------------------------------------------------------- launchers (one per .cu)
+void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t s);
+void launch_uvw(const double *ant_enu, int n_ant, const int32_t *pairs, int n_bl, const double *ha, const double *dec,
+                int n_chan, const double *freq, const double *cell, const float2 *vis, const uint8_t *flags,
+                const double *dlm, int inst0, int n_inst, int G, int W, double lat, Rec *rec,
+                double *uvw_out, int32_t *status, cudaStream_t s);
+
+// gridding (grid.cu)
+int grid_band_rows(int G);
+__host__ __device__ inline int grid_bands_per_sample(int W, int rows) { return (W - 1 + rows - 1) / rows + 1; }
+// mirror: grid w (V + i) at +uv and w (conj V + i) at -uv (imaging); otherwise grid vals[r]
+// at +uv only (adjoint of degridding).  Every band of Z is written, so Z need not be cleared.
+void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
+                 const float *tab, bool mirror, const float2 *vals, float2 *Z, int32_t *bin_off,
+                 int32_t *entries, int32_t *status, cudaStream_t s);
+
+// imaging FFT (dirty.cu)
+int dirty_strip_width(int G);
+void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T,
+                  float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
+namespace fft {
+void launch_twiddles(float2 *tw, int L, cudaStream_t s);   // tw[m] = exp(+2 pi i m / L)
+}
+
+// CLEAN, GMM, restore (clean.cu, gmm.cu, restore.cu)
+void launch_hogbom(float *R, const float *beam, int B, int N, const float *thr, float gain, int cap,
+                   int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s);
+void launch_gmm(const float *dirty, int B, int N, int bins, float *mu_a, float *mu_b, int32_t *status,
+                cudaStream_t s);
+void launch_restore(const float *R, const float *beam, const int32_t *pos, const float *flux,
+                    const int32_t *n_comp, int B, int N, int cap, float *clean, float *params, int32_t *status,
+                    cudaStream_t s);
+
+// degridding (degrid.cu)
+void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
+                           const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
+                           float2 *vis, cudaStream_t s);
+void launch_degrid_adjoint(const float2 *vis, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
+                           const float *tab, const float2 *tw, const float *gc, float K2, int32_t *bin_off,
+                           int32_t *entries, float2 *Z, float2 *T, float *img, cudaStream_t s);
+void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t n_vis, float inv_sigma2,
+                 float2 *resid, float *partial, int n_part, float *loss, cudaStream_t s);
+int chi2_blocks(int64_t n_vis);
+
+}  // namespace muser

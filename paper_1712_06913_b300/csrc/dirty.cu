@@ -1,0 +1,176 @@
+// Inverse FFT of the uv grids to dirty map and dirty beam, with grid correction
+// (Alg. 1 dirty_image; Sec. 3.2.1: the beam is twice the image; Sec. 3.2.3 grid correction).
+//
+//   I(y, x) = sum_k Z[kv][ku] exp(+2 pi i ((ku - G/2)(x - G/2) + (kv - G/2)(y - G/2)) / G)
+//           = (-1)^(x+y) sum_k (-1)^(ku+kv) Z[kv][ku] W^(kv y + ku x),  W = exp(2 pi i / G)
+// (G/2 even).  Only the central G/2 x G/2 outputs are needed (2N x 2N beam, N x N map).
+//
+// Pass 1, k_cols: a block loads a strip of S columns (all G rows), multiplies by
+//   (-1)^(ku+kv), transforms the columns, keeps rows y in [G/4, 3G/4) -> T[B][G/2][G];
+//   it also sums Im Z over the strip (the raw beam centre is sum Im Z, because every
+//   phase factor is 1 at the centre).
+// Pass 2, k_rows: a block transforms S rows of T, keeps x in [G/4, 3G/4) and writes
+//   beam = Im I (-1)^(x+y) / (gc(x) gc(y) norm) and, over the central N x N, dirty = Re I ...
+//   with norm = sum of the strip sums (fixed order), so beam[N][N] = 1.
+#include "fft.cuh"
+
+namespace muser {
+
+namespace {
+
+using fft::ColCfg;
+using fft::RowCfg;
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT) k_cols(const float2 *__restrict__ Z, const float2 *__restrict__ tw,
+                                                       float2 *__restrict__ T, float *__restrict__ partial) {
+  using C = ColCfg<G>;
+  constexpr int S = C::S, NT = C::NT;
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  __shared__ float red[32];
+  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  const float2 *Zi = Z + (size_t)inst * G * G;
+  float2 *Ti = T + (size_t)inst * (G / 2) * G;
+  struct Load {
+    const float2 *Zi;
+    int x0;
+    float im_sum;
+    __device__ float2 operator()(int i, int s) {
+      float2 z = Zi[(size_t)i * G + x0 + s];
+      im_sum += z.y;
+      return ((i + x0 + s) & 1) ? make_float2(-z.x, -z.y) : z;
+    }
+  } load{Zi, x0, 0.f};
+  struct Store {
+    float2 *Ti;
+    int x0;
+    __device__ void operator()(int o, int s, float2 v) {
+      if (o >= G / 4 && o < 3 * G / 4) Ti[(size_t)(o - G / 4) * G + x0 + s] = v;
+    }
+  } store{Ti, x0};
+  fft::run<G, S, NT, +1, true, typename C::Layout>(sm, tw, load, store);
+  // strip sum of Im Z
+  float v = load.im_sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partial[(size_t)inst * (G / S) + blockIdx.x] = t;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
+                                                       const float *__restrict__ gc, const float *__restrict__ partial,
+                                                       int N, float *__restrict__ dirty, float *__restrict__ beam,
+                                                       int32_t *__restrict__ status) {
+  using C = RowCfg<G>;
+  constexpr int S = C::S, NT = C::NT;
+  constexpr int NSTRIP = G / ColCfg<G>::S;
+  __shared__ float2 sm[C::Layout::size];
+  __shared__ float red[32];
+  __shared__ float scale_sh;
+  const int inst = blockIdx.y, y0 = blockIdx.x * S;   // rows y0.. of T, i.e. y = y0 + G/4 ..
+  // beam normalisation: sum of the strip sums in a fixed order
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < NSTRIP; i += NT) acc += partial[(size_t)inst * NSTRIP + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < NT / 32; w++) t += red[w];
+    scale_sh = t != 0.f ? 1.f / t : 0.f;
+    if (t == 0.f && blockIdx.x == 0 && status) atomicOr(status + inst, MUSER_ST_ALL_FLAGGED);
+  }
+  __syncthreads();
+  const float scale = scale_sh;
+  const float2 *Ti = T + (size_t)inst * (G / 2) * G;
+  struct Load {
+    const float2 *Ti;
+    int y0;
+    __device__ float2 operator()(int i, int s) const { return Ti[(size_t)(y0 + s) * G + i]; }
+  } load{Ti, y0};
+  struct Store {
+    const float *gc;
+    float *D, *Bm;
+    int y0, N;
+    float scale;
+    __device__ void operator()(int x, int s, float2 v) const {
+      if (x < G / 4 || x >= 3 * G / 4) return;
+      const int y = y0 + s + G / 4;
+      float f = scale / (__ldg(gc + x) * __ldg(gc + y));
+      if ((x + y) & 1) f = -f;
+      Bm[(size_t)(y - G / 4) * (2 * N) + (x - G / 4)] = v.y * f;
+      const int lo = G / 2 - N / 2;
+      if (y >= lo && y < lo + N && x >= lo && x < lo + N) D[(size_t)(y - lo) * N + (x - lo)] = v.x * f;
+    }
+  } store{gc, dirty + (size_t)inst * N * N, beam + (size_t)inst * 4 * N * N, y0, N, scale};
+  fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+}
+
+template <int G>
+void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float *gc, float2 *T, float *partial,
+                    float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+  using CC = ColCfg<G>;
+  using RC = RowCfg<G>;
+  cudaFuncSetAttribute(k_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    k_cols<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(Z + (size_t)i * G * G, tw, T + (size_t)i * (G / 2) * G,
+                                                            partial + (size_t)i * (G / CC::S));
+    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, 0, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
+                                                         partial + (size_t)i * (G / CC::S), N,
+                                                         dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
+                                                         status ? status + i : nullptr);
+  }
+}
+
+}  // namespace
+
+int dirty_strip_width(int G) {
+  switch (G) {
+    case 64: return ColCfg<64>::S;
+    case 128: return ColCfg<128>::S;
+    case 256: return ColCfg<256>::S;
+    case 512: return ColCfg<512>::S;
+    case 1024: return ColCfg<1024>::S;
+    case 2048: return ColCfg<2048>::S;
+    case 4096: return ColCfg<4096>::S;
+    default: return 0;
+  }
+}
+
+void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T, float *partial,
+                  float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+  if (B <= 0) return;
+  switch (G) {
+#define MUSER_CASE(g) \
+  case g: launch_dirty_G<g>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s); break;
+    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+#undef MUSER_CASE
+    default: break;
+  }
+}
+
+namespace fft {
+namespace {
+__global__ void k_twiddles(float2 *tw, int L) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < L) {
+    double s, c;
+    sincospi(2.0 * m / L, &s, &c);
+    tw[m] = make_float2((float)c, (float)s);
+  }
+}
+}  // namespace
+void launch_twiddles(float2 *tw, int L, cudaStream_t s) { k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L); }
+}  // namespace fft
+
+}  // namespace muser

@@ -1,0 +1,216 @@
+// Batched radix-16 Stockham FFT in shared memory (device code shared by dirty.cu and degrid.cu).
+//
+// A block transforms S sequences of length L (a power of two, 64..4096).  Stages run
+// first-to-last with radices {2,4,8} (the remainder of log2 L mod 4, if any) then 16s.
+// Stage with sub-length LS and radix R, butterfly j in [0, L/R), sequence s:
+//     v[r] = x[j + r L/R]                      r = 0..R-1
+//     v[r] *= W^(r k),  k = j mod LS,  W = exp(SIGN 2 pi i / (LS R))
+//     v = DFT_R(v)
+//     y[(j / LS) LS R + k + r LS] = v[r]
+// (self-sorting: natural order in, natural order out).  The first stage reads through
+// a Load functor (global memory, pre-modulation), the last writes through a Store functor
+// (global memory, epilogue); intermediate stages exchange through shared memory with one
+// padding slot every 16 elements.  Twiddles come from a table tw[m] = exp(+2 pi i m / L).
+#pragma once
+
+#include "common.cuh"
+
+namespace muser {
+namespace fft {
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+// --- radix kernels (natural-order outputs), SIGN = +1 inverse, -1 forward
+template <int SIGN>
+__device__ __forceinline__ float2 mul_i(float2 a) {   // a * (SIGN i)
+  return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft2(float2 &a, float2 &b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+  float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_i<SIGN>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+// exp(SIGN 2 pi i e / 16) for e = 0..9
+template <int SIGN>
+__device__ __forceinline__ float2 w16(int e) {
+  constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+  float c, s;
+  switch (e) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = c1; s = s1; break;
+    case 2: c = h; s = h; break;
+    case 3: c = s1; s = c1; break;
+    case 4: c = 0.f; s = 1.f; break;
+    case 6: c = -h; s = h; break;
+    case 9: c = -c1; s = -s1; break;
+    default: c = 0.f; s = 0.f; break;
+  }
+  return make_float2(c, SIGN > 0 ? s : -s);
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+  if constexpr (R == 2) {
+    dft2<SIGN>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    // r = b + 2a, m = m1 + 4 m2:  y[b][m1] = DFT4_a(v[b+2a]) * w8^(b m1);  X = DFT2_b
+    dft4<SIGN>(v[0], v[2], v[4], v[6]);
+    dft4<SIGN>(v[1], v[3], v[5], v[7]);
+    constexpr float h = 0.70710678118654752f;
+    const float sg = SIGN > 0 ? 1.f : -1.f;
+    v[3] = cmul(v[3], make_float2(h, sg * h));
+    v[5] = mul_i<SIGN>(v[5]);
+    v[7] = cmul(v[7], make_float2(-h, sg * h));
+    float2 o[8];
+#pragma unroll
+    for (int m1 = 0; m1 < 4; m1++) {
+      float2 a = v[2 * m1], b = v[2 * m1 + 1];
+      o[m1] = cadd(a, b);
+      o[m1 + 4] = csub(a, b);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = o[i];
+  } else {
+    static_assert(R == 16, "radix");
+    // r = b + 4a, m = m1 + 4 m2:  y[b][m1] = DFT4_a(v[b+4a]) * w16^(b m1);  X = DFT4_b
+#pragma unroll
+    for (int b = 0; b < 4; b++) dft4<SIGN>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+    // after dft4 the outputs of sub-transform b sit at v[b + 4 m1]
+#pragma unroll
+    for (int b = 1; b < 4; b++)
+#pragma unroll
+      for (int m1 = 1; m1 < 4; m1++) v[b + 4 * m1] = cmul(v[b + 4 * m1], w16<SIGN>(b * m1));
+    float2 o[16];
+#pragma unroll
+    for (int m1 = 0; m1 < 4; m1++) {
+      float2 a0 = v[4 * m1], a1 = v[4 * m1 + 1], a2 = v[4 * m1 + 2], a3 = v[4 * m1 + 3];
+      dft4<SIGN>(a0, a1, a2, a3);
+      o[m1] = a0;
+      o[m1 + 4] = a1;
+      o[m1 + 8] = a2;
+      o[m1 + 12] = a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = o[i];
+  }
+}
+
+// --- shared-memory layouts: element (i, s), one padding slot per 16 elements
+template <int L, int S>
+struct Interleaved {          // consecutive sequences adjacent: for column strips
+  static constexpr int size = (L + L / 16) * S;
+  __device__ __forceinline__ static int at(int i, int s) { return (i + (i >> 4)) * S + s; }
+};
+template <int L, int S>
+struct Sequential {           // one sequence after another: for rows
+  static constexpr int PL = L + L / 16;
+  static constexpr int size = PL * S;
+  __device__ __forceinline__ static int at(int i, int s) { return s * PL + i + (i >> 4); }
+};
+
+template <int L>
+struct Plan {
+  static constexpr int LOG2L = ilog2(L);
+  static constexpr int REM = LOG2L % 4;
+  static constexpr int NST = LOG2L / 4 + (REM ? 1 : 0);
+  template <int STAGE>
+  static constexpr int radix() { return (STAGE == 0 && REM) ? (1 << REM) : 16; }
+};
+
+// One stage and (recursively) the following ones.  SFAST: work items enumerate the
+// sequence index fastest (column strips, coalesced global rows) or the butterfly index
+// fastest (rows).  NT threads; S * L / R must be a multiple of NT.
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, class Load, class Store>
+__device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
+  constexpr int R = Plan<L>::template radix<STAGE>();
+  constexpr bool FIRST = STAGE == 0, LAST = STAGE == Plan<L>::NST - 1;
+  constexpr int NB = L / R;
+  constexpr int ITEMS = S * NB;
+  static_assert(ITEMS % NT == 0, "work items must divide among threads");
+  constexpr int BPT = ITEMS / NT;
+  float2 v[BPT][R];
+#pragma unroll
+  for (int b = 0; b < BPT; b++) {
+    const int it = threadIdx.x + b * NT;
+    const int s = SFAST ? it % S : it / NB;
+    const int j = SFAST ? it / S : it % NB;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int idx = j + r * NB;
+      if constexpr (FIRST) v[b][r] = load(idx, s);
+      else v[b][r] = sm[Layout::at(idx, s)];
+    }
+  }
+  if constexpr (!FIRST) __syncthreads();
+#pragma unroll
+  for (int b = 0; b < BPT; b++) {
+    const int it = threadIdx.x + b * NT;
+    const int s = SFAST ? it % S : it / NB;
+    const int j = SFAST ? it / S : it % NB;
+    const int k = j & (LS - 1);
+    if constexpr (LS > 1) {
+      constexpr int STEP = L / (LS * R);      // W_{LS R}^{rk} = W_L^{rk STEP}
+#pragma unroll
+      for (int r = 1; r < R; r++) {
+        float2 w = __ldg(tw + r * k * STEP);
+        if (SIGN < 0) w.y = -w.y;
+        v[b][r] = cmul(v[b][r], w);
+      }
+    }
+    dft<R, SIGN>(v[b]);
+    const int base = (j / LS) * LS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const int o = base + r * LS;
+      if constexpr (LAST) store(o, s, v[b][r]);
+      else sm[Layout::at(o, s)] = v[b][r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+    stages<L, S, NT, SIGN, SFAST, Layout, STAGE + 1, LS * R>(sm, tw, load, store);
+  }
+}
+
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, class Load, class Store>
+__device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
+  stages<L, S, NT, SIGN, SFAST, Layout, 0, 1>(sm, tw, load, store);
+}
+
+// Column strips: S columns of a G x G array per block (S = min(G, 16384 / G)), 32 complex
+// values per thread per stage.  Rows: S = min(max(1, 4096 / G), G / 2) rows per block, 16 values
+// per thread per stage.
+template <int G>
+struct ColCfg {
+  static constexpr int S = G < 16384 / G ? G : 16384 / G;
+  static constexpr int NT = S * G / 32;
+  using Layout = Interleaved<G, S>;
+  static constexpr size_t smem = sizeof(float2) * Layout::size;
+};
+template <int G>
+struct RowCfg {
+  static constexpr int S0 = 4096 / G > 1 ? 4096 / G : 1;
+  static constexpr int S = S0 < G / 2 ? S0 : G / 2;
+  static constexpr int NT = S * G / 16;
+  using Layout = Sequential<G, S>;
+  static constexpr size_t smem = sizeof(float2) * Layout::size;
+};
+
+void launch_twiddles(float2 *tw, int L, cudaStream_t s);
+
+}  // namespace fft
+}  // namespace muser

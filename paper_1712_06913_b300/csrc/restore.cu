@@ -1,0 +1,167 @@
+// Clean beam fit and restored image (Alg. 1: dirty_image also returns the clean beam).
+//
+// k_beam_fit (one block per instance): the main lobe is the 4-connected region of beam
+// pixels >= 1/2 that contains the centre, grown by repeated relaxation inside a window of
+// +-63 pixels (bounded number of sweeps; a lobe touching the window edge sets
+// MUSER_ST_BEAM_FIT).  Its second moments about the centre (integer sums, then FP64),
+// with 1/12 added on the diagonal for the unit pixel area, give Sigma = (2 / ln 2) M.
+// k_restore (one block per 32 x 32 tile): residual + sum_c f_c exp(-q' Sigma^-1 q / 2) over
+// the components whose Gaussian exceeds 1e-7 on the tile, in component order.
+#include "common.cuh"
+
+namespace muser {
+
+namespace {
+
+constexpr int kFitThreads = 1024;
+constexpr int kWin = 63;                   // half window
+constexpr int kSide = 2 * kWin + 1;
+constexpr float kTrunc = 32.2361913f;      // 2 ln(1e7): Gaussian below 1e-7 outside q' S^-1 q > kTrunc
+
+__global__ void __launch_bounds__(kFitThreads) k_beam_fit(const float *__restrict__ Ball, int N,
+                                                          float *__restrict__ params,
+                                                          int32_t *__restrict__ status) {
+  __shared__ unsigned char mask[kSide * kSide];
+  __shared__ unsigned char lab[kSide * kSide];
+  __shared__ int changed;
+  __shared__ unsigned long long acc[4];
+  const int inst = blockIdx.x;
+  const float *Bm = Ball + (size_t)inst * 4 * N * N;
+  const int win = kWin < N - 1 ? kWin : N - 1;
+  const int side = 2 * win + 1;
+  for (int i = threadIdx.x; i < side * side; i += kFitThreads) {
+    const int wy = i / side, wx = i % side;
+    const int y = N - win + wy, x = N - win + wx;
+    mask[i] = Bm[(size_t)y * 2 * N + x] >= 0.5f;
+    lab[i] = (wy == win && wx == win) ? mask[i] : 0;
+  }
+  if (threadIdx.x < 4) acc[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int sweep = 0; sweep < side * side; sweep++) {
+    if (threadIdx.x == 0) changed = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int i = threadIdx.x; i < side * side; i += kFitThreads) {
+      if (!mask[i] || lab[i]) continue;
+      const int wy = i / side, wx = i % side;
+      if ((wy > 0 && lab[i - side]) || (wy < side - 1 && lab[i + side]) || (wx > 0 && lab[i - 1]) ||
+          (wx < side - 1 && lab[i + 1])) {
+        lab[i] = 1;
+        mine = 1;
+      }
+    }
+    if (mine) changed = 1;
+    __syncthreads();
+    if (!changed) break;
+  }
+  int edge = 0;
+  unsigned long long sxx = 0, syy = 0, n = 0;
+  long long sxy = 0;
+  for (int i = threadIdx.x; i < side * side; i += kFitThreads) {
+    if (!lab[i]) continue;
+    const int wy = i / side, wx = i % side;
+    const long long dx = wx - win, dy = wy - win;
+    sxx += dx * dx;
+    syy += dy * dy;
+    sxy += dx * dy;
+    n += 1;
+    if (wy == 0 || wx == 0 || wy == side - 1 || wx == side - 1) edge = 1;
+  }
+  atomicAdd(&acc[0], sxx);
+  atomicAdd(&acc[1], syy);
+  atomicAdd(&acc[2], (unsigned long long)sxy);   // two's complement sum
+  atomicAdd(&acc[3], n);
+  if (edge) changed = 2;   // reuse as a flag; only written with the same value
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double cnt = (double)acc[3];
+    float *P = params + (size_t)inst * 3;
+    if (cnt == 0 || changed == 2) {
+      if (status) atomicOr(status + inst, MUSER_ST_BEAM_FIT);
+    }
+    if (cnt == 0) {
+      P[0] = P[1] = P[2] = 0.f;
+    } else {
+      const double k = 2.0 / log(2.0);
+      P[0] = (float)(k * ((double)acc[0] / cnt + 1.0 / 12.0));
+      P[1] = (float)(k * ((double)(long long)acc[2] / cnt));
+      P[2] = (float)(k * ((double)acc[1] / cnt + 1.0 / 12.0));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall, const int32_t *__restrict__ pos,
+                                                 const float *__restrict__ flux, const int32_t *__restrict__ n_comp,
+                                                 int N, int cap, const float *__restrict__ params,
+                                                 float *__restrict__ clean) {
+  __shared__ int cp[256];
+  __shared__ float cf[256];
+  const int inst = blockIdx.y;
+  const int tiles_x = N / 32 > 0 ? N / 32 : 1;
+  const int tw = N < 32 ? N : 32;
+  const int ty0 = (blockIdx.x / tiles_x) * tw, tx0 = (blockIdx.x % tiles_x) * tw;
+  const float *R = Rall + (size_t)inst * N * N;
+  float *C = clean + (size_t)inst * N * N;
+  const float sxx = params[inst * 3], sxy = params[inst * 3 + 1], syy = params[inst * 3 + 2];
+  const float det = sxx * syy - sxy * sxy;
+  const bool ok = det > 0.f;
+  const float ixx = ok ? syy / det : 0.f, ixy = ok ? -sxy / det : 0.f, iyy = ok ? sxx / det : 0.f;
+  const float ex = ok ? sqrtf(kTrunc * sxx) : 0.f, ey = ok ? sqrtf(kTrunc * syy) : 0.f;
+  // 4 pixels per thread (tile of tw x tw <= 1024 pixels)
+  float acc[4];
+  int py[4], px[4];
+  const int npx = tw * tw;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int p = threadIdx.x + k * 256;
+    py[k] = ty0 + (p < npx ? p / tw : 0);
+    px[k] = tx0 + (p < npx ? p % tw : 0);
+    acc[k] = 0.f;
+  }
+  const int nc = ok ? n_comp[inst] : 0;
+  for (int c0 = 0; c0 < nc; c0 += 256) {
+    __syncthreads();
+    if (c0 + threadIdx.x < nc) {
+      cp[threadIdx.x] = pos[(size_t)inst * cap + c0 + threadIdx.x];
+      cf[threadIdx.x] = flux[(size_t)inst * cap + c0 + threadIdx.x];
+    }
+    __syncthreads();
+    const int m = nc - c0 < 256 ? nc - c0 : 256;
+    for (int c = 0; c < m; c++) {
+      const int cy = cp[c] / N, cx = cp[c] % N;
+      if (cx + ex < tx0 || cx - ex > tx0 + tw - 1 || cy + ey < ty0 || cy - ey > ty0 + tw - 1) continue;
+      const float f = cf[c];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float dx = (float)(px[k] - cx), dy = (float)(py[k] - cy);
+        const float qq = ixx * dx * dx + 2.f * ixy * dx * dy + iyy * dy * dy;
+        if (qq <= kTrunc) acc[k] += f * expf(-0.5f * qq);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int p = threadIdx.x + k * 256;
+    if (p < npx) {
+      const size_t q = (size_t)py[k] * N + px[k];
+      C[q] = R[q] + acc[k];
+    }
+  }
+}
+
+}  // namespace
+
+void launch_restore(const float *R, const float *beam, const int32_t *pos, const float *flux, const int32_t *n_comp,
+                    int B, int N, int cap, float *clean, float *params, int32_t *status, cudaStream_t s) {
+  if (B <= 0) return;
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    k_beam_fit<<<n, kFitThreads, 0, s>>>(beam + (size_t)i * 4 * N * N, N, params + (size_t)i * 3,
+                                         status ? status + i : nullptr);
+    const int tiles = N >= 32 ? (N / 32) * (N / 32) : 1;
+    k_restore<<<dim3(tiles, n), 256, 0, s>>>(R + (size_t)i * N * N, pos + (size_t)i * cap, flux + (size_t)i * cap,
+                                             n_comp + i, N, cap, params + (size_t)i * 3, clean + (size_t)i * N * N);
+  }
+}
+
+}  // namespace muser
