@@ -184,7 +184,12 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
+    ap.add_argument("--case", choices=["clean", "dirty", "grid"], default=None,
+                    help="small single-kernel case of the same workload (for ncu captures)")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -339,6 +344,53 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_case(case):
+    """Small cases of the benchmark workload, a few GB on the device, for profiler captures.
+
+    clean: 148 instances (one block per SM) of the MUSER-II batch, CLEAN with 100 iterations.
+    dirty: 8 instances, gridding + FFT to dirty map and beam.
+    grid:  8 instances, gridding only.
+    """
+    import torch
+    import paper_1712_06913_b300 as m
+    import synth
+    n_inst = 148 if case == "clean" else 8
+    wl = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst)))
+    cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=100, gain=wl.gain, lat_rad=wl.lat)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    rec, _, st = m.uvw(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    off = torch.arange(n_inst + 1, dtype=torch.int64, device="cuda") * wl.n_bl
+    ws = m.Workspace()
+    N = wl.N
+    D = torch.empty((n_inst, N, N), dtype=torch.float32, device="cuda")
+    Bm = torch.empty((n_inst, 2 * N, 2 * N), dtype=torch.float32, device="cuda")
+    step = 8
+    t0 = time.perf_counter()
+    for c0 in range(0, n_inst, step):
+        n = min(step, n_inst - c0)
+        Z, s2 = m.grid(rec, off[c0:c0 + n + 1], cfg, status=st[c0:c0 + n].clone(), ws=ws)
+        if case == "grid":
+            break
+        d, b, s2 = m.dirty(Z, cfg, status=s2, ws=ws)
+        D[c0:c0 + n] = d
+        Bm[c0:c0 + n] = b
+        del Z, d, b
+    torch.cuda.synchronize()
+    if case == "clean":
+        ws.buf = None
+        torch.cuda.empty_cache()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R, pos, flux, nc, s2 = m.clean(D, Bm, cfg, status=st, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        gb = n_inst * (4.0 + 100 * 12.0) * N * N / 1e9
+        print(json.dumps({"case": case, "instances": n_inst, "clean_ms": e0.elapsed_time(e1),
+                          "GBps": gb / (e0.elapsed_time(e1) / 1e3), "n_comp_min": int(nc.min())}))
+    else:
+        print(json.dumps({"case": case, "instances": n_inst, "s": time.perf_counter() - t0}))
 
 
 def plain_and_degrid(m, wl, cell, cfg, stream):

@@ -5,8 +5,11 @@
 // bins (K = 3, weighted by the counts) in FP32 with log-space responsibilities.  Start:
 // means at the bins where the count CDF first reaches 0.25, 0.85 and 0.995 (decided in
 // FP64 on exact integer counts), variances var/3 (var of the histogram), equal weights;
-// variance floor (bin width)^2; stop when |dlogL| < 1e-12 |logL| or after 1000 iterations.
-// mu_a = lowest mean (sky), mu_b = second (disk).
+// variance floor (bin width)^2.  Stopping: the FP64 rule |dlogL| < 1e-12 |logL| cannot be
+// evaluated in FP32 (the FP32 sum of the bin log-likelihoods stops changing while the
+// parameters are still moving, ending the fit early), so the loop runs until the nine
+// parameters are bitwise unchanged between iterations, or 1000 iterations; both stop at
+// the same fixed point to within FP32 rounding.  mu_a = lowest mean (sky), mu_b = second (disk).
 #include "common.cuh"
 
 namespace muser {
@@ -124,9 +127,10 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
     var[k] = fmaxf(var0 / 3.f, floor_v);
     pi[k] = 1.f / K;
   }
-  float logL_old = 0.f;
-  bool have_old = false;
   for (int it = 0; it < 1000; it++) {
+    float prev[3 * K];
+#pragma unroll
+    for (int k = 0; k < K; k++) { prev[k] = mu[k]; prev[K + k] = var[k]; prev[2 * K + k] = pi[k]; }
     float lpi[K], c2[K], ln[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -134,9 +138,9 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
       c2[k] = -0.5f / var[k];
       ln[k] = -0.5f * logf(2.f * CUDART_PI_F * var[k]);
     }
-    float acc[2 * K + 1];
+    float acc[2 * K];
 #pragma unroll
-    for (int a = 0; a < 2 * K + 1; a++) acc[a] = 0.f;
+    for (int a = 0; a < 2 * K; a++) acc[a] = 0.f;
     float rr[kMaxBinsPerThread][K];
 #pragma unroll
     for (int j = 0; j < kMaxBinsPerThread; j++) {
@@ -159,17 +163,15 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
           acc[k] += hr;
           acc[K + k] += hr * xb[j];
         }
-        if (hb[j] > 0.f) acc[2 * K] += hb[j] * (m + logf(s));
       }
     }
-    block_sum<2 * K + 1>(acc, red);
+    block_sum<2 * K>(acc, red);
     float nk[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
       nk[k] = acc[k];
       if (nk[k] > 0.f) mu[k] = acc[K + k] / nk[k];
     }
-    const float logL = acc[2 * K];
     float sv[K];
 #pragma unroll
     for (int k = 0; k < K; k++) sv[k] = 0.f;
@@ -190,9 +192,10 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
       var[k] = fmaxf(var[k], floor_v);
       pi[k] = nk[k] / total;
     }
-    if (have_old && fabsf(logL - logL_old) < 1e-12f * fabsf(logL)) break;
-    logL_old = logL;
-    have_old = true;
+    bool same = true;
+#pragma unroll
+    for (int k = 0; k < K; k++) same &= prev[k] == mu[k] && prev[K + k] == var[k] && prev[2 * K + k] == pi[k];
+    if (same) break;     // every thread holds the same parameters: uniform exit
   }
   if (threadIdx.x == 0) {
     // ascending order of the means (stable)

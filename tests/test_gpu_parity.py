@@ -219,8 +219,11 @@ def test_image_batched_equals_per_instance(m):
             one = m.image(wl.ant_enu, wl.pairs, wl.ha[f:f + 1], wl.dec[f:f + 1], wl.freq[c:c + 1], cell[c:c + 1],
                           wl.vis[f:f + 1, c:c + 1], cfg1, flags=wl.flags[f:f + 1, c:c + 1])
             i = f * wl.n_chan + c
+            # identical components; images equal up to the order of the shared-memory
+            # float additions in gridding
             assert torch.equal(one.comp_pos[0], out.comp_pos[i])
-            assert torch.equal(one.clean[0], out.clean[i])
+            peak = float(one.clean[0].abs().max())
+            assert float((one.clean[0] - out.clean[i]).abs().max()) <= 1e-6 * peak
 
 
 def test_gmm_threshold_path(m):
@@ -326,7 +329,7 @@ def test_autograd_gradient_vs_oracle_and_fd(m):
     loss.backward()
     g = _np(x.grad)
     co, go = oop.chi2_grad(x0, ro, ro["vis"], sigma, N, cfg.G, KER)
-    assert float(loss) == pytest.approx(co, rel=1e-4)
+    assert float(loss.detach()) == pytest.approx(co, rel=1e-4)
     assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
     # finite differences of the GPU loss (chi2 is quadratic: central differences are exact up to rounding)
     h = 0.05
