@@ -315,7 +315,9 @@ def main():
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "bytes_per_launch": statistics.mean(clean_bytes),
                 "launch_ms": clean_ms,
-                "traffic": (tr["dram_bytes_per_instance"] * args.chunk) if tr else None}
+                "traffic": (statistics.mean(clean_bytes) * tr["dram_per_algorithmic"]) if tr else None,
+                "traffic_source": ("ncu dram bytes of the 148-instance x 100-iteration case, scaled to this "
+                                   "launch by algorithmic bytes") if tr else None}
     grid_bytes = args.chunk * (24.0 * wl.n_bl + 8.0 * G * G)
     extra = {"phase_ms_per_chunk": {k: statistics.mean(v) for k, v in phase.items()},
              "gridding_GBps": grid_bytes / (statistics.mean(phase["grid"]) / 1e3) / 1e9,
