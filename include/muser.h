@@ -148,6 +148,24 @@ MUSER_API int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, 
 MUSER_API int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam, void *ws,
                 size_t ws_bytes, int32_t *status, muser_stream_t stream);
 
+/* Size of the library-owned scratch array used by muser_dirty_noalloc (16 MiB). */
+#define MUSER_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* muser_dirty without a workspace, for callers that cannot allocate device memory (for
+ * example a host application whose device memory belongs to another allocator or a fixed
+ * budget, or code that must not call cudaMalloc/cudaFree because they synchronise the
+ * device).  The paper has no counterpart: this is a deployment variant of muser_dirty.
+ * Same arguments, results and status bits as muser_dirty, minus ws/ws_bytes.  Scratch
+ * comes from one static device array of MUSER_NOALLOC_SCRATCH_BYTES inside the library,
+ * held by every GPU that loads the library until exit.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current): make it
+ * before any stream capture.  All calls share the array, so calls that may overlap on the
+ * GPU (other streams or host threads) race and must be serialised.  A batch whose scratch
+ * exceeds the array, about B * (G/2) * G * 8 bytes, returns MUSER_ERR_ARG; no device memory
+ * is ever allocated. */
+MUSER_API int muser_dirty_noalloc(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam,
+                                  int32_t *status, muser_stream_t stream);
+
 /* Sky and disk brightness by a Gaussian mixture on the gmm_bins-range histogram of each
  * dirty map (Sec. 4.1; Alg. 1 pre_clean): mu_a[B] = sky (lowest mean), mu_b[B] = disk. */
 MUSER_API int muser_gmm(const float *dirty, int B, const muser_config_t *cfg, float *mu_a, float *mu_b, void *ws,

@@ -43,6 +43,7 @@ SIGNATURES = {
     "muser_uvw": (I32, [P, I32, P, I32, P, P, I32, P, P, I32, P, P, P, CFG, P, P, P, P]),
     "muser_grid": (I32, [P, P, I32, I64, CFG, P, P, SZ, P, P]),
     "muser_dirty": (I32, [P, I32, CFG, P, P, P, SZ, P, P]),
+    "muser_dirty_noalloc": (I32, [P, I32, CFG, P, P, P, P]),
     "muser_gmm": (I32, [P, I32, CFG, P, P, P, SZ, P, P]),
     "muser_clean": (I32, [P, P, I32, CFG, P, P, P, P, P, SZ, P, P]),
     "muser_restore": (I32, [P, P, P, P, P, I32, CFG, P, P, P, SZ, P, P]),
