@@ -186,9 +186,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
     ap.add_argument("--case", choices=["clean", "dirty", "grid"], default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
+    ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     args = ap.parse_args()
     if args.case:
-        run_case(args.case)
+        run_case(args.case, args.instances)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -348,7 +349,7 @@ def main():
         dist.destroy_process_group()
 
 
-def run_case(case):
+def run_case(case, n_inst=0):
     """Small cases of the benchmark workload, a few GB on the device, for profiler captures.
 
     clean: 148 instances (one block per SM) of the MUSER-II batch, CLEAN with 100 iterations.
@@ -358,7 +359,7 @@ def run_case(case):
     import torch
     import paper_1712_06913_b300 as m
     import synth
-    n_inst = 148 if case == "clean" else 8
+    n_inst = n_inst or (148 if case == "clean" else 8)
     wl = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst)))
     cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=100, gain=wl.gain, lat_rad=wl.lat)
     cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)

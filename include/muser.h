@@ -83,7 +83,9 @@ typedef struct muser_config {
   int32_t gmm_bins;     /* histogram ranges for the GMM, 2..4096; 2000 in the paper (Sec. 4.1) */
   double lat_rad;       /* array latitude (Sec. 3.2.2) */
   int32_t batch_chunk;  /* muser_image: instances per internal chunk (0 = whole batch) */
-  int32_t reserved[7];  /* must be zero */
+  int32_t clean_kernel; /* 0: residual held on chip for N = 256/512/1024 when the device allows
+                           (else streaming); 1: always stream the residual from memory */
+  int32_t reserved[6];  /* must be zero */
 } muser_config_t;
 
 /* One gridding record per visibility, 24 bytes (written by muser_uvw).

@@ -28,7 +28,8 @@ class Config(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("G", ctypes.c_int32), ("W", ctypes.c_int32), ("os", ctypes.c_int32),
                 ("weight_mode", ctypes.c_int32), ("peak_mode", ctypes.c_int32), ("thr_mode", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("gain", ctypes.c_float), ("gmm_bins", ctypes.c_int32),
-                ("lat_rad", ctypes.c_double), ("batch_chunk", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("lat_rad", ctypes.c_double), ("batch_chunk", ctypes.c_int32), ("clean_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 P = ctypes.c_void_p

@@ -34,10 +34,12 @@ class Config:
     gmm_bins: int = 2000
     lat_rad: float = 0.0
     batch_chunk: int = 0
+    clean_kernel: int = 0       # 0 auto (on-chip residual when possible), 1 streaming
 
     def c(self) -> _lib.Config:
         return _lib.Config(self.N, self.G, self.W, self.os, self.weight_mode, self.peak_mode, self.thr_mode,
-                           self.max_iter, self.gain, self.gmm_bins, self.lat_rad, self.batch_chunk)
+                           self.max_iter, self.gain, self.gmm_bins, self.lat_rad, self.batch_chunk,
+                           self.clean_kernel)
 
 
 def _p(t):

@@ -49,10 +49,13 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (!(cfg->gain > 0.f && cfg->gain <= 1.f)) return fail(MUSER_ERR_ARG, "gain must be in (0, 1]");
   if (cfg->gmm_bins < 2 || cfg->gmm_bins > 4096) return fail(MUSER_ERR_ARG, "gmm_bins must be in [2, 4096]");
   if (cfg->batch_chunk < 0) return fail(MUSER_ERR_ARG, "batch_chunk must be >= 0");
-  for (int i = 0; i < 7; i++)
+  if (cfg->clean_kernel != 0 && cfg->clean_kernel != 1) return fail(MUSER_ERR_ARG, "clean_kernel must be 0 or 1");
+  for (int i = 0; i < 6; i++)
     if (cfg->reserved[i] != 0) return fail(MUSER_ERR_ARG, "reserved fields must be zero");
   return MUSER_OK;
 }
+
+bool copies(const muser_config_t &c);
 
 // ----------------------------------------------------------------------- workspace layouts
 template <class A>
@@ -93,7 +96,7 @@ struct ImageWs {
     g.carve(a, Bc, (int64_t)Bc * n_bl, c, true);
     Z = (float2 *)a.template take<float2>((size_t)Bc * c.G * c.G);
     d.carve(a, Bc, c);
-    beam = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N);
+    beam = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
     mu_a = (float *)a.template take<float>(Bc);
     mu_b = (float *)a.template take<float>(Bc);
     params = (float *)a.template take<float>((size_t)Bc * 3);
@@ -126,6 +129,8 @@ struct SizeArena {
     return nullptr;
   }
 };
+
+bool copies(const muser_config_t &c) { return c.clean_kernel == 0 && clean_uses_copies(c.N); }
 
 int chunk_of(int B, const muser_config_t &c) { return (c.batch_chunk > 0 && c.batch_chunk < B) ? c.batch_chunk : B; }
 
@@ -188,7 +193,10 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_GRID: { GridWs<SizeArena> w; w.carve(a, B, n_vis_total, *cfg, true); break; }
     case MUSER_CALL_DIRTY: { DirtyWs<SizeArena> w; w.carve(a, B, *cfg); break; }
     case MUSER_CALL_GMM: break;
-    case MUSER_CALL_CLEAN: a.take<float>(2 * (size_t)B); break;
+    case MUSER_CALL_CLEAN:
+      a.take<float>(2 * (size_t)B);
+      if (copies(*cfg)) a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
+      break;
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
     case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
@@ -278,16 +286,25 @@ int muser_clean(float *residual, const float *beam, int B, const muser_config_t 
   if (!aligned(residual, 16)) return fail(MUSER_ERR_ARG, "residual must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;
   const float *t = thr;
+  const size_t need = muser_workspace_size(MUSER_CALL_CLEAN, B, 0, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  float *mu = a.take<float>(2 * (size_t)B);
   if (!thr && cfg->thr_mode == 1) {
-    const size_t need = muser_workspace_size(MUSER_CALL_CLEAN, B, 0, cfg);
-    MUSER_TRY(check_ws(ws, ws_bytes, need));
-    Arena a(ws, ws_bytes);
-    float *mu = a.take<float>(2 * (size_t)B);
     launch_gmm(residual, B, cfg->N, cfg->gmm_bins, mu, mu + B, status, s);
     t = mu;
   }
-  launch_hogbom(residual, beam, B, cfg->N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux, n_comp,
-                status, s);
+  const int N = cfg->N;
+  if (copies(*cfg)) {
+    float *beam4 = a.take<float>((size_t)B * 16 * N * N);
+    const size_t cstride = (size_t)B * 4 * N * N;
+    launch_beam_copies(beam, B, N, 0, beam4, cstride, s);
+    launch_hogbom(residual, beam, beam4, cstride, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
+                  comp_flux, n_comp, status, s);
+  } else {
+    launch_hogbom_stream(residual, beam, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux,
+                         n_comp, status, s);
+  }
   return check_launch("muser_clean");
 }
 
@@ -352,7 +369,11 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     } else if (thr_out) {
       k_fill<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, n, -INFINITY);
     }
-    launch_hogbom(R, w.beam, n, N, thr, cfg->gain, cap, cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+    const size_t cstride = (size_t)Bc * 4 * N * N;
+    if (copies(*cfg)) launch_beam_copies(w.beam, n, N, 1, w.beam, cstride, s);
+    launch_hogbom(
+        R, w.beam, copies(*cfg) ? w.beam : nullptr, cstride, n, N, thr, cfg->gain, cap, cfg->peak_mode,
+        comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                   comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, st, s);
     launch_restore(R, w.beam, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                    comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, n, N, cap,

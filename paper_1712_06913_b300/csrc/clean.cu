@@ -1,12 +1,21 @@
 // Hogbom CLEAN (Alg. 1 improved_clean loop; Sec. 4.3 stopping rule).
 //
-// One block of 1024 threads owns one instance for the whole loop, so no cross-block
-// synchronisation is needed and instances that stop early free their SM.  Each
-// iteration is one pass over the residual: every thread subtracts gain * peak * beam
-// from its pixels (16-byte residual accesses; the beam window starts at an arbitrary
-// column so it is read with 4-byte coalesced loads) and keeps the running argmax of the
-// updated values; a warp-shuffle + shared-memory reduction gives the next peak.  Ties go to
-// the lowest row-major index.
+// Per iteration: p = argmax of the residual (ties to the lowest row-major index), stop if
+// R[p] <= thr or the cap is reached, f = gain R[p], R[q] -= f Bm[q - p + (N, N)] for all q.
+// Two kernels, both keeping the whole loop on the device:
+//
+// k_hogbom_onchip (N = 256, 512, 1024): the residual never leaves the chip.  Each block of
+//   1024 threads owns 65536 residual pixels (a band of rows): 57344 in shared memory
+//   (224 KB) and 8 per thread in registers.  N = 256 needs one block per instance; N = 512 a
+//   cluster of 4 blocks and N = 1024 a cluster of 16, whose block maxima are combined
+//   through distributed shared memory after one cluster barrier per iteration.  An iteration
+//   then moves only the beam window (4 N^2 bytes, mostly from L2) instead of 12 N^2 bytes.
+// k_hogbom (any N, fallback): one block per instance streams the residual from HBM every
+//   iteration (16-byte residual accesses, 4-byte coalesced beam loads).
+// In both, the argmax of iteration k+1 is taken in the same pass as the subtraction of
+// iteration k (warp shuffles, then shared memory, then the cluster).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace muser {
@@ -126,10 +135,301 @@ __global__ void __launch_bounds__(kCleanThreads) k_hogbom(float *__restrict__ Ra
   }
 }
 
+// ------------------------------------------------------------------ on-chip residual
+namespace cg = cooperative_groups;
+
+constexpr int kOnT = 1024;                           // threads per block
+constexpr int kSmemPix = 57344;                      // residual pixels in shared memory (224 KB)
+constexpr int kRegPer = 8;                           // residual pixels in registers per thread
+constexpr int kBandPix = kSmemPix + kRegPer * kOnT;  // 65536 pixels per block
+constexpr size_t kOnSmem = sizeof(float) * kSmemPix;
+constexpr int kBatch = 7;                            // quads whose beam loads are in flight together
+static_assert(kSmemPix / 4 % (kBatch * kOnT) == 0, "quads divide into whole batches");
+
+__device__ __forceinline__ void warp_argmax(Peak &p) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float k = __shfl_xor_sync(0xffffffffu, p.key, o);
+    float v = __shfl_xor_sync(0xffffffffu, p.val, o);
+    int i = __shfl_xor_sync(0xffffffffu, p.idx, o);
+    if (better(k, i, p.key, p.idx)) { p.key = k; p.val = v; p.idx = i; }
+  }
+}
+
+// Argmax over the whole cluster (CS blocks); every thread of every block gets the result:
+// warp results go to wred[par], warp 0 writes the block winner to slot[par], reads the CS
+// winners through distributed shared memory after the cluster barrier and broadcasts the
+// result through shared memory.  wred and slot alternate with `par`, so a buffer is only
+// rewritten after one more barrier, when every reader is done with it.
+template <int CS>
+__device__ __forceinline__ Peak cluster_argmax(Peak p, Peak (*wred)[32], Peak *slot, int par) {
+  __shared__ Peak gpk;
+  warp_argmax(p);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wred[par][wid] = p;
+  __syncthreads();
+  if (wid == 0) {
+    Peak q = wred[par][lane];
+    warp_argmax(q);
+    if (lane == 0) {
+      if (CS > 1) slot[par] = q;
+      else gpk = q;
+    }
+  }
+  if constexpr (CS > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    if (wid == 0) {
+      Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
+      if (lane < CS) q = *cluster.map_shared_rank(slot + par, lane);
+      warp_argmax(q);
+      if (lane == 0) gpk = q;
+    }
+  }
+  __syncthreads();
+  return gpk;
+}
+
+// Pixels of thread t in its block's band: quads q = t + i kOnT (i < kQuads) in shared
+// memory, then register pixels b = kSmemPix + t + j kOnT (j < kRegPer).  Visited in this
+// order the band indices increase, so a strict ">" keeps the lowest index among equal values.
+constexpr int kQuads = kSmemPix / 4 / kOnT;          // 14 quads per thread
+
+template <int MODE>
+__device__ __forceinline__ bool beats(float v, float best) {
+  return MODE ? fabsf(v) > fabsf(best) : v > best;
+}
+
+// Band index of the thread's o-th pixel (o < 4 kQuads: quad pixels; then register pixels).
+__device__ __forceinline__ int band_index(int o, int tid) {
+  return o < 4 * kQuads ? 4 * (tid + (o >> 2) * kOnT) + (o & 3) : kSmemPix + tid + (o - 4 * kQuads) * kOnT;
+}
+
+// beam4: four copies of every instance's beam, copy k at beam4 + k * cstride holding
+// Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
+// 16-byte aligned in copy (N - px) mod 4 and each residual quad takes one aligned 16-byte load.
+template <int N, int CS, int MODE>
+__global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ Rall, const float *__restrict__ beam4,
+                                                           size_t cstride, const float *__restrict__ thr, float gain,
+                                                           int cap,
+                                                           int32_t *__restrict__ pos, float *__restrict__ flux,
+                                                           int32_t *__restrict__ n_comp,
+                                                           int32_t *__restrict__ status) {
+  static_assert(N * N == CS * kBandPix, "one band of 65536 pixels per block");
+  static_assert((4 * kOnT) % N == 0, "a step of kOnT quads spans whole rows");
+  extern __shared__ float4 res4[];
+  __shared__ Peak wred[2][32];
+  __shared__ Peak slot[2];
+  constexpr int ROWS = kBandPix / N;
+  constexpr int QSTEP = 4 * kOnT / N;                    // rows advanced per quad step
+  constexpr int RSTEP = kOnT / N > 0 ? kOnT / N : 1;     // rows advanced per register step (kOnT >= N)
+  static_assert(kOnT % N == 0, "a register step spans whole rows");
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int inst = blockIdx.x / CS;
+  if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {   // same decision in every block of the cluster
+    if (rank == 0 && threadIdx.x == 0) n_comp[inst] = 0;
+    return;
+  }
+  const int tid = threadIdx.x;
+  const int row0 = rank * ROWS;
+  const int g0 = row0 * N;                                  // global index of band pixel 0
+  float *Rb = Rall + (size_t)inst * N * N + g0;
+  const float *Bm = beam4 + (size_t)inst * 4 * N * N;     // copy 0: the beam itself
+  const float t = thr ? thr[inst] : -CUDART_INF_F;
+  // this thread's first quad and first register pixel: (row, column) inside the band
+  const int qr = (4 * tid) / N, qc = (4 * tid) % N;
+  const int rr = (kSmemPix + tid) / N, rc = (kSmemPix + tid) % N;
+
+  float best = MODE ? 0.f : -CUDART_INF_F;
+  int bo = -1;
+  {
+    const float4 *Rb4 = reinterpret_cast<const float4 *>(Rb);
+#pragma unroll
+    for (int i = 0; i < kQuads; i++) {
+      const float4 v = Rb4[tid + i * kOnT];
+      res4[tid + i * kOnT] = v;
+      if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
+      if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
+      if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
+      if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+    }
+  }
+  float rv[kRegPer];
+#pragma unroll
+  for (int j = 0; j < kRegPer; j++) {
+    rv[j] = Rb[kSmemPix + tid + j * kOnT];
+    if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+  }
+  auto to_peak = [&](float v, int o) {
+    Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
+    if (o >= 0) { q.key = MODE ? fabsf(v) : v; q.val = v; q.idx = g0 + band_index(o, tid); }
+    return q;
+  };
+  Peak p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, 0);
+  int it = 0, par = 1;
+  while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
+    const float f = gain * p.val;
+    if (rank == 0 && tid == 0) {
+      pos[(size_t)inst * cap + it] = p.idx;
+      flux[(size_t)inst * cap + it] = f;
+    }
+    const int py = p.idx / N, px = p.idx % N;
+    // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]
+    const int off = N - px;
+    const float *Bw = Bm + (size_t)(row0 - py + N) * (2 * N) + off;
+    const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
+    const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);   // aligned
+    const float *bg = Bw + (size_t)rr * (2 * N) + rc;      // + j * RSTEP * 2N for register j
+    best = MODE ? 0.f : -CUDART_INF_F;
+    bo = -1;
+    // Beam loads are issued a batch at a time (7 aligned 16-byte loads, plus the 8 register
+    // pixels' loads in the last batch) before any is used: two L2 round trips per iteration.
+#pragma unroll
+    for (int i0 = 0; i0 < kQuads; i0 += kBatch) {
+      constexpr bool kLastIsRegs = true;
+      const bool last = i0 + kBatch >= kQuads;
+      float4 bb[kBatch];
+      float breg[kRegPer];
+#pragma unroll
+      for (int k = 0; k < kBatch; k++) bb[k] = __ldg(bq + (i0 + k) * QSTEP * (2 * N / 4));
+      if (kLastIsRegs && last) {
+#pragma unroll
+        for (int j = 0; j < kRegPer; j++) breg[j] = __ldg(bg + j * RSTEP * 2 * N);
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; k++) {
+        const int i = i0 + k;
+        float4 v = res4[tid + i * kOnT];
+        v.x -= f * bb[k].x;
+        v.y -= f * bb[k].y;
+        v.z -= f * bb[k].z;
+        v.w -= f * bb[k].w;
+        res4[tid + i * kOnT] = v;
+        if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
+        if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
+        if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
+        if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+      }
+      if (kLastIsRegs && last) {
+#pragma unroll
+        for (int j = 0; j < kRegPer; j++) {
+          rv[j] -= f * breg[j];
+          if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+        }
+      }
+    }
+    p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
+    par ^= 1;
+    it++;
+  }
+  if (rank == 0 && tid == 0) {
+    n_comp[inst] = it;
+    if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status) atomicOr(status + inst, MUSER_ST_ITER_CAP);
+  }
+  float4 *Rw4 = reinterpret_cast<float4 *>(Rb);
+#pragma unroll
+  for (int i = 0; i < kQuads; i++) Rw4[tid + i * kOnT] = res4[tid + i * kOnT];
+#pragma unroll
+  for (int j = 0; j < kRegPer; j++) Rb[kSmemPix + tid + j * kOnT] = rv[j];
+  if constexpr (CS > 1) cg::this_cluster().sync();   // peers may still read our slots until here
+}
+
+// Launch the on-chip kernel if the device can host its clusters; false -> use the fallback.
+template <int N, int CS, int MODE>
+bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, const float *thr, float gain, int cap,
+                        int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  static int usable = -1;          // per process: the library runs on one device model
+  auto k = k_hogbom_onchip<N, CS, MODE>;
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(kOnT);
+  lc.dynamicSmemBytes = kOnSmem;
+  lc.stream = s;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  if (usable < 0) {
+    usable = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnSmem) == cudaSuccess &&
+        (CS <= 8 || cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
+      int nclusters = 0;
+      lc.gridDim = dim3(CS);
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &lc) == cudaSuccess && nclusters > 0) usable = 1;
+    }
+    cudaGetLastError();   // clear a failed query
+  }
+  if (!usable) return false;
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    lc.gridDim = dim3(n * CS);
+    cudaLaunchKernelEx(&lc, k, R + (size_t)i * N * N, beam4 + (size_t)i * 4 * N * N, cstride,
+                       thr ? thr + i : nullptr, gain, cap, pos + (size_t)i * cap, flux + (size_t)i * cap, n_comp + i,
+                       status ? status + i : nullptr);
+  }
+  return true;
+}
+
+template <int N, int CS>
+bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, const float *thr, float gain, int cap, int mode,
+                   int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  return mode ? launch_onchip_mode<N, CS, 1>(R, beam4, cstride, B, thr, gain, cap, pos, flux, n_comp, status, s)
+              : launch_onchip_mode<N, CS, 0>(R, beam4, cstride, B, thr, gain, cap, pos, flux, n_comp, status, s);
+}
+
+// dst copy k (k = first..3) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
+__global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, float *__restrict__ beam4,
+                             size_t cstride) {
+  const int W = 2 * N;
+  const size_t row = (size_t)blockIdx.y * W + blockIdx.x;    // (instance, y) flattened
+  const float *src = beam + row * W;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (k < first) continue;
+      beam4[k * cstride + row * W + x] = x + k < W ? src[x + k] : 0.f;
+    }
+  }
+}
+
 }  // namespace
 
-void launch_hogbom(float *R, const float *beam, int B, int N, const float *thr, float gain, int cap, int peak_mode,
-                   int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+int hogbom_onchip_clusters(int N) {
+  switch (N) {
+    case 256: return 1;
+    case 512: return 4;
+    case 1024: return 16;
+    default: return 0;
+  }
+}
+
+void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4, size_t cstride, cudaStream_t s) {
+  for (int i = 0; i < B; i += 32768) {
+    const int n = B - i < 32768 ? B - i : 32768;
+    k_beam_shift<<<dim3(2 * N, n), 256, 0, s>>>(beam + (size_t)i * 4 * N * N, N, first,
+                                                 beam4 + (size_t)i * 4 * N * N, cstride);
+  }
+}
+
+void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int B, int N, const float *thr,
+                   float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status,
+                   cudaStream_t s) {
+  if (B <= 0) return;
+  bool done = false;
+  if (beam4) {
+    if (N == 256) done = launch_onchip<256, 1>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (N == 512) done = launch_onchip<512, 4>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (N == 1024)
+      done = launch_onchip<1024, 16>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+  }
+  if (done) return;
+  launch_hogbom_stream(R, beam, B, N, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+}
+
+void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float *thr, float gain, int cap,
+                          int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
   if (B <= 0) return;
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;

@@ -118,19 +118,47 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
     px[k] = tx0 + (p < npx ? p % tw : 0);
     acc[k] = 0.f;
   }
+  // components whose truncated Gaussian reaches this tile: each thread tests a share of the
+  // list and appends survivors (in list order within a chunk) to shared memory
   const int nc = ok ? n_comp[inst] : 0;
+  __shared__ int nsurv;
   for (int c0 = 0; c0 < nc; c0 += 256) {
     __syncthreads();
-    if (c0 + threadIdx.x < nc) {
-      cp[threadIdx.x] = pos[(size_t)inst * cap + c0 + threadIdx.x];
-      cf[threadIdx.x] = flux[(size_t)inst * cap + c0 + threadIdx.x];
+    if (threadIdx.x == 0) nsurv = 0;
+    __syncthreads();
+    const int c = c0 + threadIdx.x;
+    bool hit = false;
+    int cpos = 0;
+    float cflux = 0.f;
+    if (c < nc) {
+      cpos = pos[(size_t)inst * cap + c];
+      cflux = flux[(size_t)inst * cap + c];
+      const int cy = cpos / N, cx = cpos % N;
+      hit = !(cx + ex < tx0 || cx - ex > tx0 + tw - 1 || cy + ey < ty0 || cy - ey > ty0 + tw - 1);
+    }
+    // order-preserving compaction: warp ballots, then a prefix over the 8 warps
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    __shared__ int wcount[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) wcount[wid] = __popc(mask);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; w++) base += wcount[w];
+    if (hit) {
+      const int slot = base + __popc(mask & ((1u << lane) - 1u));
+      cp[slot] = cpos;
+      cf[slot] = cflux;
+    }
+    if (threadIdx.x == 255) {
+      int tot = 0;
+      for (int w = 0; w < 8; w++) tot += wcount[w];
+      nsurv = tot;
     }
     __syncthreads();
-    const int m = nc - c0 < 256 ? nc - c0 : 256;
-    for (int c = 0; c < m; c++) {
-      const int cy = cp[c] / N, cx = cp[c] % N;
-      if (cx + ex < tx0 || cx - ex > tx0 + tw - 1 || cy + ey < ty0 || cy - ey > ty0 + tw - 1) continue;
-      const float f = cf[c];
+    const int m = nsurv;
+    for (int k2 = 0; k2 < m; k2++) {
+      const int cy = cp[k2] / N, cx = cp[k2] % N;
+      const float f = cf[k2];
 #pragma unroll
       for (int k = 0; k < 4; k++) {
         const float dx = (float)(px[k] - cx), dy = (float)(py[k] - cy);

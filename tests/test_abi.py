@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_record_and_config_layout():
     import paper_1712_06913_b300 as m
-    # 10 int32/float fields, a double at offset 40, batch_chunk and 7 reserved int32
+    # 10 int32/float fields, a double at offset 40, batch_chunk, clean_kernel and 6 reserved int32
     assert ctypes.sizeof(m._lib.Config) == 80
     assert m._lib.Config.lat_rad.offset == 40 and m._lib.Config.batch_chunk.offset == 48
     assert m.api.RECORD_FLOATS * 4 == 24

@@ -131,6 +131,32 @@ def test_clean_lockstep(m, name, cap):
             assert np.abs(fg[i] - fo).max() <= 1e-4 * np.abs(Do).max()
 
 
+ONCHIP_CASES = {
+    "N256x6": lambda: synth.small_workload(n_ant=31, N=256, n_frame=6, config_id=230, bmax=2000.0),
+    "N512x2": lambda: synth.config2_muser1_band(n_frame=1, chans=[10, 50]),
+    "N1024x2": lambda: synth.config3_muser2_uneven(n_frame=1, chans=[7, 400]),
+}
+
+
+@pytest.mark.parametrize("name", list(ONCHIP_CASES))
+def test_clean_onchip_equals_streaming_and_oracle(m, name):
+    """The on-chip-residual kernel (clusters of 1/4/16 blocks) performs the same FP32
+    operations as the streaming kernel: identical components; and both follow the oracle."""
+    import torch
+    wl = ONCHIP_CASES[name]()
+    cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
+    cfg.max_iter, cfg.thr_mode = 150, 0
+    R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
+    cfg.clean_kernel = 1
+    R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
+    assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
+    assert float((R1 - R2).abs().max()) == 0.0
+    pg, fg = _np(p1), _np(f1)
+    for i, (Zo, Do, Bo, _) in enumerate(ref):
+        lockstep(Do, Bo, pg[i], fg[i], cfg.gain)
+        identical_positions_unless_near_tie(Do, Bo, pg[i], cfg.gain, cfg.max_iter)
+
+
 def test_clean_threshold_and_abs_mode(m):
     wl = WORKLOADS["small-N64"]()
     cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
