@@ -89,6 +89,7 @@ struct ImageWs {
   Rec *rec;
   float2 *Z;
   float *beam, *mu_a, *mu_b, *params;
+  int *next;
   GridWs<A> g;
   DirtyWs<A> d;
   void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
@@ -97,6 +98,7 @@ struct ImageWs {
     Z = (float2 *)a.template take<float2>((size_t)Bc * c.G * c.G);
     d.carve(a, Bc, c);
     beam = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
+    next = (int *)a.template take<int>(1);
     mu_a = (float *)a.template take<float>(Bc);
     mu_b = (float *)a.template take<float>(Bc);
     params = (float *)a.template take<float>((size_t)Bc * 3);
@@ -195,7 +197,10 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_GMM: break;
     case MUSER_CALL_CLEAN:
       a.take<float>(2 * (size_t)B);
-      if (copies(*cfg)) a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
+      if (copies(*cfg)) {
+        a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
+        a.take<int>(1);
+      }
       break;
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
@@ -297,9 +302,10 @@ int muser_clean(float *residual, const float *beam, int B, const muser_config_t 
   const int N = cfg->N;
   if (copies(*cfg)) {
     float *beam4 = a.take<float>((size_t)B * 16 * N * N);
+    int *next = a.take<int>(1);
     const size_t cstride = (size_t)B * 4 * N * N;
     launch_beam_copies(beam, B, N, 0, beam4, cstride, s);
-    launch_hogbom(residual, beam, beam4, cstride, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
+    launch_hogbom(residual, beam, beam4, cstride, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
                   comp_flux, n_comp, status, s);
   } else {
     launch_hogbom_stream(residual, beam, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux,
@@ -372,7 +378,7 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     const size_t cstride = (size_t)Bc * 4 * N * N;
     if (copies(*cfg)) launch_beam_copies(w.beam, n, N, 1, w.beam, cstride, s);
     launch_hogbom(
-        R, w.beam, copies(*cfg) ? w.beam : nullptr, cstride, n, N, thr, cfg->gain, cap, cfg->peak_mode,
+        R, w.beam, copies(*cfg) ? w.beam : nullptr, cstride, w.next, n, N, thr, cfg->gain, cap, cfg->peak_mode,
         comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                   comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, st, s);
     launch_restore(R, w.beam, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,

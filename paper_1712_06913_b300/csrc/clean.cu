@@ -16,6 +16,8 @@
 // iteration k (warp shuffles, then shared memory, then the cluster).
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace muser {
@@ -208,10 +210,15 @@ __device__ __forceinline__ int band_index(int o, int tid) {
 // beam4: four copies of every instance's beam, copy k at beam4 + k * cstride holding
 // Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
 // 16-byte aligned in copy (N - px) mod 4 and each residual quad takes one aligned 16-byte load.
+//
+// Both kernels below are persistent workers drawing instances from one atomic counter
+// (`next`): the on-chip clusters and, on SMs that cannot host a whole cluster, streaming
+// blocks (launched on a second stream).  An instance is claimed by one worker, so the two
+// kernels share a batch without any other coordination.
 template <int N, int CS, int MODE>
 __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ Rall, const float *__restrict__ beam4,
-                                                           size_t cstride, const float *__restrict__ thr, float gain,
-                                                           int cap,
+                                                           size_t cstride, int B, int *__restrict__ next,
+                                                           const float *__restrict__ thr, float gain, int cap,
                                                            int32_t *__restrict__ pos, float *__restrict__ flux,
                                                            int32_t *__restrict__ n_comp,
                                                            int32_t *__restrict__ status) {
@@ -220,126 +227,269 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
   extern __shared__ float4 res4[];
   __shared__ Peak wred[2][32];
   __shared__ Peak slot[2];
+  __shared__ int claim[2], mine[2];
   constexpr int ROWS = kBandPix / N;
   constexpr int QSTEP = 4 * kOnT / N;                    // rows advanced per quad step
   constexpr int RSTEP = kOnT / N > 0 ? kOnT / N : 1;     // rows advanced per register step (kOnT >= N)
   static_assert(kOnT % N == 0, "a register step spans whole rows");
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int inst = blockIdx.x / CS;
-  if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {   // same decision in every block of the cluster
-    if (rank == 0 && threadIdx.x == 0) n_comp[inst] = 0;
-    return;
-  }
   const int tid = threadIdx.x;
   const int row0 = rank * ROWS;
   const int g0 = row0 * N;                                  // global index of band pixel 0
-  float *Rb = Rall + (size_t)inst * N * N + g0;
-  const float *Bm = beam4 + (size_t)inst * 4 * N * N;     // copy 0: the beam itself
-  const float t = thr ? thr[inst] : -CUDART_INF_F;
   // this thread's first quad and first register pixel: (row, column) inside the band
   const int qr = (4 * tid) / N, qc = (4 * tid) % N;
   const int rr = (kSmemPix + tid) / N, rc = (kSmemPix + tid) % N;
-
-  float best = MODE ? 0.f : -CUDART_INF_F;
-  int bo = -1;
-  {
-    const float4 *Rb4 = reinterpret_cast<const float4 *>(Rb);
-#pragma unroll
-    for (int i = 0; i < kQuads; i++) {
-      const float4 v = Rb4[tid + i * kOnT];
-      res4[tid + i * kOnT] = v;
-      if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
-      if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
-      if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
-      if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
-    }
-  }
-  float rv[kRegPer];
-#pragma unroll
-  for (int j = 0; j < kRegPer; j++) {
-    rv[j] = Rb[kSmemPix + tid + j * kOnT];
-    if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
-  }
   auto to_peak = [&](float v, int o) {
     Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
     if (o >= 0) { q.key = MODE ? fabsf(v) : v; q.val = v; q.idx = g0 + band_index(o, tid); }
     return q;
   };
-  Peak p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, 0);
-  int it = 0, par = 1;
-  while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
-    const float f = gain * p.val;
-    if (rank == 0 && tid == 0) {
-      pos[(size_t)inst * cap + it] = p.idx;
-      flux[(size_t)inst * cap + it] = f;
+  int par = 0, cpar = 0;
+  for (;;) {
+    // claim the next instance: rank 0 takes it, every block of the cluster reads it
+    if (rank == 0 && tid == 0) claim[cpar] = atomicAdd(next, 1);
+    if constexpr (CS > 1) {
+      cg::cluster_group cluster = cg::this_cluster();
+      cluster.sync();
+      if (tid == 0) mine[cpar] = *cluster.map_shared_rank(claim + cpar, 0);
+    } else {
+      if (tid == 0) mine[cpar] = claim[cpar];
     }
-    const int py = p.idx / N, px = p.idx % N;
-    // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]
-    const int off = N - px;
-    const float *Bw = Bm + (size_t)(row0 - py + N) * (2 * N) + off;
-    const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
-    const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);   // aligned
-    const float *bg = Bw + (size_t)rr * (2 * N) + rc;      // + j * RSTEP * 2N for register j
-    best = MODE ? 0.f : -CUDART_INF_F;
-    bo = -1;
-    // Beam loads are issued a batch at a time (7 aligned 16-byte loads, plus the 8 register
-    // pixels' loads in the last batch) before any is used: two L2 round trips per iteration.
+    __syncthreads();
+    const int inst = mine[cpar];
+    cpar ^= 1;
+    if (inst >= B) break;                                   // same value in every block of the cluster
+    if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {   // same decision in every block of the cluster
+      if (rank == 0 && tid == 0) n_comp[inst] = 0;
+      continue;
+    }
+    float *Rb = Rall + (size_t)inst * N * N + g0;
+    const float *Bm = beam4 + (size_t)inst * 4 * N * N;     // copy 0: the beam itself
+    const float t = thr ? thr[inst] : -CUDART_INF_F;
+
+    float best = MODE ? 0.f : -CUDART_INF_F;
+    int bo = -1;
+    {
+      const float4 *Rb4 = reinterpret_cast<const float4 *>(Rb);
 #pragma unroll
-    for (int i0 = 0; i0 < kQuads; i0 += kBatch) {
-      constexpr bool kLastIsRegs = true;
-      const bool last = i0 + kBatch >= kQuads;
-      float4 bb[kBatch];
-      float breg[kRegPer];
-#pragma unroll
-      for (int k = 0; k < kBatch; k++) bb[k] = __ldg(bq + (i0 + k) * QSTEP * (2 * N / 4));
-      if (kLastIsRegs && last) {
-#pragma unroll
-        for (int j = 0; j < kRegPer; j++) breg[j] = __ldg(bg + j * RSTEP * 2 * N);
-      }
-#pragma unroll
-      for (int k = 0; k < kBatch; k++) {
-        const int i = i0 + k;
-        float4 v = res4[tid + i * kOnT];
-        v.x -= f * bb[k].x;
-        v.y -= f * bb[k].y;
-        v.z -= f * bb[k].z;
-        v.w -= f * bb[k].w;
+      for (int i = 0; i < kQuads; i++) {
+        const float4 v = Rb4[tid + i * kOnT];
         res4[tid + i * kOnT] = v;
         if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
         if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
         if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
         if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
       }
-      if (kLastIsRegs && last) {
+    }
+    float rv[kRegPer];
 #pragma unroll
-        for (int j = 0; j < kRegPer; j++) {
-          rv[j] -= f * breg[j];
-          if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+    for (int j = 0; j < kRegPer; j++) {
+      rv[j] = Rb[kSmemPix + tid + j * kOnT];
+      if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+    }
+    Peak p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
+    par ^= 1;
+    int it = 0;
+    while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
+      const float f = gain * p.val;
+      if (rank == 0 && tid == 0) {
+        pos[(size_t)inst * cap + it] = p.idx;
+        flux[(size_t)inst * cap + it] = f;
+      }
+      const int py = p.idx / N, px = p.idx % N;
+      // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]
+      const int off = N - px;
+      const float *Bw = Bm + (size_t)(row0 - py + N) * (2 * N) + off;
+      const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
+      const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);   // aligned
+      const float *bg = Bw + (size_t)rr * (2 * N) + rc;      // + j * RSTEP * 2N for register j
+      best = MODE ? 0.f : -CUDART_INF_F;
+      bo = -1;
+      // Beam loads are issued a batch at a time (7 aligned 16-byte loads, plus the 8 register
+      // pixels' loads in the last batch) before any is used: two L2 round trips per iteration.
+#pragma unroll
+      for (int i0 = 0; i0 < kQuads; i0 += kBatch) {
+        const bool last = i0 + kBatch >= kQuads;
+        float4 bb[kBatch];
+        float breg[kRegPer];
+#pragma unroll
+        for (int k = 0; k < kBatch; k++) bb[k] = __ldg(bq + (i0 + k) * QSTEP * (2 * N / 4));
+        if (last) {
+#pragma unroll
+          for (int j = 0; j < kRegPer; j++) breg[j] = __ldg(bg + j * RSTEP * 2 * N);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; k++) {
+          const int i = i0 + k;
+          float4 v = res4[tid + i * kOnT];
+          v.x -= f * bb[k].x;
+          v.y -= f * bb[k].y;
+          v.z -= f * bb[k].z;
+          v.w -= f * bb[k].w;
+          res4[tid + i * kOnT] = v;
+          if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
+          if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
+          if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
+          if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+        }
+        if (last) {
+#pragma unroll
+          for (int j = 0; j < kRegPer; j++) {
+            rv[j] -= f * breg[j];
+            if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+          }
         }
       }
+      p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
+      par ^= 1;
+      it++;
     }
-    p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
-    par ^= 1;
-    it++;
-  }
-  if (rank == 0 && tid == 0) {
-    n_comp[inst] = it;
-    if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status) atomicOr(status + inst, MUSER_ST_ITER_CAP);
-  }
-  float4 *Rw4 = reinterpret_cast<float4 *>(Rb);
+    if (rank == 0 && tid == 0) {
+      n_comp[inst] = it;
+      if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
+        atomicOr(status + inst, MUSER_ST_ITER_CAP);
+    }
+    float4 *Rw4 = reinterpret_cast<float4 *>(Rb);
 #pragma unroll
-  for (int i = 0; i < kQuads; i++) Rw4[tid + i * kOnT] = res4[tid + i * kOnT];
+    for (int i = 0; i < kQuads; i++) Rw4[tid + i * kOnT] = res4[tid + i * kOnT];
 #pragma unroll
-  for (int j = 0; j < kRegPer; j++) Rb[kSmemPix + tid + j * kOnT] = rv[j];
+    for (int j = 0; j < kRegPer; j++) Rb[kSmemPix + tid + j * kOnT] = rv[j];
+  }
   if constexpr (CS > 1) cg::this_cluster().sync();   // peers may still read our slots until here
 }
 
-// Launch the on-chip kernel if the device can host its clusters; false -> use the fallback.
+// Streaming worker on SMs that cannot host a whole cluster: block w images instance
+// first + w with the residual in global memory, in batches of 4 quads (4 residual + 4 aligned
+// beam 16-byte loads in flight per thread).  One instance per block, assigned statically:
+// a streaming instance takes far longer than a cluster's, so only as many are given out as
+// the clusters' share of the batch can hide.
+constexpr int kSqBatch = 4;
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__ Rall, const float *__restrict__ beam4,
+                                                             size_t cstride, int first,
+                                                             const float *__restrict__ thr, float gain, int cap,
+                                                             int32_t *__restrict__ pos, float *__restrict__ flux,
+                                                             int32_t *__restrict__ n_comp,
+                                                             int32_t *__restrict__ status) {
+  constexpr int NQT = N * N / 4 / kOnT;                   // quads per thread
+  constexpr int QSTEP = 4 * kOnT / N;                     // rows advanced per quad step
+  static_assert(NQT % kSqBatch == 0 && (4 * kOnT) % N == 0, "whole batches of whole rows");
+  __shared__ Peak wred[2][32];
+  const int tid = threadIdx.x;
+  const int qr = (4 * tid) / N, qc = (4 * tid) % N;
+  int par = 0;
+  {
+    const int inst = first + blockIdx.x;
+    if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {
+      if (tid == 0) n_comp[inst] = 0;
+      return;
+    }
+    float4 *R4 = reinterpret_cast<float4 *>(Rall + (size_t)inst * N * N);
+    const float *Bm = beam4 + (size_t)inst * 4 * N * N;
+    const float t = thr ? thr[inst] : -CUDART_INF_F;
+    auto to_peak = [&](float v, int o) {
+      Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
+      if (o >= 0) { q.key = MODE ? fabsf(v) : v; q.val = v; q.idx = 4 * (tid + (o >> 2) * kOnT) + (o & 3); }
+      return q;
+    };
+    float best = MODE ? 0.f : -CUDART_INF_F;
+    int bo = -1;
+    for (int i = 0; i < NQT; i++) {
+      const float4 v = R4[tid + i * kOnT];
+      if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
+      if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
+      if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
+      if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+    }
+    Peak p = cluster_argmax<1>(to_peak(best, bo), wred, nullptr, par);
+    par ^= 1;
+    int it = 0;
+    while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
+      const float f = gain * p.val;
+      if (tid == 0) {
+        pos[(size_t)inst * cap + it] = p.idx;
+        flux[(size_t)inst * cap + it] = f;
+      }
+      const int py = p.idx / N, px = p.idx % N;
+      const int off = N - px;
+      const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(N - py) * (2 * N) + (off & ~3);
+      const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
+      best = MODE ? 0.f : -CUDART_INF_F;
+      bo = -1;
+#pragma unroll 1
+      for (int i0 = 0; i0 < NQT; i0 += kSqBatch) {
+        float4 rr[kSqBatch], bb[kSqBatch];
+#pragma unroll
+        for (int k = 0; k < kSqBatch; k++) {
+          rr[k] = R4[tid + (i0 + k) * kOnT];
+          bb[k] = __ldg(bq + (size_t)(i0 + k) * QSTEP * (2 * N / 4));
+        }
+#pragma unroll
+        for (int k = 0; k < kSqBatch; k++) {
+          const int i = i0 + k;
+          float4 v = rr[k];
+          v.x -= f * bb[k].x;
+          v.y -= f * bb[k].y;
+          v.z -= f * bb[k].z;
+          v.w -= f * bb[k].w;
+          R4[tid + i * kOnT] = v;
+          if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
+          if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
+          if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
+          if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+        }
+      }
+      p = cluster_argmax<1>(to_peak(best, bo), wred, nullptr, par);
+      par ^= 1;
+      it++;
+    }
+    if (tid == 0) {
+      n_comp[inst] = it;
+      if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
+        atomicOr(status + inst, MUSER_ST_ITER_CAP);
+    }
+  }
+}
+
+struct OnchipPlan {
+  int usable = -1;       // -1 not yet queried, 0 cannot run, 1 can run
+  int clusters = 0;      // resident clusters of the on-chip kernel
+  int leftover = 0;      // SMs that cannot host a whole cluster
+};
+
+// Second stream and fork/join events per device, for the streaming workers.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+SideStream *side_stream() {
+  static std::mutex mu;
+  static SideStream tab[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  SideStream &x = tab[dev];
+  if (!x.s) {
+    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      x.s = nullptr;
+      return nullptr;
+    }
+  }
+  return &x;
+}
+
+// Launch the queue workers if the device can host the on-chip clusters; false -> fallback.
 template <int N, int CS, int MODE>
-bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, const float *thr, float gain, int cap,
-                        int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
-  static int usable = -1;          // per process: the library runs on one device model
+bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
+                        int cap, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  static OnchipPlan plan;          // per process: the library runs on one device model
   auto k = k_hogbom_onchip<N, CS, MODE>;
+  auto ks = k_hogbom_stream_q<N, MODE>;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -351,32 +501,49 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, con
   lc.stream = s;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  if (usable < 0) {
-    usable = 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnSmem) == cudaSuccess &&
+  if (plan.usable < 0) {
+    plan.usable = 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnSmem) == cudaSuccess &&
         (CS <= 8 || cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
       int nclusters = 0;
       lc.gridDim = dim3(CS);
-      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &lc) == cudaSuccess && nclusters > 0) usable = 1;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &lc) == cudaSuccess && nclusters > 0) {
+        plan.usable = 1;
+        plan.clusters = nclusters;
+        plan.leftover = sms - nclusters * CS;
+      }
     }
     cudaGetLastError();   // clear a failed query
   }
-  if (!usable) return false;
-  for (int i = 0; i < B; i += 65535) {
-    const int n = B - i < 65535 ? B - i : 65535;
-    lc.gridDim = dim3(n * CS);
-    cudaLaunchKernelEx(&lc, k, R + (size_t)i * N * N, beam4 + (size_t)i * 4 * N * N, cstride,
-                       thr ? thr + i : nullptr, gain, cap, pos + (size_t)i * cap, flux + (size_t)i * cap, n_comp + i,
-                       status ? status + i : nullptr);
+  if (!plan.usable) return false;
+  // Streaming workers (one instance each, the last ns of the batch) only when the clusters'
+  // share is at least 24 waves, long enough to hide a streaming instance.
+  const int ns = (plan.leftover > 0 && B - plan.leftover >= 24 * plan.clusters) ? plan.leftover : 0;
+  const int Bc = B - ns;
+  const int nc = plan.clusters < Bc ? plan.clusters : Bc;
+  cudaMemsetAsync(next, 0, sizeof(int), s);
+  // Clusters first (they need whole GPCs), then the streaming workers on the SMs left over.
+  SideStream *side = ns > 0 ? side_stream() : nullptr;
+  if (ns > 0 && !side) return false;
+  if (side) cudaEventRecord(side->fork, s);
+  lc.gridDim = dim3(nc * CS);
+  cudaLaunchKernelEx(&lc, k, R, beam4, cstride, Bc, next, thr, gain, cap, pos, flux, n_comp, status);
+  if (side) {
+    cudaStreamWaitEvent(side->s, side->fork, 0);
+    ks<<<ns, kOnT, 0, side->s>>>(R, beam4, cstride, Bc, thr, gain, cap, pos, flux, n_comp, status);
+    cudaEventRecord(side->join, side->s);
+    cudaStreamWaitEvent(s, side->join, 0);
   }
   return true;
 }
 
 template <int N, int CS>
-bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, const float *thr, float gain, int cap, int mode,
-                   int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
-  return mode ? launch_onchip_mode<N, CS, 1>(R, beam4, cstride, B, thr, gain, cap, pos, flux, n_comp, status, s)
-              : launch_onchip_mode<N, CS, 0>(R, beam4, cstride, B, thr, gain, cap, pos, flux, n_comp, status, s);
+bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
+                   int cap, int mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  return mode ? launch_onchip_mode<N, CS, 1>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s)
+              : launch_onchip_mode<N, CS, 0>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
 }
 
 // dst copy k (k = first..3) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
@@ -413,16 +580,18 @@ void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4
   }
 }
 
-void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int B, int N, const float *thr,
-                   float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status,
-                   cudaStream_t s) {
+void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int *next, int B, int N,
+                   const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp,
+                   int32_t *status, cudaStream_t s) {
   if (B <= 0) return;
   bool done = false;
-  if (beam4) {
-    if (N == 256) done = launch_onchip<256, 1>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
-    if (N == 512) done = launch_onchip<512, 4>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+  if (beam4 && next) {
+    if (N == 256)
+      done = launch_onchip<256, 1>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (N == 512)
+      done = launch_onchip<512, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 1024)
-      done = launch_onchip<1024, 16>(R, beam4, cstride, B, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<1024, 16>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
   }
   if (done) return;
   launch_hogbom_stream(R, beam, B, N, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);

@@ -116,9 +116,11 @@ void launch_twiddles(float2 *tw, int L, cudaStream_t s);   // tw[m] = exp(+2 pi 
 // CLEAN: on-chip residual kernel for N = 256, 512, 1024 when beam4 (four column-shifted beam
 // copies, copy k at beam4 + k * cstride, built by launch_beam_copies) is given and the device can
 // host it; otherwise the streaming kernel on `beam`.  launch_hogbom_stream forces streaming.
-void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int B, int N, const float *thr,
-                   float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status,
-                   cudaStream_t s);
+// `next` is a device int the launch resets: the on-chip clusters (and, on SMs that cannot host a
+// whole cluster, streaming workers on a second stream) claim instances from it.
+void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int *next, int B, int N,
+                   const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp,
+                   int32_t *status, cudaStream_t s);
 // copies k = first..3 of beam [B][2N][2N] into beam4 (copy 0 at beam4 is written only if first == 0)
 void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4, size_t cstride, cudaStream_t s);
 inline bool clean_uses_copies(int N) { return N == 256 || N == 512 || N == 1024; }
