@@ -184,7 +184,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid"], default=None,
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad"], default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     args = ap.parse_args()
@@ -312,7 +312,7 @@ def main():
     achieved = statistics.mean(clean_bytes) / (clean_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     tr = recorded_traffic()
-    roofline = {"kernel": "k_hogbom (muser_clean)", "bound": "hbm", "achieved": achieved, "peak": peak,
+    roofline = {"kernel": "k_hogbom_onchip + k_hogbom_stream_q (muser_clean)", "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "bytes_per_launch": statistics.mean(clean_bytes),
                 "launch_ms": clean_ms,
@@ -352,6 +352,8 @@ def main():
 def run_case(case, n_inst=0):
     """Small cases of the benchmark workload, a few GB on the device, for profiler captures.
 
+    grad:  10 eager gradient-descent steps of the 512^2 differentiable-imaging workload.
+
     clean: 148 instances (one block per SM) of the MUSER-II batch, CLEAN with 100 iterations.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
@@ -359,6 +361,21 @@ def run_case(case, n_inst=0):
     import torch
     import paper_1712_06913_b300 as m
     import synth
+    if case == "grad":
+        import numpy as np
+        from paper_1712_06913_b300.autograd import GradientImaging
+        w4 = synth.config4_operator()
+        cfg4 = m.Config(N=w4.N, G=w4.G, lat_rad=w4.lat)
+        cell4 = np.full(w4.n_chan, 60 * synth.ARCMIN / w4.N)
+        rec, _, _ = m.uvw(w4.ant_enu, w4.pairs, w4.ha, w4.dec, w4.freq, cell4, w4.vis, cfg4, flags=w4.flags)
+        obs = torch.tensor(w4.vis.reshape(-1), dtype=torch.complex64, device="cuda")
+        gd = GradientImaging(rec, obs, float(np.sqrt(np.mean(np.abs(w4.vis) ** 2)) / 30.0), cfg4, eta=1e-9)
+        t0 = time.perf_counter()
+        for _ in range(10):
+            gd.step()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "steps": 10, "s": time.perf_counter() - t0}))
+        return
     n_inst = n_inst or (148 if case == "clean" else 8)
     wl = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst)))
     cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=100, gain=wl.gain, lat_rad=wl.lat)
@@ -401,7 +418,7 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     import numpy as np
     import torch
     import synth
-    from paper_1712_06913_b300.autograd import chi2_loss
+    from paper_1712_06913_b300.autograd import GradientImaging
     res = {}
     n_plain = 16
     cfg1 = m.Config(**{**cfg.__dict__, "batch_chunk": 0})
@@ -424,26 +441,24 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     rec, _, _ = m.uvw(w4.ant_enu, w4.pairs, w4.ha, w4.dec, w4.freq, cell4, w4.vis, cfg4, flags=w4.flags)
     obs = torch.tensor(w4.vis.reshape(-1), dtype=torch.complex64, device="cuda")
     sigma2 = float(np.mean(np.abs(w4.vis) ** 2)) / 900.0
-    x = torch.zeros((w4.N, w4.N), dtype=torch.float32, device="cuda", requires_grad=True)
-    for _ in range(5):
-        loss = chi2_loss(x, rec, obs, 1.0 / sigma2, cfg4)
-        loss.backward()
-    torch.cuda.synchronize()
+    gd = GradientImaging(rec, obs, math.sqrt(sigma2), cfg4)
+    gd.capture()                      # eta = 1/L from 20 power iterations, then one step in a graph
     steps = 100
+    torch.cuda.synchronize()
     e0.record(stream)
-    with torch.no_grad():
-        pass
-    lr = 1e-12
-    for _ in range(steps):
-        x.grad = None
-        loss = chi2_loss(x, rec, obs, 1.0 / sigma2, cfg4)
-        loss.backward()
-        with torch.no_grad():
-            x -= lr * x.grad
+    gd.replay(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     res["grad_evals_per_s"] = steps / (e0.elapsed_time(e1) / 1e3)
-    res["grad_eval_workload"] = "512^2 sky, 780 baselines x 64 channels (49,920 visibilities), G=1024"
+    res["grad_eval_workload"] = ("512^2 sky, 780 baselines x 64 channels (49,920 visibilities), G=1024; one "
+                                 "evaluation = forward + chi2 + adjoint + update, replayed from a CUDA graph")
+    # eager (no graph) for comparison
+    e0.record(stream)
+    for _ in range(20):
+        gd.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["grad_evals_per_s_eager"] = 20 / (e0.elapsed_time(e1) / 1e3)
     return res
 
 

@@ -62,7 +62,7 @@ enum {
   MUSER_ST_BEAM_FIT = 32        /* the beam main lobe did not fit the fitting window */
 };
 
-enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1 };
+enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
 
 enum {
   MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
@@ -211,7 +211,12 @@ MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pa
  *            zero-padded img / (gc gc); vis = 0 for records with w = 0.  img read, vis written.
  *  ADJOINT:  img = Re (1/K^2) (1/(gc gc)) crop_N( centred inverse DFT( grid of vis ) ), the
  *            exact adjoint of FORWARD restricted to real images.  vis read, img written.
- * K = integral of the kernel.  rec[n_vis] from muser_uvw with the same cfg. */
+ * K = integral of the kernel.  rec[n_vis] from muser_uvw with the same cfg.
+ * A call without MUSER_REUSE_PLAN plans: it writes the kernel table, grid correction,
+ * twiddles and the adjoint's sorted tile lists into ws.  OR-ing MUSER_REUSE_PLAN into
+ * `direction` skips that work and uses ws as left by an earlier call with the same rec,
+ * n_vis and cfg (ws must not have been used for anything else in between): the uv
+ * coverage is fixed during iterative imaging, only img / vis change. */
 MUSER_API int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,
                  const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream);
 

@@ -11,7 +11,7 @@ from . import _build
 
 MUSER_OK, MUSER_ERR_ARG, MUSER_ERR_CUDA, MUSER_ERR_TIMEOUT, MUSER_ERR_UNSUPPORTED, MUSER_ERR_WORKSPACE = range(6)
 ST_ALL_FLAGGED, ST_NONFINITE, ST_DROPPED, ST_GMM_DEGENERATE, ST_ITER_CAP, ST_BEAM_FIT = 1, 2, 4, 8, 16, 32
-FORWARD, ADJOINT = 0, 1
+FORWARD, ADJOINT, REUSE_PLAN = 0, 1, 4
 CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2 = range(1, 9)
 
 _ERRNAMES = {1: "MUSER_ERR_ARG", 2: "MUSER_ERR_CUDA", 3: "MUSER_ERR_TIMEOUT", 4: "MUSER_ERR_UNSUPPORTED",

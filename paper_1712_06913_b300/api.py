@@ -253,20 +253,49 @@ def image(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm
     return dataclasses.replace(o, comp_pos=o.comp_pos[:, :cap], comp_flux=o.comp_flux[:, :cap])
 
 
-def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None):
-    """FORWARD: img [N, N] f32 -> vis [n] complex64.  ADJOINT: vis -> img (real part of A^H vis)."""
+def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None, reuse_plan=False):
+    """FORWARD: img [N, N] f32 -> vis [n] complex64.  ADJOINT: vis -> img (real part of A^H vis).
+
+    reuse_plan: `ws` already holds this record set's plan from an earlier call (see DegridPlan).
+    """
     n = rec.shape[0]
     c = cfg.c()
     w, wb = (ws or _default_ws).get(workspace_size(CALL_DEGRID, 1, n, cfg))
+    flag = _lib.REUSE_PLAN if reuse_plan else 0
     if direction == _lib.FORWARD:
         img = img.contiguous()
         out = torch.empty(n, dtype=torch.complex64, device="cuda")
-        check(_lib.load().muser_degrid(0, _p(img), _p(rec), n, _p(out), ctypes.byref(c), w, wb, _stream()))
+        check(_lib.load().muser_degrid(_lib.FORWARD | flag, _p(img), _p(rec), n, _p(out), ctypes.byref(c), w, wb,
+                                       _stream()))
         return out
     vis = vis.contiguous()
     out = torch.empty((cfg.N, cfg.N), dtype=torch.float32, device="cuda")
-    check(_lib.load().muser_degrid(1, _p(out), _p(rec), n, _p(vis), ctypes.byref(c), w, wb, _stream()))
+    check(_lib.load().muser_degrid(_lib.ADJOINT | flag, _p(out), _p(rec), n, _p(vis), ctypes.byref(c), w, wb,
+                                   _stream()))
     return out
+
+
+class DegridPlan:
+    """The measurement operator of one record set (fixed uv coverage) with its own workspace.
+
+    The first call plans (kernel table, grid correction, twiddles, the adjoint's sorted tile
+    lists); later calls reuse the plan and only run the transforms.
+    """
+
+    def __init__(self, rec, cfg: Config):
+        self.rec, self.cfg = rec, cfg
+        self.ws = Workspace()
+        self.planned = False
+
+    def forward(self, img):
+        out = degrid(_lib.FORWARD, self.rec, self.cfg, img=img, ws=self.ws, reuse_plan=self.planned)
+        self.planned = True
+        return out
+
+    def adjoint(self, vis):
+        out = degrid(_lib.ADJOINT, self.rec, self.cfg, vis=vis, ws=self.ws, reuse_plan=self.planned)
+        self.planned = True
+        return out
 
 
 def chi2(pred, obs, rec, inv_sigma2: float, want_resid=True, ws: Workspace = None):

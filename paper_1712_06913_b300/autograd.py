@@ -15,17 +15,16 @@ from ._lib import ADJOINT, FORWARD
 
 
 class Degrid(torch.autograd.Function):
+    """vis = A img with a DegridPlan; backward applies the plan's adjoint."""
+
     @staticmethod
-    def forward(ctx, img, rec, cfg):
-        ctx.save_for_backward(rec)
-        ctx.cfg = cfg
-        return api.degrid(FORWARD, rec, cfg, img=img.detach())
+    def forward(ctx, img, plan):
+        ctx.plan = plan
+        return plan.forward(img.detach())
 
     @staticmethod
     def backward(ctx, grad_vis):
-        (rec,) = ctx.saved_tensors
-        g = api.degrid(ADJOINT, rec, ctx.cfg, vis=grad_vis.contiguous())
-        return g, None, None
+        return ctx.plan.adjoint(grad_vis.contiguous()), None
 
 
 class Chi2(torch.autograd.Function):
@@ -41,6 +40,73 @@ class Chi2(torch.autograd.Function):
         return resid * grad_loss, None, None, None
 
 
-def chi2_loss(img, rec, obs, inv_sigma2, cfg):
-    """chi2(img) through both autograd functions."""
-    return Chi2.apply(Degrid.apply(img, rec, cfg), obs, rec, inv_sigma2)
+def chi2_loss(img, plan, obs, inv_sigma2):
+    """chi2(img) through both autograd functions (plan: api.DegridPlan of the records)."""
+    return Chi2.apply(Degrid.apply(img, plan), obs, plan.rec, inv_sigma2)
+
+
+class GradientImaging:
+    """Gradient-descent imaging of one sky image from visibilities (chi-square data term).
+
+    Each step evaluates chi2 and its gradient through Degrid/Chi2 (forward operator,
+    chi-square seed and adjoint are library kernels) and applies x <- x - eta * grad.
+    `capture()` records one step in a CUDA graph so that `replay()` runs it without host
+    work; the image, loss and gradient live in fixed device tensors.
+    """
+
+    def __init__(self, rec, obs, sigma, cfg, x0=None, eta=None):
+        import torch
+        self.rec, self.cfg = rec, cfg
+        self.plan = api.DegridPlan(rec, cfg)
+        self.obs = obs.to(torch.complex64).contiguous()
+        self.inv_s2 = 1.0 / float(sigma) ** 2
+        self.x = (torch.zeros((cfg.N, cfg.N), dtype=torch.float32, device="cuda") if x0 is None
+                  else x0.detach().clone().float()).requires_grad_(True)
+        self.eta = eta
+        self.loss = None
+        self.graph = None
+
+    def lipschitz(self, iters=20, seed=0):
+        """Largest eigenvalue of the chi2 Hessian 2 Re(A^H W A)/sigma^2 by power iteration."""
+        import torch
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        v = torch.randn((self.cfg.N, self.cfg.N), generator=g, device="cuda")
+        v /= torch.linalg.norm(v)
+        lam = 0.0
+        for _ in range(iters):
+            y = self.plan.forward(v)
+            u = self.plan.adjoint(y) * (2.0 * self.inv_s2)
+            lam = float(torch.linalg.norm(u))
+            v = u / lam
+        return lam
+
+    def step(self):
+        import torch
+        self.x.grad = None
+        loss = chi2_loss(self.x, self.plan, self.obs, self.inv_s2)
+        loss.backward()
+        with torch.no_grad():
+            self.x -= self.eta * self.x.grad
+        self.loss = loss.detach()
+        return self.loss
+
+    def capture(self, warmup=3):
+        """Record one step in a CUDA graph (after `warmup` eager steps on a side stream)."""
+        import torch
+        if self.eta is None:
+            self.eta = 1.0 / self.lipschitz()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.static_loss = self.step()
+        return self
+
+    def replay(self, n=1):
+        for _ in range(n):
+            self.graph.replay()
+        return self.static_loss

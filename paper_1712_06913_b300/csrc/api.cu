@@ -66,7 +66,7 @@ struct GridWs {
     const int rows = grid_band_rows(c.G), nb = c.G / rows;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (nb + 1));
-    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) * grid_bands_per_sample(c.W, rows));
+    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) * tiles_per_sample(c.W, rows, c.G, c.G));
   }
 };
 
@@ -108,17 +108,25 @@ struct ImageWs {
 template <class A>
 struct DegridWs {
   float *tab, *gc;
-  float2 *tw, *T, *X;
-  int32_t *bin_off, *entries;
+  float2 *tw, *T, *X, *partial;
+  int32_t *bin_off, *entries, *tile_item0;
+  int4 *items;
+  int nb, max_items;
   void carve(A &a, int64_t n_vis, const muser_config_t &c) {
-    const int G = c.G, rows = grid_band_rows(G), nb = G / rows;
+    const int G = c.G, t = adjoint_tile(G);
+    nb = (G / t) * (G / t);
+    const int64_t n_entries = n_vis * tiles_per_sample(c.W, t, t, G);
+    max_items = grid_max_items(n_entries, nb);
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     gc = (float *)a.template take<float>(G);
     tw = (float2 *)a.template take<float2>(G);
     T = (float2 *)a.template take<float2>((size_t)(G / 2) * G);
     X = (float2 *)a.template take<float2>((size_t)G * G);
     bin_off = (int32_t *)a.template take<int32_t>(nb + 1);
-    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * grid_bands_per_sample(c.W, rows));
+    entries = (int32_t *)a.template take<int32_t>((size_t)n_entries);
+    tile_item0 = (int32_t *)a.template take<int32_t>(nb + 1);
+    items = (int4 *)a.template take<int4>(max_items);
+    partial = (float2 *)a.template take<float2>((size_t)max_items * t * t);
   }
 };
 
@@ -244,8 +252,9 @@ int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int
   w.carve(a, B, n_vis_total, *cfg, true);
   cudaStream_t s = (cudaStream_t)stream;
   launch_pswf_table(w.tab, cfg->W, cfg->os, nullptr, 0, s);
-  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, cfg->W, cfg->os, w.tab, true, nullptr, (float2 *)Z, w.bin_off,
-              w.entries, status, s);
+  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, cfg->W, cfg->os, w.tab, true, nullptr, grid_band_rows(cfg->G),
+              cfg->G, (float2 *)Z, w.bin_off,
+              w.entries, status, false, s);
   return check_launch("muser_grid");
 }
 
@@ -364,8 +373,8 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     float *R = residual + (size_t)c0 * N * N;
     launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, c0, n, G,
                cfg->W, cfg->lat_rad, w.rec, nullptr, status, s);
-    launch_grid(w.rec, nullptr, n_bl, n, G, cfg->W, cfg->os, w.g.tab, true, nullptr, w.Z, w.g.bin_off, w.g.entries, st,
-                s);
+    launch_grid(w.rec, nullptr, n_bl, n, G, cfg->W, cfg->os, w.g.tab, true, nullptr, grid_band_rows(G), G, w.Z,
+                w.g.bin_off, w.g.entries, st, false, s);
     launch_dirty(w.Z, n, N, G, w.d.tw, w.d.gc, w.d.T, w.d.partial, R, w.beam, st, s);
     const float *thr = nullptr;
     if (cfg->thr_mode == 1) {
@@ -392,7 +401,9 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
 int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,
                  const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream) {
   MUSER_TRY(check_cfg(cfg, DEGRID));
-  if (direction != MUSER_FORWARD && direction != MUSER_ADJOINT) return fail(MUSER_ERR_ARG, "direction");
+  const bool reuse = (direction & MUSER_REUSE_PLAN) != 0;
+  const int dir = direction & ~MUSER_REUSE_PLAN;
+  if (dir != MUSER_FORWARD && dir != MUSER_ADJOINT) return fail(MUSER_ERR_ARG, "direction");
   if (n_vis < 0) return fail(MUSER_ERR_ARG, "negative sizes");
   if (n_vis >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "at most 2^30 records per call");
   if (!img || (n_vis > 0 && (!rec || !vis))) return fail(MUSER_ERR_ARG, "muser_degrid: required pointer is NULL");
@@ -405,14 +416,20 @@ int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64
   cudaStream_t s = (cudaStream_t)stream;
   const Pswf &P = pswf_coefficients(cfg->W);
   const float K2 = (float)(P.K * P.K);
-  launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
-  fft::launch_twiddles(w.tw, cfg->G, s);
-  if (direction == MUSER_FORWARD)
+  if (!reuse) {           // plan: kernel table, grid correction, twiddles and the adjoint's tile lists
+    launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
+    fft::launch_twiddles(w.tw, cfg->G, s);
+    const int t = adjoint_tile(cfg->G);
+    launch_grid_sort((const Rec *)rec, nullptr, n_vis, 1, cfg->G, cfg->W, false, t, t, w.bin_off, w.entries,
+                     nullptr, s);
+    launch_grid_items_plan(w.bin_off, w.nb, w.items, w.tile_item0, s);
+  }
+  if (dir == MUSER_FORWARD)
     launch_degrid_forward(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T,
                           w.X, (float2 *)vis, s);
   else
     launch_degrid_adjoint((const float2 *)vis, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw,
-                          w.gc, K2, w.bin_off, w.entries, w.X, w.T, img, s);
+                          w.gc, K2, w.entries, w.items, w.tile_item0, w.max_items, w.partial, w.X, w.T, img, s);
   return check_launch("muser_degrid");
 }
 

@@ -242,9 +242,10 @@ void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int 
 }
 
 void launch_degrid_adjoint(const float2 *vis, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                           const float *tab, const float2 *tw, const float *gc, float K2, int32_t *bin_off,
-                           int32_t *entries, float2 *Z, float2 *T, float *img, cudaStream_t s) {
-  launch_grid(rec, nullptr, n_vis, 1, G, W, os, tab, false, vis, Z, bin_off, entries, nullptr, s);
+                           const float *tab, const float2 *tw, const float *gc, float K2, const int32_t *entries,
+                           const int4 *items, const int32_t *tile_item0, int max_items, float2 *partial, float2 *Z,
+                           float2 *T, float *img, cudaStream_t s) {
+  launch_grid_items(rec, G, W, os, tab, vis, adjoint_tile(G), entries, items, tile_item0, max_items, partial, Z, s);
   switch (G) {
 #define MUSER_CASE(g) \
   case g: adjoint_G<g>(Z, tw, gc, K2, T, img, s); break;

@@ -1,13 +1,16 @@
 // Convolutional gridding with sorted visibilities and shared-memory band tiles
 // (Sec. 3.2.3; Alg. 1 "calculating the weight and gridding").
 //
+// The grid is cut into tiles of tr rows x tc columns (the imaging path uses full-width
+// bands, tc = G; the degridding adjoint, whose records crowd the uv centre, uses 32 x 32
+// tiles so that the crowded region is spread over many blocks).
 // Step 1 (k_bin_sort, one block per instance): every kept record contributes one or two
 // samples (+uv, and the Hermitian mirror -uv when `mirror`); a sample's W x W footprint
-// spans at most grid_bands_per_sample() bands of `rows` grid rows.  A counting sort in
-// shared memory places (record, sign) codes into per-band lists.
-// Step 2 (k_grid_band, one block per (band, instance)): the block zeroes its rows x G band
-// in shared memory, accumulates every footprint tap of its list there, and writes the
-// band to HBM once with 16-byte stores.  No global atomics; the shared-memory float
+// touches at most tiles_per_sample() tiles.  A counting sort in shared memory places
+// (record, sign) codes into per-tile lists.
+// Step 2 (k_grid_tile, one block per (tile, instance)): the block zeroes its tile in shared
+// memory, accumulates every footprint tap of its list there, and writes the tile to HBM
+// once with coalesced 16-byte stores.  No global atomics; the shared-memory float
 // additions of overlapping footprints run in no fixed order (last-bit differences only).
 #include "common.cuh"
 
@@ -28,6 +31,16 @@ constexpr int kSortThreads = 512;
 __device__ __forceinline__ void band_range(int center, int h, int rows, int &b0, int &b1) {
   b0 = (center - h) / rows;
   b1 = (center + h) / rows;
+}
+
+// Apply f(tile) to every tile touched by the footprint of one sample (centre cell kv, ku).
+template <class F>
+__device__ __forceinline__ void for_tiles(int kv, int ku, int h, int tr, int tc, int ntc, F &&f) {
+  int r0, r1, c0, c1;
+  band_range(kv, h, tr, r0, r1);
+  band_range(ku, h, tc, c0, c1);
+  for (int r = r0; r <= r1; r++)
+    for (int c = c0; c <= c1; c++) f(r * ntc + c);
 }
 
 // Exclusive scan of a[0..n) in shared memory (n arbitrary), block of kSortThreads threads.
@@ -65,11 +78,12 @@ __device__ void block_exclusive_scan(int *a, int n, int *warp_tot) {
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_bin_sort(const Rec *__restrict__ rec, const int64_t *__restrict__ vis_off,
-                                                           int64_t stride, int G, int W, int rows, int mirror,
+                                                           int64_t stride, int G, int W, int tr, int tc, int mirror,
                                                            int32_t *__restrict__ bin_off, int32_t *__restrict__ entries,
                                                            int32_t *__restrict__ status) {
   extern __shared__ int sh[];
-  const int nb = G / rows;
+  const int ntc = G / tc;
+  const int nb = (G / tr) * ntc;
   int *cnt = sh;              // nb + 1
   int *cur = sh + nb + 1;     // nb
   int *wt = cur + nb;         // 32
@@ -80,7 +94,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bin_sort(const Rec *__restrict
   const int n = (int)(r1 - r0);
   const int h = (W - 1) / 2;
   const int nsgn = mirror ? 2 : 1;
-  const int64_t base = r0 * nsgn * grid_bands_per_sample(W, rows);
+  const int64_t base = r0 * nsgn * tiles_per_sample(W, tr, tc, G);
   for (int i = threadIdx.x; i <= nb; i += blockDim.x) cnt[i] = 0;
   if (threadIdx.x == 0) kept_sh = 0;
   __syncthreads();
@@ -89,11 +103,8 @@ __global__ void __launch_bounds__(kSortThreads) k_bin_sort(const Rec *__restrict
     const Rec R = rec[r0 + i];
     if (!record_ok(R, G, h)) continue;      // weight 0 or cells outside the grid: not gridded
     kept++;
-    for (int sg = 0; sg < nsgn; sg++) {
-      int b0, b1;
-      band_range(sg ? G - R.kv : R.kv, h, rows, b0, b1);
-      for (int b = b0; b <= b1; b++) atomicAdd(&cnt[b], 1);
-    }
+    for (int sg = 0; sg < nsgn; sg++)
+      for_tiles(sg ? G - R.kv : R.kv, sg ? G - R.ku : R.ku, h, tr, tc, ntc, [&](int b) { atomicAdd(&cnt[b], 1); });
   }
   if (kept) atomicAdd(&kept_sh, kept);
   __syncthreads();
@@ -105,37 +116,36 @@ __global__ void __launch_bounds__(kSortThreads) k_bin_sort(const Rec *__restrict
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const Rec R = rec[r0 + i];
     if (!record_ok(R, G, h)) continue;
-    for (int sg = 0; sg < nsgn; sg++) {
-      int b0, b1;
-      band_range(sg ? G - R.kv : R.kv, h, rows, b0, b1);
-      for (int b = b0; b <= b1; b++) {
-        int p = atomicAdd(&cur[b], 1);
+    for (int sg = 0; sg < nsgn; sg++)
+      for_tiles(sg ? G - R.kv : R.kv, sg ? G - R.ku : R.ku, h, tr, tc, ntc, [&](int b) {
+        const int p = atomicAdd(&cur[b], 1);
         entries[base + p] = (i << 1) | sg;
-      }
-    }
+      });
   }
   if (threadIdx.x == 0 && kept_sh == 0 && status) atomicOr(status + inst, MUSER_ST_ALL_FLAGGED);
 }
 
-__global__ void __launch_bounds__(256) k_grid_band(const Rec *__restrict__ rec, const int64_t *__restrict__ vis_off,
-                                                   int64_t stride, int inst0, int G, int W, int rows,
+__global__ void __launch_bounds__(256) k_grid_tile(const Rec *__restrict__ rec, const int64_t *__restrict__ vis_off,
+                                                   int64_t stride, int inst0, int G, int W, int tr, int tc,
                                                    const float *__restrict__ tab, int ntab, float os, int mirror,
                                                    const float2 *__restrict__ vals, const int32_t *__restrict__ bin_off,
                                                    const int32_t *__restrict__ entries, float2 *__restrict__ Z) {
   extern __shared__ float4 tile4[];
   float2 *tile = reinterpret_cast<float2 *>(tile4);
-  const int nb = G / rows;
-  const int band = blockIdx.x, inst = inst0 + blockIdx.y;
-  const int n4 = rows * G / 2;                   // float4 count of the band
+  const int ntc = G / tc;
+  const int nb = (G / tr) * ntc;
+  const int b = blockIdx.x, inst = inst0 + blockIdx.y;
+  const int row0 = (b / ntc) * tr, col0 = (b % ntc) * tc;
+  const int n4 = tr * tc / 2;                    // float4 count of the tile
   for (int i = threadIdx.x; i < n4; i += blockDim.x) tile4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   const int64_t r0 = vis_off ? vis_off[inst] : (int64_t)inst * stride;
   const int nsgn = mirror ? 2 : 1;
-  const int64_t base = r0 * nsgn * grid_bands_per_sample(W, rows);
+  const int64_t base = r0 * nsgn * tiles_per_sample(W, tr, tc, G);
   const int32_t *off = bin_off + (size_t)inst * (nb + 1);
-  const int e0 = off[band], e1 = off[band + 1];
-  const int row0 = band * rows;
+  const int e0 = off[b], e1 = off[b + 1];
   const int h = (W - 1) / 2, WW = W * W;
+  // one warp per list entry, its W x W taps spread over the lanes (lists are short here)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int e = e0 + warp; e < e1; e += nwarp) {
     const int code = entries[base + e];
@@ -150,39 +160,169 @@ __global__ void __launch_bounds__(256) k_grid_band(const Rec *__restrict__ rec, 
     for (int tap = lane; tap < WW; tap += 32) {
       const int tv = tap / W - h, tu = tap % W - h;
       const int row = sg ? G - R.kv - tv : R.kv + tv;
-      if (row < row0 || row >= row0 + rows) continue;
       const int col = sg ? G - R.ku - tu : R.ku + tu;
+      if (row < row0 || row >= row0 + tr || col < col0 || col >= col0 + tc) continue;
       const float c = kernel_lookup(tab, ntab, os, (float)tu + R.fu) * kernel_lookup(tab, ntab, os, (float)tv + R.fv);
-      float2 *cell = tile + (row - row0) * G + col;
+      float2 *cell = tile + (row - row0) * tc + (col - col0);
       atomicAdd(&cell->x, c * val.x);
       atomicAdd(&cell->y, c * val.y);
     }
   }
   __syncthreads();
-  float4 *dst = reinterpret_cast<float4 *>(Z + ((size_t)inst * G + row0) * G);
+  float2 *dst = Z + ((size_t)inst * G + row0) * G + col0;
+  if (tc == G) {                                  // full-width band: one contiguous block of Z
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = tile4[i];
+  } else {                                        // tile rows are G complex values apart
+    const int q4 = tc / 2;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+      const int r = i / q4, c = i - r * q4;
+      reinterpret_cast<float4 *>(dst + (size_t)r * G)[c] = tile4[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- crowded tiles (one instance)
+// The degridding adjoint grids one record set whose short baselines, at every channel, land
+// within a few cells of the uv centre: thousands of samples hit the same cells.  Its tile
+// lists are cut into work items of at most kItem entries; each item accumulates a private
+// partial tile in shared memory, and the partial tiles of a tile are summed in item order.
+constexpr int kItem = 256;
+
+// One block: items per tile = max(1, ceil(count / kItem)), their prefix, the item table.
+__global__ void __launch_bounds__(kSortThreads) k_make_items(const int32_t *__restrict__ bin_off, int nb,
+                                                             int4 *__restrict__ items, int32_t *__restrict__ tile_item0) {
+  extern __shared__ int sh[];
+  int *ni = sh;               // nb + 1
+  int *wt = sh + nb + 1;      // 32
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int c = bin_off[t + 1] - bin_off[t];
+    ni[t] = c > kItem ? (c + kItem - 1) / kItem : 1;
+  }
+  if (threadIdx.x == 0) ni[nb] = 0;
+  __syncthreads();
+  block_exclusive_scan(ni, nb + 1, wt);
+  for (int t = threadIdx.x; t <= nb; t += blockDim.x) tile_item0[t] = ni[t];
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int e0 = bin_off[t], e1 = bin_off[t + 1];
+    for (int j = ni[t], e = e0; j < ni[t + 1]; j++, e += kItem)
+      items[j] = make_int4(t, e, e + kItem < e1 ? e + kItem : e1, 0);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grid_items(const Rec *__restrict__ rec, int G, int W, int tr, int tc,
+                                                    const float *__restrict__ tab, int ntab, float os,
+                                                    const float2 *__restrict__ vals, const int32_t *__restrict__ entries,
+                                                    const int4 *__restrict__ items, const int32_t *__restrict__ tile_item0,
+                                                    int nb, float2 *__restrict__ partial) {
+  extern __shared__ float4 tile4[];
+  float2 *tile = reinterpret_cast<float2 *>(tile4);
+  const int j = blockIdx.x;
+  if (j >= tile_item0[nb]) return;                 // fewer items than the launch bound
+  const int4 it = items[j];
+  const int ntc = G / tc;
+  const int row0 = (it.x / ntc) * tr, col0 = (it.x % ntc) * tc;
+  const int n4 = tr * tc / 2;
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) tile4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const int h = (W - 1) / 2;
+  for (int e = it.y + (int)threadIdx.x; e < it.z; e += blockDim.x) {
+    const int i = entries[e] >> 1;                 // adjoint: +uv samples only
+    const Rec R = rec[i];
+    const float2 val = vals[i];
+    float cu[9];
+#pragma unroll
+    for (int t = 0; t < 9; t++) cu[t] = t < W ? kernel_lookup(tab, ntab, os, (float)(t - h) + R.fu) : 0.f;
+#pragma unroll
+    for (int a = 0; a < 9; a++) {
+      if (a >= W) break;
+      const int row = R.kv + a - h;
+      if (row < row0 || row >= row0 + tr) continue;
+      const float cv = kernel_lookup(tab, ntab, os, (float)(a - h) + R.fv);
+      const float2 cvv = make_float2(cv * val.x, cv * val.y);
+      float2 *trow = tile + (row - row0) * tc;
+#pragma unroll
+      for (int b = 0; b < 9; b++) {
+        if (b >= W) break;
+        const int col = R.ku + b - h;
+        if (col < col0 || col >= col0 + tc) continue;
+        atomicAdd(&trow[col - col0].x, cu[b] * cvv.x);
+        atomicAdd(&trow[col - col0].y, cu[b] * cvv.y);
+      }
+    }
+  }
+  __syncthreads();
+  float4 *dst = reinterpret_cast<float4 *>(partial + (size_t)j * tr * tc);
   for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = tile4[i];
+}
+
+// Z tile t = sum of its items' partial tiles, in item order.
+__global__ void __launch_bounds__(256) k_grid_combine(const float2 *__restrict__ partial,
+                                                      const int32_t *__restrict__ tile_item0, int G, int tr, int tc,
+                                                      float2 *__restrict__ Z) {
+  const int t = blockIdx.x, ntc = G / tc;
+  const int row0 = (t / ntc) * tr, col0 = (t % ntc) * tc;
+  const int j0 = tile_item0[t], j1 = tile_item0[t + 1];
+  const int n4 = tr * tc / 2, q4 = tc / 2;
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+    float4 acc = reinterpret_cast<const float4 *>(partial + (size_t)j0 * tr * tc)[i];
+    for (int j = j0 + 1; j < j1; j++) {
+      const float4 v = reinterpret_cast<const float4 *>(partial + (size_t)j * tr * tc)[i];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+    }
+    const int r = i / q4, c = i - r * q4;
+    reinterpret_cast<float4 *>(Z + (size_t)(row0 + r) * G + col0)[c] = acc;
+  }
 }
 
 }  // namespace
 
-void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
-                 const float *tab, bool mirror, const float2 *vals, float2 *Z, int32_t *bin_off, int32_t *entries,
-                 int32_t *status, cudaStream_t s) {
+void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, bool mirror,
+                      int tr, int tc, int32_t *bin_off, int32_t *entries, int32_t *status, cudaStream_t s) {
   if (B <= 0) return;
-  const int rows = grid_band_rows(G);
-  const int nb = G / rows;
+  const int nb = (G / tr) * (G / tc);
   size_t sort_smem = (size_t)(2 * nb + 1 + 32) * sizeof(int);
   if (sort_smem > 48 * 1024) cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
-  k_bin_sort<<<B, kSortThreads, sort_smem, s>>>(rec, vis_off, dense_stride, G, W, rows, mirror ? 1 : 0, bin_off,
+  k_bin_sort<<<B, kSortThreads, sort_smem, s>>>(rec, vis_off, dense_stride, G, W, tr, tc, mirror ? 1 : 0, bin_off,
                                                 entries, status);
-  size_t tile_smem = (size_t)rows * G * sizeof(float2);
-  cudaFuncSetAttribute(k_grid_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+}
+
+void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
+                 const float *tab, bool mirror, const float2 *vals, int tr, int tc, float2 *Z, int32_t *bin_off,
+                 int32_t *entries, int32_t *status, bool sorted, cudaStream_t s) {
+  if (B <= 0) return;
+  const int nb = (G / tr) * (G / tc);
+  if (!sorted) launch_grid_sort(rec, vis_off, dense_stride, B, G, W, mirror, tr, tc, bin_off, entries, status, s);
+  size_t tile_smem = (size_t)tr * tc * sizeof(float2);
+  cudaFuncSetAttribute(k_grid_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
   for (int i = 0; i < B; i += 65535) {
     int n = B - i < 65535 ? B - i : 65535;
     dim3 grid(nb, n);
-    k_grid_band<<<grid, 256, tile_smem, s>>>(rec, vis_off, dense_stride, i, G, W, rows, tab, table_len(W, os),
+    k_grid_tile<<<grid, 256, tile_smem, s>>>(rec, vis_off, dense_stride, i, G, W, tr, tc, tab, table_len(W, os),
                                              (float)os, mirror ? 1 : 0, vals, bin_off, entries, Z);
   }
+}
+
+}  // namespace muser
+
+namespace muser {
+
+int grid_max_items(int64_t n_entries, int nb) { return nb + (int)((n_entries + kItem - 1) / kItem); }
+
+void launch_grid_items_plan(const int32_t *bin_off, int nb, int4 *items, int32_t *tile_item0, cudaStream_t s) {
+  const size_t smem = (size_t)(nb + 1 + 32) * sizeof(int);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_make_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_make_items<<<1, kSortThreads, smem, s>>>(bin_off, nb, items, tile_item0);
+}
+
+void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, const float2 *vals, int t,
+                       const int32_t *entries, const int4 *items, const int32_t *tile_item0, int max_items,
+                       float2 *partial, float2 *Z, cudaStream_t s) {
+  const int nb = (G / t) * (G / t);
+  const size_t smem = (size_t)t * t * sizeof(float2);
+  k_grid_items<<<max_items, 256, smem, s>>>(rec, G, W, t, t, tab, table_len(W, os), (float)os, vals, entries, items,
+                                           tile_item0, nb, partial);
+  k_grid_combine<<<nb, 256, 0, s>>>(partial, tile_item0, G, t, t, Z);
 }
 
 }  // namespace muser
