@@ -242,10 +242,12 @@ def main():
     clocks.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
+    launches0 = m.launch_count()
     ev[0].record(stream)
     for k in range(args.steps):
         imager.run()
         ev[k + 1].record(stream)
+    launches1 = m.launch_count()
     barrier()
     clk = clocks.stop()
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
@@ -254,8 +256,7 @@ def main():
     out = imager.out
     n_comp = out.n_comp.cpu().numpy()
     status = out.status.cpu().numpy()
-    n_chunks = math.ceil(B / args.chunk)
-    gpu_launches = args.steps * (2 + 9 * n_chunks)   # tables + (uvw, sort, grid, cols, rows, thr, clean, fit, restore)
+    gpu_launches = launches1 - launches0   # counted by the library as it enqueues its kernels
 
     # ---- end to end: pinned host visibilities in, CLEAN model out, every step
     vis_host = torch.from_numpy(np.ascontiguousarray(vis.astype(np.complex64))).pin_memory()

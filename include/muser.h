@@ -59,7 +59,9 @@ enum {
   MUSER_ST_DROPPED = 4,         /* a visibility fell outside the uv grid and was dropped */
   MUSER_ST_GMM_DEGENERATE = 8,  /* a mixture component has weight < 1e-4 */
   MUSER_ST_ITER_CAP = 16,       /* CLEAN stopped at max_iter with the peak still above thr */
-  MUSER_ST_BEAM_FIT = 32        /* the beam main lobe did not fit the fitting window */
+  MUSER_ST_BEAM_FIT = 32,       /* the beam main lobe did not fit the fitting window */
+  MUSER_ST_TIMEOUT = 64         /* a bounded wait inside the CLEAN kernel ran out (about 2 s); the
+                                   instance's CLEAN outputs are invalid.  Not expected to occur. */
 };
 
 enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
@@ -101,6 +103,12 @@ typedef struct muser_vis_record {
 
 MUSER_API const char *muser_version(void);
 MUSER_API const char *muser_last_error(void);
+
+/* Diagnostics, no counterpart in the paper: the number of kernels this library has
+ * enqueued from the host since it was loaded (all threads, all devices).  Launches
+ * replayed from a captured CUDA graph are not enqueued by the library and are not
+ * counted.  Never fails. */
+MUSER_API unsigned long long muser_launch_count(void);
 
 /* Pixel size rule (host only).  Sec. 3.2.1 / Table 2: three pixels per resolution
  * element lambda / B_max; reading for a fixed image side: never smaller than

@@ -10,7 +10,7 @@ import os
 from . import _build
 
 MUSER_OK, MUSER_ERR_ARG, MUSER_ERR_CUDA, MUSER_ERR_TIMEOUT, MUSER_ERR_UNSUPPORTED, MUSER_ERR_WORKSPACE = range(6)
-ST_ALL_FLAGGED, ST_NONFINITE, ST_DROPPED, ST_GMM_DEGENERATE, ST_ITER_CAP, ST_BEAM_FIT = 1, 2, 4, 8, 16, 32
+ST_ALL_FLAGGED, ST_NONFINITE, ST_DROPPED, ST_GMM_DEGENERATE, ST_ITER_CAP, ST_BEAM_FIT, ST_TIMEOUT = 1, 2, 4, 8, 16, 32, 64
 FORWARD, ADJOINT, REUSE_PLAN = 0, 1, 4
 CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2 = range(1, 9)
 
@@ -39,6 +39,7 @@ CFG = ctypes.POINTER(Config)
 SIGNATURES = {
     "muser_version": (ctypes.c_char_p, []),
     "muser_last_error": (ctypes.c_char_p, []),
+    "muser_launch_count": (ctypes.c_ulonglong, []),
     "muser_pixel_size": (I32, [P, I32, ctypes.c_double, I32, ctypes.c_double, P]),
     "muser_workspace_size": (SZ, [I32, I32, I64, CFG]),
     "muser_uvw": (I32, [P, I32, P, I32, P, P, I32, P, P, I32, P, P, P, CFG, P, P, P, P]),

@@ -86,6 +86,11 @@ class Workspace:
 _default_ws = Workspace()
 
 
+def launch_count() -> int:
+    """Kernels the library has enqueued from the host so far (graph replays not included)."""
+    return int(_lib.load().muser_launch_count())
+
+
 def pixel_size(freq_hz, bmax_m, N, fov_min_rad):
     """Host rule of Table 2 (three pixels per resolution element, floored at fov_min / N)."""
     f = np.ascontiguousarray(freq_hz, dtype=np.float64)

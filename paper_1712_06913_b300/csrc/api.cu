@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include <cstdio>
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -12,6 +13,9 @@
 namespace muser {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -179,6 +183,8 @@ extern "C" {
 const char *muser_version(void) { return "muser-b300 0.1 (sm_103a)"; }
 
 const char *muser_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long muser_launch_count(void) { return muser::g_launches.load(std::memory_order_relaxed); }
 
 int muser_pixel_size(const double *freq_hz, int n_chan, double bmax_m, int N, double fov_min_rad,
                      double *cell_rad_out) {
@@ -380,9 +386,13 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     if (cfg->thr_mode == 1) {
       launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a, w.mu_b, st, s);
       thr = w.mu_a;
-      if (thr_out) k_copy<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, w.mu_a, n);
+      if (thr_out) {
+        k_copy<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, w.mu_a, n);
+        note_launch();
+      }
     } else if (thr_out) {
       k_fill<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, n, -INFINITY);
+      note_launch();
     }
     const size_t cstride = (size_t)Bc * 4 * N * N;
     if (copies(*cfg)) launch_beam_copies(w.beam, n, N, 1, w.beam, cstride, s);

@@ -148,48 +148,125 @@ constexpr size_t kOnSmem = sizeof(float) * kSmemPix;
 constexpr int kBatch = 7;                            // quads whose beam loads are in flight together
 static_assert(kSmemPix / 4 % (kBatch * kOnT) == 0, "quads divide into whole batches");
 
-__device__ __forceinline__ void warp_argmax(Peak &p) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    float k = __shfl_xor_sync(0xffffffffu, p.key, o);
-    float v = __shfl_xor_sync(0xffffffffu, p.val, o);
-    int i = __shfl_xor_sync(0xffffffffu, p.idx, o);
-    if (better(k, i, p.key, p.idx)) { p.key = k; p.val = v; p.idx = i; }
-  }
+// ---- packed peaks: one 64-bit word per candidate, compared as an unsigned integer.
+// hi = order-preserving key (MODE 0: the float's bits mapped so that unsigned order equals
+// float order; MODE 1: the bits of |v|); lo = (0x3fffffff - idx) << 1 | sign(v), so that equal
+// keys go to the lowest index.  0 is "no candidate" (it loses to every real candidate).
+template <int MODE>
+__device__ __forceinline__ uint2 pack_peak(float v, int idx) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned hi = MODE ? (u & 0x7fffffffu) : ((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+  return make_uint2(hi, ((0x3fffffffu - (unsigned)idx) << 1) | (MODE ? (u >> 31) : 0u));
 }
 
-// Argmax over the whole cluster (CS blocks); every thread of every block gets the result:
-// warp results go to wred[par], warp 0 writes the block winner to slot[par], reads the CS
-// winners through distributed shared memory after the cluster barrier and broadcasts the
-// result through shared memory.  wred and slot alternate with `par`, so a buffer is only
-// rewritten after one more barrier, when every reader is done with it.
+template <int MODE>
+__device__ __forceinline__ Peak unpack_peak(uint2 w) {
+  Peak p;
+  if (w.x == 0u && w.y == 0u) return Peak{-CUDART_INF_F, 0.f, 0x7fffffff};
+  const unsigned u = MODE ? (w.x | (w.y << 31)) : ((w.x & 0x80000000u) ? (w.x & 0x7fffffffu) : ~w.x);
+  p.val = __uint_as_float(u);
+  p.key = MODE ? fabsf(p.val) : p.val;
+  p.idx = (int)(0x3fffffffu - (w.y >> 1));
+  return p;
+}
+
+// Warp maximum of packed peaks (two redux.sync steps: the key, then the index among equals).
+__device__ __forceinline__ uint2 warp_max_packed(uint2 w) {
+  const unsigned m = __reduce_max_sync(0xffffffffu, w.x);
+  const unsigned l = __reduce_max_sync(0xffffffffu, w.x == m ? w.y : 0u);
+  return make_uint2(m, l);
+}
+
+// Bound on one mbarrier wait (SM clock cycles, about 2 s): a wait that runs out marks the
+// instance MUSER_ST_TIMEOUT and the cluster stops imaging instead of hanging.
+constexpr long long kWaitCycles = 1ll << 32;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// One arrival that also announces `bytes` of incoming st.async data for the current phase.
+__device__ __forceinline__ void mbar_arm(uint64_t *bar, unsigned bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Store 8 bytes into a peer block's shared memory; completion is counted on the peer's mbarrier.
+__device__ __forceinline__ void st_async_peer(uint32_t dst, uint2 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.u32 [%0], {%1, %2}, [%3];" ::"r"(dst),
+               "r"(v.x), "r"(v.y), "r"(bar)
+               : "memory");
+}
+
+// Shared state of the cluster argmax exchange (one per block).
 template <int CS>
-__device__ __forceinline__ Peak cluster_argmax(Peak p, Peak (*wred)[32], Peak *slot, int par) {
-  __shared__ Peak gpk;
-  warp_argmax(p);
+struct Exchange {
+  uint2 wred[2][32];       // warp winners, alternating buffers
+  uint2 slot[2][CS];       // block winners pushed by the CS blocks of the cluster
+  uint64_t bar[2];         // completion of slot[par]: CS x 8 bytes per phase
+  uint2 win;               // cluster winner, broadcast to the block
+  int abort;               // sticky: a wait ran out
+};
+
+// Argmax over the cluster, every thread of every block gets the result.  Each block reduces
+// its candidates (redux.sync in every warp, then in warp 0) and pushes the block winner into
+// slot[par][rank] of every block of the cluster with st.async; warp 0 waits on its own
+// mbarrier for the CS words, reduces them and broadcasts through shared memory.  Exchange k
+// uses buffers par = k & 1 and mbarrier phase parity (k >> 1) & 1; a block rewrites a peer's
+// slot[par] only after that peer has pushed exchange k+1, i.e. after it finished reading
+// exchange k, so the double buffer needs no other barrier.
+template <int CS, int MODE>
+__device__ __forceinline__ Peak cluster_argmax(uint2 w, Exchange<CS> &x, int k) {
+  const int par = k & 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) wred[par][wid] = p;
+  w = warp_max_packed(w);
+  if (lane == 0) x.wred[par][wid] = w;
   __syncthreads();
   if (wid == 0) {
-    Peak q = wred[par][lane];
-    warp_argmax(q);
-    if (lane == 0) {
-      if (CS > 1) slot[par] = q;
-      else gpk = q;
-    }
-  }
-  if constexpr (CS > 1) {
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster.sync();
-    if (wid == 0) {
-      Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
-      if (lane < CS) q = *cluster.map_shared_rank(slot + par, lane);
-      warp_argmax(q);
-      if (lane == 0) gpk = q;
+    w = warp_max_packed(x.wred[par][lane]);
+    if constexpr (CS == 1) {
+      if (lane == 0) x.win = w;
+    } else {
+      if (lane < CS) {
+        const int me = (int)cg::this_cluster().block_rank();
+        st_async_peer(peer_addr(smem_addr(&x.slot[par][me]), lane), w, peer_addr(smem_addr(&x.bar[par]), lane));
+      }
+      bool done = false;
+      if (lane == 0) {
+        const long long t0 = clock64();
+        while (!(done = mbar_try_wait(&x.bar[par], (unsigned)(k >> 1) & 1u)))
+          if (clock64() - t0 > kWaitCycles) break;
+        if (done) mbar_arm(&x.bar[par], CS * 8u);   // next use of this buffer: exchange k + 2
+        else x.abort = 1;
+      }
+      __syncwarp();
+      const uint2 q = lane < CS ? x.slot[par][lane] : make_uint2(0u, 0u);
+      w = warp_max_packed(q);
+      if (lane == 0) x.win = w;
     }
   }
   __syncthreads();
-  return gpk;
+  return unpack_peak<MODE>(x.win);
 }
 
 // Pixels of thread t in its block's band: quads q = t + i kOnT (i < kQuads) in shared
@@ -225,9 +302,8 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
   static_assert(N * N == CS * kBandPix, "one band of 65536 pixels per block");
   static_assert((4 * kOnT) % N == 0, "a step of kOnT quads spans whole rows");
   extern __shared__ float4 res4[];
-  __shared__ Peak wred[2][32];
-  __shared__ Peak slot[2];
-  __shared__ int claim[2], mine[2];
+  __shared__ Exchange<CS> xch;
+  __shared__ int claim[2], mine[2], stop_flag[2], any_abort[2];
   constexpr int ROWS = kBandPix / N;
   constexpr int QSTEP = 4 * kOnT / N;                    // rows advanced per quad step
   constexpr int RSTEP = kOnT / N > 0 ? kOnT / N : 1;     // rows advanced per register step (kOnT >= N)
@@ -239,28 +315,50 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
   // this thread's first quad and first register pixel: (row, column) inside the band
   const int qr = (4 * tid) / N, qc = (4 * tid) % N;
   const int rr = (kSmemPix + tid) / N, rc = (kSmemPix + tid) % N;
-  auto to_peak = [&](float v, int o) {
-    Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
-    if (o >= 0) { q.key = MODE ? fabsf(v) : v; q.val = v; q.idx = g0 + band_index(o, tid); }
-    return q;
-  };
-  int par = 0, cpar = 0;
+  auto packed = [&](float v, int o) { return o >= 0 ? pack_peak<MODE>(v, g0 + band_index(o, tid)) : make_uint2(0u, 0u); };
+  if (tid == 0) {
+    xch.abort = 0;
+    if constexpr (CS > 1) {
+      mbar_init(&xch.bar[0], 1);
+      mbar_init(&xch.bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mbar_arm(&xch.bar[0], CS * 8u);
+      mbar_arm(&xch.bar[1], CS * 8u);
+    }
+  }
+  int xk = 0, cpar = 0;                                     // exchanges so far; claim buffer
   for (;;) {
-    // claim the next instance: rank 0 takes it, every block of the cluster reads it
+    // claim the next instance: rank 0 takes it, every block of the cluster reads it together
+    // with every block's abort flag (all blocks then take the same decisions)
     if (rank == 0 && tid == 0) claim[cpar] = atomicAdd(next, 1);
+    if (tid == 0) stop_flag[cpar] = xch.abort;
     if constexpr (CS > 1) {
       cg::cluster_group cluster = cg::this_cluster();
       cluster.sync();
-      if (tid == 0) mine[cpar] = *cluster.map_shared_rank(claim + cpar, 0);
+      if (tid < 32) {
+        const int f = tid < CS ? *cluster.map_shared_rank(stop_flag + cpar, tid) : 0;
+        const unsigned any = __ballot_sync(0xffffffffu, f != 0);
+        if (tid == 0) {
+          mine[cpar] = *cluster.map_shared_rank(claim + cpar, 0);
+          any_abort[cpar] = any != 0u;
+        }
+      }
     } else {
-      if (tid == 0) mine[cpar] = claim[cpar];
+      if (tid == 0) {
+        mine[cpar] = claim[cpar];
+        any_abort[cpar] = stop_flag[cpar];
+      }
     }
     __syncthreads();
     const int inst = mine[cpar];
+    const bool aborted = any_abort[cpar] != 0;
     cpar ^= 1;
     if (inst >= B) break;                                   // same value in every block of the cluster
-    if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {   // same decision in every block of the cluster
-      if (rank == 0 && tid == 0) n_comp[inst] = 0;
+    if (aborted || (status && (status[inst] & MUSER_ST_ALL_FLAGGED))) {   // same decision in every block
+      if (rank == 0 && tid == 0) {
+        n_comp[inst] = 0;
+        if (aborted && status) atomicOr(status + inst, MUSER_ST_TIMEOUT);
+      }
       continue;
     }
     float *Rb = Rall + (size_t)inst * N * N + g0;
@@ -287,10 +385,9 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       rv[j] = Rb[kSmemPix + tid + j * kOnT];
       if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
     }
-    Peak p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
-    par ^= 1;
+    Peak p = cluster_argmax<CS, MODE>(packed(best, bo), xch, xk++);
     int it = 0;
-    while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
+    while (!xch.abort && it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
       const float f = gain * p.val;
       if (rank == 0 && tid == 0) {
         pos[(size_t)inst * cap + it] = p.idx;
@@ -340,10 +437,10 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
           }
         }
       }
-      p = cluster_argmax<CS>(to_peak(best, bo), wred, slot, par);
-      par ^= 1;
+      p = cluster_argmax<CS, MODE>(packed(best, bo), xch, xk++);
       it++;
     }
+    if (xch.abort && tid == 0 && status) atomicOr(status + inst, MUSER_ST_TIMEOUT);
     if (rank == 0 && tid == 0) {
       n_comp[inst] = it;
       if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
@@ -355,7 +452,11 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
 #pragma unroll
     for (int j = 0; j < kRegPer; j++) Rb[kSmemPix + tid + j * kOnT] = rv[j];
   }
-  if constexpr (CS > 1) cg::this_cluster().sync();   // peers may still read our slots until here
+  if constexpr (CS > 1) {
+    // after a wait that ran out, give stores still in flight towards this block time to land
+    if (xch.abort) __nanosleep(100000);
+    cg::this_cluster().sync();   // peers may still read our claim and flags until here
+  }
 }
 
 // Streaming worker on SMs that cannot host a whole cluster: block w images instance
@@ -375,10 +476,10 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
   constexpr int NQT = N * N / 4 / kOnT;                   // quads per thread
   constexpr int QSTEP = 4 * kOnT / N;                     // rows advanced per quad step
   static_assert(NQT % kSqBatch == 0 && (4 * kOnT) % N == 0, "whole batches of whole rows");
-  __shared__ Peak wred[2][32];
+  __shared__ Exchange<1> xch;
   const int tid = threadIdx.x;
   const int qr = (4 * tid) / N, qc = (4 * tid) % N;
-  int par = 0;
+  int xk = 0;
   {
     const int inst = first + blockIdx.x;
     if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {
@@ -388,10 +489,8 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
     float4 *R4 = reinterpret_cast<float4 *>(Rall + (size_t)inst * N * N);
     const float *Bm = beam4 + (size_t)inst * 4 * N * N;
     const float t = thr ? thr[inst] : -CUDART_INF_F;
-    auto to_peak = [&](float v, int o) {
-      Peak q{-CUDART_INF_F, 0.f, 0x7fffffff};
-      if (o >= 0) { q.key = MODE ? fabsf(v) : v; q.val = v; q.idx = 4 * (tid + (o >> 2) * kOnT) + (o & 3); }
-      return q;
+    auto packed = [&](float v, int o) {
+      return o >= 0 ? pack_peak<MODE>(v, 4 * (tid + (o >> 2) * kOnT) + (o & 3)) : make_uint2(0u, 0u);
     };
     float best = MODE ? 0.f : -CUDART_INF_F;
     int bo = -1;
@@ -402,8 +501,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
       if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
       if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
     }
-    Peak p = cluster_argmax<1>(to_peak(best, bo), wred, nullptr, par);
-    par ^= 1;
+    Peak p = cluster_argmax<1, MODE>(packed(best, bo), xch, xk++);
     int it = 0;
     while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
       const float f = gain * p.val;
@@ -440,8 +538,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
           if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
         }
       }
-      p = cluster_argmax<1>(to_peak(best, bo), wred, nullptr, par);
-      par ^= 1;
+      p = cluster_argmax<1, MODE>(packed(best, bo), xch, xk++);
       it++;
     }
     if (tid == 0) {
@@ -530,9 +627,11 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   if (side) cudaEventRecord(side->fork, s);
   lc.gridDim = dim3(nc * CS);
   cudaLaunchKernelEx(&lc, k, R, beam4, cstride, Bc, next, thr, gain, cap, pos, flux, n_comp, status);
+  note_launch();
   if (side) {
     cudaStreamWaitEvent(side->s, side->fork, 0);
     ks<<<ns, kOnT, 0, side->s>>>(R, beam4, cstride, Bc, thr, gain, cap, pos, flux, n_comp, status);
+    note_launch();
     cudaEventRecord(side->join, side->s);
     cudaStreamWaitEvent(s, side->join, 0);
   }
@@ -577,6 +676,7 @@ void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4
     const int n = B - i < 32768 ? B - i : 32768;
     k_beam_shift<<<dim3(2 * N, n), 256, 0, s>>>(beam + (size_t)i * 4 * N * N, N, first,
                                                  beam4 + (size_t)i * 4 * N * N, cstride);
+    note_launch();
   }
 }
 
@@ -605,6 +705,7 @@ void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float
     k_hogbom<<<n, kCleanThreads, 0, s>>>(R + (size_t)i * N * N, beam + (size_t)i * 4 * N * N, N,
                                           thr ? thr + i : nullptr, gain, cap, peak_mode, pos + (size_t)i * cap,
                                           flux + (size_t)i * cap, n_comp + i, status ? status + i : nullptr);
+    note_launch();
   }
 }
 

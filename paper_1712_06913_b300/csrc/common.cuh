@@ -38,6 +38,9 @@ void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int check_launch(const char *what);
 
+// Host-side count of kernels this library has launched (read through muser_launch_count).
+void note_launch();
+
 // ---------------------------------------------------------------- small device helpers
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);

@@ -171,11 +171,15 @@ void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, tw, gc, T1);
+  note_launch();
   cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(T1, tw, X);
-  if (n > 0)
+  note_launch();
+  if (n > 0) {
     k_interp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
                                                           1.f / K2, vis);
+    note_launch();
+  }
 }
 
 template <int G>
@@ -184,7 +188,9 @@ void adjoint_G(const float2 *Z, const float2 *tw, const float *gc, float K2, flo
   using RC = RowCfg<G>;
   cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_adj_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(Z, tw, T);
+  note_launch();
   k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(T, tw, gc, 1.f / K2, img);
+  note_launch();
 }
 
 constexpr int kChi2Threads = 256;
@@ -265,7 +271,9 @@ int chi2_blocks(int64_t n_vis) {
 void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t n_vis, float inv_sigma2,
                  float2 *resid, float *partial, int n_part, float *loss, cudaStream_t s) {
   k_chi2<<<n_part, kChi2Threads, 0, s>>>(pred, obs, rec, n_vis, inv_sigma2, resid, partial);
+  note_launch();
   k_chi2_final<<<1, 256, 0, s>>>(partial, n_part, loss);
+  note_launch();
 }
 
 }  // namespace muser

@@ -125,10 +125,12 @@ void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float
     const int n = B - i < 65535 ? B - i : 65535;
     k_cols<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(Z + (size_t)i * G * G, tw, T + (size_t)i * (G / 2) * G,
                                                             partial + (size_t)i * (G / CC::S));
+    note_launch();
     k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, 0, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
                                                          partial + (size_t)i * (G / CC::S), N,
                                                          dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
                                                          status ? status + i : nullptr);
+    note_launch();
   }
 }
 
@@ -170,7 +172,7 @@ __global__ void k_twiddles(float2 *tw, int L) {
   }
 }
 }  // namespace
-void launch_twiddles(float2 *tw, int L, cudaStream_t s) { k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L); }
+void launch_twiddles(float2 *tw, int L, cudaStream_t s) { k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L); note_launch(); }
 }  // namespace fft
 
 }  // namespace muser

@@ -219,6 +219,7 @@ void launch_gmm(const float *dirty, int B, int N, int bins, float *mu_a, float *
     const int n = B - i < 65535 ? B - i : 65535;
     k_gmm<<<n, kGmmThreads, bins * sizeof(int), s>>>(dirty + (size_t)i * N * N, N, bins, mu_a + i, mu_b + i,
                                                       status ? status + i : nullptr);
+    note_launch();
   }
 }
 

@@ -285,6 +285,7 @@ void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stri
   if (sort_smem > 48 * 1024) cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
   k_bin_sort<<<B, kSortThreads, sort_smem, s>>>(rec, vis_off, dense_stride, G, W, tr, tc, mirror ? 1 : 0, bin_off,
                                                 entries, status);
+  note_launch();
 }
 
 void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
@@ -300,6 +301,7 @@ void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, i
     dim3 grid(nb, n);
     k_grid_tile<<<grid, 256, tile_smem, s>>>(rec, vis_off, dense_stride, i, G, W, tr, tc, tab, table_len(W, os),
                                              (float)os, mirror ? 1 : 0, vals, bin_off, entries, Z);
+    note_launch();
   }
 }
 
@@ -313,6 +315,7 @@ void launch_grid_items_plan(const int32_t *bin_off, int nb, int4 *items, int32_t
   const size_t smem = (size_t)(nb + 1 + 32) * sizeof(int);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_make_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_make_items<<<1, kSortThreads, smem, s>>>(bin_off, nb, items, tile_item0);
+  note_launch();
 }
 
 void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, const float2 *vals, int t,
@@ -322,7 +325,9 @@ void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, c
   const size_t smem = (size_t)t * t * sizeof(float2);
   k_grid_items<<<max_items, 256, smem, s>>>(rec, G, W, t, t, tab, table_len(W, os), (float)os, vals, entries, items,
                                            tile_item0, nb, partial);
+  note_launch();
   k_grid_combine<<<nb, 256, 0, s>>>(partial, tile_item0, G, t, t, Z);
+  note_launch();
 }
 
 }  // namespace muser

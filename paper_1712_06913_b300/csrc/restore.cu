@@ -186,9 +186,11 @@ void launch_restore(const float *R, const float *beam, const int32_t *pos, const
     const int n = B - i < 65535 ? B - i : 65535;
     k_beam_fit<<<n, kFitThreads, 0, s>>>(beam + (size_t)i * 4 * N * N, N, params + (size_t)i * 3,
                                          status ? status + i : nullptr);
+    note_launch();
     const int tiles = N >= 32 ? (N / 32) * (N / 32) : 1;
     k_restore<<<dim3(tiles, n), 256, 0, s>>>(R + (size_t)i * N * N, pos + (size_t)i * cap, flux + (size_t)i * cap,
                                              n_comp + i, N, cap, params + (size_t)i * 3, clean + (size_t)i * N * N);
+    note_launch();
   }
 }
 

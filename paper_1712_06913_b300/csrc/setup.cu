@@ -169,6 +169,7 @@ void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t
   int total = ntab + (gc ? G : 0);
   if (total == 0) return;
   k_pswf_fill<<<(total + 255) / 256, 256, 0, s>>>(P, tab, ntab, W, os, gc, G);
+  note_launch();
 }
 
 }  // namespace muser

@@ -106,6 +106,7 @@ void launch_uvw(const double *ant_enu, int n_ant, const int32_t *pairs, int n_bl
     dim3 grid((n_bl + 255) / 256, n);
     k_uvw<<<grid, 256, 0, s>>>(ant_enu, pairs, n_bl, ha, dec, n_chan, freq, cell, vis, flags, dlm, inst0 + i,
                                n_ant, G, W, sin(lat), cos(lat), rec + (size_t)i * n_bl, uvw_out, status);
+    note_launch();
   }
 }
 
