@@ -5,11 +5,11 @@
 // Two kernels, both keeping the whole loop on the device:
 //
 // k_hogbom_onchip (N = 256, 512, 1024): the residual never leaves the chip.  Each block of
-//   1024 threads owns 65536 residual pixels (a band of rows): 57344 in shared memory
-//   (224 KB) and 8 per thread in registers.  N = 256 needs one block per instance; N = 512 a
-//   cluster of 4 blocks and N = 1024 a cluster of 16, whose block maxima are combined
-//   through distributed shared memory after one cluster barrier per iteration.  An iteration
-//   then moves only the beam window (4 N^2 bytes, mostly from L2) instead of 12 N^2 bytes.
+//   1024 threads keeps a band of 65536 residual pixels in its SM's tensor memory (256 KB).
+//   N = 256 needs one block per instance, N = 512 a cluster of 4 blocks and N = 1024 a cluster
+//   of 16, whose block maxima are exchanged through distributed shared memory (st.async onto
+//   each block's mbarrier) once per iteration.  An iteration then moves only the beam window
+//   (4 N^2 bytes, mostly from L2) instead of 12 N^2 bytes.
 // k_hogbom (any N, fallback): one block per instance streams the residual from HBM every
 //   iteration (16-byte residual accesses, 4-byte coalesced beam loads).
 // In both, the argmax of iteration k+1 is taken in the same pass as the subtraction of
@@ -141,12 +141,6 @@ __global__ void __launch_bounds__(kCleanThreads) k_hogbom(float *__restrict__ Ra
 namespace cg = cooperative_groups;
 
 constexpr int kOnT = 1024;                           // threads per block
-constexpr int kSmemPix = 57344;                      // residual pixels in shared memory (224 KB)
-constexpr int kRegPer = 8;                           // residual pixels in registers per thread
-constexpr int kBandPix = kSmemPix + kRegPer * kOnT;  // 65536 pixels per block
-constexpr size_t kOnSmem = sizeof(float) * kSmemPix;
-constexpr int kBatch = 7;                            // quads whose beam loads are in flight together
-static_assert(kSmemPix / 4 % (kBatch * kOnT) == 0, "quads divide into whole batches");
 
 // ---- packed peaks: one 64-bit word per candidate, compared as an unsigned integer.
 // hi = order-preserving key (MODE 0: the float's bits mapped so that unsigned order equals
@@ -269,20 +263,62 @@ __device__ __forceinline__ Peak cluster_argmax(uint2 w, Exchange<CS> &x, int k) 
   return unpack_peak<MODE>(x.win);
 }
 
-// Pixels of thread t in its block's band: quads q = t + i kOnT (i < kQuads) in shared
-// memory, then register pixels b = kSmemPix + t + j kOnT (j < kRegPer).  Visited in this
-// order the band indices increase, so a strict ">" keeps the lowest index among equal values.
-constexpr int kQuads = kSmemPix / 4 / kOnT;          // 14 quads per thread
+// ---- tensor memory holds the residual (tcgen05.alloc / ld / st).  Each block keeps a band of
+// kTmPix = 65536 pixels in all 512 columns x 128 lanes of its SM's tensor memory: warp w owns
+// lanes 32 (w mod 4) .. +31 and columns 64 (w / 4) .. +63, so every thread keeps 64 private
+// 32-bit cells, its 16 pixel quads q = t + i kOnT (i < 16) of the band, read and written eight
+// cells (two quads) at a time.  Visited in increasing i the band indices increase, so a strict
+// ">" keeps the lowest index among equal values.  Tensor memory moves data to and from the
+// registers several times faster than shared memory, and leaves the load path to the beam.
+constexpr int kTmPix = 65536;
+constexpr int kTmQuads = kTmPix / 4 / kOnT;            // 16 quads per thread
+constexpr int kTmBatch = 8;                            // beam quads in flight together
+static_assert(kTmQuads % kTmBatch == 0 && kTmBatch % 2 == 0, "whole batches of column groups");
 
+__device__ __forceinline__ void tm_ld8(uint32_t a, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(a)
+               : "memory");
+}
+__device__ __forceinline__ void tm_st8(uint32_t a, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(a), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Running per-thread argmax.  Pixels are offered in increasing index order and a strict ">"
+// keeps the first of equal keys.  `quad` takes four consecutive pixels at once: their largest
+// key (a tree of fmaxf) and its first position are found off the dependency chain, so the
+// serial chain through the running maximum is one compare-select per quad, not per pixel.
+// NaN never becomes the maximum (fmaxf ignores it and every comparison with it fails).
 template <int MODE>
-__device__ __forceinline__ bool beats(float v, float best) {
-  return MODE ? fabsf(v) > fabsf(best) : v > best;
-}
+struct Cand {
+  float key;   // running maximum of value (MODE 0) or |value| (MODE 1)
+  float val;   // its signed value (MODE 1)
+  int o;       // its ordinal, -1: none yet
+  __device__ __forceinline__ Cand() : key(MODE ? 0.f : -__builtin_huge_valf()), val(0.f), o(-1) {}
+  __device__ __forceinline__ float value() const { return MODE ? val : key; }
+  __device__ __forceinline__ void px(float v, int oo) {
+    const float k = MODE ? fabsf(v) : v;
+    if (k > key) { key = k; val = v; o = oo; }
+  }
+  __device__ __forceinline__ void quad(float a, float b, float c, float d, int o4) {
+    const float ka = MODE ? fabsf(a) : a, kb = MODE ? fabsf(b) : b, kc = MODE ? fabsf(c) : c, kd = MODE ? fabsf(d) : d;
+    const float m = fmaxf(fmaxf(ka, kb), fmaxf(kc, kd));
+    const int at = ka == m ? 0 : (kb == m ? 1 : (kc == m ? 2 : 3));
+    const float v = ka == m ? a : (kb == m ? b : (kc == m ? c : d));
+    if (m > key) { key = m; val = v; o = o4 + at; }
+  }
+  __device__ __forceinline__ void quad(float4 q, int o4) { quad(q.x, q.y, q.z, q.w, o4); }
+};
 
-// Band index of the thread's o-th pixel (o < 4 kQuads: quad pixels; then register pixels).
-__device__ __forceinline__ int band_index(int o, int tid) {
-  return o < 4 * kQuads ? 4 * (tid + (o >> 2) * kOnT) + (o & 3) : kSmemPix + tid + (o - 4 * kQuads) * kOnT;
-}
+// Band index of the thread's o-th pixel (o < 64: quad o / 4, element o mod 4).
+__device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o >> 2) * kOnT) + (o & 3); }
 
 // beam4: four copies of every instance's beam, copy k at beam4 + k * cstride holding
 // Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
@@ -292,6 +328,8 @@ __device__ __forceinline__ int band_index(int o, int tid) {
 // (`next`): the on-chip clusters and, on SMs that cannot host a whole cluster, streaming
 // blocks (launched on a second stream).  An instance is claimed by one worker, so the two
 // kernels share a batch without any other coordination.
+//
+// Per block, a band of kTmPix / N rows of the residual (CS blocks per instance).
 template <int N, int CS, int MODE>
 __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ Rall, const float *__restrict__ beam4,
                                                            size_t cstride, int B, int *__restrict__ next,
@@ -299,22 +337,18 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
                                                            int32_t *__restrict__ pos, float *__restrict__ flux,
                                                            int32_t *__restrict__ n_comp,
                                                            int32_t *__restrict__ status) {
-  static_assert(N * N == CS * kBandPix, "one band of 65536 pixels per block");
-  static_assert((4 * kOnT) % N == 0, "a step of kOnT quads spans whole rows");
-  extern __shared__ float4 res4[];
+  static_assert(N * N == CS * kTmPix, "one band per block");
+  static_assert((4 * kOnT) % N == 0, "a quad step spans whole rows");
   __shared__ Exchange<CS> xch;
   __shared__ int claim[2], mine[2], stop_flag[2], any_abort[2];
-  constexpr int ROWS = kBandPix / N;
+  __shared__ uint32_t tm_base;
+  constexpr int ROWS = kTmPix / N;
   constexpr int QSTEP = 4 * kOnT / N;                    // rows advanced per quad step
-  constexpr int RSTEP = kOnT / N > 0 ? kOnT / N : 1;     // rows advanced per register step (kOnT >= N)
-  static_assert(kOnT % N == 0, "a register step spans whole rows");
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int row0 = rank * ROWS;
   const int g0 = row0 * N;                                  // global index of band pixel 0
-  // this thread's first quad and first register pixel: (row, column) inside the band
-  const int qr = (4 * tid) / N, qc = (4 * tid) % N;
-  const int rr = (kSmemPix + tid) / N, rc = (kSmemPix + tid) % N;
+  const int qr = (4 * tid) / N, qc = (4 * tid) % N;         // this thread's first quad in the band
   auto packed = [&](float v, int o) { return o >= 0 ? pack_peak<MODE>(v, g0 + band_index(o, tid)) : make_uint2(0u, 0u); };
   if (tid == 0) {
     xch.abort = 0;
@@ -326,6 +360,16 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       mbar_arm(&xch.bar[1], CS * 8u);
     }
   }
+  // one block per SM (its shared-memory request), so all 512 columns are free
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&tm_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tm_fence_before();
+  __syncthreads();
+  tm_fence_after();
+  const uint32_t tm = tm_base + ((32u * (warp & 3)) << 16) + 64u * (warp >> 2);   // this thread's first cell
   int xk = 0, cpar = 0;                                     // exchanges so far; claim buffer
   for (;;) {
     // claim the next instance: rank 0 takes it, every block of the cluster reads it together
@@ -365,27 +409,22 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
     const float *Bm = beam4 + (size_t)inst * 4 * N * N;     // copy 0: the beam itself
     const float t = thr ? thr[inst] : -CUDART_INF_F;
 
-    float best = MODE ? 0.f : -CUDART_INF_F;
-    int bo = -1;
+    // residual band -> tensor memory, with the first argmax
+    Cand<MODE> cb;
     {
-      const float4 *Rb4 = reinterpret_cast<const float4 *>(Rb);
+      const float4 *R4 = reinterpret_cast<const float4 *>(Rb);
 #pragma unroll
-      for (int i = 0; i < kQuads; i++) {
-        const float4 v = Rb4[tid + i * kOnT];
-        res4[tid + i * kOnT] = v;
-        if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
-        if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
-        if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
-        if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+      for (int i = 0; i < kTmQuads; i += 2) {
+        const float4 a = R4[tid + i * kOnT], b = R4[tid + (i + 1) * kOnT];
+        const uint32_t u[8] = {__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w),
+                               __float_as_uint(b.x), __float_as_uint(b.y), __float_as_uint(b.z), __float_as_uint(b.w)};
+        cb.quad(a, 4 * i);
+        cb.quad(b, 4 * i + 4);
+        tm_st8(tm + 4 * i, u);
       }
     }
-    float rv[kRegPer];
-#pragma unroll
-    for (int j = 0; j < kRegPer; j++) {
-      rv[j] = Rb[kSmemPix + tid + j * kOnT];
-      if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
-    }
-    Peak p = cluster_argmax<CS, MODE>(packed(best, bo), xch, xk++);
+    tm_wait_st();
+    Peak p = cluster_argmax<CS, MODE>(packed(cb.value(), cb.o), xch, xk++);
     int it = 0;
     while (!xch.abort && it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
       const float f = gain * p.val;
@@ -394,50 +433,39 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
         flux[(size_t)inst * cap + it] = f;
       }
       const int py = p.idx / N, px = p.idx % N;
-      // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]
+      // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]; its
+      // aligned copy (N - px) mod 4 starts each quad on a 16-byte boundary
       const int off = N - px;
-      const float *Bw = Bm + (size_t)(row0 - py + N) * (2 * N) + off;
       const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
-      const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);   // aligned
-      const float *bg = Bw + (size_t)rr * (2 * N) + rc;      // + j * RSTEP * 2N for register j
-      best = MODE ? 0.f : -CUDART_INF_F;
-      bo = -1;
-      // Beam loads are issued a batch at a time (7 aligned 16-byte loads, plus the 8 register
-      // pixels' loads in the last batch) before any is used: two L2 round trips per iteration.
+      const float4 *bt = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
+      cb = Cand<MODE>();
+      // kTmBatch aligned beam loads in flight, then the residual read, updated and written back
+      // eight cells at a time
+#pragma unroll 1
+      for (int i0 = 0; i0 < kTmQuads; i0 += kTmBatch) {   // not unrolled: keeps the batches apart
+        float4 bb[kTmBatch];
 #pragma unroll
-      for (int i0 = 0; i0 < kQuads; i0 += kBatch) {
-        const bool last = i0 + kBatch >= kQuads;
-        float4 bb[kBatch];
-        float breg[kRegPer];
+        for (int k = 0; k < kTmBatch; k++) bb[k] = __ldg(bt + (i0 + k) * QSTEP * (2 * N / 4));
 #pragma unroll
-        for (int k = 0; k < kBatch; k++) bb[k] = __ldg(bq + (i0 + k) * QSTEP * (2 * N / 4));
-        if (last) {
-#pragma unroll
-          for (int j = 0; j < kRegPer; j++) breg[j] = __ldg(bg + j * RSTEP * 2 * N);
-        }
-#pragma unroll
-        for (int k = 0; k < kBatch; k++) {
+        for (int k = 0; k < kTmBatch; k += 2) {
           const int i = i0 + k;
-          float4 v = res4[tid + i * kOnT];
-          v.x -= f * bb[k].x;
-          v.y -= f * bb[k].y;
-          v.z -= f * bb[k].z;
-          v.w -= f * bb[k].w;
-          res4[tid + i * kOnT] = v;
-          if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
-          if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
-          if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
-          if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
-        }
-        if (last) {
+          uint32_t u[8];
+          tm_ld8(tm + 4 * i, u);
+          tm_wait_ld();
+          const float b8[8] = {bb[k].x, bb[k].y, bb[k].z, bb[k].w, bb[k + 1].x, bb[k + 1].y, bb[k + 1].z, bb[k + 1].w};
+          float v[8];
 #pragma unroll
-          for (int j = 0; j < kRegPer; j++) {
-            rv[j] -= f * breg[j];
-            if (beats<MODE>(rv[j], best)) { best = rv[j]; bo = 4 * kQuads + j; }
+          for (int e = 0; e < 8; e++) {
+            v[e] = __uint_as_float(u[e]) - f * b8[e];
+            u[e] = __float_as_uint(v[e]);
           }
+          tm_st8(tm + 4 * i, u);
+          cb.quad(v[0], v[1], v[2], v[3], 4 * i);
+          cb.quad(v[4], v[5], v[6], v[7], 4 * i + 4);
         }
       }
-      p = cluster_argmax<CS, MODE>(packed(best, bo), xch, xk++);
+      tm_wait_st();
+      p = cluster_argmax<CS, MODE>(packed(cb.value(), cb.o), xch, xk++);
       it++;
     }
     if (xch.abort && tid == 0 && status) atomicOr(status + inst, MUSER_ST_TIMEOUT);
@@ -446,12 +474,23 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
         atomicOr(status + inst, MUSER_ST_ITER_CAP);
     }
-    float4 *Rw4 = reinterpret_cast<float4 *>(Rb);
+    // tensor memory -> residual band
+    float4 *R4 = reinterpret_cast<float4 *>(Rb);
 #pragma unroll
-    for (int i = 0; i < kQuads; i++) Rw4[tid + i * kOnT] = res4[tid + i * kOnT];
-#pragma unroll
-    for (int j = 0; j < kRegPer; j++) Rb[kSmemPix + tid + j * kOnT] = rv[j];
+    for (int i = 0; i < kTmQuads; i += 2) {
+      uint32_t u[8];
+      tm_ld8(tm + 4 * i, u);
+      tm_wait_ld();
+      R4[tid + i * kOnT] = make_float4(__uint_as_float(u[0]), __uint_as_float(u[1]), __uint_as_float(u[2]),
+                                       __uint_as_float(u[3]));
+      R4[tid + (i + 1) * kOnT] = make_float4(__uint_as_float(u[4]), __uint_as_float(u[5]), __uint_as_float(u[6]),
+                                             __uint_as_float(u[7]));
+    }
   }
+  tm_fence_before();
+  __syncthreads();
+  tm_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tm_base) : "memory");
   if constexpr (CS > 1) {
     // after a wait that ran out, give stores still in flight towards this block time to land
     if (xch.abort) __nanosleep(100000);
@@ -492,16 +531,9 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
     auto packed = [&](float v, int o) {
       return o >= 0 ? pack_peak<MODE>(v, 4 * (tid + (o >> 2) * kOnT) + (o & 3)) : make_uint2(0u, 0u);
     };
-    float best = MODE ? 0.f : -CUDART_INF_F;
-    int bo = -1;
-    for (int i = 0; i < NQT; i++) {
-      const float4 v = R4[tid + i * kOnT];
-      if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
-      if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
-      if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
-      if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
-    }
-    Peak p = cluster_argmax<1, MODE>(packed(best, bo), xch, xk++);
+    Cand<MODE> cb;
+    for (int i = 0; i < NQT; i++) cb.quad(R4[tid + i * kOnT], 4 * i);
+    Peak p = cluster_argmax<1, MODE>(packed(cb.value(), cb.o), xch, xk++);
     int it = 0;
     while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
       const float f = gain * p.val;
@@ -513,8 +545,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
       const int off = N - px;
       const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(N - py) * (2 * N) + (off & ~3);
       const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
-      best = MODE ? 0.f : -CUDART_INF_F;
-      bo = -1;
+      cb = Cand<MODE>();
 #pragma unroll 1
       for (int i0 = 0; i0 < NQT; i0 += kSqBatch) {
         float4 rr[kSqBatch], bb[kSqBatch];
@@ -532,13 +563,10 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
           v.z -= f * bb[k].z;
           v.w -= f * bb[k].w;
           R4[tid + i * kOnT] = v;
-          if (beats<MODE>(v.x, best)) { best = v.x; bo = 4 * i; }
-          if (beats<MODE>(v.y, best)) { best = v.y; bo = 4 * i + 1; }
-          if (beats<MODE>(v.z, best)) { best = v.z; bo = 4 * i + 2; }
-          if (beats<MODE>(v.w, best)) { best = v.w; bo = 4 * i + 3; }
+          cb.quad(v, 4 * i);
         }
       }
-      p = cluster_argmax<1, MODE>(packed(best, bo), xch, xk++);
+      p = cluster_argmax<1, MODE>(packed(cb.value(), cb.o), xch, xk++);
       it++;
     }
     if (tid == 0) {
@@ -586,6 +614,9 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
                         int cap, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
   static OnchipPlan plan;          // per process: the library runs on one device model
   auto k = k_hogbom_onchip<N, CS, MODE>;
+  // the residual lives in tensor memory; the kernel still asks for more than half of an SM's
+  // shared memory so that no two of its blocks (each allocating all 512 columns) share an SM
+  const size_t smem = (size_t)116 * 1024;
   auto ks = k_hogbom_stream_q<N, MODE>;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute attr[1];
@@ -594,7 +625,7 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   lc.blockDim = dim3(kOnT);
-  lc.dynamicSmemBytes = kOnSmem;
+  lc.dynamicSmemBytes = smem;
   lc.stream = s;
   lc.attrs = attr;
   lc.numAttrs = 1;
@@ -602,7 +633,7 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
     plan.usable = 0;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnSmem) == cudaSuccess &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
         (CS <= 8 || cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
       int nclusters = 0;
       lc.gridDim = dim3(CS);
@@ -616,8 +647,9 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   }
   if (!plan.usable) return false;
   // Streaming workers (one instance each, the last ns of the batch) only when the clusters'
-  // share is at least 24 waves, long enough to hide a streaming instance.
-  const int ns = (plan.leftover > 0 && B - plan.leftover >= 24 * plan.clusters) ? plan.leftover : 0;
+  // share is at least 40 waves, long enough to hide a streaming instance (which takes about
+  // 40 times as long as a cluster's at N = 1024).
+  const int ns = (plan.leftover > 0 && B - plan.leftover >= 40 * plan.clusters) ? plan.leftover : 0;
   const int Bc = B - ns;
   const int nc = plan.clusters < Bc ? plan.clusters : Bc;
   cudaMemsetAsync(next, 0, sizeof(int), s);
