@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -88,26 +89,66 @@ struct DirtyWs {
   }
 };
 
+// muser_image runs two chunks at once: chunk c is CLEANed on a higher-priority stream (so that
+// the CLEAN clusters take their SMs first) while the caller's stream grids, transforms and
+// thresholds chunk c + 1 and then restores chunk c.  Buffers that CLEAN and restore read
+// (beam and its copies, threshold) come in two sets, by chunk parity.
 template <class A>
 struct ImageWs {
   Rec *rec;
-  float2 *Z;
-  float *beam, *mu_a, *mu_b, *params;
+  float *tab;
+  int32_t *bin_off, *entries;   // per-strip sample lists of the fused gridding
+  float *beam[2], *mu_a[2], *mu_b[2], *params;
   int *next;
-  GridWs<A> g;
   DirtyWs<A> d;
   void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
+    const int S = dirty_strip_width(c.G);
     rec = (Rec *)a.template take<Rec>((size_t)Bc * n_bl);
-    g.carve(a, Bc, (int64_t)Bc * n_bl, c, true);
-    Z = (float2 *)a.template take<float2>((size_t)Bc * c.G * c.G);
+    tab = (float *)a.template take<float>(table_len(c.W, c.os));
+    bin_off = (int32_t *)a.template take<int32_t>((size_t)Bc * (c.G / S + 1));
+    entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(c.W, c.G, S, c.G));
     d.carve(a, Bc, c);
-    beam = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
+    for (int k = 0; k < 2; k++) {
+      beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
+      mu_a[k] = (float *)a.template take<float>(Bc);
+      mu_b[k] = (float *)a.template take<float>(Bc);
+    }
     next = (int *)a.template take<int>(1);
-    mu_a = (float *)a.template take<float>(Bc);
-    mu_b = (float *)a.template take<float>(Bc);
     params = (float *)a.template take<float>((size_t)Bc * 3);
   }
 };
+
+// Per device: the CLEAN stream of muser_image (highest priority) and its events.  `busy` is
+// held while one call enqueues its work, so that calls from several host threads do not
+// interleave their event records and waits.
+struct ImagePipe {
+  std::mutex busy;
+  cudaStream_t clean = nullptr;
+  cudaEvent_t prepped[2] = {nullptr, nullptr}, cleaned[2] = {nullptr, nullptr};
+};
+
+ImagePipe *image_pipe() {
+  static std::mutex mu;
+  static ImagePipe tab[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  ImagePipe &x = tab[dev];
+  if (!x.clean) {
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+              cudaStreamCreateWithPriority(&x.clean, cudaStreamNonBlocking, greatest) == cudaSuccess;
+    for (int k = 0; ok && k < 2; k++)
+      ok = cudaEventCreateWithFlags(&x.prepped[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x.cleaned[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      x.clean = nullptr;
+      return nullptr;
+    }
+  }
+  return &x;
+}
 
 template <class A>
 struct DegridWs {
@@ -369,43 +410,61 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   ImageWs<Arena> w;
   w.carve(a, Bc, n_bl, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
+  ImagePipe *pp = image_pipe();
+  if (!pp) return fail(MUSER_ERR_CUDA, "muser_image: cannot create its CLEAN stream");
+  std::lock_guard<std::mutex> enqueue(pp->busy);
+  cudaStream_t hs = pp->clean;
   const int N = cfg->N, G = cfg->G, cap = cfg->max_iter;
+  const int n_chunks = (B + Bc - 1) / Bc;
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
-  launch_pswf_table(w.g.tab, cfg->W, cfg->os, w.d.gc, G, s);
+  launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s);
   fft::launch_twiddles(w.d.tw, G, s);
-  for (int c0 = 0; c0 < B; c0 += Bc) {
-    const int n = B - c0 < Bc ? B - c0 : Bc;
+  // chunk c up to its CLEAN input, on the caller's stream
+  auto prepare = [&](int c) {
+    const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
     int32_t *st = status + c0;
     float *R = residual + (size_t)c0 * N * N;
     launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, c0, n, G,
                cfg->W, cfg->lat_rad, w.rec, nullptr, status, s);
-    launch_grid(w.rec, nullptr, n_bl, n, G, cfg->W, cfg->os, w.g.tab, true, nullptr, grid_band_rows(G), G, w.Z,
-                w.g.bin_off, w.g.entries, st, false, s);
-    launch_dirty(w.Z, n, N, G, w.d.tw, w.d.gc, w.d.T, w.d.partial, R, w.beam, st, s);
-    const float *thr = nullptr;
+    launch_dirty_gridded(w.rec, n_bl, n, N, G, cfg->W, cfg->os, w.tab, w.bin_off, w.entries, w.d.tw, w.d.gc, w.d.T,
+                         w.d.partial, R, w.beam[k], st, s);
     if (cfg->thr_mode == 1) {
-      launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a, w.mu_b, st, s);
-      thr = w.mu_a;
+      launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a[k], w.mu_b[k], st, s);
       if (thr_out) {
-        k_copy<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, w.mu_a, n);
+        k_copy<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, w.mu_a[k], n);
         note_launch();
       }
     } else if (thr_out) {
       k_fill<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, n, -INFINITY);
       note_launch();
     }
-    const size_t cstride = (size_t)Bc * 4 * N * N;
-    if (copies(*cfg)) launch_beam_copies(w.beam, n, N, 1, w.beam, cstride, s);
-    launch_hogbom(
-        R, w.beam, copies(*cfg) ? w.beam : nullptr, cstride, w.next, n, N, thr, cfg->gain, cap, cfg->peak_mode,
-        comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
-                  comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, st, s);
-    launch_restore(R, w.beam, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+    if (copies(*cfg)) launch_beam_copies(w.beam[k], n, N, 1, w.beam[k], (size_t)Bc * 4 * N * N, s);
+    cudaEventRecord(pp->prepped[k], s);
+  };
+  auto restore = [&](int c) {
+    const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
+    cudaStreamWaitEvent(s, pp->cleaned[k], 0);
+    launch_restore(residual + (size_t)c0 * N * N, w.beam[k], comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                    comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, n, N, cap,
-                   clean_img + (size_t)c0 * N * N, beam_params ? beam_params + (size_t)c0 * 3 : w.params, st, s);
+                   clean_img + (size_t)c0 * N * N, beam_params ? beam_params + (size_t)c0 * 3 : w.params,
+                   status + c0, s);
+  };
+  prepare(0);
+  for (int c = 0; c < n_chunks; c++) {
+    const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
+    cudaStreamWaitEvent(hs, pp->prepped[k], 0);
+    launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
+                  (size_t)Bc * 4 * N * N, w.next, n, N, cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
+                  cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+                  comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);
+    cudaEventRecord(pp->cleaned[k], hs);
+    // the caller's stream: next chunk's preparation (set k ^ 1, free once chunk c - 1 was
+    // restored, earlier on this stream), then this chunk's restore
+    if (c + 1 < n_chunks) prepare(c + 1);
+    restore(c);
     MUSER_TRY(check_launch("muser_image"));
   }
-  return MUSER_OK;
+  return check_launch("muser_image");
 }
 
 int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,

@@ -583,8 +583,10 @@ struct OnchipPlan {
   int leftover = 0;      // SMs that cannot host a whole cluster
 };
 
-// Second stream and fork/join events per device, for the streaming workers.
+// Second stream and fork/join events per device, for the streaming workers (`busy` is held
+// from the fork to the join, so that calls from several host threads do not interleave).
 struct SideStream {
+  std::mutex busy;
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
@@ -656,7 +658,11 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   // Clusters first (they need whole GPCs), then the streaming workers on the SMs left over.
   SideStream *side = ns > 0 ? side_stream() : nullptr;
   if (ns > 0 && !side) return false;
-  if (side) cudaEventRecord(side->fork, s);
+  std::unique_lock<std::mutex> forked;
+  if (side) {
+    forked = std::unique_lock<std::mutex>(side->busy);
+    cudaEventRecord(side->fork, s);
+  }
   lc.gridDim = dim3(nc * CS);
   cudaLaunchKernelEx(&lc, k, R, beam4, cstride, Bc, next, thr, gain, cap, pos, flux, n_comp, status);
   note_launch();

@@ -126,6 +126,12 @@ void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, c
 
 // imaging FFT (dirty.cu)
 int dirty_strip_width(int G);
+// Gridding fused into the column pass (the G x G grid never reaches HBM): sorts the dense
+// records [B][stride] into per-strip lists (bin_off [B][G/S + 1], entries [B][stride][2][tiles]),
+// then column pass and row pass as launch_dirty.
+void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
+                          int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
+                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
 void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T,
                   float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
 namespace fft {

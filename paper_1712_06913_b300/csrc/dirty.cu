@@ -9,6 +9,9 @@
 //   (-1)^(ku+kv), transforms the columns, keeps rows y in [G/4, 3G/4) -> T[B][G/2][G];
 //   it also sums Im Z over the strip (the raw beam centre is sum Im Z, because every
 //   phase factor is 1 at the centre).
+// k_cols_grid (used by muser_image) is pass 1 with the gridding fused in: the block grids the
+//   samples whose footprints touch its strip (sorted into per-strip lists by k_bin_sort)
+//   straight into its shared-memory strip, so the G x G grid never goes to HBM.
 // Pass 2, k_rows: a block transforms S rows of T, keeps x in [G/4, 3G/4) and writes
 //   beam = Im I (-1)^(x+y) / (gc(x) gc(y) norm) and, over the central N x N, dirty = Re I ...
 //   with norm = sum of the strip sums (fixed order), so beam[N][N] = 1.
@@ -61,6 +64,81 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols(const float2 *__restrict
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (threadIdx.x == 0) partial[(size_t)inst * (G / S) + blockIdx.x] = t;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restrict__ rec, int64_t stride, int W,
+                                                            const float *__restrict__ tab, int ntab, float os,
+                                                            const int32_t *__restrict__ bin_off,
+                                                            const int32_t *__restrict__ entries,
+                                                            const float2 *__restrict__ tw, float2 *__restrict__ T,
+                                                            float *__restrict__ partial) {
+  using C = ColCfg<G>;
+  using Lay = typename C::Layout;
+  constexpr int S = C::S, NT = C::NT, NS = G / S;
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  __shared__ float red[32];
+  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  for (int i = threadIdx.x; i < Lay::size / 2; i += NT) smem4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  // grid the strip: one warp per (sample, sign) entry, its W x W taps over the lanes; taps
+  // outside the strip's columns belong to a neighbouring block
+  {
+    const int32_t *off = bin_off + (size_t)inst * (NS + 1);
+    const int e1 = off[blockIdx.x + 1];
+    const int32_t *ent = entries + (size_t)inst * stride * 2 * tiles_per_sample(W, G, S, G);
+    const Rec *ri = rec + (size_t)inst * stride;
+    const int h = (W - 1) / 2, WW = W * W;
+    const int lane = threadIdx.x & 31;
+    for (int e = off[blockIdx.x] + (threadIdx.x >> 5); e < e1; e += NT / 32) {
+      const int code = ent[e];
+      const int sg = code & 1;
+      const Rec R = ri[code >> 1];
+      const float2 val = make_float2(R.v.x * R.w, (sg ? -R.v.y : R.v.y) * R.w + R.w);   // w (V + i), mirror w (V* + i)
+      for (int tap = lane; tap < WW; tap += 32) {
+        const int tv = tap / W - h, tu = tap % W - h;
+        const int col = (sg ? G - R.ku - tu : R.ku + tu) - x0;
+        if (col < 0 || col >= S) continue;
+        const int row = sg ? G - R.kv - tv : R.kv + tv;
+        const float c = kernel_lookup(tab, ntab, os, (float)tu + R.fu) * kernel_lookup(tab, ntab, os, (float)tv + R.fv);
+        float2 *cell = sm + Lay::at(row, col);
+        atomicAdd(&cell->x, c * val.x);
+        atomicAdd(&cell->y, c * val.y);
+      }
+    }
+  }
+  __syncthreads();
+  struct Load {
+    const float2 *sm;
+    int x0;
+    float im_sum;
+    __device__ float2 operator()(int i, int s) {
+      float2 z = sm[Lay::at(i, s)];
+      im_sum += z.y;
+      return ((i + x0 + s) & 1) ? make_float2(-z.x, -z.y) : z;
+    }
+  } load{sm, x0, 0.f};
+  float2 *Ti = T + (size_t)inst * (G / 2) * G;
+  struct Store {
+    float2 *Ti;
+    int x0;
+    __device__ void operator()(int o, int s, float2 v) {
+      if (o >= G / 4 && o < 3 * G / 4) Ti[(size_t)(o - G / 4) * G + x0 + s] = v;
+    }
+  } store{Ti, x0};
+  fft::run<G, S, NT, +1, true, Lay, true>(sm, tw, load, store);
+  float v = load.im_sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partial[(size_t)inst * NS + blockIdx.x] = t;
   }
 }
 
@@ -134,6 +212,28 @@ void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float
   }
 }
 
+template <int G>
+void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W, int os, const float *tab,
+                            const int32_t *bin_off, const int32_t *entries, const float2 *tw, const float *gc,
+                            float2 *T, float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+  using CC = ColCfg<G>;
+  using RC = RowCfg<G>;
+  cudaFuncSetAttribute(k_cols_grid<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  const int tps = tiles_per_sample(W, G, CC::S, G);
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    k_cols_grid<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(
+        rec + (size_t)i * stride, stride, W, tab, table_len(W, os), (float)os, bin_off + (size_t)i * (G / CC::S + 1),
+        entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S));
+    note_launch();
+    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, 0, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
+                                                         partial + (size_t)i * (G / CC::S), N,
+                                                         dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
+                                                         status ? status + i : nullptr);
+    note_launch();
+  }
+}
+
 }  // namespace
 
 int dirty_strip_width(int G) {
@@ -155,6 +255,25 @@ void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const 
   switch (G) {
 #define MUSER_CASE(g) \
   case g: launch_dirty_G<g>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s); break;
+    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+#undef MUSER_CASE
+    default: break;
+  }
+}
+
+void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
+                          int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
+                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+  if (B <= 0) return;
+  const int S = dirty_strip_width(G);
+  if (S == 0) return;
+  launch_grid_sort(rec, nullptr, stride, B, G, W, true, G, S, bin_off, entries, status, s);
+  switch (G) {
+#define MUSER_CASE(g)                                                                                          \
+  case g:                                                                                                      \
+    launch_dirty_gridded_G<g>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial, dirty, beam, \
+                              status, s);                                                                      \
+    break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
 #undef MUSER_CASE
     default: break;

@@ -134,7 +134,7 @@ struct Plan {
 // One stage and (recursively) the following ones.  SFAST: work items enumerate the
 // sequence index fastest (column strips, coalesced global rows) or the butterfly index
 // fastest (rows).  NT threads; S * L / R must be a multiple of NT.
-template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, class Load, class Store>
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, bool SYNC0, class Load, class Store>
 __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
   constexpr int R = Plan<L>::template radix<STAGE>();
   constexpr bool FIRST = STAGE == 0, LAST = STAGE == Plan<L>::NST - 1;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw
       else v[b][r] = sm[Layout::at(idx, s)];
     }
   }
-  if constexpr (!FIRST) __syncthreads();
+  if constexpr (!FIRST || SYNC0) __syncthreads();
 #pragma unroll
   for (int b = 0; b < BPT; b++) {
     const int it = threadIdx.x + b * NT;
@@ -182,13 +182,15 @@ __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw
   }
   if constexpr (!LAST) {
     __syncthreads();
-    stages<L, S, NT, SIGN, SFAST, Layout, STAGE + 1, LS * R>(sm, tw, load, store);
+    stages<L, S, NT, SIGN, SFAST, Layout, STAGE + 1, LS * R, false>(sm, tw, load, store);
   }
 }
 
-template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, class Load, class Store>
+// SYNC0: the Load functor reads the block's own shared memory (data placed there before the
+// call), so the first stage waits for every load before it stores.
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, bool SYNC0 = false, class Load, class Store>
 __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
-  stages<L, S, NT, SIGN, SFAST, Layout, 0, 1>(sm, tw, load, store);
+  stages<L, S, NT, SIGN, SFAST, Layout, 0, 1, SYNC0>(sm, tw, load, store);
 }
 
 // Column strips: S columns of a G x G array per block (S = min(G, 16384 / G)), 32 complex
