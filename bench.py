@@ -345,8 +345,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "instances_per_gpu": B, "batch_chunk": args.chunk,
-                           "l2": "inputs larger than L2: per step 17 GB of residual, 68 GB of beams (+ 3 shifted copies) and 283 GB of column-pass output stream through HBM"
-                                 "grids streamed per step)"},
+                           "l2": "inputs larger than L2: per step 17 GB of residual, 68 GB of beams (+ 3 shifted "
+                                 "copies) and 283 GB of column-pass output stream through HBM"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "images/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
