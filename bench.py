@@ -211,8 +211,9 @@ def main():
     import synth
 
     # each rank images its own batch (different frames): weak scaling, no data-path collective
+    from paper_1712_06913_b300 import dist as mdist
     wl = synth.config3_muser2_uneven(n_frame=args.frames * world)
-    sl = slice(rank * args.frames, (rank + 1) * args.frames)
+    sl = mdist.block(args.frames * world, rank, world)
     ha, dec, vis, flags = wl.ha[sl], wl.dec[sl], wl.vis[sl], wl.flags[sl]
     B = len(ha) * wl.n_chan
     cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=wl.max_iter, gain=wl.gain, lat_rad=wl.lat,
@@ -227,11 +228,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return mdist.all_max(x, device="cuda")
 
     # ---- warm-up
     for _ in range(args.warmup):

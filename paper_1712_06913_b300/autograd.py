@@ -11,6 +11,7 @@ from __future__ import annotations
 import torch
 
 from . import api
+from . import dist as _dist
 from ._lib import ADJOINT, FORWARD
 
 
@@ -52,6 +53,10 @@ class GradientImaging:
     chi-square seed and adjoint are library kernels) and applies x <- x - eta * grad.
     `capture()` records one step in a CUDA graph so that `replay()` runs it without host
     work; the image, loss and gradient live in fixed device tensors.
+
+    Under torch.distributed each rank passes the records and visibilities of its own block of
+    channels (`dist.block`); the loss and the gradient are summed over ranks every step, so
+    every rank applies the same update to its copy of the image.
     """
 
     def __init__(self, rec, obs, sigma, cfg, x0=None, eta=None):
@@ -75,7 +80,7 @@ class GradientImaging:
         lam = 0.0
         for _ in range(iters):
             y = self.plan.forward(v)
-            u = self.plan.adjoint(y) * (2.0 * self.inv_s2)
+            u = _dist.all_sum_(self.plan.adjoint(y) * (2.0 * self.inv_s2))
             lam = float(torch.linalg.norm(u))
             v = u / lam
         return lam
@@ -86,8 +91,10 @@ class GradientImaging:
         loss = chi2_loss(self.x, self.plan, self.obs, self.inv_s2)
         loss.backward()
         with torch.no_grad():
+            _dist.all_sum_(self.x.grad)
+            loss = _dist.all_sum_(loss.detach().clone())
             self.x -= self.eta * self.x.grad
-        self.loss = loss.detach()
+        self.loss = loss
         return self.loss
 
     def capture(self, warmup=3):
