@@ -281,6 +281,18 @@ def main():
     e2e_value = B * world * args.steps / (e2e_ms / 1e3)
     assert np.array_equal(nc_host.numpy(), n_comp)
 
+    # ---- the same batch replayed from one CUDA graph (every chunk, both streams)
+    imager.capture()
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for k in range(args.steps):
+        imager.replay()
+    g1.record(stream)
+    barrier()
+    graph_value = B * world * args.steps / (max_over_ranks(g0.elapsed_time(g1)) / 1e3)
+    assert np.array_equal(imager.out.n_comp.cpu().numpy(), n_comp)
+
     # ---- per-phase timing (same kernels through the separate calls) for the roofline
     rec, _, st = m.uvw(wl.ant_enu, wl.pairs, ha, dec, wl.freq, cell, vis, cfg, flags=flags)
     off = torch.arange(B + 1, dtype=torch.int64, device="cuda") * wl.n_bl
@@ -328,7 +340,8 @@ def main():
              "gridding_GBps": grid_bytes / (statistics.mean(phase["grid"]) / 1e3) / 1e9,
              "dirty_fft_GBps": args.chunk * (8.0 * G * G + 4.0 * G * G * 2 + 4.0 * N * N + 16.0 * N * N)
              / (statistics.mean(phase["dirty"]) / 1e3) / 1e9,
-             "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum())}
+             "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum()),
+             "graph_replay_images_per_s": graph_value}
 
     if not args.no_extras and rank == 0:
         extra.update(plain_and_degrid(m, wl, cell, cfg, stream))
@@ -465,7 +478,43 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     res["grad_evals_per_s_eager"] = 20 / (e0.elapsed_time(e1) / 1e3)
+    # algorithmic bytes of one evaluation: forward (image in, two FFT passes over the 2N x 2N
+    # grid, gathers) and the adjoint (the same, transposed)
+    N4, G4 = w4.N, w4.G
+    ev_bytes = 2 * (4.0 * N4 * N4 + 2 * 16.0 * G4 * G4 + 8.0 * w4.vis.size)
+    res["grad_GBps"] = res["grad_evals_per_s"] * ev_bytes / 1e9
+    res.update(fft_vs_cufft(m, wl, cell, cfg, stream))
     return res
+
+
+def fft_vs_cufft(m, wl, cell, cfg, stream, n=32):
+    """The dirty-map transform (muser_dirty: pruned column + row passes with the grid-correction
+    epilogue) against cuFFT's full complex inverse 2-D FFT of the same grids (torch.fft)."""
+    import torch
+    rec, _, st = m.uvw(wl.ant_enu, wl.pairs, wl.ha[:1], wl.dec[:1], wl.freq[:n], cell[:n], wl.vis[:1, :n], cfg,
+                       flags=wl.flags[:1, :n])
+    off = torch.arange(n + 1, dtype=torch.int64, device="cuda") * wl.n_bl
+    ws = m.Workspace()
+    Z, st = m.grid(rec, off, cfg, status=st, ws=ws)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):
+        m.dirty(Z, cfg, ws=ws)
+        torch.fft.ifft2(Z)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(3):
+        D, Bm, _ = m.dirty(Z, cfg, ws=ws)
+    e[1].record(stream)
+    e[2].record(stream)
+    for _ in range(3):
+        F = torch.fft.ifft2(Z)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    del F, D, Bm, Z
+    return {"dirty_ms_per_instance": e[0].elapsed_time(e[1]) / 3 / n,
+            "cufft_ifft2_ms_per_instance": e[2].elapsed_time(e[3]) / 3 / n,
+            "fft_comparison": f"{n} MUSER-II grids of {cfg.G}^2: muser_dirty (pruned, with epilogue) vs "
+                              "torch.fft.ifft2 (cuFFT, full transform, no epilogue)"}
 
 
 if __name__ == "__main__":

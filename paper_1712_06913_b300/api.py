@@ -249,6 +249,27 @@ class Imager:
             _p(o.beam_params), w, wb, _p(o.status), _stream()))
         return o
 
+    def capture(self):
+        """Record the whole batch (every chunk, both of muser_image's streams) in one CUDA graph.
+
+        One eager run first creates the library's streams and plans outside the capture.
+        `replay()` then re-runs the batch with no host work, reading the visibilities from
+        `self.vis` (copy new data into it before a replay) and writing `self.out`.
+        """
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
+
 
 def image(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None):
     """Whole hot path for a batch; returns an ImageResult with comp arrays cut to max_iter."""

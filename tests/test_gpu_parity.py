@@ -252,6 +252,28 @@ def test_image_batched_equals_per_instance(m):
             assert float((one.clean[0] - out.clean[i]).abs().max()) <= 1e-6 * peak
 
 
+@pytest.mark.parametrize("key,chunk", [("small-N32-3frames", 2), ("N256x6", 4)])
+def test_image_graph_replay(m, key, chunk):
+    """The whole batch captured in one CUDA graph (both streams of muser_image, several
+    chunks) replays to the eager result."""
+    import torch
+    wl = (WORKLOADS.get(key) or ONCHIP_CASES[key])()
+    cfg = cfg_for(m, wl, max_iter=60, batch_chunk=chunk)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    ref = im.run()
+    torch.cuda.synchronize()
+    pos, n, clean = ref.comp_pos.clone(), ref.n_comp.clone(), ref.clean.clone()
+    im.capture()
+    for _ in range(2):
+        out = im.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out.n_comp, n)
+    assert torch.equal(out.comp_pos, pos)
+    peak = float(clean.abs().max())
+    assert float((out.clean - clean).abs().max()) <= 1e-6 * peak
+
+
 def test_gmm_threshold_path(m):
     wl = synth.small_workload(n_ant=10, N=64, config_id=205, bmax=300.0, max_iter=1000)
     cfg = cfg_for(m, wl, thr_mode=1)
