@@ -221,7 +221,9 @@ MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pa
  *            exact adjoint of FORWARD restricted to real images.  vis read, img written.
  * K = integral of the kernel.  rec[n_vis] from muser_uvw with the same cfg.
  * A call without MUSER_REUSE_PLAN plans: it writes the kernel table, grid correction,
- * twiddles and the adjoint's sorted tile lists into ws.  OR-ing MUSER_REUSE_PLAN into
+ * twiddles and the adjoint's tap lists (every tap of every record, grouped by grid cell;
+ * the order within a cell is fixed by the plan, so adjoints with one plan are bitwise
+ * repeatable) into ws.  OR-ing MUSER_REUSE_PLAN into
  * `direction` skips that work and uses ws as left by an earlier call with the same rec,
  * n_vis and cfg (ws must not have been used for anything else in between): the uv
  * coverage is fixed during iterative imaging, only img / vis change. */

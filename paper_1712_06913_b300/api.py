@@ -304,8 +304,8 @@ def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None
 class DegridPlan:
     """The measurement operator of one record set (fixed uv coverage) with its own workspace.
 
-    The first call plans (kernel table, grid correction, twiddles, the adjoint's sorted tile
-    lists); later calls reuse the plan and only run the transforms.
+    The first call plans (kernel table, grid correction, twiddles, the adjoint's tap lists by
+    grid cell); later calls reuse the plan and only run the transforms.
     """
 
     def __init__(self, rec, cfg: Config):

@@ -91,9 +91,11 @@ class GradientImaging:
         loss = chi2_loss(self.x, self.plan, self.obs, self.inv_s2)
         loss.backward()
         with torch.no_grad():
-            _dist.all_sum_(self.x.grad)
-            loss = _dist.all_sum_(loss.detach().clone())
-            self.x -= self.eta * self.x.grad
+            loss = loss.detach()
+            if _dist.rank_world()[1] > 1:
+                _dist.all_sum_(self.x.grad)
+                loss = _dist.all_sum_(loss.clone())
+            self.x.add_(self.x.grad, alpha=-self.eta)
         self.loss = loss
         return self.loss
 

@@ -153,25 +153,27 @@ ImagePipe *image_pipe() {
 template <class A>
 struct DegridWs {
   float *tab, *gc;
-  float2 *tw, *T, *X, *partial;
-  int32_t *bin_off, *entries, *tile_item0;
-  int4 *items;
-  int nb, max_items;
+  float2 *tw, *T, *X;
+  int32_t *cnt, *cell_off, *sums, *counts;
+  int2 *taps;
+  int4 *long_cells, *pieces;
+  float2 *partial;
   void carve(A &a, int64_t n_vis, const muser_config_t &c) {
-    const int G = c.G, t = adjoint_tile(G);
-    nb = (G / t) * (G / t);
-    const int64_t n_entries = n_vis * tiles_per_sample(c.W, t, t, G);
-    max_items = grid_max_items(n_entries, nb);
+    const int G = c.G;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     gc = (float *)a.template take<float>(G);
     tw = (float2 *)a.template take<float2>(G);
     T = (float2 *)a.template take<float2>((size_t)(G / 2) * G);
     X = (float2 *)a.template take<float2>((size_t)G * G);
-    bin_off = (int32_t *)a.template take<int32_t>(nb + 1);
-    entries = (int32_t *)a.template take<int32_t>((size_t)n_entries);
-    tile_item0 = (int32_t *)a.template take<int32_t>(nb + 1);
-    items = (int4 *)a.template take<int4>(max_items);
-    partial = (float2 *)a.template take<float2>((size_t)max_items * t * t);
+    cnt = (int32_t *)a.template take<int32_t>((size_t)G * G);
+    cell_off = (int32_t *)a.template take<int32_t>((size_t)G * G + 1);
+    sums = (int32_t *)a.template take<int32_t>(degrid_plan_scan_blocks(G));
+    taps = (int2 *)a.template take<int2>((size_t)n_vis * c.W * c.W);
+    const int64_t np = degrid_plan_pieces(n_vis, G, c.W);
+    long_cells = (int4 *)a.template take<int4>((size_t)np);
+    pieces = (int4 *)a.template take<int4>((size_t)np);
+    partial = (float2 *)a.template take<float2>((size_t)np);
+    counts = (int32_t *)a.template take<int32_t>(2);
   }
 };
 
@@ -485,20 +487,18 @@ int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64
   cudaStream_t s = (cudaStream_t)stream;
   const Pswf &P = pswf_coefficients(cfg->W);
   const float K2 = (float)(P.K * P.K);
-  if (!reuse) {           // plan: kernel table, grid correction, twiddles and the adjoint's tile lists
+  if (!reuse) {           // plan: kernel table, grid correction, twiddles and the adjoint's tap lists
     launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
     fft::launch_twiddles(w.tw, cfg->G, s);
-    const int t = adjoint_tile(cfg->G);
-    launch_grid_sort((const Rec *)rec, nullptr, n_vis, 1, cfg->G, cfg->W, false, t, t, w.bin_off, w.entries,
-                     nullptr, s);
-    launch_grid_items_plan(w.bin_off, w.nb, w.items, w.tile_item0, s);
+    launch_degrid_plan((const Rec *)rec, n_vis, cfg->G, cfg->W, cfg->os, w.tab, w.cnt, w.cell_off, w.sums, w.taps,
+                       w.long_cells, w.pieces, w.counts, s);
   }
   if (dir == MUSER_FORWARD)
     launch_degrid_forward(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T,
                           w.X, (float2 *)vis, s);
   else
-    launch_degrid_adjoint((const float2 *)vis, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw,
-                          w.gc, K2, w.entries, w.items, w.tile_item0, w.max_items, w.partial, w.X, w.T, img, s);
+    launch_degrid_adjoint((const float2 *)vis, cfg->N, cfg->G, w.tw, w.gc, K2, w.cell_off, w.taps, w.long_cells,
+                          w.pieces, w.counts, w.partial, w.X, w.T, img, s);
   return check_launch("muser_degrid");
 }
 

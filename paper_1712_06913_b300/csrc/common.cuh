@@ -106,7 +106,6 @@ __host__ __device__ inline int grid_bands_per_sample(int W, int rows) { return (
 __host__ __device__ inline int tiles_per_sample(int W, int tr, int tc, int G) {
   return (tr >= G ? 1 : grid_bands_per_sample(W, tr)) * (tc >= G ? 1 : grid_bands_per_sample(W, tc));
 }
-inline int adjoint_tile(int G) { return G < 32 ? G : 32; }   // tile side of the degridding adjoint
 // mirror: grid w (V + i) at +uv and w (conj V + i) at -uv (imaging); otherwise grid vals[r]
 // at +uv only (adjoint of degridding).  Tiles of tr x tc cells (tc >= 2); every tile of Z is
 // written, so Z need not be cleared.  sorted: bin_off/entries already hold this record set's
@@ -116,13 +115,6 @@ void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, i
                  int32_t *entries, int32_t *status, bool sorted, cudaStream_t s);
 void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, bool mirror,
                       int tr, int tc, int32_t *bin_off, int32_t *entries, int32_t *status, cudaStream_t s);
-// One-instance gridding of crowded records (degridding adjoint): tile lists cut into items of
-// at most 256 entries, each accumulated into a partial tile, partial tiles summed per tile.
-int grid_max_items(int64_t n_entries, int nb);
-void launch_grid_items_plan(const int32_t *bin_off, int nb, int4 *items, int32_t *tile_item0, cudaStream_t s);
-void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, const float2 *vals, int t,
-                       const int32_t *entries, const int4 *items, const int32_t *tile_item0, int max_items,
-                       float2 *partial, float2 *Z, cudaStream_t s);
 
 // imaging FFT (dirty.cu)
 int dirty_strip_width(int G);
@@ -163,10 +155,20 @@ void launch_restore(const float *R, const float *beam, const int32_t *pos, const
 void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
                            const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
                            float2 *vis, cudaStream_t s);
-void launch_degrid_adjoint(const float2 *vis, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                           const float *tab, const float2 *tw, const float *gc, float K2, const int32_t *entries,
-                           const int4 *items, const int32_t *tile_item0, int max_items, float2 *partial, float2 *Z,
-                           float2 *T, float *img, cudaStream_t s);
+// Adjoint plan: tap lists by cell (cell_off [G*G + 1], taps [n_vis * W * W] {record, weight}),
+// the cells with long lists (long_cells {cell, first piece, pieces}) and their pieces
+// ({cell, first tap, end tap}; at most degrid_plan_pieces of each), counts {long cells,
+// pieces}; built with cnt [G*G] and scan scratch sums [degrid_plan_scan_blocks(G)].
+void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, const float *tab, int32_t *cnt,
+                        int32_t *cell_off, int32_t *sums, int2 *taps, int4 *long_cells, int4 *pieces,
+                        int32_t *counts, cudaStream_t s);
+int degrid_plan_scan_blocks(int G);
+int64_t degrid_plan_pieces(int64_t n_vis, int G, int W);
+// partial: degrid_plan_pieces entries; Z: G x G scratch.
+void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
+                           const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
+                           const int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
+                           cudaStream_t s);
 
 void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t n_vis, float inv_sigma2,
                  float2 *resid, float *partial, int n_part, float *loss, cudaStream_t s);

@@ -8,17 +8,28 @@
 //     pass 1 (rows, only the N nonzero padded rows): T1[py'][ku]
 //     pass 2 (columns, only the N nonzero inputs):   X[kv][ku]
 //     pass 3: one thread per record gathers its W x W taps from X (L2 resident).
-//   ADJOINT   Z = grid of vis (no Hermitian mirror), via the sorted band gridding;
+//   ADJOINT   Z = grid of vis (no Hermitian mirror), Z[cell] = sum over the taps on the cell of
+//             C(tu + fu) C(tv + fv) vis[record], gathered cell by cell from the plan's tap lists
+//             (every tap of every record, grouped by cell): one thread per cell; lists longer
+//             than kLongList (short baselines at every channel crowd a few cells near the uv
+//             centre with thousands of taps) are cut into pieces of kPiece taps, one warp per
+//             piece, and a cell's pieces are added in order.  The order of a list is fixed when
+//             the plan is built, so every adjoint with one plan sums in the same order, without
+//             atomics;
 //     pass 1 (columns, outputs pruned to the central N rows), pass 2 (rows, central N
 //     columns), img = Re(...) (-1)^(x+y) / (K^2 gc(x) gc(y)).
+//   One instance per call: the passes use strips a quarter as wide as the batched imaging
+//   passes (fft::ColCfg1 / RowCfg1), so that one transform still spreads over the SMs.
 #include "fft.cuh"
 
 namespace muser {
 
 namespace {
 
-using fft::ColCfg;
-using fft::RowCfg;
+template <int G>
+using ColCfg = fft::ColCfg1<G>;
+template <int G>
+using RowCfg = fft::RowCfg1<G>;
 
 // FORWARD pass 1: rows of the padded image.
 template <int G>
@@ -108,7 +119,138 @@ __global__ void __launch_bounds__(256) k_interp(const float2 *__restrict__ X, co
   vis[r] = acc;
 }
 
-// ADJOINT pass 1: columns of the gridded vis, outputs kept for the central N rows.
+// FORWARD pass 3 for W <= 8: eight lanes per record, lane tv sums its row of taps; the
+// eight partial sums are combined with shuffles (more loads in flight than one thread per
+// record).
+__global__ void __launch_bounds__(256) k_interp8(const float2 *__restrict__ X, const Rec *__restrict__ rec, int64_t n,
+                                                 int G, int W, const float *__restrict__ tab, int ntab, float os,
+                                                 float invK2, float2 *__restrict__ vis) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int tv = threadIdx.x & 7;
+  const int h = (W - 1) / 2;
+  Rec R;
+  bool ok = false;
+  if (r < n) {
+    R = rec[r];
+    ok = record_ok(R, G, h);
+  }
+  float2 acc = make_float2(0.f, 0.f);
+  if (ok && tv < W) {
+    const float cv = kernel_lookup(tab, ntab, os, (float)(tv - h) + R.fv);
+    const float2 *row = X + (size_t)(R.kv + tv - h) * G + (R.ku - h);
+    for (int tu = 0; tu < W; tu++) {
+      const float c = cv * kernel_lookup(tab, ntab, os, (float)(tu - h) + R.fu);
+      const float2 x = __ldg(row + tu);
+      acc.x += c * x.x;
+      acc.y += c * x.y;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (r < n && tv == 0) vis[r] = ok ? make_float2(acc.x * invK2, acc.y * invK2) : make_float2(0.f, 0.f);
+}
+
+// ADJOINT gather: Z[c] = sum of its taps' weight x vis.  Short lists: one thread per cell;
+// lists longer than kLongList: skipped here, summed by a warp in k_adj_gather_long.
+constexpr int kLongList = 32;
+
+__global__ void k_adj_gather(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
+                             const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int a = cell_off[c], e = cell_off[c + 1];
+  if (e - a > kLongList) return;
+  float2 z = make_float2(0.f, 0.f);
+  int j = a;
+  for (; j + 4 <= e; j += 4) {                  // four gathers in flight, added in list order
+    int2 t[4];
+    float2 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
+#pragma unroll
+    for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float w = __int_as_float(t[k].y);
+      z.x += w * v[k].x;
+      z.y += w * v[k].y;
+    }
+  }
+  for (; j < e; j++) {
+    const int2 t = __ldg(taps + j);
+    const float w = __int_as_float(t.y);
+    const float2 v = __ldg(vis + t.x);
+    z.x += w * v.x;
+    z.y += w * v.y;
+  }
+  Z[c] = z;
+}
+
+constexpr int kPiece = 512;
+
+// One warp per piece of a long list: its partial sum (lanes stride the piece, then a fixed
+// shuffle tree).
+__global__ void k_adj_pieces(const int2 *__restrict__ taps, const float2 *__restrict__ vis,
+                             const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
+                             float2 *__restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int np = *n_pieces;
+  for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < np; k += nw) {
+    const int4 pc = pieces[k];                 // {cell, first tap, end tap, -}
+    float2 z = make_float2(0.f, 0.f);
+    int j = pc.y + lane;
+    for (; j + 96 < pc.z; j += 128) {           // four gathers per lane in flight, added in order
+      int2 t[4];
+      float2 v[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + 32 * k);
+#pragma unroll
+      for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float w = __int_as_float(t[k].y);
+        z.x += w * v[k].x;
+        z.y += w * v[k].y;
+      }
+    }
+    for (; j < pc.z; j += 32) {
+      const int2 t = __ldg(taps + j);
+      const float w = __int_as_float(t.y);
+      const float2 v = __ldg(vis + t.x);
+      z.x += w * v.x;
+      z.y += w * v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+      z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+    }
+    if (lane == 0) partial[k] = z;
+  }
+}
+
+// One thread per long cell: its pieces' partial sums in order.
+__global__ void k_adj_long(const int4 *__restrict__ long_cells, const int32_t *__restrict__ n_long,
+                           const float2 *__restrict__ partial, float2 *__restrict__ Z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nl = *n_long;
+  for (int k = i; k < nl; k += gridDim.x * blockDim.x) {
+    const int4 lc = long_cells[k];             // {cell, first piece, pieces, -}
+    float2 z = make_float2(0.f, 0.f);
+    for (int q = 0; q < lc.z; q++) {
+      const float2 v = partial[lc.y + q];
+      z.x += v.x;
+      z.y += v.y;
+    }
+    Z[lc.x] = z;
+  }
+}
+
+// ADJOINT pass 1: columns of the grid, outputs kept for the central N rows.
 template <int G>
 __global__ void __launch_bounds__(ColCfg<G>::NT) k_adj_cols(const float2 *__restrict__ Z, const float2 *__restrict__ tw,
                                                            float2 *__restrict__ T) {
@@ -175,7 +317,11 @@ void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const
   cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(T1, tw, X);
   note_launch();
-  if (n > 0) {
+  if (n > 0 && W <= 8) {
+    k_interp8<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
+                                                               1.f / K2, vis);
+    note_launch();
+  } else if (n > 0) {
     k_interp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
                                                           1.f / K2, vis);
     note_launch();
@@ -191,6 +337,122 @@ void adjoint_G(const float2 *Z, const float2 *tw, const float *gc, float K2, flo
   note_launch();
   k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(T, tw, gc, 1.f / K2, img);
   note_launch();
+}
+
+// ---- adjoint plan: tap lists by cell
+__global__ void k_tap_count(const Rec *__restrict__ rec, int64_t n, int G, int W, int32_t *__restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = (W - 1) / 2;
+  if (r >= n) return;
+  const Rec R = rec[r];
+  if (!record_ok(R, G, h)) return;
+  for (int tv = -h; tv <= h; tv++)
+    for (int tu = -h; tu <= h; tu++) atomicAdd(cnt + (size_t)(R.kv + tv) * G + (R.ku + tu), 1);
+}
+
+// Exclusive scan of a[0..n) in place, in blocks of kScanPer elements (4 per thread).
+constexpr int kScanThreads = 1024, kScanPer = 4 * kScanThreads;
+
+__device__ int block_scan_excl(int x, int *wsum) {   // exclusive prefix of x over the block
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wsum[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    wsum[lane] = t;                                      // inclusive prefix of the warp totals
+  }
+  __syncthreads();
+  const int r = v - x + (wid > 0 ? wsum[wid - 1] : 0);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(int32_t *__restrict__ a, int64_t n,
+                                                              int32_t *__restrict__ sums) {
+  __shared__ int wsum[32];
+  const int64_t base = (int64_t)blockIdx.x * kScanPer + 4 * threadIdx.x;
+  int v[4], t = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    v[k] = base + k < n ? a[base + k] : 0;
+    t += v[k];
+  }
+  int run = block_scan_excl(t, wsum);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (base + k < n) a[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = run;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int32_t *__restrict__ sums, int nb) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+    const int i = b0 + threadIdx.x;
+    const int x = i < nb ? sums[i] : 0;
+    const int e = block_scan_excl(x, wsum) + carry;
+    if (i < nb) sums[i] = e;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = e + x;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(int32_t *__restrict__ a, int64_t n,
+                                                           const int32_t *__restrict__ sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanPer + 4 * threadIdx.x;
+  const int add = sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < 4; k++)
+    if (base + k < n) a[base + k] += add;
+}
+
+__global__ void k_tap_fill(const Rec *__restrict__ rec, int64_t n, int G, int W, const float *__restrict__ tab,
+                           int ntab, float os, const int32_t *__restrict__ cell_off, int32_t *__restrict__ cursor,
+                           int2 *__restrict__ taps) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = (W - 1) / 2;
+  if (r >= n) return;
+  const Rec R = rec[r];
+  if (!record_ok(R, G, h)) return;
+  for (int tv = -h; tv <= h; tv++) {
+    const float cv = kernel_lookup(tab, ntab, os, (float)tv + R.fv);
+    for (int tu = -h; tu <= h; tu++) {
+      const size_t c = (size_t)(R.kv + tv) * G + (R.ku + tu);
+      const int p = cell_off[c] + atomicAdd(cursor + c, 1);
+      taps[p] = make_int2((int)r, __float_as_int(kernel_lookup(tab, ntab, os, (float)tu + R.fu) * cv));
+    }
+  }
+}
+
+// The cells whose lists are long, in no particular order, each with its run of pieces
+// (placed contiguously, in list order).
+__global__ void k_long_cells(const int32_t *__restrict__ cell_off, int64_t ncell, int4 *__restrict__ long_cells,
+                             int32_t *__restrict__ counts, int4 *__restrict__ pieces) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int a = cell_off[c], e = cell_off[c + 1];
+  if (e - a <= kLongList) return;
+  const int np = (e - a + kPiece - 1) / kPiece;
+  const int i = atomicAdd(counts, 1);
+  const int p0 = atomicAdd(counts + 1, np);
+  long_cells[i] = make_int4((int)c, p0, np, 0);
+  for (int q = 0; q < np; q++) pieces[p0 + q] = make_int4((int)c, a + q * kPiece, min(e, a + (q + 1) * kPiece), 0);
 }
 
 constexpr int kChi2Threads = 256;
@@ -247,11 +509,52 @@ void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int 
   }
 }
 
-void launch_degrid_adjoint(const float2 *vis, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                           const float *tab, const float2 *tw, const float *gc, float K2, const int32_t *entries,
-                           const int4 *items, const int32_t *tile_item0, int max_items, float2 *partial, float2 *Z,
-                           float2 *T, float *img, cudaStream_t s) {
-  launch_grid_items(rec, G, W, os, tab, vis, adjoint_tile(G), entries, items, tile_item0, max_items, partial, Z, s);
+void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, const float *tab, int32_t *cnt,
+                        int32_t *cell_off, int32_t *sums, int2 *taps, int4 *long_cells, int4 *pieces,
+                        int32_t *counts, cudaStream_t s) {
+  const int64_t ncell = (int64_t)G * G;
+  cudaMemsetAsync(cell_off, 0, sizeof(int32_t) * (size_t)(ncell + 1), s);
+  const unsigned rb = (unsigned)((n_vis + 255) / 256);
+  if (n_vis > 0) {
+    k_tap_count<<<rb, 256, 0, s>>>(rec, n_vis, G, W, cell_off);
+    note_launch();
+  }
+  const int nb = (int)((ncell + 1 + kScanPer - 1) / kScanPer);
+  k_scan_blocks<<<nb, kScanThreads, 0, s>>>(cell_off, ncell + 1, sums);
+  note_launch();
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb);
+  note_launch();
+  k_scan_add<<<nb, kScanThreads, 0, s>>>(cell_off, ncell + 1, sums);
+  note_launch();
+  if (n_vis > 0) {
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)ncell, s);
+    k_tap_fill<<<rb, 256, 0, s>>>(rec, n_vis, G, W, tab, table_len(W, os), (float)os, cell_off, cnt, taps);
+    note_launch();
+  }
+  cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), s);
+  k_long_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(cell_off, ncell, long_cells, counts, pieces);
+  note_launch();
+}
+
+int64_t degrid_plan_pieces(int64_t n_vis, int G, int W) {
+  const int64_t taps = n_vis * W * W, ncell = (int64_t)G * G;
+  const int64_t longs = taps / (kLongList + 1) < ncell ? taps / (kLongList + 1) : ncell;
+  return taps / kPiece + longs + 1;
+}
+
+int degrid_plan_scan_blocks(int G) { return (int)(((int64_t)G * G + 1 + kScanPer - 1) / kScanPer); }
+
+void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
+                           const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
+                           const int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
+                           cudaStream_t s) {
+  const int64_t ncell = (int64_t)G * G;
+  k_adj_gather<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(cell_off, taps, vis, ncell, Z);
+  note_launch();
+  k_adj_pieces<<<592, 256, 0, s>>>(taps, vis, pieces, counts + 1, partial);
+  note_launch();
+  k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, partial, Z);
+  note_launch();
   switch (G) {
 #define MUSER_CASE(g) \
   case g: adjoint_G<g>(Z, tw, gc, K2, T, img, s); break;

@@ -193,24 +193,35 @@ __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, L
   stages<L, S, NT, SIGN, SFAST, Layout, 0, 1, SYNC0>(sm, tw, load, store);
 }
 
-// Column strips: S columns of a G x G array per block (S = min(G, 16384 / G)), 32 complex
-// values per thread per stage.  Rows: S = min(max(1, 4096 / G), G / 2) rows per block, 16 values
-// per thread per stage.
-template <int G>
-struct ColCfg {
-  static constexpr int S = G < 16384 / G ? G : 16384 / G;
+// Column strips: S columns of a G x G array per block, 32 complex values per thread per stage;
+// rows: S rows per block, 16 values per thread per stage.  ColCfg / RowCfg (S = min(G, 16384 / G)
+// columns, min(max(1, 4096 / G), G / 2) rows) fill the SMs when many instances are transformed
+// at once; ColCfg1 / RowCfg1 (max(4, 4096 / G) columns, max(1, 2048 / G) rows) give one
+// transform 4 times as many blocks.
+template <int G, int S_>
+struct ColStrip {
+  static constexpr int S = S_;
   static constexpr int NT = S * G / 32;
   using Layout = Interleaved<G, S>;
   static constexpr size_t smem = sizeof(float2) * Layout::size;
 };
-template <int G>
-struct RowCfg {
-  static constexpr int S0 = 4096 / G > 1 ? 4096 / G : 1;
-  static constexpr int S = S0 < G / 2 ? S0 : G / 2;
+template <int G, int S_>
+struct RowStrip {
+  static constexpr int S = S_;
   static constexpr int NT = S * G / 16;
   using Layout = Sequential<G, S>;
   static constexpr size_t smem = sizeof(float2) * Layout::size;
 };
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+template <int G>
+using ColCfg = ColStrip<G, cmin(G, 16384 / G)>;
+template <int G>
+using RowCfg = RowStrip<G, cmin(cmax(1, 4096 / G), G / 2)>;
+template <int G>
+using ColCfg1 = ColStrip<G, cmin(G, cmax(4, 4096 / G))>;
+template <int G>
+using RowCfg1 = RowStrip<G, cmin(cmax(1, 2048 / G), G / 2)>;
 
 void launch_twiddles(float2 *tw, int L, cudaStream_t s);
 

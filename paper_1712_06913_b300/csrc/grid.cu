@@ -1,9 +1,9 @@
 // Convolutional gridding with sorted visibilities and shared-memory band tiles
 // (Sec. 3.2.3; Alg. 1 "calculating the weight and gridding").
 //
-// The grid is cut into tiles of tr rows x tc columns (the imaging path uses full-width
-// bands, tc = G; the degridding adjoint, whose records crowd the uv centre, uses 32 x 32
-// tiles so that the crowded region is spread over many blocks).
+// The grid is cut into tiles of tr rows x tc columns (muser_grid uses full-width bands,
+// tc = G; the gridding fused into muser_image's column transform uses strips of the
+// transform's width, tr = G).
 // Step 1 (k_bin_sort, one block per instance): every kept record contributes one or two
 // samples (+uv, and the Hermitian mirror -uv when `mirror`); a sample's W x W footprint
 // touches at most tiles_per_sample() tiles.  A counting sort in shared memory places
@@ -182,99 +182,6 @@ __global__ void __launch_bounds__(256) k_grid_tile(const Rec *__restrict__ rec, 
   }
 }
 
-// ---------------------------------------------------------------- crowded tiles (one instance)
-// The degridding adjoint grids one record set whose short baselines, at every channel, land
-// within a few cells of the uv centre: thousands of samples hit the same cells.  Its tile
-// lists are cut into work items of at most kItem entries; each item accumulates a private
-// partial tile in shared memory, and the partial tiles of a tile are summed in item order.
-constexpr int kItem = 256;
-
-// One block: items per tile = max(1, ceil(count / kItem)), their prefix, the item table.
-__global__ void __launch_bounds__(kSortThreads) k_make_items(const int32_t *__restrict__ bin_off, int nb,
-                                                             int4 *__restrict__ items, int32_t *__restrict__ tile_item0) {
-  extern __shared__ int sh[];
-  int *ni = sh;               // nb + 1
-  int *wt = sh + nb + 1;      // 32
-  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-    const int c = bin_off[t + 1] - bin_off[t];
-    ni[t] = c > kItem ? (c + kItem - 1) / kItem : 1;
-  }
-  if (threadIdx.x == 0) ni[nb] = 0;
-  __syncthreads();
-  block_exclusive_scan(ni, nb + 1, wt);
-  for (int t = threadIdx.x; t <= nb; t += blockDim.x) tile_item0[t] = ni[t];
-  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
-    const int e0 = bin_off[t], e1 = bin_off[t + 1];
-    for (int j = ni[t], e = e0; j < ni[t + 1]; j++, e += kItem)
-      items[j] = make_int4(t, e, e + kItem < e1 ? e + kItem : e1, 0);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_grid_items(const Rec *__restrict__ rec, int G, int W, int tr, int tc,
-                                                    const float *__restrict__ tab, int ntab, float os,
-                                                    const float2 *__restrict__ vals, const int32_t *__restrict__ entries,
-                                                    const int4 *__restrict__ items, const int32_t *__restrict__ tile_item0,
-                                                    int nb, float2 *__restrict__ partial) {
-  extern __shared__ float4 tile4[];
-  float2 *tile = reinterpret_cast<float2 *>(tile4);
-  const int j = blockIdx.x;
-  if (j >= tile_item0[nb]) return;                 // fewer items than the launch bound
-  const int4 it = items[j];
-  const int ntc = G / tc;
-  const int row0 = (it.x / ntc) * tr, col0 = (it.x % ntc) * tc;
-  const int n4 = tr * tc / 2;
-  for (int i = threadIdx.x; i < n4; i += blockDim.x) tile4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncthreads();
-  const int h = (W - 1) / 2;
-  for (int e = it.y + (int)threadIdx.x; e < it.z; e += blockDim.x) {
-    const int i = entries[e] >> 1;                 // adjoint: +uv samples only
-    const Rec R = rec[i];
-    const float2 val = vals[i];
-    float cu[9];
-#pragma unroll
-    for (int t = 0; t < 9; t++) cu[t] = t < W ? kernel_lookup(tab, ntab, os, (float)(t - h) + R.fu) : 0.f;
-#pragma unroll
-    for (int a = 0; a < 9; a++) {
-      if (a >= W) break;
-      const int row = R.kv + a - h;
-      if (row < row0 || row >= row0 + tr) continue;
-      const float cv = kernel_lookup(tab, ntab, os, (float)(a - h) + R.fv);
-      const float2 cvv = make_float2(cv * val.x, cv * val.y);
-      float2 *trow = tile + (row - row0) * tc;
-#pragma unroll
-      for (int b = 0; b < 9; b++) {
-        if (b >= W) break;
-        const int col = R.ku + b - h;
-        if (col < col0 || col >= col0 + tc) continue;
-        atomicAdd(&trow[col - col0].x, cu[b] * cvv.x);
-        atomicAdd(&trow[col - col0].y, cu[b] * cvv.y);
-      }
-    }
-  }
-  __syncthreads();
-  float4 *dst = reinterpret_cast<float4 *>(partial + (size_t)j * tr * tc);
-  for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = tile4[i];
-}
-
-// Z tile t = sum of its items' partial tiles, in item order.
-__global__ void __launch_bounds__(256) k_grid_combine(const float2 *__restrict__ partial,
-                                                      const int32_t *__restrict__ tile_item0, int G, int tr, int tc,
-                                                      float2 *__restrict__ Z) {
-  const int t = blockIdx.x, ntc = G / tc;
-  const int row0 = (t / ntc) * tr, col0 = (t % ntc) * tc;
-  const int j0 = tile_item0[t], j1 = tile_item0[t + 1];
-  const int n4 = tr * tc / 2, q4 = tc / 2;
-  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-    float4 acc = reinterpret_cast<const float4 *>(partial + (size_t)j0 * tr * tc)[i];
-    for (int j = j0 + 1; j < j1; j++) {
-      const float4 v = reinterpret_cast<const float4 *>(partial + (size_t)j * tr * tc)[i];
-      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
-    }
-    const int r = i / q4, c = i - r * q4;
-    reinterpret_cast<float4 *>(Z + (size_t)(row0 + r) * G + col0)[c] = acc;
-  }
-}
-
 }  // namespace
 
 void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, bool mirror,
@@ -307,27 +214,3 @@ void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, i
 
 }  // namespace muser
 
-namespace muser {
-
-int grid_max_items(int64_t n_entries, int nb) { return nb + (int)((n_entries + kItem - 1) / kItem); }
-
-void launch_grid_items_plan(const int32_t *bin_off, int nb, int4 *items, int32_t *tile_item0, cudaStream_t s) {
-  const size_t smem = (size_t)(nb + 1 + 32) * sizeof(int);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k_make_items, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_make_items<<<1, kSortThreads, smem, s>>>(bin_off, nb, items, tile_item0);
-  note_launch();
-}
-
-void launch_grid_items(const Rec *rec, int G, int W, int os, const float *tab, const float2 *vals, int t,
-                       const int32_t *entries, const int4 *items, const int32_t *tile_item0, int max_items,
-                       float2 *partial, float2 *Z, cudaStream_t s) {
-  const int nb = (G / t) * (G / t);
-  const size_t smem = (size_t)t * t * sizeof(float2);
-  k_grid_items<<<max_items, 256, smem, s>>>(rec, G, W, t, t, tab, table_len(W, os), (float)os, vals, entries, items,
-                                           tile_item0, nb, partial);
-  note_launch();
-  k_grid_combine<<<nb, 256, 0, s>>>(partial, tile_item0, G, t, t, Z);
-  note_launch();
-}
-
-}  // namespace muser
