@@ -92,14 +92,15 @@ struct DirtyWs {
 // muser_image runs two chunks at once: chunk c is CLEANed on a higher-priority stream (so that
 // the CLEAN clusters take their SMs first) while the caller's stream grids, transforms and
 // thresholds chunk c + 1 and then restores chunk c.  Buffers that CLEAN and restore read
-// (beam and its copies, threshold) come in two sets, by chunk parity.
+// (beam and its copies, threshold, the clusters' instance counter) come in two sets, by
+// chunk parity; so do the CLEAN streams.
 template <class A>
 struct ImageWs {
   Rec *rec;
   float *tab;
   int32_t *bin_off, *entries;   // per-strip sample lists of the fused gridding
   float *beam[2], *mu_a[2], *mu_b[2], *params;
-  int *next;
+  int *next[2];
   DirtyWs<A> d;
   void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
     const int S = dirty_strip_width(c.G);
@@ -113,17 +114,18 @@ struct ImageWs {
       mu_a[k] = (float *)a.template take<float>(Bc);
       mu_b[k] = (float *)a.template take<float>(Bc);
     }
-    next = (int *)a.template take<int>(1);
+    for (int k = 0; k < 2; k++) next[k] = (int *)a.template take<int>(1);
     params = (float *)a.template take<float>((size_t)Bc * 3);
   }
 };
 
-// Per device: the CLEAN stream of muser_image (highest priority) and its events.  `busy` is
-// held while one call enqueues its work, so that calls from several host threads do not
-// interleave their event records and waits.
+// Per device: the CLEAN streams of muser_image (highest priority; chunks alternate between
+// them, so that the next chunk's clusters start on the SMs the last instances of a chunk
+// leave) and their events.  `busy` is held while one call enqueues its work, so that calls
+// from several host threads do not interleave their event records and waits.
 struct ImagePipe {
   std::mutex busy;
-  cudaStream_t clean = nullptr;
+  cudaStream_t clean[2] = {nullptr, nullptr};
   cudaEvent_t prepped[2] = {nullptr, nullptr}, cleaned[2] = {nullptr, nullptr};
 };
 
@@ -134,16 +136,16 @@ ImagePipe *image_pipe() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lk(mu);
   ImagePipe &x = tab[dev];
-  if (!x.clean) {
+  if (!x.clean[0]) {
     int least = 0, greatest = 0;
-    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
-              cudaStreamCreateWithPriority(&x.clean, cudaStreamNonBlocking, greatest) == cudaSuccess;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
     for (int k = 0; ok && k < 2; k++)
-      ok = cudaEventCreateWithFlags(&x.prepped[k], cudaEventDisableTiming) == cudaSuccess &&
+      ok = cudaStreamCreateWithPriority(&x.clean[k], cudaStreamNonBlocking, greatest) == cudaSuccess &&
+           cudaEventCreateWithFlags(&x.prepped[k], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&x.cleaned[k], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
-      x.clean = nullptr;
+      x.clean[0] = nullptr;
       return nullptr;
     }
   }
@@ -415,7 +417,6 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   ImagePipe *pp = image_pipe();
   if (!pp) return fail(MUSER_ERR_CUDA, "muser_image: cannot create its CLEAN stream");
   std::lock_guard<std::mutex> enqueue(pp->busy);
-  cudaStream_t hs = pp->clean;
   const int N = cfg->N, G = cfg->G, cap = cfg->max_iter;
   const int n_chunks = (B + Bc - 1) / Bc;
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
@@ -454,9 +455,10 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   prepare(0);
   for (int c = 0; c < n_chunks; c++) {
     const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
+    cudaStream_t hs = pp->clean[k];
     cudaStreamWaitEvent(hs, pp->prepped[k], 0);
     launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
-                  (size_t)Bc * 4 * N * N, w.next, n, N, cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
+                  (size_t)Bc * 4 * N * N, w.next[k], n, N, cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
                   cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                   comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);
     cudaEventRecord(pp->cleaned[k], hs);
