@@ -109,6 +109,25 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   }
 }
 
+// w[r] = w[1]^r for r = 2 .. R-1, each a product of at most four table-accurate factors.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 (&w)[R]) {
+  if constexpr (R >= 4) {
+    w[2] = cmul(w[1], w[1]);
+    w[3] = cmul(w[2], w[1]);
+  }
+  if constexpr (R >= 8) {
+    w[4] = cmul(w[2], w[2]);
+#pragma unroll
+    for (int r = 5; r < 8; r++) w[r] = cmul(w[4], w[r - 4]);
+  }
+  if constexpr (R >= 16) {
+    w[8] = cmul(w[4], w[4]);
+#pragma unroll
+    for (int r = 9; r < 16; r++) w[r] = cmul(w[8], w[r - 8]);
+  }
+}
+
 // --- shared-memory layouts: element (i, s), one padding slot per 16 elements
 template <int L, int S>
 struct Interleaved {          // consecutive sequences adjacent: for column strips
@@ -164,12 +183,15 @@ __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw
     const int k = j & (LS - 1);
     if constexpr (LS > 1) {
       constexpr int STEP = L / (LS * R);      // W_{LS R}^{rk} = W_L^{rk STEP}
+      // one table load per butterfly; the other powers by products of at most four factors
+      // (the lanes of a warp read scattered table entries, so fifteen loads per butterfly
+      // would be fifteen scattered L1 accesses)
+      float2 w[R];
+      w[1] = __ldg(tw + k * STEP);
+      if (SIGN < 0) w[1].y = -w[1].y;
+      twiddle_powers<R>(w);
 #pragma unroll
-      for (int r = 1; r < R; r++) {
-        float2 w = __ldg(tw + r * k * STEP);
-        if (SIGN < 0) w.y = -w.y;
-        v[b][r] = cmul(v[b][r], w);
-      }
+      for (int r = 1; r < R; r++) v[b][r] = cmul(v[b][r], w[r]);
     }
     dft<R, SIGN>(v[b]);
     const int base = (j / LS) * LS * R + k;
