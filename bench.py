@@ -316,6 +316,16 @@ def main():
         torch.cuda.synchronize()
         for j, k in enumerate(phase):
             phase[k].append(evs[j].elapsed_time(evs[j + 1]))
+        if c0 == 0:                 # disk centring (Sec. 4.2) of the chunk's dirty maps, timed alone
+            mu_a, mu_b, _ = m.gmm(D, cfg)
+            cell_i = torch.tensor(np.tile(cell, len(ha))[:n], dtype=torch.float64, device="cuda")
+            m.center(D, mu_a, mu_b, cell_i, cfg, ws=ws)
+            ec = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ec[0].record(stream)
+            m.center(D, mu_a, mu_b, cell_i, cfg, ws=ws)
+            ec[1].record(stream)
+            torch.cuda.synchronize()
+            center_ms = ec[0].elapsed_time(ec[1])
         iters = nc.cpu().numpy().astype(np.float64)
         # on-chip CLEAN: beam copies (read the 2N x 2N beam, write three shifted copies), residual
         # read and written once, one N x N beam window read per iteration
@@ -341,7 +351,9 @@ def main():
              "dirty_fft_GBps": args.chunk * (8.0 * G * G + 4.0 * G * G * 2 + 4.0 * N * N + 16.0 * N * N)
              / (statistics.mean(phase["dirty"]) / 1e3) / 1e9,
              "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum()),
-             "graph_replay_images_per_s": graph_value}
+             "graph_replay_images_per_s": graph_value,
+             "center_ms_per_chunk": center_ms,
+             "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3)}
 
     if not args.no_extras and rank == 0:
         extra.update(plain_and_degrid(m, wl, cell, cfg, stream))

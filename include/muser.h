@@ -60,15 +60,17 @@ enum {
   MUSER_ST_GMM_DEGENERATE = 8,  /* a mixture component has weight < 1e-4 */
   MUSER_ST_ITER_CAP = 16,       /* CLEAN stopped at max_iter with the peak still above thr */
   MUSER_ST_BEAM_FIT = 32,       /* the beam main lobe did not fit the fitting window */
-  MUSER_ST_TIMEOUT = 64         /* a bounded wait inside the CLEAN kernel ran out (about 2 s); the
+  MUSER_ST_TIMEOUT = 64,        /* a bounded wait inside the CLEAN kernel ran out (about 2 s); the
                                    instance's CLEAN outputs are invalid.  Not expected to occur. */
+  MUSER_ST_NO_DISK = 128        /* muser_center: no pixel above the mask level; offset 0 */
 };
 
 enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
 
 enum {
   MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
-  MUSER_CALL_RESTORE = 5, MUSER_CALL_IMAGE = 6, MUSER_CALL_DEGRID = 7, MUSER_CALL_CHI2 = 8
+  MUSER_CALL_RESTORE = 5, MUSER_CALL_IMAGE = 6, MUSER_CALL_DEGRID = 7, MUSER_CALL_CHI2 = 8,
+  MUSER_CALL_CENTER = 9
 };
 
 /* Imaging parameters (host struct, passed by pointer). */
@@ -236,6 +238,23 @@ MUSER_API int muser_degrid(int direction, float *img, const muser_vis_record_t *
  * the sky image is muser_degrid(ADJOINT) of resid. */
 MUSER_API int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *rec, int64_t n_vis,
                float inv_sigma2, float *resid, float *loss, void *ws, size_t ws_bytes, muser_stream_t stream);
+
+/* Solar-disk centring (Sec. 4.2, Alg. 1 pre_clean): the offset of the solar disk in each of B
+ * residual images that were CLEANed down to the disk level mu_b (muser_clean with thr = mu_b).
+ *  mask M(p) = R(p) if R(p) > (mu_a + mu_b) / 2 else 0 (the bright points, with their values;
+ *    the literal R > mu_b is empty after that CLEAN);
+ *  disk S(p) = 1 within 16 arcmin / cell_rad[b] pixels of (N/2, N/2);
+ *  Cc(s) = sum_p M(p) S(p - s) for |s_x|, |s_y| <= N/4 (zero-padded FFTs of side 2N);
+ *  s* = argmax Cc (ties: smallest |s|, then lowest row-major index), refined per axis by a
+ *    3-point parabola (clipped to +-1/2 pixel);  dlm_out[b] = (s*_x, s*_y) * cell_rad[b] (rad).
+ * residual[B][N][N] f32, mu_a/mu_b[B] f32 (muser_gmm), cell_rad[B] f64, all device.  Outputs:
+ * dlm_out[B][2] f64; shift_out[B][2] f32 pixels (NULL = not written); corr_out[B][N/2+1][N/2+1]
+ * f32 (NULL = not written).  Pass dlm_out to muser_uvw / muser_image to phase-correct the
+ * visibilities (exp(+2 pi i (u dl + v dm))) and re-image.  The RA offset is dl / cos(dec).
+ * Instances whose mask is empty get MUSER_ST_NO_DISK and offset 0.  N <= 1024. */
+MUSER_API int muser_center(const float *residual, const float *mu_a, const float *mu_b, const double *cell_rad, int B,
+                           const muser_config_t *cfg, float *corr_out, double *dlm_out, float *shift_out, void *ws,
+                           size_t ws_bytes, int32_t *status, muser_stream_t stream);
 
 #ifdef __cplusplus
 }

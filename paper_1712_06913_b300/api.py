@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CALL_CHI2, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
+from ._lib import CALL_CENTER, CALL_CHI2, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
 
 RECORD_FLOATS = 6          # 24-byte record viewed as float32[6]
 
@@ -180,6 +180,22 @@ def clean(D, Bm, cfg: Config, thr=None, status=None, ws: Workspace = None):
     return R, pos[:, :cap], flux[:, :cap], nc, st
 
 
+def center(R, mu_a, mu_b, cell, cfg: Config, status=None, want_corr=False, ws: Workspace = None):
+    """Disk offsets of residuals CLEANed to the disk level: (dlm [B, 2] rad, shift [B, 2] px,
+    corr [B, N/2+1, N/2+1] or None, status)."""
+    B, N = R.shape[0], cfg.N
+    dlm = torch.empty((B, 2), dtype=torch.float64, device="cuda")
+    shift = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    corr = torch.empty((B, N // 2 + 1, N // 2 + 1), dtype=torch.float32, device="cuda") if want_corr else None
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    cl = _dev(cell, torch.float64)
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_CENTER, B, 0, cfg))
+    check(_lib.load().muser_center(_p(R.contiguous()), _p(mu_a), _p(mu_b), _p(cl), B, ctypes.byref(c), _p(corr),
+                                   _p(dlm), _p(shift), w, wb, _p(st), _stream()))
+    return dlm, shift, corr, st
+
+
 def restore(R, Bm, pos, flux, n_comp, cfg: Config, status=None):
     B = R.shape[0]
     out = torch.empty_like(R)
@@ -277,6 +293,30 @@ def image(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm
     o = im.run()
     cap = cfg.max_iter
     return dataclasses.replace(o, comp_pos=o.comp_pos[:, :cap], comp_flux=o.comp_flux[:, :cap])
+
+
+def image_centred(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, pre_cap=1000):
+    """Alg. 1 with the centring of Sec. 4.2: dirty map -> GMM levels -> CLEAN down to the disk
+    level mu_b (at most pre_cap iterations) -> disk offset (muser_center) -> phase-corrected
+    re-imaging with the sky threshold mu_a (muser_image, thr_mode 1).
+
+    Returns (ImageResult of the corrected visibilities, dlm [B, 2] rad, shift [B, 2] px).
+    The first pass holds every instance's G x G grid at once: call it on batches that fit.
+    """
+    F, C = len(ha), len(freq)
+    pre = Config(**{**cfg.__dict__, "thr_mode": 0, "max_iter": pre_cap})
+    rec, _, st = uvw(ant_enu, pairs, ha, dec, freq, cell, vis, pre, flags=flags)
+    nb = int(np.asarray(pairs).shape[0])
+    off = torch.arange(F * C + 1, dtype=torch.int64, device="cuda") * nb
+    Z, st = grid(rec, off, pre, status=st)
+    D, Bm, st = dirty(Z, pre, status=st)
+    del Z
+    mu_a, mu_b, st = gmm(D, pre, status=st)
+    R, _, _, _, st = clean(D, Bm, pre, thr=mu_b, status=st)
+    dlm, shift, _, st = center(R, mu_a, mu_b, np.tile(np.asarray(cell, float), F), pre, status=st)
+    out = image(ant_enu, pairs, ha, dec, freq, cell, vis, Config(**{**cfg.__dict__, "thr_mode": 1}), flags=flags,
+                dlm=dlm)
+    return out, dlm, shift
 
 
 def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None, reuse_plan=False):

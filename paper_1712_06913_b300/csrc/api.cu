@@ -179,6 +179,23 @@ struct DegridWs {
   }
 };
 
+template <class A>
+struct CenterWs {
+  float2 *tw, *F, *U;
+  float *thr, *r2, *Cc;
+  int32_t *masked;
+  void carve(A &a, int B, const muser_config_t &c, bool own_corr) {
+    const int N = c.N, P = 2 * N, W = N / 2 + 1;
+    tw = (float2 *)a.template take<float2>(P);
+    thr = (float *)a.template take<float>(B);
+    r2 = (float *)a.template take<float>(B);
+    masked = (int32_t *)a.template take<int32_t>(B);
+    F = (float2 *)a.template take<float2>((size_t)B * P * P);
+    U = (float2 *)a.template take<float2>((size_t)B * W * P);
+    Cc = own_corr ? (float *)a.template take<float>((size_t)B * W * W) : nullptr;
+  }
+};
+
 // Size-only arena with the same interface as Arena.
 struct SizeArena {
   size_t off = 0;
@@ -264,6 +281,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
     case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
+    case MUSER_CALL_CENTER: { CenterWs<SizeArena> w; w.carve(a, B, *cfg, true); break; }
     default: return SIZE_MAX;
   }
   return a.off;
@@ -514,6 +532,26 @@ int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *re
   launch_chi2((const float2 *)pred, (const float2 *)obs, (const Rec *)rec, n_vis, inv_sigma2, (float2 *)resid,
               (float *)ws, nb, loss, (cudaStream_t)stream);
   return check_launch("muser_chi2");
+}
+
+int muser_center(const float *residual, const float *mu_a, const float *mu_b, const double *cell_rad, int B,
+                 const muser_config_t *cfg, float *corr_out, double *dlm_out, float *shift_out, void *ws,
+                 size_t ws_bytes, int32_t *status, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (cfg->N < 32) return fail(MUSER_ERR_UNSUPPORTED, "muser_center needs N >= 32");
+  if (!residual || !mu_a || !mu_b || !cell_rad || !dlm_out) return fail(MUSER_ERR_ARG, "muser_center: required pointer is NULL");
+  const size_t need = muser_workspace_size(MUSER_CALL_CENTER, B, 0, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  CenterWs<Arena> w;
+  w.carve(a, B, *cfg, true);
+  cudaStream_t s = (cudaStream_t)stream;
+  fft::launch_twiddles(w.tw, 2 * cfg->N, s);
+  launch_center(residual, mu_a, mu_b, cell_rad, B, cfg->N, w.tw, w.thr, w.r2, w.masked, w.F, w.U,
+                corr_out ? corr_out : w.Cc, dlm_out, shift_out, status, s);
+  return check_launch("muser_center");
 }
 
 }  // extern "C"

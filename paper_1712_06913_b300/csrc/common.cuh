@@ -174,4 +174,10 @@ void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t 
                  float2 *resid, float *partial, int n_part, float *loss, cudaStream_t s);
 int chi2_blocks(int64_t n_vis);
 
+// centring (center.cu): Cc [B][N/2+1][N/2+1], dlm [B][2], shift [B][2] (nullable); scratch
+// thr, r2 [B] f32, masked [B] i32, F [B][2N][2N] c64, U [B][N/2+1][2N] c64, tw [2N] twiddles.
+void launch_center(const float *R, const float *mu_a, const float *mu_b, const double *cell, int B, int N,
+                   const float2 *tw, float *thr, float *r2, int32_t *masked, float2 *F, float2 *U, float *Cc,
+                   double *dlm, float *shift, int32_t *status, cudaStream_t s);
+
 }  // namespace muser

@@ -461,3 +461,81 @@ def test_gradient_descent_imaging_vs_oracle_and_graph_replay(m):
     gd3 = GradientImaging(rec, obs, sigma, cfg, x0=x_before, eta=eta)
     gd3.step()
     assert float((gd3.x.detach() - x_replay).abs().max()) <= 1e-6 * float(x_replay.abs().max())
+
+
+# ------------------------------------------------------------------------------ disk centring (Sec. 4.2)
+def _centring_case(off_px, N=128, seed=110):
+    wl0 = synth.small_workload(n_ant=31, N=N, config_id=seed, bmax=600.0, snr=0)
+    cell = pipeline.cell_sizes(wl0)[0]
+    sky = synth.Sky(disk_lm=(off_px[0] * cell, off_px[1] * cell))
+    wl = synth.make_workload("c", wl0.ant_enu, wl0.pairs, wl0.ha, wl0.dec, wl0.freq, N, 4 * N,
+                             config_id=seed, skies=[sky], snr=30, bmax=600.0)
+    return wl, cell
+
+
+@pytest.mark.parametrize("off_px", [(5.0, -3.0), (-11.4, 7.6)])
+def test_center_correlation_and_shift_vs_oracle(m, off_px):
+    """muser_center on the oracle's pre-cleaned residual: the disk correlation over all
+    shifts within 1e-5 of its peak, the best shift and its parabolic refinement equal."""
+    import torch
+    from oracle import centering
+    wl, cell = _centring_case(off_px)
+    N = wl.N
+    rec = pipeline.records(wl)
+    ker = pipeline.spheroidal(7, 1024)
+    _, D, Bm, _ = pipeline.dirty(rec, N, 4 * N, ker)
+    mu_a, mu_b, _ = ogmm.sky_and_disk(D)
+    R, _, _ = oclean.hogbom(D, Bm, 0.1, mu_b, 1000)
+    # both sides decide the mask in FP32 from the same FP32 inputs
+    R32, a32, b32 = R.astype(np.float32), np.float32(mu_a), np.float32(mu_b)
+    thr = np.float32(0.5) * (a32 + b32)
+    r = centering.SUN_RADIUS / cell if hasattr(centering, "SUN_RADIUS") else 16 * np.pi / 180 / 60 / cell
+    d2 = ((np.arange(N) - N // 2)[:, None] ** 2 + (np.arange(N) - N // 2)[None, :] ** 2).astype(float)
+    assert np.abs(d2 - r * r).min() > 1e-3, "disk radius sits on a pixel-distance tie"
+    M = np.where(R32 > thr, R32, np.float32(0)).astype(np.float64)
+    S = centering.disk_model(N, r)
+    Cc = centering.correlation(M, S, N // 4)
+    cfg = m.Config(N=N, G=4 * N)
+    dlm, shift, corr, st = m.center(torch.tensor(R32[None], device="cuda"),
+                                    torch.tensor([a32], device="cuda"), torch.tensor([b32], device="cuda"),
+                                    np.array([cell]), cfg, want_corr=True)
+    Cg = _np(corr)[0]
+    assert np.abs(Cg - Cc).max() <= 1e-5 * np.abs(Cc).max()
+    sx, sy = centering.best_shift(Cc, N // 4)
+    gs = _np(shift)[0]
+    assert abs(gs[0] - sx) <= 1e-3 and abs(gs[1] - sy) <= 1e-3, (gs, sx, sy)
+    np.testing.assert_allclose(_np(dlm)[0], [gs[0] * cell, gs[1] * cell], rtol=1e-6)
+    assert int(_np(st)[0]) & m.ST_NO_DISK == 0
+
+
+def test_image_centred_end_to_end(m):
+    """GPU pipeline (dirty -> GMM -> CLEAN to the disk level -> centring -> corrected
+    re-imaging) against the oracle's disk_offset, and the known offset."""
+    from oracle import centering
+    off = (6.0, -4.0)
+    wl, cell = _centring_case(off)
+    N = wl.N
+    cfg = cfg_for(m, wl, max_iter=300)
+    cells = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    out, dlm, shift = m.image_centred(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cells, wl.vis, cfg,
+                                      flags=wl.flags)
+    rec = pipeline.records(wl)
+    ker = pipeline.spheroidal(7, 1024)
+    _, D, Bm, _ = pipeline.dirty(rec, N, 4 * N, ker)
+    mu_a, mu_b, _ = ogmm.sky_and_disk(D)
+    dl, dm, _, _, _ = centering.disk_offset(D, Bm, mu_a, mu_b, cell, wl.dec[0])
+    gs = _np(shift)[0]
+    assert abs(gs[0] - dl / cell) <= 0.05 and abs(gs[1] - dm / cell) <= 0.05, (gs, dl / cell, dm / cell)
+    assert abs(gs[0] - off[0]) <= 0.3 and abs(gs[1] - off[1]) <= 0.3
+    assert int(_np(out.n_comp)[0]) > 0
+
+
+def test_center_empty_mask(m):
+    import torch
+    N = 64
+    cfg = m.Config(N=N, G=4 * N)
+    R = torch.zeros((2, N, N), device="cuda")
+    mu = torch.ones(2, device="cuda")
+    dlm, shift, _, st = m.center(R, mu, mu, np.full(2, 1e-4), cfg)
+    assert np.array_equal(_np(dlm), np.zeros((2, 2)))
+    assert all(int(v) & m.ST_NO_DISK for v in _np(st))
