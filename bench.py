@@ -184,7 +184,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad"], default=None,
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0"], default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     ap.add_argument("--iters", type=int, default=100, help="CLEAN iterations of --case clean")
@@ -384,6 +384,8 @@ def run_case(case, n_inst=0, iters=100):
     grad:  10 eager gradient-descent steps of the 512^2 differentiable-imaging workload.
 
     clean: 148 instances of the MUSER-II batch (N = 1024), CLEAN with `iters` iterations.
+    image0: muser_image on MUSER-II instances with max_iter 0 (the preparation kernels of the
+            pipeline: uvw, strip sort, fused gridding + column pass, row pass, beam copies).
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -407,6 +409,17 @@ def run_case(case, n_inst=0, iters=100):
         return
     n_inst = n_inst or (148 if case == "clean" else 8)
     wl = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst)))
+    if case == "image0":
+        cfg0 = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=0, gain=wl.gain, lat_rad=wl.lat)
+        cell0 = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+        im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell0, wl.vis, cfg0, flags=wl.flags)
+        im.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        im.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "instances": n_inst, "s": time.perf_counter() - t0}))
+        return
     cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=iters, gain=wl.gain, lat_rad=wl.lat)
     cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
     rec, _, st = m.uvw(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)

@@ -345,23 +345,48 @@ class DegridPlan:
     """The measurement operator of one record set (fixed uv coverage) with its own workspace.
 
     The first call plans (kernel table, grid correction, twiddles, the adjoint's tap lists by
-    grid cell); later calls reuse the plan and only run the transforms.
+    grid cell); later calls reuse the plan and only run the transforms.  The configuration
+    structure, workspace and chi-square scratch are set up once, so an evaluation costs the
+    library calls only.
     """
 
     def __init__(self, rec, cfg: Config):
         self.rec, self.cfg = rec, cfg
+        self.n = rec.shape[0]
+        self.c = cfg.c()
         self.ws = Workspace()
+        self.w, self.wb = self.ws.get(workspace_size(CALL_DEGRID, 1, self.n, cfg))
+        self.cws = Workspace()
+        self.cw, self.cwb = self.cws.get(workspace_size(CALL_CHI2, 1, self.n, None))
         self.planned = False
+        self.lib = _lib.load()
+
+    def _flag(self, d):
+        f = d | (_lib.REUSE_PLAN if self.planned else 0)
+        self.planned = True
+        return f
 
     def forward(self, img):
-        out = degrid(_lib.FORWARD, self.rec, self.cfg, img=img, ws=self.ws, reuse_plan=self.planned)
-        self.planned = True
+        img = img.contiguous()
+        out = torch.empty(self.n, dtype=torch.complex64, device="cuda")
+        check(self.lib.muser_degrid(self._flag(_lib.FORWARD), _p(img), _p(self.rec), self.n, _p(out),
+                                    ctypes.byref(self.c), self.w, self.wb, _stream()))
         return out
 
     def adjoint(self, vis):
-        out = degrid(_lib.ADJOINT, self.rec, self.cfg, vis=vis, ws=self.ws, reuse_plan=self.planned)
-        self.planned = True
+        vis = vis.contiguous()
+        out = torch.empty((self.cfg.N, self.cfg.N), dtype=torch.float32, device="cuda")
+        check(self.lib.muser_degrid(self._flag(_lib.ADJOINT), _p(out), _p(self.rec), self.n, _p(vis),
+                                    ctypes.byref(self.c), self.w, self.wb, _stream()))
         return out
+
+    def chi2(self, pred, obs, inv_sigma2: float):
+        """(loss, residual seed) of predicted visibilities against obs (see muser_chi2)."""
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        resid = torch.empty(self.n, dtype=torch.complex64, device="cuda")
+        check(self.lib.muser_chi2(_p(pred.contiguous()), _p(obs.contiguous()), _p(self.rec), self.n,
+                                  float(inv_sigma2), _p(resid), _p(loss), self.cw, self.cwb, _stream()))
+        return loss[0], resid
 
 
 def chi2(pred, obs, rec, inv_sigma2: float, want_resid=True, ws: Workspace = None):

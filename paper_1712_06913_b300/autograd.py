@@ -30,8 +30,8 @@ class Degrid(torch.autograd.Function):
 
 class Chi2(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, pred, obs, rec, inv_sigma2):
-        loss, resid = api.chi2(pred.detach(), obs, rec, inv_sigma2, want_resid=True)
+    def forward(ctx, pred, obs, plan, inv_sigma2):
+        loss, resid = plan.chi2(pred.detach(), obs, inv_sigma2)
         ctx.save_for_backward(resid)
         return loss
 
@@ -43,7 +43,7 @@ class Chi2(torch.autograd.Function):
 
 def chi2_loss(img, plan, obs, inv_sigma2):
     """chi2(img) through both autograd functions (plan: api.DegridPlan of the records)."""
-    return Chi2.apply(Degrid.apply(img, plan), obs, plan.rec, inv_sigma2)
+    return Chi2.apply(Degrid.apply(img, plan), obs, plan, inv_sigma2)
 
 
 class GradientImaging:
