@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import test_oracle_pins as pins
-from oracle import clean, geometry, gmm, imaging, operator, pswf
+from oracle import clean, geometry, gmm, imaging, operator, pswf, steer
 
 
 def _fails(fn, *args):
@@ -104,3 +104,33 @@ def test_gmm_unweighted_variance_is_caught(monkeypatch):
         return orig(np.where(h > 0, 1.0, 0.0), x, width, K, max_iter, tol)   # counts dropped
     monkeypatch.setattr(gmm, "em", bad)
     _fails(pins.test_gmm_recovers_known_mixture)
+
+
+def test_steer_beam_not_recentred_is_caught(monkeypatch):
+    def bad(C, Bm):
+        N = C.shape[0]
+        P = 2 * N
+        Z = np.fft.ifft2(np.fft.fft2(C, (P, P)) * np.fft.fft2(Bm, (P, P))).real
+        return Z[N - 1:2 * N - 1, N:2 * N]      # off by one row
+    monkeypatch.setattr(steer, "convolve_beam", bad)
+    _fails(pins.test_steer_with_clip_one_is_hogbom)
+
+
+def test_steer_scaling_over_selection_only_is_caught(monkeypatch):
+    orig = steer.steer
+
+    def bad(D, Bm, gain, thr, cap, clip=0.9):
+        R = np.array(D, dtype=np.float64, copy=True)
+        model = np.zeros_like(R)
+        for c in range(cap):
+            m = R.max()
+            if m <= thr or m <= 0:
+                return R, model, c
+            C = np.where(R >= clip * m, R, 0.0)
+            Y = steer.convolve_beam(C, Bm)
+            a = gain * m / (gain * m + Y.max())   # wrong normalisation
+            R -= a * Y
+            model += a * C
+        return R, model, cap
+    monkeypatch.setattr(steer, "steer", bad)
+    _fails(pins.test_steer_linear_invariant_and_threshold)

@@ -12,7 +12,7 @@ import pytest
 from scipy.special import pro_ang1, pro_cv
 
 import synth
-from oracle import centering, clean, geometry, gmm, imaging, operator, pipeline, restore
+from oracle import centering, clean, geometry, gmm, imaging, operator, pipeline, restore, steer
 from oracle.pswf import Spheroidal
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -270,6 +270,43 @@ def test_hogbom_tie_break_and_abs_mode():
 
 
 # ----------------------------------------------------------------------------- restore
+# ----------------------------------------------------------------------------- Steer clean
+def test_steer_beam_convolution_fft_equals_bruteforce():
+    rng = np.random.default_rng(3)
+    N = 12
+    Bm = rng.normal(size=(2 * N, 2 * N))
+    C = np.where(rng.uniform(size=(N, N)) < 0.2, rng.normal(size=(N, N)), 0.0)
+    np.testing.assert_allclose(steer.convolve_beam(C, Bm), steer.convolve_beam_bruteforce(C, Bm), atol=1e-12)
+
+
+def test_steer_with_clip_one_is_hogbom():
+    """clip = 1 keeps the peak alone: every cycle is one Hogbom step with the same gain."""
+    wl = synth.small_workload(n_ant=10, N=32, config_id=131, bmax=300.0)
+    _, D, Bm, _ = pipeline.dirty(pipeline.records(wl), 32, 128, KER)
+    R_h, pos, flux = clean.hogbom(D, Bm, 0.1, -np.inf, 25)
+    R_s, model, cycles = steer.steer(D, Bm, 0.1, -np.inf, 25, clip=1.0)
+    assert cycles == 25
+    expect = np.zeros_like(D)
+    np.add.at(expect.ravel(), pos, flux)
+    np.testing.assert_allclose(model, expect, atol=1e-12 * np.abs(D).max())
+    np.testing.assert_allclose(R_s, R_h, atol=1e-12 * np.abs(D).max())
+
+
+def test_steer_linear_invariant_and_threshold():
+    """D = R + Bm * model after any number of cycles; the stop rule is the peak threshold."""
+    wl = synth.small_workload(n_ant=12, N=32, config_id=132, bmax=300.0)
+    _, D, Bm, _ = pipeline.dirty(pipeline.records(wl), 32, 128, KER)
+    R, model, cycles = steer.steer(D, Bm, 0.1, -np.inf, 30, clip=0.9)
+    assert cycles == 30 and np.count_nonzero(model) > 30      # several pixels per cycle
+    np.testing.assert_allclose(R + steer.convolve_beam(model, Bm), D, atol=1e-10 * np.abs(D).max())
+    thr = 0.5 * D.max()
+    R2, _, c2 = steer.steer(D, Bm, 0.1, thr, 1000, clip=0.9)
+    assert R2.max() <= thr and c2 > 0
+    # every cycle removes gain times the peak at most (the scaling of the subtraction)
+    Rp, _, _ = steer.steer(D, Bm, 0.1, -np.inf, 1, clip=0.9)
+    assert (D - Rp).max() == pytest.approx(0.1 * D.max(), rel=1e-12)
+
+
 def test_clean_beam_of_exact_gaussian():
     """The moment fit returns the covariance of a sampled Gaussian beam; the pixel
     lattice's boundary error shrinks with the lobe area (about 9 % at 27 pixels,
