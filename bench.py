@@ -20,6 +20,7 @@ Reported (one JSON line on rank 0):
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -326,6 +327,15 @@ def main():
             ec[1].record(stream)
             torch.cuda.synchronize()
             center_ms = ec[0].elapsed_time(ec[1])
+            # Steer clean (Sec. 3.2) of the same chunk, 20 major cycles at clip 0.9, timed alone
+            scfg = dataclasses.replace(cfg, max_iter=20)
+            m.steer(D, Bm, scfg, clip=0.9, ws=ws)
+            ec[0].record(stream)
+            _, _, snc, _ = m.steer(D, Bm, scfg, clip=0.9, ws=ws)
+            ec[1].record(stream)
+            torch.cuda.synchronize()
+            steer_ms = ec[0].elapsed_time(ec[1])
+            steer_cycles = int(snc.sum())
         iters = nc.cpu().numpy().astype(np.float64)
         # on-chip CLEAN: beam copies (read the 2N x 2N beam, write three shifted copies), residual
         # read and written once, one N x N beam window read per iteration
@@ -353,7 +363,12 @@ def main():
              "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum()),
              "graph_replay_images_per_s": graph_value,
              "center_ms_per_chunk": center_ms,
-             "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3)}
+             "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3),
+             "steer_ms_per_chunk_20_cycles": steer_ms, "steer_instance_cycles": steer_cycles,
+             "steer_us_per_instance_cycle": steer_ms * 1e3 / max(steer_cycles, 1),
+             # per instance-cycle: peak, selection and update read/write 32 N^2 bytes, the four FFT
+             # passes of side 2N move 160 N^2 (half-planes where C or Y is zero)
+             "steer_GBps": 192.0 * N * N * steer_cycles / (steer_ms / 1e3) / 1e9}
 
     if not args.no_extras and rank == 0:
         extra.update(plain_and_degrid(m, wl, cell, cfg, stream))

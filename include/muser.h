@@ -70,7 +70,7 @@ enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
 enum {
   MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
   MUSER_CALL_RESTORE = 5, MUSER_CALL_IMAGE = 6, MUSER_CALL_DEGRID = 7, MUSER_CALL_CHI2 = 8,
-  MUSER_CALL_CENTER = 9
+  MUSER_CALL_CENTER = 9, MUSER_CALL_STEER = 10
 };
 
 /* Imaging parameters (host struct, passed by pointer). */
@@ -255,6 +255,21 @@ MUSER_API int muser_chi2(const float *pred, const float *obs, const muser_vis_re
 MUSER_API int muser_center(const float *residual, const float *mu_a, const float *mu_b, const double *cell_rad, int B,
                            const muser_config_t *cfg, float *corr_out, double *dlm_out, float *shift_out, void *ws,
                            size_t ws_bytes, int32_t *status, muser_stream_t stream);
+
+/* Steer CLEAN (Steer, Dewdney & Ito 1984; the paper's production clean, Sec. 3.2 and Alg. 1,
+ * whose selection level and scaling the paper leaves open), in major cycles, per instance:
+ *   m = max R (signed); stop when m <= thr[b], m <= 0, or after cfg->max_iter cycles;
+ *   C = R where R >= clip m, else 0;  Y(q) = sum_p C(p) Bm(q - p + (N, N)) over the image;
+ *   a = cfg->gain m / max Y;  R -= a Y;  model += a C.
+ * With clip = 1 every cycle is one Hogbom step.  Y is computed with FFTs of side 2N.
+ * residual[B][N][N] (in: dirty map, out: residual), beam[B][2N][2N], thr[B] (NULL: no
+ * threshold, or the GMM sky level when cfg->thr_mode = 1), model[B][N][N] (out, zeroed by the
+ * call), n_cycles[B] (out).  0 < clip <= 1.  Every instance runs in the same launches: a batch
+ * enqueues 6 kernels per cycle up to cfg->max_iter cycles, and an instance that has stopped
+ * returns from them at once.  N <= 1024. */
+MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr,
+                          float clip, float *model, int32_t *n_cycles, void *ws, size_t ws_bytes, int32_t *status,
+                          muser_stream_t stream);
 
 #ifdef __cplusplus
 }

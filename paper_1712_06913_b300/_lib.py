@@ -13,7 +13,8 @@ MUSER_OK, MUSER_ERR_ARG, MUSER_ERR_CUDA, MUSER_ERR_TIMEOUT, MUSER_ERR_UNSUPPORTE
 (ST_ALL_FLAGGED, ST_NONFINITE, ST_DROPPED, ST_GMM_DEGENERATE, ST_ITER_CAP, ST_BEAM_FIT, ST_TIMEOUT,
  ST_NO_DISK) = 1, 2, 4, 8, 16, 32, 64, 128
 FORWARD, ADJOINT, REUSE_PLAN = 0, 1, 4
-CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2, CALL_CENTER = range(1, 10)
+(CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2, CALL_CENTER,
+ CALL_STEER) = range(1, 11)
 
 _ERRNAMES = {1: "MUSER_ERR_ARG", 2: "MUSER_ERR_CUDA", 3: "MUSER_ERR_TIMEOUT", 4: "MUSER_ERR_UNSUPPORTED",
              5: "MUSER_ERR_WORKSPACE"}
@@ -54,6 +55,7 @@ SIGNATURES = {
     "muser_degrid": (I32, [I32, P, P, I64, P, CFG, P, SZ, P]),
     "muser_chi2": (I32, [P, P, P, I64, F32, P, P, P, SZ, P]),
     "muser_center": (I32, [P, P, P, P, I32, CFG, P, P, P, P, SZ, P, P]),
+    "muser_steer": (I32, [P, P, I32, CFG, P, F32, P, P, P, SZ, P, P]),
 }
 
 _lib = None

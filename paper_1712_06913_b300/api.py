@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CALL_CENTER, CALL_CHI2, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
+from ._lib import CALL_CENTER, CALL_CHI2, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
 
 RECORD_FLOATS = 6          # 24-byte record viewed as float32[6]
 
@@ -194,6 +194,22 @@ def center(R, mu_a, mu_b, cell, cfg: Config, status=None, want_corr=False, ws: W
     check(_lib.load().muser_center(_p(R.contiguous()), _p(mu_a), _p(mu_b), _p(cl), B, ctypes.byref(c), _p(corr),
                                    _p(dlm), _p(shift), w, wb, _p(st), _stream()))
     return dlm, shift, corr, st
+
+
+def steer(D, Bm, cfg: Config, thr=None, clip=0.9, status=None, ws: Workspace = None):
+    """Steer CLEAN in major cycles (cfg.max_iter cycles at most): (residual, model, n_cycles,
+    status).  D is not modified."""
+    B, N = D.shape[0], cfg.N
+    R = D.clone()
+    model = torch.empty((B, N, N), dtype=torch.float32, device="cuda")
+    nc = torch.empty(B, dtype=torch.int32, device="cuda")
+    st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
+    th = _dev(thr, torch.float32) if thr is not None else None
+    c = cfg.c()
+    w, wb = (ws or _default_ws).get(workspace_size(CALL_STEER, B, 0, cfg))
+    check(_lib.load().muser_steer(_p(R), _p(Bm.contiguous()), B, ctypes.byref(c), _p(th), float(clip), _p(model),
+                                  _p(nc), w, wb, _p(st), _stream()))
+    return R, model, nc, st
 
 
 def restore(R, Bm, pos, flux, n_comp, cfg: Config, status=None):

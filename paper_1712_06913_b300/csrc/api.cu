@@ -196,6 +196,23 @@ struct CenterWs {
   }
 };
 
+template <class A>
+struct SteerWs {
+  float2 *tw, *FB, *F, *U;
+  float *Y, *mu;
+  void *state;
+  void carve(A &a, int B, const muser_config_t &c) {
+    const int N = c.N, P = 2 * N;
+    tw = (float2 *)a.template take<float2>(P);
+    FB = (float2 *)a.template take<float2>((size_t)B * P * P);
+    F = (float2 *)a.template take<float2>((size_t)B * P * P);
+    U = (float2 *)a.template take<float2>((size_t)B * N * P);
+    Y = (float *)a.template take<float>((size_t)B * N * N);
+    mu = (float *)a.template take<float>(2 * (size_t)B);
+    state = (void *)a.template take<unsigned char>((size_t)B * steer_state_bytes());
+  }
+};
+
 // Size-only arena with the same interface as Arena.
 struct SizeArena {
   size_t off = 0;
@@ -282,6 +299,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
     case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
     case MUSER_CALL_CENTER: { CenterWs<SizeArena> w; w.carve(a, B, *cfg, true); break; }
+    case MUSER_CALL_STEER: { SteerWs<SizeArena> w; w.carve(a, B, *cfg); break; }
     default: return SIZE_MAX;
   }
   return a.off;
@@ -552,6 +570,31 @@ int muser_center(const float *residual, const float *mu_a, const float *mu_b, co
   launch_center(residual, mu_a, mu_b, cell_rad, B, cfg->N, w.tw, w.thr, w.r2, w.masked, w.F, w.U,
                 corr_out ? corr_out : w.Cc, dlm_out, shift_out, status, s);
   return check_launch("muser_center");
+}
+
+int muser_steer(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr, float clip,
+                float *model, int32_t *n_cycles, void *ws, size_t ws_bytes, int32_t *status, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 0) return fail(MUSER_ERR_ARG, "negative sizes");
+  if (B == 0) return MUSER_OK;
+  if (cfg->N < 32) return fail(MUSER_ERR_UNSUPPORTED, "muser_steer needs N >= 32");
+  if (!(clip > 0.f && clip <= 1.f)) return fail(MUSER_ERR_ARG, "clip must be in (0, 1]");
+  if (!residual || !beam || !model || !n_cycles) return fail(MUSER_ERR_ARG, "muser_steer: required pointer is NULL");
+  const size_t need = muser_workspace_size(MUSER_CALL_STEER, B, 0, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  SteerWs<Arena> w;
+  w.carve(a, B, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const float *t = thr;
+  if (!thr && cfg->thr_mode == 1) {
+    launch_gmm(residual, B, cfg->N, cfg->gmm_bins, w.mu, w.mu + B, status, s);
+    t = w.mu;
+  }
+  fft::launch_twiddles(w.tw, 2 * cfg->N, s);
+  launch_steer(residual, beam, B, cfg->N, cfg->gain, cfg->max_iter, t, clip, model, n_cycles, w.tw, w.FB, w.F, w.U,
+               w.Y, w.state, status, s);
+  return check_launch("muser_steer");
 }
 
 }  // extern "C"

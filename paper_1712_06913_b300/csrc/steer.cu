@@ -1,0 +1,330 @@
+// Steer CLEAN (Steer, Dewdney & Ito 1984) in major cycles: the paper's production clean
+// (Sec. 3.2 "Steer clean", Alg. 1), with the selection and scaling it leaves open read as:
+//   m = max R; stop when m <= thr, m <= 0, or after cap cycles (per instance);
+//   C = R where R >= clip m, else 0;   Y(q) = sum_p C(p) Bm(q - p + (N, N)) over the image;
+//   a = gain m / max Y;   R -= a Y;   model += a C.
+// (clip = 1 keeps the peak alone and a = gain: one Hogbom step.)
+//
+// Y comes from circular convolutions of side P = 2N: C (N x N at the origin) with the beam
+// (2N x 2N): Y(q) = (C (*) Bm)(q + (N, N)), nothing wraps.  The beam spectrum FB is computed
+// once per call.  Per cycle (every instance of the batch at once; an instance that has stopped
+// returns from every kernel at once):
+//   k_st_peak   block max of R -> m, threshold, active flag, reset of max Y;
+//   k_st_cols   forward column pass of C (only the N columns and rows where C can be non-zero);
+//   k_st_rows   forward row pass, multiplied by FB on the way out;
+//   k_st_icols  inverse column pass, output rows N .. 2N - 1 only;
+//   k_st_irows  inverse row pass, output columns N .. 2N - 1 only -> Y (/ P^2), block maxima of Y;
+//   k_st_update R -= a Y, model += a C (C re-derived from the same R and threshold).
+#include "fft.cuh"
+
+namespace muser {
+
+namespace {
+
+using fft::ColCfg;
+using fft::RowCfg;
+
+// order-preserving float <-> int for atomicMax on a float
+__device__ __forceinline__ int ordered(float v) {
+  const int i = __float_as_int(v);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+struct SteerState {      // per instance
+  float m, tau;
+  int ymax;              // ordered(max Y)
+  int active;
+  int cycles;
+};
+
+// beam spectrum: columns (pass 1) then rows (pass 2) of the real 2N x 2N beam
+template <int P>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_beam_cols(const float *__restrict__ beam, const float2 *__restrict__ tw,
+                                                               float2 *__restrict__ FB) {
+  using C = ColCfg<P>;
+  constexpr int S = C::S, NT = C::NT;
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  const float *Bi = beam + (size_t)inst * P * P;
+  struct Load {
+    const float *Bi;
+    int x0;
+    __device__ float2 operator()(int i, int s) const { return make_float2(Bi[(size_t)i * P + x0 + s], 0.f); }
+  } load{Bi, x0};
+  float2 *Fi = FB + (size_t)inst * P * P;
+  struct Store {
+    float2 *Fi;
+    int x0;
+    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)o * P + x0 + s] = v; }
+  } store{Fi, x0};
+  fft::run<P, S, NT, -1, true, typename C::Layout>(sm, tw, load, store);
+}
+
+template <int P>
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_beam_rows(const float2 *__restrict__ tw, float2 *__restrict__ FB) {
+  using C = RowCfg<P>;
+  constexpr int S = C::S, NT = C::NT;
+  __shared__ float2 sm[C::Layout::size];
+  const int inst = blockIdx.y, y0 = blockIdx.x * S;
+  float2 *Fi = FB + (size_t)inst * P * P;
+  struct Load {
+    const float2 *Fi;
+    int y0;
+    __device__ float2 operator()(int i, int s) const { return Fi[(size_t)(y0 + s) * P + i]; }
+  } load{Fi, y0};
+  struct Store {
+    float2 *Fi;
+    int y0;
+    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)(y0 + s) * P + o] = v; }
+  } store{Fi, y0};
+  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);   // in place (loads precede stores)
+}
+
+__global__ void __launch_bounds__(1024) k_st_peak(const float *__restrict__ R, int N, int cap, const float *__restrict__ thr,
+                                                  float clip, SteerState *__restrict__ st) {
+  __shared__ float red[32];
+  const int inst = blockIdx.x;
+  SteerState &S = st[inst];
+  if (!S.active) return;                                // (uniform per block)
+  const float *Ri = R + (size_t)inst * N * N;
+  float m = -CUDART_INF_F;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) m = fmaxf(m, Ri[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 32; w++) m = fmaxf(m, red[w]);
+    const float t = thr ? thr[inst] : -CUDART_INF_F;
+    if (S.cycles >= cap || !(m > t) || !(m > 0.f)) {
+      S.active = 0;
+    } else {
+      S.m = m;
+      S.tau = clip * m;
+      S.ymax = ordered(-CUDART_INF_F);
+    }
+  }
+}
+
+// forward column pass of C = R [R >= tau] (columns and rows < N)
+template <int P>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restrict__ R, const SteerState *__restrict__ st,
+                                                          const float2 *__restrict__ tw, float2 *__restrict__ F) {
+  using C = ColCfg<P>;
+  constexpr int N = P / 2, S = C::S, NT = C::NT;
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  if (!st[inst].active) return;
+  const float *Ri = R + (size_t)inst * N * N;
+  struct Load {
+    const float *Ri;
+    float tau;
+    int x0;
+    __device__ float2 operator()(int i, int s) const {
+      const int x = x0 + s;
+      if (i >= N || x >= N) return make_float2(0.f, 0.f);
+      const float r = Ri[(size_t)i * N + x];
+      return make_float2(r >= tau ? r : 0.f, 0.f);
+    }
+  } load{Ri, st[inst].tau, x0};
+  float2 *Fi = F + (size_t)inst * P * P;
+  struct Store {
+    float2 *Fi;
+    int x0;
+    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)o * P + x0 + s] = v; }
+  } store{Fi, x0};
+  fft::run<P, S, NT, -1, true, typename C::Layout>(sm, tw, load, store);
+}
+
+// forward row pass (columns >= N of pass 1 are zero), times the beam spectrum, in place
+template <int P>
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_rows(const SteerState *__restrict__ st, const float2 *__restrict__ tw,
+                                                          const float2 *__restrict__ FB, float2 *__restrict__ F) {
+  using C = RowCfg<P>;
+  constexpr int N = P / 2, S = C::S, NT = C::NT;
+  __shared__ float2 sm[C::Layout::size];
+  const int inst = blockIdx.y, y0 = blockIdx.x * S;
+  if (!st[inst].active) return;
+  float2 *Fi = F + (size_t)inst * P * P;
+  const float2 *Bi = FB + (size_t)inst * P * P;
+  struct Load {
+    const float2 *Fi;
+    int y0;
+    __device__ float2 operator()(int i, int s) const {
+      return i < N ? Fi[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
+    }
+  } load{Fi, y0};
+  struct Store {
+    float2 *Fi;
+    const float2 *Bi;
+    int y0;
+    __device__ void operator()(int o, int s, float2 v) const {
+      const size_t k = (size_t)(y0 + s) * P + o;
+      Fi[k] = cmul(v, Bi[k]);
+    }
+  } store{Fi, Bi, y0};
+  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
+}
+
+// inverse column pass, output rows N .. 2N - 1 -> U[row - N][P]
+template <int P>
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_icols(const SteerState *__restrict__ st, const float2 *__restrict__ F,
+                                                           const float2 *__restrict__ tw, float2 *__restrict__ U) {
+  using C = ColCfg<P>;
+  constexpr int N = P / 2, S = C::S, NT = C::NT;
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  if (!st[inst].active) return;
+  const float2 *Fi = F + (size_t)inst * P * P;
+  float2 *Ui = U + (size_t)inst * N * P;
+  struct Load {
+    const float2 *Fi;
+    int x0;
+    __device__ float2 operator()(int i, int s) const { return Fi[(size_t)i * P + x0 + s]; }
+  } load{Fi, x0};
+  struct Store {
+    float2 *Ui;
+    int x0;
+    __device__ void operator()(int o, int s, float2 v) const {
+      if (o >= N) Ui[(size_t)(o - N) * P + x0 + s] = v;
+    }
+  } store{Ui, x0};
+  fft::run<P, S, NT, +1, true, typename C::Layout>(sm, tw, load, store);
+}
+
+// inverse row pass, output columns N .. 2N - 1 -> Y (real part / P^2), and max Y
+template <int P>
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_irows(SteerState *__restrict__ st, const float2 *__restrict__ U,
+                                                           const float2 *__restrict__ tw, float *__restrict__ Y) {
+  using C = RowCfg<P>;
+  constexpr int N = P / 2, S = C::S, NT = C::NT;
+  __shared__ float2 sm[C::Layout::size];
+  __shared__ float red[NT / 32 > 0 ? NT / 32 : 1];
+  const int inst = blockIdx.y, y0 = blockIdx.x * S;
+  if (!st[inst].active) return;
+  const float2 *Ui = U + (size_t)inst * N * P;
+  float *Yi = Y + (size_t)inst * N * N;
+  struct Load {
+    const float2 *Ui;
+    int y0;
+    __device__ float2 operator()(int i, int s) const { return Ui[(size_t)(y0 + s) * P + i]; }
+  } load{Ui, y0};
+  struct Store {
+    float *Yi;
+    int y0;
+    float mx;
+    __device__ void operator()(int o, int s, float2 v) {
+      if (o < N) return;
+      const float y = v.x * (1.f / ((float)P * (float)P));
+      Yi[(size_t)(y0 + s) * N + (o - N)] = y;
+      mx = fmaxf(mx, y);
+    }
+  } store{Yi, y0, -CUDART_INF_F};
+  fft::run<P, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+  float m = store.mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < NT / 32; w++) m = fmaxf(m, red[w]);
+    atomicMax(&st[inst].ymax, ordered(m));
+  }
+}
+
+// R -= a Y, model += a C; one block row per instance slice
+__global__ void k_st_update(float *__restrict__ R, const float *__restrict__ Y, float *__restrict__ model, int N,
+                            float gain, SteerState *__restrict__ st) {
+  const int inst = blockIdx.y;
+  SteerState &S = st[inst];
+  if (!S.active) return;
+  const float ym = unordered(S.ymax);
+  if (!(ym > 0.f)) {                                    // nothing to subtract: the instance stops
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.active = 0;
+    return;
+  }
+  const float a = gain * S.m / ym, tau = S.tau;
+  const size_t base = (size_t)inst * N * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N; i += gridDim.x * blockDim.x) {
+    const float r = R[base + i];
+    if (r >= tau) model[base + i] += a * r;
+    R[base + i] = r - a * Y[base + i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) S.cycles++;
+}
+
+__global__ void k_st_init(SteerState *__restrict__ st, int B, const int32_t *__restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B) return;
+  st[i].active = status && (status[i] & MUSER_ST_ALL_FLAGGED) ? 0 : 1;
+  st[i].cycles = 0;
+  st[i].m = 0.f;
+  st[i].tau = 0.f;
+  st[i].ymax = 0;
+}
+
+__global__ void k_st_finish(const SteerState *__restrict__ st, int B, int32_t *__restrict__ n_cycles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B) n_cycles[i] = st[i].cycles;
+}
+
+template <int P>
+void steer_P(float *R, const float *beam, int B, float gain, int cap, const float *thr, float clip, float *model,
+             int32_t *n_cycles, const float2 *tw, float2 *FB, float2 *F, float2 *U, float *Y, SteerState *st,
+             const int32_t *status, cudaStream_t s) {
+  using CC = ColCfg<P>;
+  using RC = RowCfg<P>;
+  constexpr int N = P / 2;
+  const dim3 g1(B);
+  cudaFuncSetAttribute(k_st_beam_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_st_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_st_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaMemsetAsync(model, 0, sizeof(float) * (size_t)B * N * N, s);
+  k_st_init<<<(B + 255) / 256, 256, 0, s>>>(st, B, status);
+  note_launch();
+  k_st_beam_cols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(beam, tw, FB);
+  note_launch();
+  k_st_beam_rows<P><<<dim3(P / RC::S, B), RC::NT, 0, s>>>(tw, FB);
+  note_launch();
+  for (int c = 0; c < cap; c++) {
+    k_st_peak<<<g1, 1024, 0, s>>>(R, N, cap, thr, clip, st);
+    note_launch();
+    k_st_cols<P><<<dim3((N + CC::S - 1) / CC::S, B), CC::NT, CC::smem, s>>>(R, st, tw, F);
+    note_launch();
+    k_st_rows<P><<<dim3(P / RC::S, B), RC::NT, 0, s>>>(st, tw, FB, F);
+    note_launch();
+    k_st_icols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(st, F, tw, U);
+    note_launch();
+    k_st_irows<P><<<dim3(N / RC::S, B), RC::NT, 0, s>>>(st, U, tw, Y);
+    note_launch();
+    k_st_update<<<dim3((N * N + 1023) / 1024 < 64 ? (N * N + 1023) / 1024 : 64, B), 1024, 0, s>>>(R, Y, model, N,
+                                                                                                 gain, st);
+    note_launch();
+  }
+  k_st_finish<<<(B + 255) / 256, 256, 0, s>>>(st, B, n_cycles);
+  note_launch();
+}
+
+}  // namespace
+
+size_t steer_state_bytes() { return sizeof(SteerState); }
+
+void launch_steer(float *R, const float *beam, int B, int N, float gain, int cap, const float *thr, float clip,
+                  float *model, int32_t *n_cycles, const float2 *tw, float2 *FB, float2 *F, float2 *U, float *Y,
+                  void *state, const int32_t *status, cudaStream_t s) {
+  if (B <= 0) return;
+  SteerState *st = (SteerState *)state;
+  switch (2 * N) {
+#define MUSER_CASE(p) \
+  case p: steer_P<p>(R, beam, B, gain, cap, thr, clip, model, n_cycles, tw, FB, F, U, Y, st, status, s); break;
+    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048)
+#undef MUSER_CASE
+    default: break;
+  }
+}
+
+}  // namespace muser

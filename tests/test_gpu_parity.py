@@ -539,3 +539,152 @@ def test_center_empty_mask(m):
     dlm, shift, _, st = m.center(R, mu, mu, np.full(2, 1e-4), cfg)
     assert np.array_equal(_np(dlm), np.zeros((2, 2)))
     assert all(int(v) & m.ST_NO_DISK for v in _np(st))
+
+
+# ------------------------------------------------------------------------------ Steer CLEAN
+def _oracle_maps(wl):
+    """FP32 copies of the oracle's dirty maps and beams: both sides start from the same values."""
+    ro = oracle_records(wl)
+    out = []
+    for i in range(wl.n_inst):
+        ri = geometry.instance_slice(ro, i, wl.n_bl)
+        Do, Bo, _ = imaging.dirty_and_beam(imaging.grid(ri, wl.G, KER), wl.N, KER)
+        out.append((Do.astype(np.float32), Bo.astype(np.float32)))
+    return out
+
+
+def _steer_inputs(m, maps):
+    import torch
+    D = torch.tensor(np.stack([d for d, _ in maps]), device="cuda")
+    Bm = torch.tensor(np.stack([b for _, b in maps]), device="cuda")
+    return D, Bm
+
+
+def _oracle_steer_chain(D, Bo, gain, clip, cap, thr=-np.inf):
+    """The oracle's Steer clean run one cycle at a time, with the smallest distance (relative to
+    the peak) of any pixel from the selection level (clip < 1) or of the runner-up from the peak
+    (clip = 1) over the run."""
+    from oracle import steer as osteer
+    R = D.astype(np.float64)
+    model = np.zeros_like(R)
+    cycles, gap = 0, np.inf
+    for _ in range(cap):
+        mx = R.max()
+        if clip < 1:
+            gap = min(gap, np.abs(R - clip * mx).min() / mx)
+        else:
+            s = np.partition(R.ravel(), -2)[-2:]
+            gap = min(gap, (s[1] - s[0]) / mx)
+        R, md, c = osteer.steer(R, Bo.astype(np.float64), gain, thr, 1, clip)
+        if c == 0:
+            break
+        model += md
+        cycles += 1
+    return R, model, cycles, gap
+
+
+@pytest.mark.parametrize("name,clip,cycles", [("small-N64", 0.9, 16), ("small-N32-3frames", 0.7, 40),
+                                              ("plain-N256", 0.7, 6), ("N1024x1", 0.8, 2)])
+def test_steer_cycle_lockstep(m, name, clip, cycles):
+    """One major cycle at a time from the GPU's own residual: C is decided in FP32 from the same
+    FP32 residual on both sides (so near-ties cannot split them); Y, a and the update follow
+    the oracle's FP64 convolution."""
+    from oracle import steer as osteer
+    wl = (synth.config3_muser2_uneven(n_frame=1, chans=[7]) if name == "N1024x1" else WORKLOADS[name]())
+    maps = _oracle_maps(wl)
+    N = wl.N
+    cfg = m.Config(N=N, G=4 * N)
+    cfg.max_iter = 1
+    R, Bm = _steer_inputs(m, maps)
+    for _ in range(cycles):
+        Rp = _np(R)
+        R, model, nc, _ = m.steer(R, Bm, cfg, clip=clip)
+        Rg, Mg, ncg = _np(R), _np(model), _np(nc)
+        for i, (_, Bo) in enumerate(maps):
+            r = Rp[i]
+            mx = r.max()
+            tau = np.float32(clip) * mx
+            C = np.where(r >= tau, r, np.float32(0)).astype(np.float64)
+            Y = osteer.convolve_beam(C, Bo.astype(np.float64))
+            a = cfg.gain * float(mx) / Y.max()
+            assert ncg[i] == 1
+            scale = float(np.abs(r).max())
+            assert np.abs(Rg[i] - (r - a * Y)).max() <= 1e-5 * scale
+            assert np.array_equal(Mg[i] != 0, C != 0)
+            assert np.abs(Mg[i] - a * C).max() <= 1e-5 * np.abs(a * C).max()
+
+
+@pytest.mark.parametrize("name,clip,cap", [("small-N64", 0.9, 12), ("small-N32-3frames", 0.9, 40),
+                                           ("plain-N256", 0.9, 15), ("small-N64", 1.0, 60),
+                                           ("plain-N256", 1.0, 60)])
+def test_steer_vs_oracle(m, name, clip, cap):
+    """Whole runs against the oracle (runs with no pixel within 1e-5 of the peak of its selection
+    level, so FP32 and FP64 choose the same maps): cycle counts equal, residual and model
+    within 1e-4 of the peak, and D = R + Bm * model.  With clip = 1 the cycles are Hogbom steps:
+    the model equals the oracle Hogbom components accumulated into a map."""
+    from oracle import steer as osteer
+    wl = WORKLOADS[name]()
+    maps = _oracle_maps(wl)
+    cfg = m.Config(N=wl.N, G=4 * wl.N)
+    cfg.max_iter = cap
+    D, Bm = _steer_inputs(m, maps)
+    R, model, nc, st = m.steer(D, Bm, cfg, clip=clip)
+    Rg, Mg, ncg = _np(R), _np(model), _np(nc)
+    for i, (Do, Bo) in enumerate(maps):
+        Ro, Mo, co, gap = _oracle_steer_chain(Do, Bo, cfg.gain, clip, cap)
+        assert gap > 1e-5, "the oracle run has a near-tie at its selection level"
+        peak = float(np.abs(Do).max())
+        assert ncg[i] == co == cap
+        assert np.abs(Rg[i] - Ro).max() <= 1e-4 * peak
+        assert np.abs(Mg[i] - Mo).max() <= 1e-4 * peak
+        resid = Do.astype(np.float64) - Rg[i] - osteer.convolve_beam(Mg[i].astype(np.float64), Bo.astype(np.float64))
+        assert np.abs(resid).max() <= 1e-4 * peak
+        if clip == 1.0:
+            _, po, fo = oclean.hogbom(Do.astype(np.float64), Bo.astype(np.float64), cfg.gain, -np.inf, cap)
+            Mh = np.zeros_like(Mo)
+            np.add.at(Mh, (po[:, 0], po[:, 1]) if po.ndim == 2 else np.unravel_index(po, Mh.shape), fo)
+            assert np.array_equal(Mg[i] != 0, Mh != 0)
+            assert np.abs(Mg[i] - Mh).max() <= 1e-4 * peak
+
+
+def test_steer_thresholds_batch_and_edges(m):
+    """Per-instance thresholds stop instances at different cycles (as in the oracle); a batch
+    equals its instances run alone, bit for bit; the GMM threshold mode equals passing the GMM
+    sky level; flagged instances, all-negative maps and a zero beam run no cycle."""
+    import torch
+    wl = WORKLOADS["small-N32-3frames"]()
+    maps = _oracle_maps(wl)
+    cfg = m.Config(N=wl.N, G=4 * wl.N)
+    cfg.max_iter = 200
+    D, Bm = _steer_inputs(m, maps)
+    peaks = np.array([d.max() for d, _ in maps])
+    thr = np.float32([0.5, 0.2, 0.05, 0.3, 0.1, 0.02]) * peaks.astype(np.float32)
+    R, model, nc, _ = m.steer(D, Bm, cfg, thr=thr, clip=0.9)
+    ncg = _np(nc)
+    for i, (Do, Bo) in enumerate(maps):
+        _, _, co, _ = _oracle_steer_chain(Do, Bo, cfg.gain, 0.9, 200, thr=float(thr[i]))
+        assert abs(int(ncg[i]) - co) <= 1
+        assert _np(R)[i].max() <= thr[i] or ncg[i] == 200
+    assert ncg[0] < ncg[1] < ncg[2]
+    for i in range(len(maps)):
+        R1, M1, n1, _ = m.steer(D[i:i + 1], Bm[i:i + 1], cfg, thr=thr[i:i + 1], clip=0.9)
+        assert torch.equal(R1[0], R[i]) and torch.equal(M1[0], model[i]) and int(n1[0]) == int(nc[i])
+    # GMM threshold mode
+    cfg.thr_mode = 1
+    mu_a, _, _ = m.gmm(D, cfg)
+    Ra, Ma, na, _ = m.steer(D, Bm, cfg, clip=0.9)
+    cfg.thr_mode = 0
+    Rb, Mb, nb, _ = m.steer(D, Bm, cfg, thr=mu_a, clip=0.9)
+    assert torch.equal(Ra, Rb) and torch.equal(Ma, Mb) and torch.equal(na, nb)
+    # edges
+    st = torch.tensor([m.ST_ALL_FLAGGED, 0, 0], dtype=torch.int32, device="cuda")
+    D, Bm = D[:3], Bm[:3]
+    Dn = D.clone()
+    Dn[1] = -Dn[1].abs() - 1.0
+    Bz = Bm.clone()
+    Bz[2] = 0
+    R, model, nc, _ = m.steer(Dn, Bz, cfg, clip=0.9, status=st)
+    assert _np(nc).tolist() == [0, 0, 0]
+    assert torch.equal(R, Dn) and float(model.abs().max()) == 0.0
+    R, model, nc, _ = m.steer(D[:0], Bm[:0], cfg)
+    assert nc.numel() == 0
