@@ -53,7 +53,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("clean.cu", "common.cuh"):
+    for name in ("clean.cu",):
         with open(os.path.join(ROOT, "paper_1712_06913_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -185,7 +185,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0"], default=None,
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer"], default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     ap.add_argument("--iters", type=int, default=100, help="CLEAN iterations of --case clean")
@@ -401,6 +401,7 @@ def run_case(case, n_inst=0, iters=100):
     clean: 148 instances of the MUSER-II batch (N = 1024), CLEAN with `iters` iterations.
     image0: muser_image on MUSER-II instances with max_iter 0 (the preparation kernels of the
             pipeline: uvw, strip sort, fused gridding + column pass, row pass, beam copies).
+    steer: `n_inst` instances (default 8), Steer clean with `iters` major cycles at clip 0.9.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -455,6 +456,18 @@ def run_case(case, n_inst=0, iters=100):
         Bm[c0:c0 + n] = b
         del Z, d, b
     torch.cuda.synchronize()
+    if case == "steer":
+        cfg.max_iter = iters
+        m.steer(D, Bm, cfg, clip=0.9, ws=ws)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R, model, nc, s2 = m.steer(D, Bm, cfg, clip=0.9, ws=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        cyc = int(nc.sum())
+        print(json.dumps({"case": case, "instances": n_inst, "steer_ms": e0.elapsed_time(e1), "instance_cycles": cyc,
+                          "us_per_instance_cycle": e0.elapsed_time(e1) * 1e3 / max(cyc, 1),
+                          "GBps": 192.0 * N * N * cyc / (e0.elapsed_time(e1) / 1e3) / 1e9}))
     if case == "clean":
         ws.buf = None
         torch.cuda.empty_cache()
