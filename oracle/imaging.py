@@ -123,3 +123,47 @@ def direct_dirty(rec, N: int, cell: float, weights=None):
     for y in range(2 * N):
         Bm[y] = (np.cos(2 * math.pi * (np.outer(lb, u) + (lb[y] * v)[None, :])) * wk[None, :]).sum(1) / sw
     return D, Bm
+
+
+def grid_cells(rec, G: int, ker: Spheroidal, weights=None):
+    """The non-zero cells of `grid` as (kv, ku, value) arrays: the same taps and values, kept
+    sparse so that grids too large to hold densely (G up to 20480) can be evaluated."""
+    h = (ker.W - 1) // 2
+    w = rec["w"] if weights is None else weights
+    keep = np.nonzero(rec["w"] > 0)[0]
+    taps = np.arange(-h, h + 1)
+    kvs, kus, vals = [], [], []
+    for i in keep:
+        wk = w[i] * np.outer(ker.kernel(taps + rec["fv"][i]), ker.kernel(taps + rec["fu"][i]))
+        ku, kv, V = rec["ku"][i], rec["kv"][i], rec["vis"][i]
+        rr, cc = np.meshgrid(kv + taps, ku + taps, indexing="ij")
+        kvs += [rr.ravel(), (G - rr).ravel()]
+        kus += [cc.ravel(), (G - cc).ravel()]
+        vals += [(wk * (V + 1j)).ravel(), (wk * (np.conj(V) + 1j)).ravel()]
+    if not kvs:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, np.complex128)
+    kv, ku, val = np.concatenate(kvs), np.concatenate(kus), np.concatenate(vals)
+    key, inv = np.unique(kv * G + ku, return_inverse=True)
+    acc = np.zeros(len(key), np.complex128)
+    np.add.at(acc, inv, val)
+    return key // G, key % G, acc
+
+
+def dirty_and_beam_at(rec, G: int, N: int, ker: Spheroidal, dirty_px, beam_px):
+    """Selected pixels of `dirty_and_beam`, each the centred inverse DFT of the sparse grid at
+    one point: dirty_px [n, 2] (y, x) of the N x N map, beam_px [m, 2] of the 2N x 2N beam.
+    Returns (D values, Bm values, norm)."""
+    kv, ku, val = grid_cells(rec, G, ker)
+    gc = ker.grid_correction(G)
+    norm = val.imag.sum() / gc[G // 2] ** 2     # Im I at the grid centre: every phase factor is 1
+
+    def at(y, x):
+        ph = np.exp(2j * math.pi * ((ku - G // 2) * (x - G // 2) + (kv - G // 2) * (y - G // 2)) / G)
+        return (val * ph).sum() / (gc[x] * gc[y])
+
+    lo_d, lo_b = G // 2 - N // 2, G // 2 - N
+    D = np.array([at(lo_d + y, lo_d + x).real for y, x in np.asarray(dirty_px).reshape(-1, 2)])
+    Bm = np.array([at(lo_b + y, lo_b + x).imag for y, x in np.asarray(beam_px).reshape(-1, 2)])
+    if norm == 0:
+        return np.zeros_like(D), np.zeros_like(Bm), 0.0
+    return D / norm, Bm / norm, norm

@@ -41,10 +41,16 @@ enum Mode { IMAGING, DEGRID };
 int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (!cfg) return fail(MUSER_ERR_ARG, "cfg is NULL");
   const int N = cfg->N, G = cfg->G;
-  if (!is_pow2(N) || N < 16 || N > 1024) return fail(MUSER_ERR_ARG, "N must be a power of two in [16, 1024]");
+  // image sides: 2^a in [16, 1024], or for imaging 5 * 2^a in [160, 5120] (the 1280, 2560 and
+  // 5120 pixel images of the high bands, Table 2)
+  const bool n2 = is_pow2(N) && N >= 16 && N <= 1024;
+  const bool n5 = N % 5 == 0 && is_pow2(N / 5) && N >= 160 && N <= 5120;
+  if (!n2 && !(n5 && mode == IMAGING))
+    return fail(MUSER_ERR_ARG, mode == IMAGING ? "N must be 2^a in [16, 1024] or 5 * 2^a in [160, 5120]"
+                                                : "N must be a power of two in [16, 1024]");
   if (mode == IMAGING && G != 4 * N) return fail(MUSER_ERR_ARG, "imaging needs G = 4 N");
   if (mode == DEGRID && G != 2 * N) return fail(MUSER_ERR_ARG, "degridding needs G = 2 N");
-  if (G < 64 || G > 4096) return fail(MUSER_ERR_UNSUPPORTED, "G must be in [64, 4096]");
+  if (n2 && (G < 64 || G > 4096)) return fail(MUSER_ERR_UNSUPPORTED, "G must be in [64, 4096]");
   if (cfg->W < 3 || cfg->W > 9 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "W must be odd in [3, 9]");
   if (cfg->os < 16 || cfg->os > 4096) return fail(MUSER_ERR_ARG, "os must be in [16, 4096]");
   if (cfg->weight_mode != 0) return fail(MUSER_ERR_UNSUPPORTED, "only natural weighting (weight_mode 0) is implemented");
@@ -204,7 +210,7 @@ struct SteerWs {
   void carve(A &a, int B, const muser_config_t &c) {
     const int N = c.N, P = 2 * N;
     tw = (float2 *)a.template take<float2>(P);
-    FB = (float2 *)a.template take<float2>((size_t)B * P * P);
+    FB = (float2 *)a.template take<float2>((size_t)B * P * (P / 2 + 1));
     F = (float2 *)a.template take<float2>((size_t)B * P * P);
     U = (float2 *)a.template take<float2>((size_t)B * N * P);
     Y = (float *)a.template take<float>((size_t)B * N * N);

@@ -68,7 +68,8 @@ template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_rows(const float2 *__restrict__ tw, float2 *__restrict__ F) {
   using C = RowCfg<P>;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
-  __shared__ float2 sm[C::Layout::size];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
   float2 *Fi = F + (size_t)inst * P * P;
   struct Load {
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_irows(const float2 *__res
                                                             float *__restrict__ Cc) {
   using C = RowCfg<P>;
   constexpr int N = P / 2, SM = N / 4, W = 2 * SM + 1, S = C::S, NT = C::NT;
-  __shared__ float2 sm[C::Layout::size];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
   const float2 *Ui = U + (size_t)inst * W * P;
   float *Ci = Cc + (size_t)inst * W * W;
@@ -265,13 +267,15 @@ void center_P(const float *R, const float *mu_a, const float *mu_b, const double
   note_launch();
   cudaFuncSetAttribute(k_ctr_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_ctr_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_ctr_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
+  cudaFuncSetAttribute(k_ctr_irows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
     float2 *Fi = F + (size_t)i * P * P;
     k_ctr_cols<P><<<dim3((N + CC::S - 1) / CC::S, n), CC::NT, CC::smem, s>>>(R + (size_t)i * N * N, thr + i, r2 + i, tw, Fi,
                                                                 masked + i);
     note_launch();
-    k_ctr_rows<P><<<dim3(P / RC::S, n), RC::NT, 0, s>>>(tw, Fi);
+    k_ctr_rows<P><<<dim3(P / RC::S, n), RC::NT, RC::smem, s>>>(tw, Fi);
     note_launch();
     k_ctr_pair<P><<<dim3((unsigned)(((int64_t)(P / 2 - 1) * P + 255) / 256), n), 256, 0, s>>>(Fi);
     note_launch();
@@ -279,7 +283,7 @@ void center_P(const float *R, const float *mu_a, const float *mu_b, const double
     note_launch();
     k_ctr_icols<P><<<dim3(P / CC::S, n), CC::NT, CC::smem, s>>>(Fi, tw, U + (size_t)i * W * P);
     note_launch();
-    k_ctr_irows<P><<<dim3((W + RC::S - 1) / RC::S, n), RC::NT, 0, s>>>(U + (size_t)i * W * P, tw,
+    k_ctr_irows<P><<<dim3((W + RC::S - 1) / RC::S, n), RC::NT, RC::smem, s>>>(U + (size_t)i * W * P, tw,
                                                                         Cc + (size_t)i * W * W);
     note_launch();
   }
@@ -297,6 +301,7 @@ void launch_center(const float *R, const float *mu_a, const float *mu_b, const d
 #define MUSER_CASE(p) \
   case p: center_P<p>(R, mu_a, mu_b, cell, B, tw, thr, r2, masked, F, U, Cc, dlm, shift, status, s); break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048)
+    MUSER_CASE(320) MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240)
 #undef MUSER_CASE
     default: break;
   }

@@ -176,7 +176,7 @@ int chi2_blocks(int64_t n_vis);
 
 // centring (center.cu): Cc [B][N/2+1][N/2+1], dlm [B][2], shift [B][2] (nullable); scratch
 // thr, r2 [B] f32, masked [B] i32, F [B][2N][2N] c64, U [B][N/2+1][2N] c64, tw [2N] twiddles.
-// Steer clean (steer.cu): scratch FB, F [B][2N][2N] c64, U [B][N][2N] c64, Y [B][N][N] f32,
+// Steer clean (steer.cu): scratch FB [B][2N][N + 1] c64, F [B][2N][2N] c64, U [B][N][2N] c64, Y [B][N][N] f32,
 // state [B][steer_state_bytes()], tw [2N] twiddles.
 size_t steer_state_bytes();
 void launch_steer(float *R, const float *beam, int B, int N, float gain, int cap, const float *thr, float clip,

@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
   using C = RowCfg<G>;
   constexpr int S = C::S, NT = C::NT;
   constexpr int NSTRIP = G / ColCfg<G>::S;
-  __shared__ float2 sm[C::Layout::size];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   __shared__ float red[32];
   __shared__ float scale_sh;
   const int inst = blockIdx.y, y0 = blockIdx.x * S;   // rows y0.. of T, i.e. y = y0 + G/4 ..
@@ -199,12 +200,13 @@ void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   cudaFuncSetAttribute(k_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
     k_cols<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(Z + (size_t)i * G * G, tw, T + (size_t)i * (G / 2) * G,
                                                             partial + (size_t)i * (G / CC::S));
     note_launch();
-    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, 0, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
+    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
                                                          partial + (size_t)i * (G / CC::S), N,
                                                          dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
                                                          status ? status + i : nullptr);
@@ -219,6 +221,7 @@ void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W,
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   cudaFuncSetAttribute(k_cols_grid<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   const int tps = tiles_per_sample(W, G, CC::S, G);
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
@@ -226,7 +229,7 @@ void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W,
         rec + (size_t)i * stride, stride, W, tab, table_len(W, os), (float)os, bin_off + (size_t)i * (G / CC::S + 1),
         entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S));
     note_launch();
-    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, 0, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
+    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
                                                          partial + (size_t)i * (G / CC::S), N,
                                                          dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
                                                          status ? status + i : nullptr);
@@ -245,6 +248,12 @@ int dirty_strip_width(int G) {
     case 1024: return ColCfg<1024>::S;
     case 2048: return ColCfg<2048>::S;
     case 4096: return ColCfg<4096>::S;
+    case 640: return ColCfg<640>::S;
+    case 1280: return ColCfg<1280>::S;
+    case 2560: return ColCfg<2560>::S;
+    case 5120: return ColCfg<5120>::S;
+    case 10240: return ColCfg<10240>::S;
+    case 20480: return ColCfg<20480>::S;
     default: return 0;
   }
 }
@@ -256,6 +265,7 @@ void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const 
 #define MUSER_CASE(g) \
   case g: launch_dirty_G<g>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s); break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+    MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240) MUSER_CASE(20480)
 #undef MUSER_CASE
     default: break;
   }
@@ -275,6 +285,7 @@ void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, i
                               status, s);                                                                      \
     break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+    MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240) MUSER_CASE(20480)
 #undef MUSER_CASE
     default: break;
   }

@@ -1,7 +1,9 @@
-// Batched radix-16 Stockham FFT in shared memory (device code shared by dirty.cu and degrid.cu).
+// Batched radix-16 Stockham FFT in shared memory (device code shared by the imaging, degridding,
+// centring and Steer transforms).
 //
-// A block transforms S sequences of length L (a power of two, 64..4096).  Stages run
-// first-to-last with radices {2,4,8} (the remainder of log2 L mod 4, if any) then 16s.
+// A block transforms S sequences of length L = 2^m or 5 * 2^m.  Stages run first-to-last:
+// for L = 2^m a radix {2, 4, 8} stage (the remainder of m mod 4, if any) then 16s; for
+// L = 5 * 2^m one radix 5 * 2^(m mod 4) stage (5, 10, 20 or 40) then 16s.
 // Stage with sub-length LS and radix R, butterfly j in [0, L/R), sequence s:
 //     v[r] = x[j + r L/R]                      r = 0..R-1
 //     v[r] *= W^(r k),  k = j mod LS,  W = exp(SIGN 2 pi i / (LS R))
@@ -60,9 +62,77 @@ __device__ __forceinline__ float2 w16(int e) {
   return make_float2(c, SIGN > 0 ? s : -s);
 }
 
+// X[m] = sum_p x[p] w^(p m), w = exp(SIGN 2 pi i / 5): the pairs (1, 4) and (2, 3) share
+// cosines and have opposite sines.
+template <int SIGN>
+__device__ __forceinline__ void dft5(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 &x4) {
+  constexpr float c1 = 0.30901699437494742f, c2 = -0.80901699437494742f;   // cos 72, cos 144 deg
+  constexpr float s1 = 0.95105651629515357f, s2 = 0.58778525229247313f;    // sin 72, sin 144 deg
+  const float2 t1 = cadd(x1, x4), t2 = cadd(x2, x3), t3 = csub(x1, x4), t4 = csub(x2, x3);
+  const float2 a1 = make_float2(x0.x + c1 * t1.x + c2 * t2.x, x0.y + c1 * t1.y + c2 * t2.y);
+  const float2 a2 = make_float2(x0.x + c2 * t1.x + c1 * t2.x, x0.y + c2 * t1.y + c1 * t2.y);
+  const float2 b1 = mul_i<SIGN>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+  const float2 b2 = mul_i<SIGN>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+  x0 = cadd(x0, cadd(t1, t2));
+  x1 = cadd(a1, b1);
+  x4 = csub(a1, b1);
+  x2 = cadd(a2, b2);
+  x3 = csub(a2, b2);
+}
+
+// exp(SIGN 2 pi i j / 40), j in [0, 40) (constant-folded for constant j)
+template <int SIGN>
+__device__ __forceinline__ float2 w40(int j) {
+  constexpr float C[11] = {1.f, 0.98768834059513777f, 0.95105651629515357f, 0.89100652418836787f,
+                           0.80901699437494742f, 0.70710678118654752f, 0.58778525229247313f,
+                           0.45399049973954680f, 0.30901699437494742f, 0.15643446504023087f, 0.f};
+  const int q = j / 10, k = j % 10;
+  const float ck = C[k], sk = C[10 - k];
+  float c, s;
+  switch (q) {
+    case 0: c = ck; s = sk; break;
+    case 1: c = -sk; s = ck; break;
+    case 2: c = -ck; s = -sk; break;
+    default: c = sk; s = -ck; break;
+  }
+  return make_float2(c, SIGN > 0 ? s : -s);
+}
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(float2 (&v)[R]);
+
+// R = 5 Q (Q = 1, 2, 4, 8): r = q + Q p, m = m1 + 5 m2:
+//   X[m1 + 5 m2] = sum_q w_Q^(q m2) w_R^(q m1) DFT5_p(x[q + Q p])[m1]
+template <int R, int SIGN>
+__device__ __forceinline__ void dft5q(float2 (&v)[R]) {
+  constexpr int Q = R / 5;
+  float2 y[Q][5];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+#pragma unroll
+    for (int p = 0; p < 5; p++) y[q][p] = v[q + Q * p];
+    dft5<SIGN>(y[q][0], y[q][1], y[q][2], y[q][3], y[q][4]);
+  }
+#pragma unroll
+  for (int q = 1; q < Q; q++)
+#pragma unroll
+    for (int m1 = 1; m1 < 5; m1++) y[q][m1] = cmul(y[q][m1], w40<SIGN>(q * m1 * (40 / R)));
+#pragma unroll
+  for (int m1 = 0; m1 < 5; m1++) {
+    float2 z[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) z[q] = y[q][m1];
+    if constexpr (Q > 1) dft<Q, SIGN>(z);
+#pragma unroll
+    for (int m2 = 0; m2 < Q; m2++) v[m1 + 5 * m2] = z[m2];
+  }
+}
+
 template <int R, int SIGN>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
-  if constexpr (R == 2) {
+  if constexpr (R % 5 == 0) {
+    dft5q<R, SIGN>(v);
+  } else if constexpr (R == 2) {
     dft2<SIGN>(v[0], v[1]);
   } else if constexpr (R == 4) {
     dft4<SIGN>(v[0], v[1], v[2], v[3]);
@@ -143,28 +213,34 @@ struct Sequential {           // one sequence after another: for rows
 
 template <int L>
 struct Plan {
-  static constexpr int LOG2L = ilog2(L);
+  static constexpr bool F5 = L % 5 == 0;
+  static constexpr int L2 = F5 ? L / 5 : L;            // the power-of-two factor
+  static_assert(L2 > 0 && (L2 & (L2 - 1)) == 0, "L = 2^m or 5 * 2^m");
+  static constexpr int LOG2L = ilog2(L2);
   static constexpr int REM = LOG2L % 4;
-  static constexpr int NST = LOG2L / 4 + (REM ? 1 : 0);
+  static constexpr int NST = LOG2L / 4 + ((REM || F5) ? 1 : 0);
   template <int STAGE>
-  static constexpr int radix() { return (STAGE == 0 && REM) ? (1 << REM) : 16; }
+  static constexpr int radix() { return STAGE == 0 ? (F5 ? 5 << REM : (REM ? 1 << REM : 16)) : 16; }
 };
 
 // One stage and (recursively) the following ones.  SFAST: work items enumerate the
 // sequence index fastest (column strips, coalesced global rows) or the butterfly index
-// fastest (rows).  NT threads; S * L / R must be a multiple of NT.
+// fastest (rows).  NT threads; a stage whose S * L / R items are not a multiple of NT leaves
+// the last round's surplus threads idle (the radix 5 Q stages).
 template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, bool SYNC0, class Load, class Store>
 __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
   constexpr int R = Plan<L>::template radix<STAGE>();
   constexpr bool FIRST = STAGE == 0, LAST = STAGE == Plan<L>::NST - 1;
   constexpr int NB = L / R;
   constexpr int ITEMS = S * NB;
-  static_assert(ITEMS % NT == 0, "work items must divide among threads");
-  constexpr int BPT = ITEMS / NT;
+  static_assert(ITEMS % NT == 0 || R % 5 == 0, "work items must divide among threads");
+  constexpr int BPT = (ITEMS + NT - 1) / NT;
+  constexpr bool RAGGED = ITEMS % NT != 0;
   float2 v[BPT][R];
 #pragma unroll
   for (int b = 0; b < BPT; b++) {
     const int it = threadIdx.x + b * NT;
+    if (RAGGED && it >= ITEMS) break;
     const int s = SFAST ? it % S : it / NB;
     const int j = SFAST ? it / S : it % NB;
 #pragma unroll
@@ -178,9 +254,10 @@ __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw
 #pragma unroll
   for (int b = 0; b < BPT; b++) {
     const int it = threadIdx.x + b * NT;
+    if (RAGGED && it >= ITEMS) break;
     const int s = SFAST ? it % S : it / NB;
     const int j = SFAST ? it / S : it % NB;
-    const int k = j & (LS - 1);
+    const int k = j % LS;
     if constexpr (LS > 1) {
       constexpr int STEP = L / (LS * R);      // W_{LS R}^{rk} = W_L^{rk STEP}
       // one table load per butterfly; the other powers by products of at most four factors
@@ -216,10 +293,12 @@ __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, L
 }
 
 // Column strips: S columns of a G x G array per block, 32 complex values per thread per stage;
-// rows: S rows per block, 16 values per thread per stage.  ColCfg / RowCfg (S = min(G, 16384 / G)
-// columns, min(max(1, 4096 / G), G / 2) rows) fill the SMs when many instances are transformed
-// at once; ColCfg1 / RowCfg1 (max(4, 4096 / G) columns, max(1, 2048 / G) rows) give one
-// transform 4 times as many blocks.
+// rows: S rows per block, 16 values per thread per stage (32 above G = 10240, so that a row
+// still fits in 1024 threads).  ColCfg / RowCfg (S = min(G, 16384 / G) columns,
+// min(max(1, 4096 / G), G / 2) rows; 20480 / G and 5120 / G for G = 5 * 2^m) fill the SMs when
+// many instances are transformed at once; ColCfg1 / RowCfg1 (max(4, 4096 / G) columns,
+// max(1, 2048 / G) rows) give one transform 4 times as many blocks.  Row kernels whose strip
+// exceeds 48 KB (G >= 8192) take their shared memory dynamically (RowStrip::dyn).
 template <int G, int S_>
 struct ColStrip {
   static constexpr int S = S_;
@@ -230,16 +309,17 @@ struct ColStrip {
 template <int G, int S_>
 struct RowStrip {
   static constexpr int S = S_;
-  static constexpr int NT = S * G / 16;
+  static constexpr int NT = S * G / (S * G > 10240 ? 32 : 16);
   using Layout = Sequential<G, S>;
   static constexpr size_t smem = sizeof(float2) * Layout::size;
+  static constexpr bool dyn = smem > 48 * 1024;
 };
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 template <int G>
-using ColCfg = ColStrip<G, cmin(G, 16384 / G)>;
+using ColCfg = ColStrip<G, cmin(G, (G % 5 ? 16384 : 20480) / G)>;
 template <int G>
-using RowCfg = RowStrip<G, cmin(cmax(1, 4096 / G), G / 2)>;
+using RowCfg = RowStrip<G, cmin(cmax(1, (G % 5 ? 4096 : 5120) / G), G / 2)>;
 template <int G>
 using ColCfg1 = ColStrip<G, cmin(G, cmax(4, 4096 / G))>;
 template <int G>

@@ -17,9 +17,8 @@
 namespace muser {
 
 int grid_band_rows(int G) {
-  int rows = 8192 / G;           // 64 KB of complex64 per band
-  if (rows < 1) rows = 1;
-  if (rows > G) rows = G;
+  int rows = 1;                  // up to 64 KB of complex64 per band; a power of two dividing G
+  while (2 * rows * G <= 8192 && G % (2 * rows) == 0) rows *= 2;
   return rows;
 }
 

@@ -9,12 +9,14 @@
 // (2N x 2N): Y(q) = (C (*) Bm)(q + (N, N)), nothing wraps.  The beam spectrum FB is computed
 // once per call.  Per cycle (every instance of the batch at once; an instance that has stopped
 // returns from every kernel at once):
-//   k_st_peak   block max of R -> m, threshold, active flag, reset of max Y;
+//   k_st_decide max R (gathered by the previous update) -> m, threshold, active flag;
 //   k_st_cols   forward column pass of C (only the N columns and rows where C can be non-zero);
 //   k_st_rows   forward row pass, multiplied by FB on the way out;
 //   k_st_icols  inverse column pass, output rows N .. 2N - 1 only;
 //   k_st_irows  inverse row pass, output columns N .. 2N - 1 only -> Y (/ P^2), block maxima of Y;
-//   k_st_update R -= a Y, model += a C (C re-derived from the same R and threshold).
+//   k_st_update R -= a Y, model += a C (C re-derived from the same R and threshold), block
+//               maxima of the new R for the next cycle.
+// The beam is real, so FB(-v, -u) = conj FB(v, u): only the columns u <= P/2 are stored.
 #include "fft.cuh"
 
 namespace muser {
@@ -34,9 +36,33 @@ __device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0
 struct SteerState {      // per instance
   float m, tau;
   int ymax;              // ordered(max Y)
+  int mnext;             // ordered(max R) for the next cycle
   int active;
   int cycles;
 };
+
+template <int P>
+struct HalfSpec {        // FB stored as [P][P/2 + 1]
+  static constexpr int H = P / 2 + 1;
+  __device__ static float2 get(const float2 *__restrict__ F, int v, int u) {
+    if (u <= P / 2) return F[(size_t)v * H + u];
+    const float2 c = F[(size_t)(v == 0 ? 0 : P - v) * H + (P - u)];
+    return make_float2(c.x, -c.y);
+  }
+};
+
+// block max of a float over the block's threads -> atomicMax on an ordered int
+__device__ __forceinline__ void block_max_to(float m, int *dst) {
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
+    atomicMax(dst, ordered(m));
+  }
+}
 
 // beam spectrum: columns (pass 1) then rows (pass 2) of the real 2N x 2N beam
 template <int P>
@@ -63,49 +89,58 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_beam_cols(const float *__r
 }
 
 template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_beam_rows(const float2 *__restrict__ tw, float2 *__restrict__ FB) {
+__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_beam_rows(const float2 *__restrict__ tw, const float2 *__restrict__ FB,
+                                                                float2 *__restrict__ FBh) {
   using C = RowCfg<P>;
   constexpr int S = C::S, NT = C::NT;
-  __shared__ float2 sm[C::Layout::size];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
-  float2 *Fi = FB + (size_t)inst * P * P;
+  const float2 *Fi = FB + (size_t)inst * P * P;
   struct Load {
     const float2 *Fi;
     int y0;
     __device__ float2 operator()(int i, int s) const { return Fi[(size_t)(y0 + s) * P + i]; }
   } load{Fi, y0};
+  float2 *Hi = FBh + (size_t)inst * P * HalfSpec<P>::H;
   struct Store {
-    float2 *Fi;
+    float2 *Hi;
     int y0;
-    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)(y0 + s) * P + o] = v; }
-  } store{Fi, y0};
-  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);   // in place (loads precede stores)
+    __device__ void operator()(int o, int s, float2 v) const {
+      if (o <= P / 2) Hi[(size_t)(y0 + s) * HalfSpec<P>::H + o] = v;
+    }
+  } store{Hi, y0};
+  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
 }
 
-__global__ void __launch_bounds__(1024) k_st_peak(const float *__restrict__ R, int N, int cap, const float *__restrict__ thr,
-                                                  float clip, SteerState *__restrict__ st) {
-  __shared__ float red[32];
-  const int inst = blockIdx.x;
-  SteerState &S = st[inst];
-  if (!S.active) return;                                // (uniform per block)
-  const float *Ri = R + (size_t)inst * N * N;
+// max of R per instance (the first cycle; later cycles take it from k_st_update)
+__global__ void __launch_bounds__(1024) k_st_max(const float *__restrict__ R, int N, SteerState *__restrict__ st) {
+  const int inst = blockIdx.y;
+  if (!st[inst].active) return;
+  const float4 *Ri = reinterpret_cast<const float4 *>(R + (size_t)inst * N * N);
   float m = -CUDART_INF_F;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) m = fmaxf(m, Ri[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < 32; w++) m = fmaxf(m, red[w]);
-    const float t = thr ? thr[inst] : -CUDART_INF_F;
-    if (S.cycles >= cap || !(m > t) || !(m > 0.f)) {
-      S.active = 0;
-    } else {
-      S.m = m;
-      S.tau = clip * m;
-      S.ymax = ordered(-CUDART_INF_F);
-    }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N / 4; i += gridDim.x * blockDim.x) {
+    const float4 v = Ri[i];
+    m = fmaxf(fmaxf(m, fmaxf(v.x, v.y)), fmaxf(v.z, v.w));
   }
+  block_max_to(m, &st[inst].mnext);
+}
+
+__global__ void k_st_decide(SteerState *__restrict__ st, int B, int cap, const float *__restrict__ thr, float clip) {
+  const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+  if (inst >= B) return;
+  SteerState &S = st[inst];
+  if (!S.active) return;
+  const float m = unordered(S.mnext);
+  const float t = thr ? thr[inst] : -CUDART_INF_F;
+  if (S.cycles >= cap || !(m > t) || !(m > 0.f)) {
+    S.active = 0;
+    return;
+  }
+  S.m = m;
+  S.tau = clip * m;
+  S.ymax = ordered(-CUDART_INF_F);
+  S.mnext = ordered(-CUDART_INF_F);
 }
 
 // forward column pass of C = R [R >= tau] (columns and rows < N)
@@ -145,11 +180,12 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_rows(const SteerState *__r
                                                           const float2 *__restrict__ FB, float2 *__restrict__ F) {
   using C = RowCfg<P>;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
-  __shared__ float2 sm[C::Layout::size];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
   if (!st[inst].active) return;
   float2 *Fi = F + (size_t)inst * P * P;
-  const float2 *Bi = FB + (size_t)inst * P * P;
+  const float2 *Bi = FB + (size_t)inst * P * HalfSpec<P>::H;
   struct Load {
     const float2 *Fi;
     int y0;
@@ -162,8 +198,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_rows(const SteerState *__r
     const float2 *Bi;
     int y0;
     __device__ void operator()(int o, int s, float2 v) const {
-      const size_t k = (size_t)(y0 + s) * P + o;
-      Fi[k] = cmul(v, Bi[k]);
+      Fi[(size_t)(y0 + s) * P + o] = cmul(v, HalfSpec<P>::get(Bi, y0 + s, o));
     }
   } store{Fi, Bi, y0};
   fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
@@ -202,8 +237,8 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_irows(SteerState *__restri
                                                            const float2 *__restrict__ tw, float *__restrict__ Y) {
   using C = RowCfg<P>;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
-  __shared__ float2 sm[C::Layout::size];
-  __shared__ float red[NT / 32 > 0 ? NT / 32 : 1];
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
   if (!st[inst].active) return;
   const float2 *Ui = U + (size_t)inst * N * P;
@@ -225,15 +260,7 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_irows(SteerState *__restri
     }
   } store{Yi, y0, -CUDART_INF_F};
   fft::run<P, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
-  float m = store.mx;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < NT / 32; w++) m = fmaxf(m, red[w]);
-    atomicMax(&st[inst].ymax, ordered(m));
-  }
+  block_max_to(store.mx, &st[inst].ymax);
 }
 
 // R -= a Y, model += a C; one block row per instance slice
@@ -249,12 +276,16 @@ __global__ void k_st_update(float *__restrict__ R, const float *__restrict__ Y, 
   }
   const float a = gain * S.m / ym, tau = S.tau;
   const size_t base = (size_t)inst * N * N;
+  float mx = -CUDART_INF_F;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N; i += gridDim.x * blockDim.x) {
     const float r = R[base + i];
     if (r >= tau) model[base + i] += a * r;
-    R[base + i] = r - a * Y[base + i];
+    const float rn = r - a * Y[base + i];
+    R[base + i] = rn;
+    mx = fmaxf(mx, rn);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) S.cycles++;
+  block_max_to(mx, &S.mnext);
 }
 
 __global__ void k_st_init(SteerState *__restrict__ st, int B, const int32_t *__restrict__ status) {
@@ -265,6 +296,7 @@ __global__ void k_st_init(SteerState *__restrict__ st, int B, const int32_t *__r
   st[i].m = 0.f;
   st[i].tau = 0.f;
   st[i].ymax = 0;
+  st[i].mnext = ordered(-CUDART_INF_F);
 }
 
 __global__ void k_st_finish(const SteerState *__restrict__ st, int B, int32_t *__restrict__ n_cycles) {
@@ -279,27 +311,32 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
   using CC = ColCfg<P>;
   using RC = RowCfg<P>;
   constexpr int N = P / 2;
-  const dim3 g1(B);
   cudaFuncSetAttribute(k_st_beam_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_st_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_st_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_st_beam_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
+  cudaFuncSetAttribute(k_st_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
+  cudaFuncSetAttribute(k_st_irows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   cudaMemsetAsync(model, 0, sizeof(float) * (size_t)B * N * N, s);
   k_st_init<<<(B + 255) / 256, 256, 0, s>>>(st, B, status);
   note_launch();
-  k_st_beam_cols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(beam, tw, FB);
+  k_st_beam_cols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(beam, tw, F);    // F: scratch here
   note_launch();
-  k_st_beam_rows<P><<<dim3(P / RC::S, B), RC::NT, 0, s>>>(tw, FB);
+  k_st_beam_rows<P><<<dim3(P / RC::S, B), RC::NT, RC::smem, s>>>(tw, F, FB);
+  note_launch();
+  const int mb = N * N / 4 / 1024 < 1 ? 1 : (N * N / 4 / 1024 > 64 ? 64 : N * N / 4 / 1024);
+  k_st_max<<<dim3(mb, B), 1024, 0, s>>>(R, N, st);
   note_launch();
   for (int c = 0; c < cap; c++) {
-    k_st_peak<<<g1, 1024, 0, s>>>(R, N, cap, thr, clip, st);
+    k_st_decide<<<(B + 255) / 256, 256, 0, s>>>(st, B, cap, thr, clip);
     note_launch();
     k_st_cols<P><<<dim3((N + CC::S - 1) / CC::S, B), CC::NT, CC::smem, s>>>(R, st, tw, F);
     note_launch();
-    k_st_rows<P><<<dim3(P / RC::S, B), RC::NT, 0, s>>>(st, tw, FB, F);
+    k_st_rows<P><<<dim3(P / RC::S, B), RC::NT, RC::smem, s>>>(st, tw, FB, F);
     note_launch();
     k_st_icols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(st, F, tw, U);
     note_launch();
-    k_st_irows<P><<<dim3(N / RC::S, B), RC::NT, 0, s>>>(st, U, tw, Y);
+    k_st_irows<P><<<dim3(N / RC::S, B), RC::NT, RC::smem, s>>>(st, U, tw, Y);
     note_launch();
     k_st_update<<<dim3((N * N + 1023) / 1024 < 64 ? (N * N + 1023) / 1024 : 64, B), 1024, 0, s>>>(R, Y, model, N,
                                                                                                  gain, st);
@@ -322,6 +359,7 @@ void launch_steer(float *R, const float *beam, int B, int N, float gain, int cap
 #define MUSER_CASE(p) \
   case p: steer_P<p>(R, beam, B, gain, cap, thr, clip, model, n_cycles, tw, FB, F, U, Y, st, status, s); break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048)
+    MUSER_CASE(320) MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240)
 #undef MUSER_CASE
     default: break;
   }

@@ -264,6 +264,23 @@ def config3_muser2_uneven(n_frame=8, chans=None) -> Workload:
                          flag_max=0.3, max_iter=1000)
 
 
+LARGE_BANDS = {1280: (2.0e9, 4.0e9), 2560: (4.0e9, 8.0e9), 5120: (8.0e9, 15.0e9)}
+
+
+def config5_muser2_large(N=2560, n_frame=1, chans=None) -> Workload:
+    """MUSER-II high-band images of Table 2: 2-4 GHz at 1280^2, 4-8 GHz at 2560^2, 8-15 GHz at
+    5120^2 (G = 4N), 60 antennas, 0-30 % of baselines flagged per frame, 1000 iterations.
+    ``chans`` indexes the channels of the band."""
+    lo, hi = LARGE_BANDS[N]
+    allf = muser2_channels()
+    band = allf[(allf >= lo) & (allf <= hi)]
+    freq = band if chans is None else band[chans]
+    ant = muser2_array()
+    ha = EARTH_RATE * 0.20625 * np.arange(n_frame)
+    return make_workload(f"muser2-band-N{N}", ant, baseline_pairs(60), ha, np.full(n_frame, DEC_SUN), freq,
+                         N, 4 * N, config_id=5 + N, flag_max=0.3, max_iter=1000)
+
+
 def config4_operator() -> Workload:
     """Differentiable imaging: 512 x 512 sky, 780 baselines x 64 channels, G = 2N."""
     ant = muser1_array()

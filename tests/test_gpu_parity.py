@@ -473,14 +473,13 @@ def _centring_case(off_px, N=128, seed=110):
     return wl, cell
 
 
-@pytest.mark.parametrize("off_px", [(5.0, -3.0), (-11.4, 7.6)])
-def test_center_correlation_and_shift_vs_oracle(m, off_px):
+@pytest.mark.parametrize("off_px,N", [((5.0, -3.0), 128), ((-11.4, 7.6), 128), ((7.3, 4.2), 160)])
+def test_center_correlation_and_shift_vs_oracle(m, off_px, N):
     """muser_center on the oracle's pre-cleaned residual: the disk correlation over all
     shifts within 1e-5 of its peak, the best shift and its parabolic refinement equal."""
     import torch
     from oracle import centering
-    wl, cell = _centring_case(off_px)
-    N = wl.N
+    wl, cell = _centring_case(off_px, N=N)
     rec = pipeline.records(wl)
     ker = pipeline.spheroidal(7, 1024)
     _, D, Bm, _ = pipeline.dirty(rec, N, 4 * N, ker)
@@ -584,13 +583,15 @@ def _oracle_steer_chain(D, Bo, gain, clip, cap, thr=-np.inf):
 
 
 @pytest.mark.parametrize("name,clip,cycles", [("small-N64", 0.9, 16), ("small-N32-3frames", 0.7, 40),
-                                              ("plain-N256", 0.7, 6), ("N1024x1", 0.8, 2)])
+                                              ("plain-N256", 0.7, 6), ("N1024x1", 0.8, 2), ("N160", 0.9, 8),
+                                              ("N320x2", 0.8, 4)])
 def test_steer_cycle_lockstep(m, name, clip, cycles):
     """One major cycle at a time from the GPU's own residual: C is decided in FP32 from the same
     FP32 residual on both sides (so near-ties cannot split them); Y, a and the update follow
     the oracle's FP64 convolution."""
     from oracle import steer as osteer
-    wl = (synth.config3_muser2_uneven(n_frame=1, chans=[7]) if name == "N1024x1" else WORKLOADS[name]())
+    wl = (synth.config3_muser2_uneven(n_frame=1, chans=[7]) if name == "N1024x1"
+          else (FIVE_CASES.get(name) or WORKLOADS[name])())
     maps = _oracle_maps(wl)
     N = wl.N
     cfg = m.Config(N=N, G=4 * N)
@@ -688,3 +689,94 @@ def test_steer_thresholds_batch_and_edges(m):
     assert torch.equal(R, Dn) and float(model.abs().max()) == 0.0
     R, model, nc, _ = m.steer(D[:0], Bm[:0], cfg)
     assert nc.numel() == 0
+
+
+# ------------------------------------------------------------------------------ image sides 5 * 2^a
+# Table 2's high-band images are 1280, 2560 and 5120 pixels on a side (grids of 5 * 2^m cells):
+# the transforms then start with one radix-5, -10, -20 or -40 stage.
+FIVE_CASES = {
+    "N160": lambda: synth.small_workload(n_ant=12, N=160, config_id=250, bmax=600.0),          # G 640: 40, 16
+    "N320x2": lambda: synth.small_workload(n_ant=16, N=320, n_frame=2, config_id=251, bmax=1200.0,
+                                           flag_max=0.3),                                     # G 1280: 5, 16, 16
+    "N640": lambda: synth.small_workload(n_ant=21, N=640, config_id=252, bmax=2000.0),         # G 2560: 10, 16, 16
+    "N1280": lambda: synth.config5_muser2_large(1280, chans=[3, 70]),                          # G 5120: 20, 16, 16
+}
+
+
+@pytest.mark.parametrize("name", list(FIVE_CASES))
+def test_grid_and_dirty_five(m, name):
+    wl = FIVE_CASES[name]()
+    cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
+    Zg, Dg, Bg = _np(Z), _np(D), _np(Bm)
+    for i, (Zo, Do, Bo, norm) in enumerate(ref):
+        assert np.abs(Zg[i] - Zo).max() <= 1e-5 * np.abs(Zo).max()
+        assert np.abs(Dg[i] - Do).max() <= 1e-4 * np.abs(Do).max(), i
+        assert np.abs(Bg[i] - Bo).max() <= 1e-4, i
+        assert abs(Bg[i][wl.N, wl.N] - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [2560, 5120])
+def test_dirty_largest_sides_sampled(m, N):
+    """One MUSER-II instance at 2560^2 (G = 10240) and 5120^2 (G = 20480): sampled pixels of the
+    map and the beam against the oracle's per-pixel transform of the sparse grid."""
+    from oracle import imaging as oim
+    wl = synth.config5_muser2_large(N, chans=[5])
+    cfg = cfg_for(m, wl)
+    rec, _, st, off, _ = gpu_records(m, wl, cfg, want_uvw=False)
+    Z, st = m.grid(rec, off, cfg, status=st)
+    D, Bm, st = m.dirty(Z, cfg, status=st)
+    del Z
+    Dg, Bg = _np(D)[0], _np(Bm)[0]
+    ri = geometry.instance_slice(oracle_records(wl), 0, wl.n_bl)
+    rng = np.random.default_rng(N)
+    ym, xm = np.unravel_index(np.argmax(np.abs(Dg)), Dg.shape)
+    dp = np.concatenate([rng.integers(0, N, (24, 2)), [[ym, xm], [N // 2, N // 2], [0, N - 1]]])
+    bp = np.concatenate([rng.integers(0, 2 * N, (16, 2)), [[N, N], [N, N + 1], [N - 3, N + 2]]])
+    Do, Bo, _ = oim.dirty_and_beam_at(ri, wl.G, N, KER, dp, bp)
+    scale = np.abs(Dg).max()
+    assert np.abs(Dg[dp[:, 0], dp[:, 1]] - Do).max() <= 1e-4 * scale
+    assert np.abs(Bg[bp[:, 0], bp[:, 1]] - Bo).max() <= 1e-4
+    assert abs(Bg[N, N] - 1.0) <= 1e-6
+
+
+@pytest.mark.parametrize("name,cap", [("N320x2", 150), ("N1280", 100)])
+def test_image_five_end_to_end(m, name, cap):
+    """muser_image at 5 * 2^a sides (gridding fused into the radix-5 column pass, streaming
+    CLEAN, restore) against the oracle pipeline, component by component."""
+    wl = FIVE_CASES[name]()
+    cfg = cfg_for(m, wl, max_iter=cap)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    out = m.image(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    ro = oracle_records(wl)
+    for i in range(wl.n_inst):
+        o = pipeline.image_instance(geometry.instance_slice(ro, i, wl.n_bl), wl.N, wl.G, gain=wl.gain, cap=cap)
+        pg, fg = _np(out.comp_pos)[i], _np(out.comp_flux)[i]
+        assert int(_np(out.n_comp)[i]) == cap
+        lockstep(o["D"], o["Bm"], pg, fg, wl.gain)
+        identical_positions_unless_near_tie(o["D"], o["Bm"], pg, wl.gain, cap)
+        np.testing.assert_allclose(_np(out.beam_params)[i], o["S"], rtol=1e-5)
+        if np.array_equal(o["pos"], pg):
+            assert np.abs(_np(out.clean)[i] - o["clean"]).max() <= 1e-4 * np.abs(o["clean"]).max()
+            assert np.abs(_np(out.residual)[i] - o["R"]).max() <= 1e-4 * np.abs(o["D"]).max()
+
+
+def test_clean_5120_streaming(m):
+    """CLEAN at 5120^2 (streaming residual, one block per instance): a seeded map and beam of
+    that size, 40 Hogbom steps against the oracle."""
+    import torch
+    N = 5120
+    rng = np.random.default_rng(5120)
+    yy, xx = np.mgrid[-N:N, -N:N].astype(np.float32)
+    Bo = np.exp(-(xx * xx + yy * yy) / np.float32(2 * 9.0 ** 2)) + np.float32(0.05) * np.cos(xx / np.float32(7)) * \
+        np.cos(yy / np.float32(11))
+    Bo = (Bo / Bo[N, N]).astype(np.float32)
+    del yy, xx
+    Do = rng.normal(size=(N, N)).astype(np.float32)
+    Do[1000, 4000] += 40.0
+    Do[3000, 17] += 25.0
+    cfg = m.Config(N=N, G=4 * N, max_iter=40)
+    R, pos, flux, nc, _ = m.clean(torch.tensor(Do[None], device="cuda"), torch.tensor(Bo[None], device="cuda"), cfg)
+    pg, fg = _np(pos)[0], _np(flux)[0]
+    assert int(_np(nc)[0]) == 40
+    lockstep(Do, Bo, pg, fg, 0.1)
+    identical_positions_unless_near_tie(Do, Bo, pg, 0.1, 40)

@@ -177,6 +177,27 @@ def test_gridded_image_matches_direct_dft(N, n_ant, cfg):
     assert np.abs(Bm - Bd).max() <= 4e-4
 
 
+@pytest.mark.parametrize("N,n_ant,cfg", [(32, 7, 105), (40, 9, 106)])
+def test_gridded_image_at_5x2a_side_matches_direct_dft(N, n_ant, cfg):
+    """Image sides 5 * 2^a (grids of 5 * 2^(a+2) cells, the 1280-5120 pixel images of Table 2):
+    the same bound against the direct transform, and the sparse per-pixel evaluation equals the
+    dense transform at sampled pixels."""
+    wl, rec = _tiny(N=N, n_ant=n_ant, seed_cfg=cfg, bmax=40.0 * N / 32 * 5)
+    Z = imaging.grid(rec, wl.G, KER)
+    D, Bm, norm = imaging.dirty_and_beam(Z, N, KER)
+    if N % 5 == 0:
+        Dd, Bd = imaging.direct_dirty(rec, N, pipeline.cell_sizes(wl)[0])
+        assert np.abs(D - Dd).max() <= 2e-4 * np.abs(Dd).max()
+        assert np.abs(Bm - Bd).max() <= 4e-4
+    rng = np.random.default_rng(cfg)
+    dp = np.concatenate([rng.integers(0, N, (12, 2)), [[N // 2, N // 2], [0, 0], [N - 1, N - 1]]])
+    bp = np.concatenate([rng.integers(0, 2 * N, (12, 2)), [[N, N], [0, 2 * N - 1]]])
+    Ds, Bs, ns = imaging.dirty_and_beam_at(rec, wl.G, N, KER, dp, bp)
+    assert ns == pytest.approx(norm, rel=1e-12)
+    np.testing.assert_allclose(Ds, D[dp[:, 0], dp[:, 1]], rtol=0, atol=1e-10 * np.abs(D).max())
+    np.testing.assert_allclose(Bs, Bm[bp[:, 0], bp[:, 1]], rtol=0, atol=1e-10)
+
+
 def test_uniform_weights_matches_weighted_dft_and_sums_to_one_per_cell():
     wl, rec = _tiny(N=32, n_ant=10, seed_cfg=104, bmax=200.0)
     w = imaging.uniform_weights(rec, wl.G, wl.N)
