@@ -185,13 +185,14 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer"], default=None,
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large"], default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     ap.add_argument("--iters", type=int, default=100, help="CLEAN iterations of --case clean")
+    ap.add_argument("--size", type=int, default=2560, choices=[1280, 2560, 5120], help="image side of --case large")
     args = ap.parse_args()
     if args.case:
-        run_case(args.case, args.instances, args.iters)
+        run_case(args.case, args.instances, args.iters, args.size)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -393,7 +394,7 @@ def main():
         dist.destroy_process_group()
 
 
-def run_case(case, n_inst=0, iters=100):
+def run_case(case, n_inst=0, iters=100, size=2560):
     """Small cases of the benchmark workload, a few GB on the device, for profiler captures.
 
     grad:  10 eager gradient-descent steps of the 512^2 differentiable-imaging workload.
@@ -402,12 +403,17 @@ def run_case(case, n_inst=0, iters=100):
     image0: muser_image on MUSER-II instances with max_iter 0 (the preparation kernels of the
             pipeline: uvw, strip sort, fused gridding + column pass, row pass, beam copies).
     steer: `n_inst` instances (default 8), Steer clean with `iters` major cycles at clip 0.9.
+    large: the large-image leg of the benchmark at one image side (`size`).
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
     import torch
     import paper_1712_06913_b300 as m
     import synth
+    if case == "large":
+        import paper_1712_06913_b300 as m2
+        print(json.dumps({"case": case, **large_images(m2, torch.cuda.current_stream(), sizes=(size,))}))
+        return
     if case == "grad":
         import numpy as np
         from paper_1712_06913_b300.autograd import GradientImaging
@@ -537,6 +543,48 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     ev_bytes = 2 * (4.0 * N4 * N4 + 2 * 16.0 * G4 * G4 + 8.0 * w4.vis.size)
     res["grad_GBps"] = res["grad_evals_per_s"] * ev_bytes / 1e9
     res.update(fft_vs_cufft(m, wl, cell, cfg, stream))
+    res["large_images"] = large_images(m, stream)
+    return res
+
+
+LARGE = {1280: (148, 148), 2560: (148, 74), 5120: (64, 32)}     # N: (instances, chunk)
+
+
+def large_images(m, stream, sizes=(1280, 2560, 5120)):
+    """Table 2's high-band image sides through muser_image (G = 4N, 1000 Hogbom iterations,
+    streaming CLEAN): images/s with inputs on the device, and the CLEAN bytes rate (read and
+    write the residual and read one beam window per iteration: 12 N^2)."""
+    import numpy as np
+    import torch
+    import synth
+    res = {}
+    for N in sizes:
+        B, chunk = LARGE[N]
+        n_band = int(((synth.muser2_channels() >= synth.LARGE_BANDS[N][0]) &
+                      (synth.muser2_channels() <= synth.LARGE_BANDS[N][1])).sum())
+        nf = -(-B // n_band)
+        wl = synth.config5_muser2_large(N, n_frame=nf, chans=list(range(min(B, n_band))))
+        cfg = m.Config(N=N, G=4 * N, W=wl.W, os=wl.OS, max_iter=1000, gain=wl.gain, lat_rad=wl.lat, batch_chunk=chunk)
+        cell = m.pixel_size(wl.freq, wl.bmax, N, wl.fov_min)
+        warm = m.Imager(wl.ant_enu, wl.pairs, wl.ha[:1], wl.dec[:1], wl.freq[:1], cell[:1], wl.vis[:1, :1],
+                        m.Config(**{**cfg.__dict__, "max_iter": 5, "batch_chunk": 0}), flags=wl.flags[:1, :1])
+        warm.run()
+        torch.cuda.synchronize()
+        del warm
+        im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+        im.ws.get(im.ws_bytes)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = im.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        Bt = wl.n_inst
+        iters = float(out.n_comp.double().sum())
+        res[f"N{N}"] = {"instances": Bt, "chunk": chunk, "ms": ms, "images_per_s": Bt / (ms / 1e3),
+                        "clean_iterations": iters, "algorithmic_GBps_clean_bytes": 12.0 * N * N * iters / (ms / 1e3) / 1e9}
+        del im, out
+        torch.cuda.empty_cache()
     return res
 
 
