@@ -20,6 +20,8 @@ Modules
   restore    -- clean beam fit and restored image                          (Alg. 1)
   centering  -- solar-disk centring and phase correction                   (Sec. 4.2, Alg. 1)
   operator   -- degridding forward operator, adjoint, chi-square gradient
+  steer      -- Steer clean in major cycles                                (Sec. 3.2, Alg. 1)
+  wproj      -- w-projection: w-kernel tables, gridding, direct transform with w (Sec. 6.1, Alg. 1)
   pipeline   -- one instance end to end
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests except where

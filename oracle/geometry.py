@@ -89,7 +89,9 @@ def grid_records(uvw_fcb, vis, flags, cell, G, W, dlm=None):
 
     Returns dict of arrays flattened over (frame, channel, baseline):
     ku, kv (int64, -1 when dropped), fu, fv, w (1 kept / 0 dropped), vis (complex128),
-    g (the two grid coordinates, for near-tie checks) and uvw.
+    g (the two grid coordinates, for near-tie checks), uvw, and wg = w (G cell)^2 (the w
+    coordinate in grid units, which selects the w-projection plane; 0 when dropped).
+    With w-projection W is the w-kernel support, so that its footprint stays on the grid.
     """
     F, C, nb, _ = uvw_fcb.shape
     h = (W - 1) // 2
@@ -115,6 +117,7 @@ def grid_records(uvw_fcb, vis, flags, cell, G, W, dlm=None):
         "vis": np.where(keep, V, 0).ravel(),
         "gu": gu.ravel(), "gv": gv.ravel(),
         "uvw": uvw_fcb.reshape(-1, 3),
+        "wg": np.where(keep, uvw_fcb[..., 2] * scale * np.asarray(cell, float)[None, :, None] * G, 0.0).ravel(),
     }
     return rec
 

@@ -102,12 +102,12 @@ def draw_sky(rng: np.random.Generator, n_bursts: int = 3, disk_lm=(0.0, 0.0)) ->
                burst_flux=rng.uniform(0.1, 2.0, size=n_bursts))
 
 
-def _sky_plane_projection(ant_enu, pairs, lat, ha, dec, freq):
+def _sky_plane_projection(ant_enu, pairs, lat, ha, dec, freq, with_w=False):
     """Baseline projections (u, v) in wavelengths via the sky-plane basis vectors.
 
     The local frame is expressed in equatorial axes (x: meridian on the equator,
     y: east, z: pole); the phase centre s0 points to (ha, dec); e_u = unit(z x s0)
-    and e_v = s0 x e_u.  Returns u, v of shape [F, C, n_bl].
+    and e_v = s0 x e_u.  Returns u, v of shape [F, C, n_bl] (and w = b . s0 with with_w).
     """
     east = np.array([0.0, 1.0, 0.0])
     north = np.array([-math.sin(lat), 0.0, math.cos(lat)])
@@ -118,6 +118,7 @@ def _sky_plane_projection(ant_enu, pairs, lat, ha, dec, freq):
     F, C = len(ha), len(freq)
     u = np.empty((F, C, len(pairs)))
     v = np.empty_like(u)
+    w = np.empty_like(u)
     zhat = np.array([0.0, 0.0, 1.0])
     for f in range(F):
         s0 = np.array([math.cos(dec[f]) * math.cos(-ha[f]),
@@ -130,7 +131,8 @@ def _sky_plane_projection(ant_enu, pairs, lat, ha, dec, freq):
         inv_lam = freq / C_LIGHT
         u[f] = inv_lam[:, None] * bu[None, :]
         v[f] = inv_lam[:, None] * bv[None, :]
-    return u, v
+        w[f] = inv_lam[:, None] * (b @ s0)[None, :]
+    return (u, v, w) if with_w else (u, v)
 
 
 def sky_visibilities(sky: Sky, u: np.ndarray, v: np.ndarray) -> np.ndarray:
@@ -143,6 +145,16 @@ def sky_visibilities(sky: Sky, u: np.ndarray, v: np.ndarray) -> np.ndarray:
     V = sky.disk_flux * disk * np.exp(-2j * math.pi * (u * l0 + v * m0))
     for (lb, mb), s, S in zip(sky.burst_lm, sky.burst_sigma, sky.burst_flux):
         V = V + S * np.exp(-2 * math.pi ** 2 * s ** 2 * q ** 2) * np.exp(-2j * math.pi * (u * lb + v * mb))
+    return V
+
+
+def point_visibilities_w(points, u, v, w):
+    """Noise-free visibilities of point sources [(l, m, flux), ...] with the w-term:
+    V = sum_j F_j exp(-2 pi i (u l_j + v m_j + w (n_j - 1))), n_j = sqrt(1 - l_j^2 - m_j^2)."""
+    V = np.zeros(np.shape(u), np.complex128)
+    for l, m, f in points:
+        n = math.sqrt(1.0 - l * l - m * m)
+        V = V + f * np.exp(-2j * math.pi * (u * l + v * m + w * (n - 1.0)))
     return V
 
 
@@ -279,6 +291,34 @@ def config5_muser2_large(N=2560, n_frame=1, chans=None) -> Workload:
     ha = EARTH_RATE * 0.20625 * np.arange(n_frame)
     return make_workload(f"muser2-band-N{N}", ant, baseline_pairs(60), ha, np.full(n_frame, DEC_SUN), freq,
                          N, 4 * N, config_id=5 + N, flag_max=0.3, max_iter=1000)
+
+
+def wterm_workload(N=64, n_ant=10, bmax=300.0, ha=0.8, freq=(1.7e9,), n_frame=1, config_id=400,
+                   snr=100.0) -> Workload:
+    """Point sources seen far from transit (hour angle ``ha`` rad), so that |w| reaches the
+    longest baselines and the w-term phase pi (l^2 + m^2) w is of order 1 rad at the edge of
+    the field (Sec. 6.1): seven sources over the image, visibilities with the w-term."""
+    ant = spiral_array(n_ant, 4.0, centre=(n_ant % 3 == 1), bmax=bmax)
+    pairs = baseline_pairs(n_ant)
+    has = ha + EARTH_RATE * 0.025 * np.arange(n_frame)
+    dec = np.full(n_frame, DEC_SUN)
+    freq = np.asarray(freq, float)
+    u, v, w = _sky_plane_projection(ant, pairs, MINGANTU_LAT, has, dec, freq, with_w=True)
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_ROOT, config_id])))
+    fov = 60.0 * ARCMIN
+    pts = [(float(a), float(b), float(c)) for a, b, c in
+           zip(rng.uniform(-0.45, 0.45, 7) * fov, rng.uniform(-0.45, 0.45, 7) * fov, rng.uniform(0.3, 1.0, 7))]
+    vis = np.empty((n_frame, len(freq), len(pairs)), np.complex64)
+    for f in range(n_frame):
+        Vm = point_visibilities_w(pts, u[f], v[f], w[f])
+        for c in range(len(freq)):
+            nrng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_ROOT, config_id, f, c])))
+            sig = math.sqrt(np.mean(np.abs(Vm[c]) ** 2)) / snr
+            noise = nrng.normal(size=(len(pairs), 2)) * (sig / math.sqrt(2.0))
+            vis[f, c] = (Vm[c] + noise[:, 0] + 1j * noise[:, 1]).astype(np.complex64)
+    return Workload(name=f"wterm-N{N}", ant_enu=ant, pairs=pairs, lat=MINGANTU_LAT, ha=has, dec=dec, freq=freq,
+                    vis=vis, flags=np.zeros(vis.shape, np.uint8), N=N, G=4 * N, bmax=bmax, max_iter=100,
+                    skies=[pts])
 
 
 def config4_operator() -> Workload:

@@ -134,3 +134,26 @@ def test_steer_scaling_over_selection_only_is_caught(monkeypatch):
         return R, model, cap
     monkeypatch.setattr(steer, "steer", bad)
     _fails(pins.test_steer_linear_invariant_and_threshold)
+
+
+def test_wproj_negative_w_not_conjugated_is_caught(monkeypatch):
+    from oracle import wproj
+    orig_grid = wproj.grid
+
+    def bad(rec, G, tabs, wg_max, Ww, OS):
+        r = dict(rec)
+        r["wg"] = np.abs(rec["wg"])                 # every sample treated as w >= 0
+        return orig_grid(r, G, tabs, wg_max, Ww, OS)
+    monkeypatch.setattr(wproj, "grid", bad)
+    _fails(pins.test_wproj_dirty_matches_direct_transform_with_w)
+
+
+def test_wproj_screen_sign_flipped_is_caught(monkeypatch):
+    from oracle import wproj
+    orig = wproj.kernel_tables
+
+    def bad(*a, **k):
+        return np.conj(orig(*a, **k))                # exp(+i pi wg xi^2): the opposite chirp
+    monkeypatch.setattr(wproj, "kernel_tables", bad)
+    _fails(pins.test_wproj_dirty_matches_direct_transform_with_w)
+    _fails(pins.test_wproj_kernel_image_plane_is_screen_times_correction)

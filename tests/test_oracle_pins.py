@@ -461,3 +461,76 @@ def test_gradient_descent_decreases_chi2():
     x, hist = operator.gradient_descent(rec, rec["vis"], 0.5, N, G, KER, steps=15)
     assert np.all(np.diff(hist) <= 1e-9 * hist[0])
     assert hist[-1] < 0.5 * hist[0]
+
+
+# ----------------------------------------------------------------------------- w-projection
+def _wterm_case(Ww=15):
+    wl = synth.wterm_workload()
+    uvw = geometry.uvw(wl.ant_enu, wl.pairs, wl.lat, wl.ha, wl.dec, wl.freq)
+    rec = geometry.grid_records(uvw, wl.vis, wl.flags, pipeline.cell_sizes(wl), wl.G, Ww)
+    return wl, rec
+
+
+def test_wproj_plane0_kernel_is_the_spheroidal():
+    """k_0 (no w) transforms back to the spheroidal kernel up to its aliasing (Sec. 3.2.3)."""
+    from oracle import wproj
+    tabs = wproj.kernel_tables(10.0, 8, 15, 1024, KER)
+    d = np.arange(tabs.shape[1]) / 1024
+    assert np.abs(tabs[0].imag).max() < 1e-14
+    assert np.abs(tabs[0] - KER.kernel(d)).max() <= 3e-4
+    # tabulated kernel as a function of wg: only the first plane is real
+    assert np.abs(tabs[1].imag).max() > 1e-3
+
+
+def test_wproj_kernel_image_plane_is_screen_times_correction():
+    """The transform of k_p over its support is gc(xi) exp(-i pi wg_p xi^2) (normalised) inside
+    the band that the kernel support resolves."""
+    from oracle import wproj
+    P, Ww, OS, wgmax = 5, 21, 256, 8.0
+    tabs = wproj.kernel_tables(wgmax, P, Ww, OS, KER)
+    d = np.arange(-(Ww // 2) * OS, (Ww // 2) * OS + 1) / OS
+    xi = np.linspace(-0.35, 0.35, 15)
+    g_norm = np.sum(np.polynomial.legendre.leggauss(256)[1] * 0.5 * KER.psi(np.polynomial.legendre.leggauss(256)[0]))
+    for p in range(P):
+        k = wproj.lookup(tabs[p], OS, d)
+        ft = (k[None, :] * np.exp(2j * np.pi * np.outer(xi, d))).sum(1) / OS
+        want = KER.psi(2 * xi) * np.exp(-1j * np.pi * p * wgmax / (P - 1) * xi * xi) / g_norm
+        assert np.abs(ft - want).max() <= 2e-3, p
+
+
+def test_wproj_dirty_matches_direct_transform_with_w():
+    """Far from transit (|w| up to 1550 wavelengths, phase error ~1 rad at the field edge) the
+    w-projected map and beam follow the direct transform with the w-term; 2-D gridding
+    does not (Sec. 6.1)."""
+    from oracle import wproj
+    wl, rec = _wterm_case()
+    assert np.abs(rec["uvw"][:, 2]).max() > 1000
+    wgmax = np.abs(rec["wg"]).max()
+    tabs = wproj.kernel_tables(wgmax, 128, 15, 1024, KER)
+    Z = wproj.grid(rec, wl.G, tabs, wgmax, 15, 1024)
+    D, Bm, _ = imaging.dirty_and_beam(Z, wl.N, KER)
+    Dd, Bd = wproj.direct_dirty_w(rec, wl.N, pipeline.cell_sizes(wl)[0])
+    err_d = np.abs(D - Dd).max() / np.abs(Dd).max()
+    err_b = np.abs(Bm - Bd).max()
+    assert err_d <= 5e-4 and err_b <= 2.5e-3
+    D2, B2, _ = imaging.dirty_and_beam(imaging.grid(rec, wl.G, KER), wl.N, KER)
+    assert np.abs(D2 - Dd).max() / np.abs(Dd).max() > 20 * 5e-4
+    assert np.abs(B2 - Bd).max() > 20 * 2.5e-3
+    # map and beam are real transforms of Hermitian grids
+    G = wl.G
+    ZV = 0.5 * (Z + np.conj(Z[(-np.arange(G)) % G][:, (-np.arange(G)) % G]))
+    I = imaging.centred_inverse_dft2(ZV)
+    assert np.abs(I.imag).max() <= 1e-9 * np.abs(I.real).max()
+
+
+def test_wproj_zero_w_is_plain_gridding_with_plane0():
+    """With every w = 0 the w-projected grid is the 2-D grid of the plane-0 kernel, which is the
+    spheroidal up to its aliasing."""
+    from oracle import wproj
+    wl, rec = _wterm_case(Ww=7)
+    rec = dict(rec)
+    rec["wg"] = np.zeros_like(rec["wg"])
+    tabs = wproj.kernel_tables(5.0, 16, 7, 1024, KER)
+    Z = wproj.grid(rec, wl.G, tabs, 5.0, 7, 1024)
+    Z0 = imaging.grid(rec, wl.G, KER)
+    assert np.abs(Z - Z0).max() <= 1e-3 * np.abs(Z0).max()
