@@ -356,7 +356,7 @@ def main():
                                    "bytes") if tr else None,
                 "note": "beam windows are served mostly from L2, so achieved bytes/s can exceed the HBM copy rate",
                 "hbm_equivalent_GBps": statistics.mean(hbm_equiv_bytes) / (clean_ms / 1e3) / 1e9}
-    grid_bytes = args.chunk * (24.0 * wl.n_bl + 8.0 * G * G)
+    grid_bytes = args.chunk * (32.0 * wl.n_bl + 8.0 * G * G)
     extra = {"phase_ms_per_chunk": {k: statistics.mean(v) for k, v in phase.items()},
              "gridding_GBps": grid_bytes / (statistics.mean(phase["grid"]) / 1e3) / 1e9,
              "dirty_fft_GBps": args.chunk * (8.0 * G * G + 4.0 * G * G * 2 + 4.0 * N * N + 16.0 * N * N)

@@ -89,18 +89,28 @@ typedef struct muser_config {
   int32_t batch_chunk;  /* muser_image: instances per internal chunk (0 = whole batch) */
   int32_t clean_kernel; /* 0: residual held on chip for N = 256/512/1024 when the device allows
                            (else streaming); 1: always stream the residual from memory */
-  int32_t reserved[6];  /* must be zero */
+  int32_t w_planes;     /* w-projection (Alg. 1 dirty_image, Sec. 6.1): number of w-planes P, 0 = off
+                           (2-D imaging), else 2..1024.  Imaging calls only (not muser_degrid). */
+  float w_max;          /* largest |wg| the planes cover (wg = w (G cell)^2, record field wg);
+                           planes at p w_max / (P - 1); larger |wg| take the last plane */
+  int32_t w_support;    /* w-kernel support in cells, odd, W..31 (used when w_planes > 0) */
+  int32_t reserved[3];  /* must be zero */
 } muser_config_t;
 
-/* One gridding record per visibility, 24 bytes (written by muser_uvw).
+/* One gridding record per visibility, 32 bytes (written by muser_uvw).
  * (ku, kv) is the nearest uv cell of the +uv sample, (fu, fv) = k - g in [-1/2, 1/2]
- * its offset from the exact grid coordinate g, vis the phase-corrected visibility and
- * w its weight (0 = not imaged: flagged, non-finite or off-grid; ku = kv = -1 then). */
+ * its offset from the exact grid coordinate g, vis the phase-corrected visibility,
+ * w its weight (0 = not imaged: flagged, non-finite or off-grid; ku = kv = -1 then) and
+ * wg = w_coordinate (G cell)^2, the w-term in grid units (selects the w-projection plane;
+ * 0 when not imaged).  With w-projection on, a record is kept only if the w_support-wide
+ * footprint of both samples lies on the grid. */
 typedef struct muser_vis_record {
   float vis_re, vis_im;
   float fu, fv;
   int16_t ku, kv;
   float w;
+  float wg;
+  int32_t pad;          /* 0 */
 } muser_vis_record_t;
 
 MUSER_API const char *muser_version(void);

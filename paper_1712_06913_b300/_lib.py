@@ -31,7 +31,8 @@ class Config(ctypes.Structure):
                 ("weight_mode", ctypes.c_int32), ("peak_mode", ctypes.c_int32), ("thr_mode", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("gain", ctypes.c_float), ("gmm_bins", ctypes.c_int32),
                 ("lat_rad", ctypes.c_double), ("batch_chunk", ctypes.c_int32), ("clean_kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("w_planes", ctypes.c_int32), ("w_max", ctypes.c_float), ("w_support", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 P = ctypes.c_void_p

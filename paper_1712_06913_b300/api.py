@@ -16,7 +16,7 @@ import torch
 from . import _lib
 from ._lib import CALL_CENTER, CALL_CHI2, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
 
-RECORD_FLOATS = 6          # 24-byte record viewed as float32[6]
+RECORD_FLOATS = 8          # 32-byte record viewed as float32[8]
 
 
 @dataclasses.dataclass
@@ -35,11 +35,14 @@ class Config:
     lat_rad: float = 0.0
     batch_chunk: int = 0
     clean_kernel: int = 0       # 0 auto (on-chip residual when possible), 1 streaming
+    w_planes: int = 0           # w-projection planes (0: 2-D imaging)
+    w_max: float = 0.0          # largest |wg| = |w| (G cell)^2 the planes cover
+    w_support: int = 15         # w-kernel support (cells, odd)
 
     def c(self) -> _lib.Config:
         return _lib.Config(self.N, self.G, self.W, self.os, self.weight_mode, self.peak_mode, self.thr_mode,
                            self.max_iter, self.gain, self.gmm_bins, self.lat_rad, self.batch_chunk,
-                           self.clean_kernel)
+                           self.clean_kernel, self.w_planes, self.w_max, self.w_support)
 
 
 def _p(t):
@@ -101,7 +104,7 @@ def pixel_size(freq_hz, bmax_m, N, fov_min_rad):
 
 
 def uvw(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None, want_uvw=False, status=None):
-    """Records [F*C*nb, 6] float32 (24-byte muser_vis_record_t), optional uvw [F*C*nb, 3] f64."""
+    """Records [F*C*nb, 8] float32 (32-byte muser_vis_record_t), optional uvw [F*C*nb, 3] f64."""
     ant = _dev(ant_enu, torch.float64)
     pr = _dev(pairs, torch.int32)
     ha_t, dec_t = _dev(ha, torch.float64), _dev(dec, torch.float64)
@@ -120,10 +123,10 @@ def uvw(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=N
 
 
 def record_fields(rec: torch.Tensor):
-    """Split [n, 6] float32 records into (vis complex64, fu, fv, ku, kv, w)."""
+    """Split [n, 8] float32 records into (vis complex64, fu, fv, ku, kv, w, wg)."""
     vis = torch.complex(rec[:, 0], rec[:, 1])
     k = rec[:, 4].contiguous().view(torch.int16)
-    return vis, rec[:, 2], rec[:, 3], k[0::2].to(torch.int64), k[1::2].to(torch.int64), rec[:, 5]
+    return vis, rec[:, 2], rec[:, 3], k[0::2].to(torch.int64), k[1::2].to(torch.int64), rec[:, 5], rec[:, 6]
 
 
 def grid(rec, vis_off, cfg: Config, status=None, ws: Workspace = None):

@@ -61,23 +61,44 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (cfg->gmm_bins < 2 || cfg->gmm_bins > 4096) return fail(MUSER_ERR_ARG, "gmm_bins must be in [2, 4096]");
   if (cfg->batch_chunk < 0) return fail(MUSER_ERR_ARG, "batch_chunk must be >= 0");
   if (cfg->clean_kernel != 0 && cfg->clean_kernel != 1) return fail(MUSER_ERR_ARG, "clean_kernel must be 0 or 1");
-  for (int i = 0; i < 6; i++)
+  for (int i = 0; i < 3; i++)
     if (cfg->reserved[i] != 0) return fail(MUSER_ERR_ARG, "reserved fields must be zero");
+  if (cfg->w_planes != 0) {
+    if (mode != IMAGING) return fail(MUSER_ERR_UNSUPPORTED, "w-projection applies to imaging calls only");
+    if (cfg->w_planes < 2 || cfg->w_planes > 1024) return fail(MUSER_ERR_ARG, "w_planes must be 0 or in [2, 1024]");
+    if (!(cfg->w_max > 0.f) || !isfinite(cfg->w_max)) return fail(MUSER_ERR_ARG, "w_max must be positive and finite");
+    if (cfg->w_support < cfg->W || cfg->w_support > 31 || (cfg->w_support & 1) == 0)
+      return fail(MUSER_ERR_ARG, "w_support must be odd in [W, 31]");
+  }
   return MUSER_OK;
 }
 
 bool copies(const muser_config_t &c);
 
 // ----------------------------------------------------------------------- workspace layouts
+// w-projection kernel tables [w_planes][table_len(w_support, os)] (none for 2-D imaging)
+template <class A>
+float2 *carve_wtab(A &a, const muser_config_t &c) {
+  return c.w_planes > 0 ? (float2 *)a.template take<float2>((size_t)c.w_planes * table_len(c.w_support, c.os))
+                        : nullptr;
+}
+WProj make_wproj(const float2 *tab, const muser_config_t &c) {
+  if (!tab) return no_wproj();
+  return WProj{tab, c.w_planes, table_len(c.w_support, c.os), (float)(c.w_planes - 1) / c.w_max};
+}
+
 template <class A>
 struct GridWs {
   float *tab;
+  float2 *wtab;
   int32_t *bin_off, *entries;
   void carve(A &a, int B, int64_t n_vis, const muser_config_t &c, bool mirror) {
     const int rows = grid_band_rows(c.G), nb = c.G / rows;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
+    wtab = carve_wtab(a, c);
     bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (nb + 1));
-    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) * tiles_per_sample(c.W, rows, c.G, c.G));
+    entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) *
+                                                  tiles_per_sample(w_footprint(c), rows, c.G, c.G));
   }
 };
 
@@ -104,6 +125,7 @@ template <class A>
 struct ImageWs {
   Rec *rec;
   float *tab;
+  float2 *wtab;                 // w-projection tables (nullptr for 2-D imaging)
   int32_t *bin_off, *entries;   // per-strip sample lists of the fused gridding
   float *beam[2], *mu_a[2], *mu_b[2], *params;
   int *next[2];
@@ -112,8 +134,9 @@ struct ImageWs {
     const int S = dirty_strip_width(c.G);
     rec = (Rec *)a.template take<Rec>((size_t)Bc * n_bl);
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
+    wtab = carve_wtab(a, c);
     bin_off = (int32_t *)a.template take<int32_t>((size_t)Bc * (c.G / S + 1));
-    entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(c.W, c.G, S, c.G));
+    entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(w_footprint(c), c.G, S, c.G));
     d.carve(a, Bc, c);
     for (int k = 0; k < 2; k++) {
       beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
@@ -317,15 +340,18 @@ int muser_uvw(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_b
               muser_vis_record_t *rec_out, double *uvw_out, int32_t *status, muser_stream_t stream) {
   if (!cfg) return fail(MUSER_ERR_ARG, "cfg is NULL");
   if (cfg->G < 8 || cfg->G > 32767 || cfg->W < 3 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "invalid G or W");
+  if (cfg->w_planes > 0 && (cfg->w_support < cfg->W || (cfg->w_support & 1) == 0))
+    return fail(MUSER_ERR_ARG, "w_support must be odd and >= W");
   if (n_ant < 2 || n_bl < 0 || n_frame < 0 || n_chan < 0) return fail(MUSER_ERR_ARG, "negative sizes");
   const int64_t n_inst = (int64_t)n_frame * n_chan;
   if (n_inst * n_bl == 0) return MUSER_OK;
   if (!ant_enu || !bl_pairs || !ha || !dec || !freq_hz || !cell_rad || !vis || !rec_out)
     return fail(MUSER_ERR_ARG, "muser_uvw: required pointer is NULL");
   if (n_inst > INT32_MAX) return fail(MUSER_ERR_ARG, "too many instances");
-  if (!aligned(vis, 8) || !aligned(rec_out, 8)) return fail(MUSER_ERR_ARG, "vis and rec_out must be 8-byte aligned");
+  if (!aligned(vis, 8) || !aligned(rec_out, 16)) return fail(MUSER_ERR_ARG, "vis must be 8-, rec_out 16-byte aligned");
   launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, 0,
-             (int)n_inst, cfg->G, cfg->W, cfg->lat_rad, (Rec *)rec_out, uvw_out, status, (cudaStream_t)stream);
+             (int)n_inst, cfg->G, w_footprint(*cfg), cfg->lat_rad, (Rec *)rec_out, uvw_out, status,
+             (cudaStream_t)stream);
   return check_launch("muser_uvw");
 }
 
@@ -345,9 +371,11 @@ int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int
   w.carve(a, B, n_vis_total, *cfg, true);
   cudaStream_t s = (cudaStream_t)stream;
   launch_pswf_table(w.tab, cfg->W, cfg->os, nullptr, 0, s);
-  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, cfg->W, cfg->os, w.tab, true, nullptr, grid_band_rows(cfg->G),
-              cfg->G, (float2 *)Z, w.bin_off,
-              w.entries, status, false, s);
+  if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
+                          cfg->W, s);
+  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, w_footprint(*cfg), cfg->os, w.tab, true, nullptr,
+              grid_band_rows(cfg->G), cfg->G, (float2 *)Z, w.bin_off, w.entries, status, false, s,
+              make_wproj(w.wtab, *cfg));
   return check_launch("muser_grid");
 }
 
@@ -463,6 +491,10 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   const int n_chunks = (B + Bc - 1) / Bc;
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
   launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s);
+  if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
+                          cfg->W, s);
+  const WProj wp = make_wproj(w.wtab, *cfg);
+  const int Wf = w_footprint(*cfg);
   fft::launch_twiddles(w.d.tw, G, s);
   // chunk c up to its CLEAN input, on the caller's stream
   auto prepare = [&](int c) {
@@ -470,9 +502,9 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     int32_t *st = status + c0;
     float *R = residual + (size_t)c0 * N * N;
     launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, c0, n, G,
-               cfg->W, cfg->lat_rad, w.rec, nullptr, status, s);
-    launch_dirty_gridded(w.rec, n_bl, n, N, G, cfg->W, cfg->os, w.tab, w.bin_off, w.entries, w.d.tw, w.d.gc, w.d.T,
-                         w.d.partial, R, w.beam[k], st, s);
+               Wf, cfg->lat_rad, w.rec, nullptr, status, s);
+    launch_dirty_gridded(w.rec, n_bl, n, N, G, Wf, cfg->os, w.tab, w.bin_off, w.entries, w.d.tw, w.d.gc, w.d.T,
+                         w.d.partial, R, w.beam[k], st, s, wp);
     if (cfg->thr_mode == 1) {
       launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a[k], w.mu_b[k], st, s);
       if (thr_out) {

@@ -11,15 +11,17 @@
 
 namespace muser {
 
-// 24-byte gridding record, identical layout to muser_vis_record_t.
-struct __align__(8) Rec {
+// 32-byte gridding record, identical layout to muser_vis_record_t (one 32-byte sector).
+struct __align__(16) Rec {
   float2 v;
   float fu, fv;
   short ku, kv;
   float w;
+  float wg;      // w coordinate x (G cell)^2: the w-projection plane selector
+  int pad;
 };
-static_assert(sizeof(Rec) == 24, "record must be 24 bytes");
-static_assert(sizeof(muser_vis_record_t) == 24, "public record must be 24 bytes");
+static_assert(sizeof(Rec) == 32, "record must be 32 bytes");
+static_assert(sizeof(muser_vis_record_t) == 32, "public record must be 32 bytes");
 
 constexpr int kMaxLegendre = 32;   // even Legendre terms of the spheroidal expansion
 
@@ -67,6 +69,41 @@ __device__ __forceinline__ bool record_ok(const Rec &R, int G, int h) {
 // Pixel-size independent sizes of the spheroidal kernel table.
 inline int table_len(int W, int os) { return (W * os) / 2 + 2; }
 
+// ---- w-projection (the w-term correction of dirty_image): P planes of complex 1-D kernels,
+// tab[p][j] = k_p(j / os), k_p(d) = int gc(xi) exp(-i pi wg_p xi^2) exp(-2 pi i d xi) dxi /
+// int gc(xi) dxi over xi in [-1/2, 1/2], wg_p = p w_max / (P - 1) (paraxial w-term in grid
+// units wg = w (G cell)^2).  A sample takes plane min(P - 1, floor(|wg| (P - 1) / w_max + 1/2)),
+// the product k_p(tu + fu) k_p(tv + fv), conjugated when wg < 0; its mirror the conjugate.
+struct WProj {
+  const float2 *tab;   // nullptr: 2-D imaging with the spheroidal kernel
+  int P, ntab;
+  float inv_dw;        // (P - 1) / w_max
+};
+inline WProj no_wproj() { return WProj{nullptr, 0, 0, 0.f}; }
+inline int w_footprint(const muser_config_t &c) { return c.w_planes > 0 ? c.w_support : c.W; }
+
+__device__ __forceinline__ float2 wkernel_lookup(const float2 *__restrict__ tab, int ntab, float os, float d) {
+  float pos = fabsf(d) * os;
+  int i = (int)floorf(pos);
+  float t = pos - (float)i;
+  if (i > ntab - 2) return make_float2(0.f, 0.f);
+  const float2 a = __ldg(tab + i), b = __ldg(tab + i + 1);
+  return make_float2(a.x * (1.f - t) + b.x * t, a.y * (1.f - t) + b.y * t);
+}
+// plane table of a record and whether its kernel is conjugated (w < 0 xor mirrored sample)
+__device__ __forceinline__ const float2 *wplane(const WProj &wp, const Rec &R, int sg, bool &conj) {
+  const int p = min(wp.P - 1, (int)floorf(fabsf(R.wg) * wp.inv_dw + 0.5f));
+  conj = (R.wg < 0.f) != (sg != 0);
+  return wp.tab + (size_t)p * wp.ntab;
+}
+__device__ __forceinline__ float2 wtap(const float2 *__restrict__ t, int ntab, float os, bool conj, float du,
+                                       float dv) {
+  float2 K = cmul(wkernel_lookup(t, ntab, os, du), wkernel_lookup(t, ntab, os, dv));
+  if (conj) K.y = -K.y;
+  return K;
+}
+void launch_wtab(float2 *tab, int P, int ntab, int os, int Ww, float w_max, int W, cudaStream_t s);
+
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
 // Simple bump allocator over a caller workspace.
@@ -110,9 +147,10 @@ __host__ __device__ inline int tiles_per_sample(int W, int tr, int tc, int G) {
 // at +uv only (adjoint of degridding).  Tiles of tr x tc cells (tc >= 2); every tile of Z is
 // written, so Z need not be cleared.  sorted: bin_off/entries already hold this record set's
 // tile lists (same rec, offsets, G, W, tr, tc, mirror), so the sort is skipped.
+// W is the footprint (the w-kernel support when wp.tab is set).
 void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
                  const float *tab, bool mirror, const float2 *vals, int tr, int tc, float2 *Z, int32_t *bin_off,
-                 int32_t *entries, int32_t *status, bool sorted, cudaStream_t s);
+                 int32_t *entries, int32_t *status, bool sorted, cudaStream_t s, WProj wp = WProj{nullptr, 0, 0, 0.f});
 void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, bool mirror,
                       int tr, int tc, int32_t *bin_off, int32_t *entries, int32_t *status, cudaStream_t s);
 
@@ -123,7 +161,8 @@ int dirty_strip_width(int G);
 // then column pass and row pass as launch_dirty.
 void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
                           int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
-                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
+                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
+                          WProj wp = WProj{nullptr, 0, 0, 0.f});
 void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T,
                   float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
 namespace fft {

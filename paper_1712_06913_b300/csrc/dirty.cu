@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restri
                                                             const int32_t *__restrict__ bin_off,
                                                             const int32_t *__restrict__ entries,
                                                             const float2 *__restrict__ tw, float2 *__restrict__ T,
-                                                            float *__restrict__ partial) {
+                                                            float *__restrict__ partial, WProj wp) {
   using C = ColCfg<G>;
   using Lay = typename C::Layout;
   constexpr int S = C::S, NT = C::NT, NS = G / S;
@@ -97,6 +97,21 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restri
       const int sg = code & 1;
       const Rec R = ri[code >> 1];
       const float2 val = make_float2(R.v.x * R.w, (sg ? -R.v.y : R.v.y) * R.w + R.w);   // w (V + i), mirror w (V* + i)
+      if (wp.tab) {                               // w-projection: complex taps of the sample's plane
+        bool cj;
+        const float2 *wt = wplane(wp, R, sg, cj);
+        for (int tap = lane; tap < WW; tap += 32) {
+          const int tv = tap / W - h, tu = tap % W - h;
+          const int col = (sg ? G - R.ku - tu : R.ku + tu) - x0;
+          if (col < 0 || col >= S) continue;
+          const int row = sg ? G - R.kv - tv : R.kv + tv;
+          const float2 a = cmul(wtap(wt, wp.ntab, os, cj, (float)tu + R.fu, (float)tv + R.fv), val);
+          float2 *cell = sm + Lay::at(row, col);
+          atomicAdd(&cell->x, a.x);
+          atomicAdd(&cell->y, a.y);
+        }
+        continue;
+      }
       for (int tap = lane; tap < WW; tap += 32) {
         const int tv = tap / W - h, tu = tap % W - h;
         const int col = (sg ? G - R.ku - tu : R.ku + tu) - x0;
@@ -217,7 +232,8 @@ void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float
 template <int G>
 void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W, int os, const float *tab,
                             const int32_t *bin_off, const int32_t *entries, const float2 *tw, const float *gc,
-                            float2 *T, float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+                            float2 *T, float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
+                            WProj wp) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   cudaFuncSetAttribute(k_cols_grid<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
@@ -227,7 +243,7 @@ void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W,
     const int n = B - i < 65535 ? B - i : 65535;
     k_cols_grid<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(
         rec + (size_t)i * stride, stride, W, tab, table_len(W, os), (float)os, bin_off + (size_t)i * (G / CC::S + 1),
-        entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S));
+        entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S), wp);
     note_launch();
     k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
                                                          partial + (size_t)i * (G / CC::S), N,
@@ -273,7 +289,7 @@ void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const 
 
 void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
                           int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
-                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s, WProj wp) {
   if (B <= 0) return;
   const int S = dirty_strip_width(G);
   if (S == 0) return;
@@ -282,7 +298,7 @@ void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, i
 #define MUSER_CASE(g)                                                                                          \
   case g:                                                                                                      \
     launch_dirty_gridded_G<g>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial, dirty, beam, \
-                              status, s);                                                                      \
+                              status, s, wp);                                                                  \
     break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
     MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240) MUSER_CASE(20480)

@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(256) k_grid_tile(const Rec *__restrict__ rec, 
                                                    int64_t stride, int inst0, int G, int W, int tr, int tc,
                                                    const float *__restrict__ tab, int ntab, float os, int mirror,
                                                    const float2 *__restrict__ vals, const int32_t *__restrict__ bin_off,
-                                                   const int32_t *__restrict__ entries, float2 *__restrict__ Z) {
+                                                   const int32_t *__restrict__ entries, float2 *__restrict__ Z,
+                                                   WProj wp) {
   extern __shared__ float4 tile4[];
   float2 *tile = reinterpret_cast<float2 *>(tile4);
   const int ntc = G / tc;
@@ -155,6 +156,21 @@ __global__ void __launch_bounds__(256) k_grid_tile(const Rec *__restrict__ rec, 
       val = vals[r0 + i];
     } else {
       val = make_float2(R.v.x * R.w, (sg ? -R.v.y : R.v.y) * R.w + R.w);   // w (V + i) or w (conj V + i)
+    }
+    if (wp.tab) {                                 // w-projection: complex taps of the sample's plane
+      bool cj;
+      const float2 *wt = wplane(wp, R, sg, cj);
+      for (int tap = lane; tap < WW; tap += 32) {
+        const int tv = tap / W - h, tu = tap % W - h;
+        const int row = sg ? G - R.kv - tv : R.kv + tv;
+        const int col = sg ? G - R.ku - tu : R.ku + tu;
+        if (row < row0 || row >= row0 + tr || col < col0 || col >= col0 + tc) continue;
+        const float2 a = cmul(wtap(wt, wp.ntab, os, cj, (float)tu + R.fu, (float)tv + R.fv), val);
+        float2 *cell = tile + (row - row0) * tc + (col - col0);
+        atomicAdd(&cell->x, a.x);
+        atomicAdd(&cell->y, a.y);
+      }
+      continue;
     }
     for (int tap = lane; tap < WW; tap += 32) {
       const int tv = tap / W - h, tu = tap % W - h;
@@ -196,7 +212,7 @@ void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stri
 
 void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
                  const float *tab, bool mirror, const float2 *vals, int tr, int tc, float2 *Z, int32_t *bin_off,
-                 int32_t *entries, int32_t *status, bool sorted, cudaStream_t s) {
+                 int32_t *entries, int32_t *status, bool sorted, cudaStream_t s, WProj wp) {
   if (B <= 0) return;
   const int nb = (G / tr) * (G / tc);
   if (!sorted) launch_grid_sort(rec, vis_off, dense_stride, B, G, W, mirror, tr, tc, bin_off, entries, status, s);
@@ -206,7 +222,7 @@ void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, i
     int n = B - i < 65535 ? B - i : 65535;
     dim3 grid(nb, n);
     k_grid_tile<<<grid, 256, tile_smem, s>>>(rec, vis_off, dense_stride, i, G, W, tr, tc, tab, table_len(W, os),
-                                             (float)os, mirror ? 1 : 0, vals, bin_off, entries, Z);
+                                             (float)os, mirror ? 1 : 0, vals, bin_off, entries, Z, wp);
     note_launch();
   }
 }

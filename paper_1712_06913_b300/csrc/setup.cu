@@ -148,6 +148,64 @@ __global__ void k_pswf_fill(Pswf P, float *tab, int ntab, int W, int os, float *
   }
 }
 
+// ---- w-projection kernel tables
+// Gauss-Legendre rule of kGL nodes on [-1, 1]: node i by Newton's method on P_n from
+// x0 = cos(pi (i + 3/4) / (n + 1/2)), P_n and P_{n-1} by the three-term recurrence,
+// P_n'(x) = n (x P_n - P_{n-1}) / (x^2 - 1); weight 2 / ((1 - x^2) P_n'(x)^2).  i < n/2 gives
+// the positive half of the (symmetric) node set.
+constexpr int kGL = 256;
+__device__ void gl_node(int i, int n, double &x, double &wgt) {
+  x = cos(M_PI * (i + 0.75) / (n + 0.5));
+  double dp = 1.0;
+  for (int it = 0; it < 64; it++) {
+    double p0 = 1.0, p1 = x;
+    for (int m = 1; m < n; m++) {
+      const double p2 = ((2.0 * m + 1.0) * x * p1 - m * p0) / (m + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (x * p1 - p0) / (x * x - 1.0);
+    const double dx = p1 / dp;
+    x -= dx;
+    if (fabs(dx) < 1e-16) break;
+  }
+  wgt = 2.0 / ((1.0 - x * x) * dp * dp);
+}
+
+// tab[p][j] = k_p(j / os) = sum over nodes of g(xi) exp(-i pi wg_p xi^2) exp(-2 pi i d xi) / sum g,
+// g = quadrature weight x gc(xi), xi = node / 2; the nodes +-xi are summed as one cosine.
+__global__ void __launch_bounds__(256) k_wtab(Pswf Ps, int ntab, int os, int Ww, double dwg, float2 *tab) {
+  __shared__ double xs[kGL / 2], cr[kGL / 2], ci[kGL / 2], gs[kGL / 2];
+  const int p = blockIdx.y, t = threadIdx.x;
+  if (t < kGL / 2) {
+    double x, wq;
+    gl_node(t, kGL, x, wq);
+    const double xi = 0.5 * x;
+    const double g = 0.5 * wq * psi_dev(Ps, 2.0 * xi);
+    double sn, cs;
+    sincospi(-(p * dwg) * xi * xi, &sn, &cs);
+    xs[t] = xi;
+    cr[t] = 2.0 * g * cs;
+    ci[t] = 2.0 * g * sn;
+    gs[t] = 2.0 * g;
+  }
+  __syncthreads();
+  double norm = 0.0;
+  for (int k = 0; k < kGL / 2; k++) norm += gs[k];
+  for (int j = blockIdx.x * blockDim.x + t; j < ntab; j += gridDim.x * blockDim.x) {
+    const double d = (double)j / os;
+    double re = 0.0, im = 0.0;
+    if (d <= 0.5 * Ww) {
+      for (int k = 0; k < kGL / 2; k++) {
+        const double c = cospi(2.0 * d * xs[k]);
+        re += cr[k] * c;
+        im += ci[k] * c;
+      }
+    }
+    tab[(size_t)p * ntab + j] = make_float2((float)(re / norm), (float)(im / norm));
+  }
+}
+
 }  // namespace
 
 const Pswf &pswf_coefficients(int W) {
@@ -169,6 +227,15 @@ void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t
   int total = ntab + (gc ? G : 0);
   if (total == 0) return;
   k_pswf_fill<<<(total + 255) / 256, 256, 0, s>>>(P, tab, ntab, W, os, gc, G);
+  note_launch();
+}
+
+void launch_wtab(float2 *tab, int P, int ntab, int os, int Ww, float w_max, int W, cudaStream_t s) {
+  if (P <= 0 || ntab <= 0) return;
+  const Pswf &Ps = pswf_coefficients(W);
+  const double dwg = P > 1 ? (double)w_max / (P - 1) : 0.0;
+  const int bx = (ntab + 255) / 256 < 16 ? (ntab + 255) / 256 : 16;
+  k_wtab<<<dim3(bx, P), 256, 0, s>>>(Ps, ntab, os, Ww, dwg, tab);
   note_launch();
 }
 

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) k_uvw(const double *__restrict__ ant, con
     const bool finite = isfinite(V.x) && isfinite(V.y);
     const bool flagged = (flags != nullptr && flags[r] != 0) || !pair_ok;
     Rec out;
+    out.pad = 0;
     if (inside && finite && !flagged) {
       if (dlm) {
         double turns = u * dlm[2 * inst] + v * dlm[2 * inst + 1];
@@ -79,11 +80,13 @@ __global__ void __launch_bounds__(256) k_uvw(const double *__restrict__ ant, con
       out.ku = (short)ku;
       out.kv = (short)kv;
       out.w = 1.f;
+      out.wg = (float)(w * scale * scale);
     } else {
       out.v = make_float2(0.f, 0.f);
       out.fu = out.fv = 0.f;
       out.ku = out.kv = -1;
       out.w = 0.f;
+      out.wg = 0.f;
       if (!finite && !flagged) bits |= MUSER_ST_NONFINITE;
       if (!inside && finite && !flagged) bits |= MUSER_ST_DROPPED;
     }

@@ -29,7 +29,7 @@ def test_record_and_config_layout():
     # 10 int32/float fields, a double at offset 40, batch_chunk, clean_kernel and 6 reserved int32
     assert ctypes.sizeof(m._lib.Config) == 80
     assert m._lib.Config.lat_rad.offset == 40 and m._lib.Config.batch_chunk.offset == 48
-    assert m.api.RECORD_FLOATS * 4 == 24
+    assert m.api.RECORD_FLOATS * 4 == 32
 
 
 def test_host_pixel_size_and_workspace_queries():

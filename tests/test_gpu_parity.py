@@ -53,8 +53,9 @@ def test_uvw_records(m, name):
     ro = oracle_records(wl)
     assert_no_ties(ro, wl.G, wl.W)
     np.testing.assert_allclose(_np(uvw), ro["uvw"], rtol=1e-12, atol=1e-9)
-    vis, fu, fv, ku, kv, w = (_np(x) for x in m.record_fields(rec))
+    vis, fu, fv, ku, kv, w, wg = (_np(x) for x in m.record_fields(rec))
     np.testing.assert_array_equal(w, ro["w"])
+    np.testing.assert_allclose(wg, ro["wg"], rtol=1e-6, atol=1e-6 * np.abs(ro["wg"]).max())
     np.testing.assert_array_equal(ku, ro["ku"])
     np.testing.assert_array_equal(kv, ro["kv"])
     keep = ro["w"] > 0
@@ -780,3 +781,68 @@ def test_clean_5120_streaming(m):
     assert int(_np(nc)[0]) == 40
     lockstep(Do, Bo, pg, fg, 0.1)
     identical_positions_unless_near_tie(Do, Bo, pg, 0.1, 40)
+
+
+# ------------------------------------------------------------------------------ w-projection
+W_CASES = {
+    "N64": lambda: synth.wterm_workload(),
+    "N64x2ch": lambda: synth.wterm_workload(freq=(1.2e9, 1.7e9), n_frame=2, config_id=401),
+    "N256": lambda: synth.wterm_workload(N=256, n_ant=31, bmax=1200.0, config_id=402),
+}
+
+
+def _wproj_setup(m, wl, P=128, Ww=15):
+    """Both sides take the same plane spacing: w_max = float32(1.01 max |wg|) of the oracle's
+    records; no sample may sit within 1e-4 of a plane boundary."""
+    from oracle import wproj
+    uvw = geometry.uvw(wl.ant_enu, wl.pairs, wl.lat, wl.ha, wl.dec, wl.freq)
+    ro = geometry.grid_records(uvw, wl.vis, wl.flags, pipeline.cell_sizes(wl), wl.G, Ww)
+    w_max = float(np.float32(1.01 * np.abs(ro["wg"]).max()))
+    x = np.abs(ro["wg"][ro["w"] > 0]) * (P - 1) / w_max
+    assert np.abs(x - np.floor(x) - 0.5).min() > 1e-4, "a sample sits on a w-plane boundary"
+    cfg = cfg_for(m, wl)
+    cfg.w_planes, cfg.w_max, cfg.w_support = P, w_max, Ww
+    tabs = wproj.kernel_tables(w_max, P, Ww, wl.OS, KER)
+    return cfg, ro, tabs, w_max
+
+
+@pytest.mark.parametrize("name", list(W_CASES))
+def test_wproj_grid_and_dirty(m, name):
+    """w-projected grid, map and beam against the oracle's w-projection (plane tables, complex
+    taps, conjugates for w < 0 and for the mirrored samples)."""
+    from oracle import wproj
+    wl = W_CASES[name]()
+    cfg, ro, tabs, w_max = _wproj_setup(m, wl)
+    assert np.abs(ro["uvw"][:, 2]).max() > 500
+    rec, _, st, off, _ = gpu_records(m, wl, cfg, want_uvw=False)
+    Z, st = m.grid(rec, off, cfg, status=st)
+    D, Bm, st = m.dirty(Z, cfg, status=st)
+    Zg, Dg, Bg = _np(Z), _np(D), _np(Bm)
+    for i in range(wl.n_inst):
+        ri = geometry.instance_slice(ro, i, wl.n_bl)
+        Zo = wproj.grid(ri, wl.G, tabs, w_max, 15, wl.OS)
+        Do, Bo, _ = imaging.dirty_and_beam(Zo, wl.N, KER)
+        assert np.abs(Zg[i] - Zo).max() <= 1e-5 * np.abs(Zo).max(), i
+        assert np.abs(Dg[i] - Do).max() <= 1e-4 * np.abs(Do).max(), i
+        assert np.abs(Bg[i] - Bo).max() <= 1e-4, i
+        assert abs(Bg[i][wl.N, wl.N] - 1.0) <= 1e-6
+
+
+def test_wproj_image_end_to_end(m):
+    """muser_image with w-projection (the fused gridding of the column pass) against the
+    oracle's w-projected map and beam, Hogbom CLEAN and restore."""
+    from oracle import restore as orest
+    from oracle import wproj
+    wl = W_CASES["N64x2ch"]()
+    cfg, ro, tabs, w_max = _wproj_setup(m, wl)
+    cfg.max_iter = 60
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    out = m.image(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    for i in range(wl.n_inst):
+        ri = geometry.instance_slice(ro, i, wl.n_bl)
+        Do, Bo, _ = imaging.dirty_and_beam(wproj.grid(ri, wl.G, tabs, w_max, 15, wl.OS), wl.N, KER)
+        pg, fg = _np(out.comp_pos)[i], _np(out.comp_flux)[i]
+        assert int(_np(out.n_comp)[i]) == 60
+        lockstep(Do, Bo, pg, fg, cfg.gain)
+        identical_positions_unless_near_tie(Do, Bo, pg, cfg.gain, 60)
+        np.testing.assert_allclose(_np(out.beam_params)[i], orest.clean_beam(Bo), rtol=1e-5)
