@@ -185,7 +185,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large"], default=None,
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "wproj"],
+                    default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
     ap.add_argument("--iters", type=int, default=100, help="CLEAN iterations of --case clean")
@@ -404,15 +405,18 @@ def run_case(case, n_inst=0, iters=100, size=2560):
             pipeline: uvw, strip sort, fused gridding + column pass, row pass, beam copies).
     steer: `n_inst` instances (default 8), Steer clean with `iters` major cycles at clip 0.9.
     large: the large-image leg of the benchmark at one image side (`size`).
+    wproj: the w-projection leg (MUSER-I band, about `n_inst` instances) with and without it.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
     import torch
     import paper_1712_06913_b300 as m
     import synth
+    if case == "wproj":
+        print(json.dumps({"case": case, **wproj_leg(m, torch.cuda.current_stream(), n=n_inst or 296)}))
+        return
     if case == "large":
-        import paper_1712_06913_b300 as m2
-        print(json.dumps({"case": case, **large_images(m2, torch.cuda.current_stream(), sizes=(size,))}))
+        print(json.dumps({"case": case, **large_images(m, torch.cuda.current_stream(), sizes=(size,))}))
         return
     if case == "grad":
         import numpy as np
@@ -544,6 +548,40 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     res["grad_GBps"] = res["grad_evals_per_s"] * ev_bytes / 1e9
     res.update(fft_vs_cufft(m, wl, cell, cfg, stream))
     res["large_images"] = large_images(m, stream)
+    res["w_projection"] = wproj_leg(m, stream)
+    return res
+
+
+def wproj_leg(m, stream, n=296, P=128):
+    """MUSER-I band instances (N = 512, G = 2048; 1000 Hogbom iterations) imaged with and without
+    w-projection (P planes, Ww-cell kernels, w_max from the instances' own records): images/s of
+    each.  The kernel support is the one that resolves the w-chirp over the map's field,
+    W + 2 |wg|_max / 8 cells (at most 63)."""
+    import torch
+    import synth
+    wl = synth.config2_muser1_band(n_frame=-(-n // 64))
+    cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=1000, gain=wl.gain, lat_rad=wl.lat)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    rec, _, _ = m.uvw(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis,
+                      m.Config(**{**cfg.__dict__, "w_planes": 2, "w_max": 1.0, "w_support": 63}), flags=wl.flags)
+    w_max = float(m.record_fields(rec)[6].abs().max()) * 1.01
+    del rec
+    # support that resolves the chirp over the map's field (|xi| <= 1/8): W + 2 |wg| / 8
+    Ww = min(63, 2 * ((wl.W + 2 * math.ceil(w_max / 8)) // 2) + 1)
+    res = {"workload": f"MUSER-I band, {wl.n_inst} instances of 512^2 (G 2048), 1000 iterations"}
+    for name, c in (("2d", cfg), ("wproj", m.Config(**{**cfg.__dict__, "w_planes": P, "w_max": w_max,
+                                                      "w_support": Ww}))):
+        im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, c, flags=wl.flags)
+        im.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        im.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[f"{name}_images_per_s"] = wl.n_inst / (e0.elapsed_time(e1) / 1e3)
+        del im
+    res.update(w_planes=P, w_support=Ww, w_max_grid_units=w_max)
     return res
 
 

@@ -93,7 +93,9 @@ typedef struct muser_config {
                            (2-D imaging), else 2..1024.  Imaging calls only (not muser_degrid). */
   float w_max;          /* largest |wg| the planes cover (wg = w (G cell)^2, record field wg);
                            planes at p w_max / (P - 1); larger |wg| take the last plane */
-  int32_t w_support;    /* w-kernel support in cells, odd, W..31 (used when w_planes > 0) */
+  int32_t w_support;    /* w-kernel support in cells, odd, W..63 (used when w_planes > 0); the chirp
+                           of plane wg spreads a sample over |wg| xi cells at field radius xi
+                           (xi = 1/8 at the map's edge, 1/4 at the beam's) */
   int32_t reserved[3];  /* must be zero */
 } muser_config_t;
 

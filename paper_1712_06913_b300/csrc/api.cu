@@ -67,8 +67,8 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
     if (mode != IMAGING) return fail(MUSER_ERR_UNSUPPORTED, "w-projection applies to imaging calls only");
     if (cfg->w_planes < 2 || cfg->w_planes > 1024) return fail(MUSER_ERR_ARG, "w_planes must be 0 or in [2, 1024]");
     if (!(cfg->w_max > 0.f) || !isfinite(cfg->w_max)) return fail(MUSER_ERR_ARG, "w_max must be positive and finite");
-    if (cfg->w_support < cfg->W || cfg->w_support > 31 || (cfg->w_support & 1) == 0)
-      return fail(MUSER_ERR_ARG, "w_support must be odd in [W, 31]");
+    if (cfg->w_support < cfg->W || cfg->w_support > 63 || (cfg->w_support & 1) == 0)
+      return fail(MUSER_ERR_ARG, "w_support must be odd in [W, 63]");
   }
   return MUSER_OK;
 }
