@@ -185,7 +185,7 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "wproj"],
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "wproj", "mixed"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -406,12 +406,16 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     steer: `n_inst` instances (default 8), Steer clean with `iters` major cycles at clip 0.9.
     large: the large-image leg of the benchmark at one image side (`size`).
     wproj: the w-projection leg (MUSER-I band, about `n_inst` instances) with and without it.
+    mixed: the mixed stream of `n_inst` (default 10,000) MUSER-I / MUSER-II instances.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
     import torch
     import paper_1712_06913_b300 as m
     import synth
+    if case == "mixed":
+        print(json.dumps({"case": case, **mixed_stream(m, torch.cuda.current_stream(), n_total=n_inst or 10000)}))
+        return
     if case == "wproj":
         print(json.dumps({"case": case, **wproj_leg(m, torch.cuda.current_stream(), n=n_inst or 296)}))
         return
@@ -549,6 +553,7 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     res.update(fft_vs_cufft(m, wl, cell, cfg, stream))
     res["large_images"] = large_images(m, stream)
     res["w_projection"] = wproj_leg(m, stream)
+    res["mixed_stream"] = mixed_stream(m, stream)
     return res
 
 
@@ -585,6 +590,61 @@ def wproj_leg(m, stream, n=296, P=128):
     return res
 
 
+def mixed_stream(m, stream, n_total=10000, n_plain=8):
+    """The mixed stream: n_total instances, half MUSER-I (256^2 or 512^2 by the Table 2 rule),
+    half MUSER-II (1024^2), 1000 iterations, imaged by size class (MixedImager: one muser_image
+    batch per class, all replayed from one CUDA graph) against the plain path (one instance per
+    muser_image call), the latter timed on n_plain instances of each class."""
+    import torch
+    import synth
+    w1, w2, _ = synth.config5_mixed_stream(n_total)
+    n1 = n_total // 2
+
+    def sources(w, n, n_max):
+        F, rest = divmod(n, w.n_chan)
+        kw = dict(bmax=w.bmax, fov_min=w.fov_min, n_max=n_max, max_iter=1000, lat_rad=w.lat, batch_chunk=296)
+        out = [m.Source(w.ant_enu, w.pairs, w.ha[:F], w.dec[:F], w.freq, w.vis[:F], w.flags[:F], **kw)] if F else []
+        if rest:
+            out.append(m.Source(w.ant_enu, w.pairs, w.ha[F:F + 1], w.dec[F:F + 1], w.freq[:rest],
+                                w.vis[F:F + 1, :rest], w.flags[F:F + 1, :rest], **kw))
+        return out
+
+    mix = m.MixedImager(sources(w1, n1, 512) + sources(w2, n_total - n1, 1024))
+    mix.capture()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mix.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / 1e3
+    per_class, t_plain = {}, 0.0
+    for si, c0, nc, im in mix.classes:
+        n_cls = im.B
+        cfg1 = m.Config(**{**im.cfg.__dict__, "batch_chunk": 0})
+        ims = [m.Imager(im.ant, im.pairs, im.ha[:1], im.dec[:1], im.freq[c:c + 1], im.cell[c:c + 1],
+                        im.vis[:1, c:c + 1], cfg1, flags=None if im.flags is None else im.flags[:1, c:c + 1])
+               for c in range(min(n_plain, im.C))]
+        ims[0].run()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for one in ims:
+            one.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rate = len(ims) / (e0.elapsed_time(e1) / 1e3)
+        key = f"N{im.cfg.N}"
+        per_class[key] = per_class.get(key, 0) + n_cls
+        t_plain += n_cls / rate
+        del ims, cfg1
+    res = {"instances": sum(per_class.values()), "per_class": per_class,
+           "batched_images_per_s": n_total / t_batched, "plain_images_per_s": n_total / t_plain,
+           "plain_sample": f"{n_plain} instances per class, one muser_image call each"}
+    del mix
+    torch.cuda.empty_cache()
+    return res
+
+
 LARGE = {1280: (148, 148), 2560: (148, 74), 5120: (64, 32)}     # N: (instances, chunk)
 
 
@@ -601,7 +661,7 @@ def large_images(m, stream, sizes=(1280, 2560, 5120)):
         n_band = int(((synth.muser2_channels() >= synth.LARGE_BANDS[N][0]) &
                       (synth.muser2_channels() <= synth.LARGE_BANDS[N][1])).sum())
         nf = -(-B // n_band)
-        wl = synth.config5_muser2_large(N, n_frame=nf, chans=list(range(min(B, n_band))))
+        wl = synth.muser2_large_band(N, n_frame=nf, chans=list(range(min(B, n_band))))
         cfg = m.Config(N=N, G=4 * N, W=wl.W, os=wl.OS, max_iter=1000, gain=wl.gain, lat_rad=wl.lat, batch_chunk=chunk)
         cell = m.pixel_size(wl.freq, wl.bmax, N, wl.fov_min)
         warm = m.Imager(wl.ant_enu, wl.pairs, wl.ha[:1], wl.dec[:1], wl.freq[:1], cell[:1], wl.vis[:1, :1],

@@ -306,6 +306,105 @@ class Imager:
         return self.out
 
 
+# Table 2: image side by observing frequency (upper band edges in Hz)
+TABLE2_SIDES = ((0.6e9, 256), (1.2e9, 512), (2.0e9, 1024), (4.0e9, 1280), (8.0e9, 2560), (float("inf"), 5120))
+
+
+def image_side(freq_hz, n_max=5120):
+    """Image side of Table 2 for each channel frequency (0.4-0.6 GHz: 256 ... 8-15 GHz: 5120),
+    capped at n_max."""
+    out = []
+    for f in np.atleast_1d(np.asarray(freq_hz, float)):
+        side = next(n for edge, n in TABLE2_SIDES if f < edge)
+        out.append(min(side, n_max))
+    return np.array(out, np.int64)
+
+
+@dataclasses.dataclass
+class Source:
+    """One array's observations for a mixed stream: [F, C, nb] visibilities, imaging parameters
+    shared by its channels; image sides come from Table 2 (capped at n_max)."""
+    ant_enu: object
+    pairs: object
+    ha: object
+    dec: object
+    freq: object
+    vis: object
+    flags: object = None
+    bmax: float = 3000.0
+    fov_min: float = math.pi / 180.0
+    n_max: int = 1024
+    W: int = 7
+    os: int = 1024
+    gain: float = 0.1
+    max_iter: int = 1000
+    lat_rad: float = 0.0
+    batch_chunk: int = 296
+
+
+def size_classes(freq_hz, n_max=5120):
+    """Runs of consecutive channels with the same Table 2 side: [(first, end, side), ...]."""
+    sides = image_side(freq_hz, n_max)
+    runs, c0 = [], 0
+    while c0 < len(sides):
+        c1 = c0
+        while c1 < len(sides) and sides[c1] == sides[c0]:
+            c1 += 1
+        runs.append((c0, c1, int(sides[c0])))
+        c0 = c1
+    return runs
+
+
+class MixedImager:
+    """A stream of instances of several image sizes, batched by size class: each source's channels
+    are split into runs of equal Table 2 side, each run imaged as one muser_image batch (chunked
+    inside), all batches launched back to back on the current stream or replayed from one CUDA
+    graph.  `locate(source, instance)` maps a stream instance (frame * n_chan + chan of its
+    source) to (class, index in that class's ImageResult)."""
+
+    def __init__(self, sources):
+        self.classes = []           # (source index, first channel, n channels, Imager)
+        for si, src in enumerate(sources):
+            freq = np.asarray(src.freq, float)
+            for c0, c1, N in size_classes(freq, src.n_max):
+                cfg = Config(N=N, G=4 * N, W=src.W, os=src.os, max_iter=src.max_iter, gain=src.gain,
+                             lat_rad=src.lat_rad, batch_chunk=src.batch_chunk)
+                fr = freq[c0:c1]
+                cell = pixel_size(fr, src.bmax, N, src.fov_min)
+                vis = np.asarray(src.vis)[:, c0:c1]
+                flags = np.asarray(src.flags)[:, c0:c1] if src.flags is not None else None
+                im = Imager(src.ant_enu, src.pairs, src.ha, src.dec, fr, cell, np.ascontiguousarray(vis), cfg,
+                            flags=None if flags is None else np.ascontiguousarray(flags))
+                self.classes.append((si, c0, c1 - c0, im))
+        self.n_chan = [len(np.asarray(src.freq)) for src in sources]
+        self.graph = None
+
+    def locate(self, source, instance):
+        f, c = divmod(instance, self.n_chan[source])
+        for k, (si, c0, nc, im) in enumerate(self.classes):
+            if si == source and c0 <= c < c0 + nc:
+                return k, f * nc + (c - c0)
+        raise IndexError("instance not in any size class")
+
+    def run(self):
+        return [im.run() for _, _, _, im in self.classes]
+
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return [im.out for _, _, _, im in self.classes]
+
+
 def image(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, dlm=None):
     """Whole hot path for a batch; returns an ImageResult with comp arrays cut to max_iter."""
     im = Imager(ant_enu, pairs, ha, dec, freq, cell, vis, cfg, flags, dlm)

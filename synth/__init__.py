@@ -279,7 +279,7 @@ def config3_muser2_uneven(n_frame=8, chans=None) -> Workload:
 LARGE_BANDS = {1280: (2.0e9, 4.0e9), 2560: (4.0e9, 8.0e9), 5120: (8.0e9, 15.0e9)}
 
 
-def config5_muser2_large(N=2560, n_frame=1, chans=None) -> Workload:
+def muser2_large_band(N=2560, n_frame=1, chans=None) -> Workload:
     """MUSER-II high-band images of Table 2: 2-4 GHz at 1280^2, 4-8 GHz at 2560^2, 8-15 GHz at
     5120^2 (G = 4N), 60 antennas, 0-30 % of baselines flagged per frame, 1000 iterations.
     ``chans`` indexes the channels of the band."""
@@ -319,6 +319,36 @@ def wterm_workload(N=64, n_ant=10, bmax=300.0, ha=0.8, freq=(1.7e9,), n_frame=1,
     return Workload(name=f"wterm-N{N}", ant_enu=ant, pairs=pairs, lat=MINGANTU_LAT, ha=has, dec=dec, freq=freq,
                     vis=vis, flags=np.zeros(vis.shape, np.uint8), N=N, G=4 * N, bmax=bmax, max_iter=100,
                     skies=[pts])
+
+
+def config5_mixed_stream(n_total=10000):
+    """Mixed stream: n_total (frame, channel) instances, half MUSER-I (40 antennas, 64 channels
+    per 25 ms frame, 0.4-2 GHz) and half MUSER-II (60 antennas, 528 channels per 206.25 ms
+    frame, 2-15 GHz), 0-30 % of baselines flagged per frame, 1000 iterations.
+
+    Returns (muser1, muser2, order): the two workloads (whole frames, the last one trimmed in
+    channels) and the stream order, a list of (instrument 0/1, instance) pairs interleaving
+    the two instruments frame by frame."""
+    n1 = n_total // 2
+    n2 = n_total - n1
+    f1, f2 = -(-n1 // 64), -(-n2 // 528)
+    ant1, ant2 = muser1_array(), muser2_array()
+    w1 = make_workload("mixed-muser1", ant1, baseline_pairs(40), EARTH_RATE * 0.025 * np.arange(f1),
+                       np.full(f1, DEC_SUN), muser1_channels(), 512, 2048, config_id=51, flag_max=0.3, max_iter=1000)
+    w2 = make_workload("mixed-muser2", ant2, baseline_pairs(60), EARTH_RATE * 0.20625 * np.arange(f2),
+                       np.full(f2, DEC_SUN), muser2_channels(), 1024, 4096, config_id=52, flag_max=0.3,
+                       max_iter=1000)
+    order, i1, i2 = [], 0, 0
+    while i1 < n1 or i2 < n2:                      # 8 MUSER-I frames per MUSER-II frame (25 vs 206 ms)
+        for _ in range(8 * 64):
+            if i1 < n1:
+                order.append((0, i1))
+                i1 += 1
+        for _ in range(528):
+            if i2 < n2:
+                order.append((1, i2))
+                i2 += 1
+    return w1, w2, order
 
 
 def config4_operator() -> Workload:

@@ -700,7 +700,7 @@ FIVE_CASES = {
     "N320x2": lambda: synth.small_workload(n_ant=16, N=320, n_frame=2, config_id=251, bmax=1200.0,
                                            flag_max=0.3),                                     # G 1280: 5, 16, 16
     "N640": lambda: synth.small_workload(n_ant=21, N=640, config_id=252, bmax=2000.0),         # G 2560: 10, 16, 16
-    "N1280": lambda: synth.config5_muser2_large(1280, chans=[3, 70]),                          # G 5120: 20, 16, 16
+    "N1280": lambda: synth.muser2_large_band(1280, chans=[3, 70]),                          # G 5120: 20, 16, 16
 }
 
 
@@ -721,7 +721,7 @@ def test_dirty_largest_sides_sampled(m, N):
     """One MUSER-II instance at 2560^2 (G = 10240) and 5120^2 (G = 20480): sampled pixels of the
     map and the beam against the oracle's per-pixel transform of the sparse grid."""
     from oracle import imaging as oim
-    wl = synth.config5_muser2_large(N, chans=[5])
+    wl = synth.muser2_large_band(N, chans=[5])
     cfg = cfg_for(m, wl)
     rec, _, st, off, _ = gpu_records(m, wl, cfg, want_uvw=False)
     Z, st = m.grid(rec, off, cfg, status=st)
@@ -846,3 +846,54 @@ def test_wproj_image_end_to_end(m):
         lockstep(Do, Bo, pg, fg, cfg.gain)
         identical_positions_unless_near_tie(Do, Bo, pg, cfg.gain, 60)
         np.testing.assert_allclose(_np(out.beam_params)[i], orest.clean_beam(Bo), rtol=1e-5)
+
+
+# ------------------------------------------------------------------------------ mixed stream
+def test_mixed_stream_by_size_class(m):
+    """A mixed stream (MUSER-I channels at 256^2 and 512^2, MUSER-II at 1024^2 by the Table 2
+    rule) through the size-class batches equals imaging each class alone, eager and replayed
+    from one CUDA graph; a 256^2 instance follows the oracle."""
+    import torch
+    w1, w2, _ = synth.config5_mixed_stream(n_total=40)
+    ch1 = [0, 5, 20, 50]                      # 0.41, 0.54 GHz -> 256; 0.91, 1.66 GHz -> 512 (capped)
+    src1 = m.Source(w1.ant_enu, w1.pairs, w1.ha[:2], w1.dec[:2], w1.freq[ch1], w1.vis[:2][:, ch1],
+                    w1.flags[:2][:, ch1], bmax=w1.bmax, fov_min=w1.fov_min, n_max=512, max_iter=80,
+                    lat_rad=w1.lat, batch_chunk=3)
+    src2 = m.Source(w2.ant_enu, w2.pairs, w2.ha[:1], w2.dec[:1], w2.freq[[10, 300]], w2.vis[:1][:, [10, 300]],
+                    w2.flags[:1][:, [10, 300]], bmax=w2.bmax, fov_min=w2.fov_min, n_max=1024, max_iter=80,
+                    lat_rad=w2.lat)
+    mix = m.MixedImager([src1, src2])
+    assert [(si, c0, nc, im.cfg.N) for si, c0, nc, im in mix.classes] == [(0, 0, 2, 256), (0, 2, 2, 512),
+                                                                          (1, 0, 2, 1024)]
+    outs = [dataclasses_copy(o) for o in mix.run()]
+    for k, (si, c0, nc, im) in enumerate(mix.classes):
+        src = (src1, src2)[si]
+        one = m.image(src.ant_enu, src.pairs, src.ha, src.dec, src.freq[c0:c0 + nc],
+                      m.pixel_size(src.freq[c0:c0 + nc], src.bmax, im.cfg.N, src.fov_min),
+                      np.ascontiguousarray(src.vis[:, c0:c0 + nc]), im.cfg,
+                      flags=np.ascontiguousarray(src.flags[:, c0:c0 + nc]))
+        assert torch.equal(one.comp_pos, outs[k].comp_pos[:, :80])
+        peak = float(one.clean.abs().max())
+        assert float((one.clean - outs[k].clean).abs().max()) <= 1e-6 * peak
+    # stream instance -> class
+    assert mix.locate(0, 1 * 4 + 3) == (1, 1 * 2 + 1)
+    assert mix.locate(1, 1) == (2, 1)
+    # graph replay
+    mix.capture()
+    rep = mix.replay()
+    torch.cuda.synchronize()
+    for k in range(3):
+        assert torch.equal(rep[k].comp_pos, outs[k].comp_pos)
+    # a 256^2 instance against the oracle
+    wl = synth.make_workload("mix-check", w1.ant_enu, w1.pairs, w1.ha[:1], w1.dec[:1], w1.freq[[0]], 256, 1024,
+                             config_id=51, flag_max=0.3)
+    ro = pipeline.records(wl)
+    o = pipeline.image_instance(geometry.instance_slice(ro, 0, wl.n_bl), 256, 1024, gain=0.1, cap=80)
+    _, li = mix.locate(0, 0)
+    assert li == 0
+    lockstep(o["D"], o["Bm"], _np(outs[0].comp_pos)[0][:80], _np(outs[0].comp_flux)[0][:80], 0.1)
+
+
+def dataclasses_copy(o):
+    import dataclasses
+    return dataclasses.replace(o, **{f.name: getattr(o, f.name).clone() for f in dataclasses.fields(o)})
