@@ -283,6 +283,20 @@ MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser
                           float clip, float *model, int32_t *n_cycles, void *ws, size_t ws_bytes, int32_t *status,
                           muser_stream_t stream);
 
+/* Launch-shape autotuner.  Times the candidates of one call's launch shape on the given batch
+ * and keeps the fastest for later calls of this process with the same grid size (and
+ * footprint): MUSER_CALL_GRID chooses the rows of the full-width gridding bands (powers of two
+ * dividing G, at most 200 KB of shared memory per band); MUSER_CALL_DIRTY the column-pass
+ * strip width (variant 0: 16384/G columns, 20480/G for G = 5 2^m; variant 1: half as wide).
+ * rec/vis_off as muser_grid (required for MUSER_CALL_GRID, ignored otherwise); the timed calls
+ * run on `stream` with scratch the call allocates and frees itself.  Synchronous; not for use
+ * inside a CUDA graph capture.  choice (host, nullable) receives the chosen value.
+ * muser_set_tuning sets the value directly (0 = the built-in choice).  Results differ between
+ * shapes only in the order of floating-point sums. */
+MUSER_API int muser_autotune(int call_id, const muser_vis_record_t *rec, const int64_t *vis_off, int B,
+                             int64_t n_vis_total, const muser_config_t *cfg, int32_t *choice, muser_stream_t stream);
+MUSER_API int muser_set_tuning(int call_id, const muser_config_t *cfg, int value);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,8 @@ SIGNATURES = {
     "muser_chi2": (I32, [P, P, P, I64, F32, P, P, P, SZ, P]),
     "muser_center": (I32, [P, P, P, P, I32, CFG, P, P, P, P, SZ, P, P]),
     "muser_steer": (I32, [P, P, I32, CFG, P, F32, P, P, P, SZ, P, P]),
+    "muser_autotune": (I32, [I32, P, P, I32, I64, CFG, P, P]),
+    "muser_set_tuning": (I32, [I32, CFG, I32]),
 }
 
 _lib = None

@@ -306,6 +306,24 @@ class Imager:
         return self.out
 
 
+def autotune(call_id, cfg: Config, rec=None, vis_off=None, B=1):
+    """Time the launch-shape candidates of muser_grid (band rows; needs rec, vis_off) or
+    muser_dirty (column-strip width) on one batch and keep the fastest; returns the choice."""
+    vo = _dev(vis_off, torch.int64) if vis_off is not None else None
+    if vo is not None:
+        B = vo.numel() - 1
+    n = int(vo[-1].item()) if vo is not None and B > 0 else 0
+    out = ctypes.c_int32(0)
+    c = cfg.c()
+    check(_lib.load().muser_autotune(call_id, _p(rec), _p(vo), B, n, ctypes.byref(c), ctypes.byref(out), _stream()))
+    return out.value
+
+
+def set_tuning(call_id, cfg: Config, value: int):
+    c = cfg.c()
+    check(_lib.load().muser_set_tuning(call_id, ctypes.byref(c), int(value)))
+
+
 # Table 2: image side by observing frequency (upper band edges in Hz)
 TABLE2_SIDES = ((0.6e9, 256), (1.2e9, 512), (2.0e9, 1024), (4.0e9, 1280), (8.0e9, 2560), (float("inf"), 5120))
 

@@ -6,8 +6,10 @@
 #include <cstdio>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -96,9 +98,12 @@ struct GridWs {
     const int rows = grid_band_rows(c.G), nb = c.G / rows;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     wtab = carve_wtab(a, c);
-    bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (nb + 1));
+    // sized for bands of one row, the narrowest muser_autotune may choose
+    bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (c.G + 1));
     entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) *
-                                                  tiles_per_sample(w_footprint(c), rows, c.G, c.G));
+                                                  tiles_per_sample(w_footprint(c), 1, c.G, c.G));
+    (void)rows;
+    (void)nb;
   }
 };
 
@@ -112,7 +117,7 @@ struct DirtyWs {
     gc = (float *)a.template take<float>(G);
     tw = (float2 *)a.template take<float2>(G);
     T = (float2 *)a.template take<float2>((size_t)B * (G / 2) * G);
-    partial = (float *)a.template take<float>((size_t)B * (G / dirty_strip_width(G)));
+    partial = (float *)a.template take<float>((size_t)B * (G / dirty_min_strip_width(G)));
   }
 };
 
@@ -254,6 +259,7 @@ struct SizeArena {
 
 bool copies(const muser_config_t &c) { return c.clean_kernel == 0 && clean_uses_copies(c.N); }
 
+
 int chunk_of(int B, const muser_config_t &c) { return (c.batch_chunk > 0 && c.batch_chunk < B) ? c.batch_chunk : B; }
 
 int check_ws(void *ws, size_t ws_bytes, size_t need) {
@@ -282,6 +288,32 @@ __global__ void k_copy(float *dst, const float *src, int n) {
   } while (0)
 
 }  // namespace
+
+// ----------------------------------------------------------------------- tuned launch shapes
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_band_rows;   // (G, footprint) -> rows
+std::map<int, int> g_dirty_variant;               // G -> column-pass variant
+}  // namespace
+int tuned_band_rows(int G, int W) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_band_rows.find({G, W});
+  return it == g_band_rows.end() ? 0 : it->second;
+}
+void set_tuned_band_rows(int G, int W, int rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_band_rows[{G, W}] = rows;
+}
+int tuned_dirty_variant(int G) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_dirty_variant.find(G);
+  return it == g_dirty_variant.end() ? 0 : it->second;
+}
+void set_tuned_dirty_variant(int G, int variant) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_dirty_variant[G] = variant;
+}
+
 }  // namespace muser
 
 using namespace muser;
@@ -373,8 +405,9 @@ int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int
   launch_pswf_table(w.tab, cfg->W, cfg->os, nullptr, 0, s);
   if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
                           cfg->W, s);
+  const int rows = tuned_band_rows(cfg->G, w_footprint(*cfg));
   launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, w_footprint(*cfg), cfg->os, w.tab, true, nullptr,
-              grid_band_rows(cfg->G), cfg->G, (float2 *)Z, w.bin_off, w.entries, status, false, s,
+              rows > 0 ? rows : grid_band_rows(cfg->G), cfg->G, (float2 *)Z, w.bin_off, w.entries, status, false, s,
               make_wproj(w.wtab, *cfg));
   return check_launch("muser_grid");
 }
@@ -394,7 +427,8 @@ int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, 
   cudaStream_t s = (cudaStream_t)stream;
   launch_pswf_table(nullptr, cfg->W, cfg->os, w.gc, cfg->G, s);    // grid correction only
   fft::launch_twiddles(w.tw, cfg->G, s);
-  launch_dirty((const float2 *)Z, B, cfg->N, cfg->G, w.tw, w.gc, w.T, w.partial, dirty, beam, status, s);
+  launch_dirty((const float2 *)Z, B, cfg->N, cfg->G, w.tw, w.gc, w.T, w.partial, dirty, beam, status, s,
+               tuned_dirty_variant(cfg->G));
   return check_launch("muser_dirty");
 }
 
@@ -633,6 +667,92 @@ int muser_steer(float *residual, const float *beam, int B, const muser_config_t 
   launch_steer(residual, beam, B, cfg->N, cfg->gain, cfg->max_iter, t, clip, model, n_cycles, w.tw, w.FB, w.F, w.U,
                w.Y, w.state, status, s);
   return check_launch("muser_steer");
+}
+
+int muser_set_tuning(int call_id, const muser_config_t *cfg, int value) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (call_id == MUSER_CALL_GRID) {
+    if (value < 0 || value > cfg->G || (value > 0 && cfg->G % value != 0) ||
+        (size_t)value * cfg->G * sizeof(float2) > 200 * 1024)
+      return fail(MUSER_ERR_ARG, "band rows must divide G and fit 200 KB of shared memory (0 = built-in)");
+    set_tuned_band_rows(cfg->G, w_footprint(*cfg), value);
+    return MUSER_OK;
+  }
+  if (call_id == MUSER_CALL_DIRTY) {
+    if (value < 0 || value > 1) return fail(MUSER_ERR_ARG, "column-pass variant must be 0 or 1");
+    set_tuned_dirty_variant(cfg->G, value);
+    return MUSER_OK;
+  }
+  return fail(MUSER_ERR_UNSUPPORTED, "muser_set_tuning: MUSER_CALL_GRID or MUSER_CALL_DIRTY");
+}
+
+int muser_autotune(int call_id, const muser_vis_record_t *rec, const int64_t *vis_off, int B, int64_t n_vis_total,
+                   const muser_config_t *cfg, int32_t *choice, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (B < 1 || n_vis_total < 0) return fail(MUSER_ERR_ARG, "muser_autotune needs B >= 1");
+  if (call_id != MUSER_CALL_GRID && call_id != MUSER_CALL_DIRTY)
+    return fail(MUSER_ERR_UNSUPPORTED, "muser_autotune: MUSER_CALL_GRID or MUSER_CALL_DIRTY");
+  if (call_id == MUSER_CALL_GRID && (!rec || !vis_off)) return fail(MUSER_ERR_ARG, "muser_autotune: records needed");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int G = cfg->G;
+  std::vector<int> cand;
+  if (call_id == MUSER_CALL_GRID) {
+    for (int r = 1; r <= G && (size_t)r * G * sizeof(float2) <= 200 * 1024; r *= 2)
+      if (G % r == 0) cand.push_back(r);
+  } else {
+    cand = {0, 1};
+  }
+  // scratch of the timed calls (this call is synchronous and not for graph capture)
+  const size_t zbytes = (size_t)B * G * G * sizeof(float2);
+  const size_t wsb = muser_workspace_size(call_id, B, n_vis_total, cfg);
+  void *Z = nullptr, *ws = nullptr, *out = nullptr;
+  int32_t *st = nullptr;
+  const size_t outb = call_id == MUSER_CALL_DIRTY ? (size_t)B * 5 * cfg->N * cfg->N * sizeof(float) : 0;
+  bool ok = cudaMalloc(&Z, zbytes) == cudaSuccess && cudaMalloc(&ws, wsb) == cudaSuccess &&
+            cudaMalloc((void **)&st, sizeof(int32_t) * B) == cudaSuccess &&
+            (outb == 0 || cudaMalloc(&out, outb) == cudaSuccess);
+  int best = cand[0];
+  float best_ms = 1e30f;
+  if (ok) {
+    cudaMemsetAsync(Z, 0, zbytes, s);
+    cudaMemsetAsync(st, 0, sizeof(int32_t) * B, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int c : cand) {
+      muser_set_tuning(call_id, cfg, c);
+      float ms = 0.f;
+      for (int rep = 0; rep < 4 && ok; rep++) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        int rc = call_id == MUSER_CALL_GRID
+                     ? muser_grid(rec, vis_off, B, n_vis_total, cfg, (float *)Z, ws, wsb, st, stream)
+                     : muser_dirty((const float *)Z, B, cfg, (float *)out, (float *)out + (size_t)B * cfg->N * cfg->N,
+                                   ws, wsb, st, stream);
+        ok = rc == MUSER_OK;
+      }
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ok && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(Z);
+  cudaFree(ws);
+  cudaFree(st);
+  if (out) cudaFree(out);
+  if (!ok) {
+    muser_set_tuning(call_id, cfg, 0);
+    return fail(MUSER_ERR_CUDA, "muser_autotune: scratch allocation or a timed call failed");
+  }
+  muser_set_tuning(call_id, cfg, best);
+  if (choice) *choice = best;
+  return check_launch("muser_autotune");
 }
 
 }  // extern "C"

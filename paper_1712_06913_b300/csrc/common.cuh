@@ -163,8 +163,18 @@ void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, i
                           int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
                           float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
                           WProj wp = WProj{nullptr, 0, 0, 0.f});
+// variant 0: column strips of dirty_strip_width(G); 1: half as wide (dirty_min_strip_width);
+// partial holds B x G / dirty_min_strip_width(G) floats.
+int dirty_min_strip_width(int G);
 void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T,
-                  float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s);
+                  float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s, int variant = 0);
+
+// Tuned launch shapes (muser_autotune): gridding band rows per (G, footprint), column-pass
+// variant per G.  0 = not tuned (the built-in choice).
+int tuned_band_rows(int G, int W);
+void set_tuned_band_rows(int G, int W, int rows);
+int tuned_dirty_variant(int G);
+void set_tuned_dirty_variant(int G, int variant);
 namespace fft {
 void launch_twiddles(float2 *tw, int L, cudaStream_t s);   // tw[m] = exp(+2 pi i m / L)
 }

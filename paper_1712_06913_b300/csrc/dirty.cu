@@ -24,10 +24,11 @@ namespace {
 using fft::ColCfg;
 using fft::RowCfg;
 
-template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT) k_cols(const float2 *__restrict__ Z, const float2 *__restrict__ tw,
-                                                       float2 *__restrict__ T, float *__restrict__ partial) {
-  using C = ColCfg<G>;
+template <int G, int S_>
+__global__ void __launch_bounds__(fft::ColStrip<G, S_>::NT) k_cols(const float2 *__restrict__ Z,
+                                                                  const float2 *__restrict__ tw,
+                                                                  float2 *__restrict__ T, float *__restrict__ partial) {
+  using C = fft::ColStrip<G, S_>;
   constexpr int S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
@@ -160,11 +161,10 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restri
 template <int G>
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
                                                        const float *__restrict__ gc, const float *__restrict__ partial,
-                                                       int N, float *__restrict__ dirty, float *__restrict__ beam,
-                                                       int32_t *__restrict__ status) {
+                                                       int nstrip, int N, float *__restrict__ dirty,
+                                                       float *__restrict__ beam, int32_t *__restrict__ status) {
   using C = RowCfg<G>;
   constexpr int S = C::S, NT = C::NT;
-  constexpr int NSTRIP = G / ColCfg<G>::S;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
   __shared__ float red[32];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
   const int inst = blockIdx.y, y0 = blockIdx.x * S;   // rows y0.. of T, i.e. y = y0 + G/4 ..
   // beam normalisation: sum of the strip sums in a fixed order
   float acc = 0.f;
-  for (int i = threadIdx.x; i < NSTRIP; i += NT) acc += partial[(size_t)inst * NSTRIP + i];
+  for (int i = threadIdx.x; i < nstrip; i += NT) acc += partial[(size_t)inst * nstrip + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -209,24 +209,35 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
   fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
 }
 
-template <int G>
-void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float *gc, float2 *T, float *partial,
-                    float *dirty, float *beam, int32_t *status, cudaStream_t s) {
-  using CC = ColCfg<G>;
+// the column pass with strips of S columns (the tuned alternative is S / 2)
+template <int G, int S>
+void launch_dirty_GS(const float2 *Z, int B, int N, const float2 *tw, const float *gc, float2 *T, float *partial,
+                     float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+  using CC = fft::ColStrip<G, S>;
   using RC = RowCfg<G>;
-  cudaFuncSetAttribute(k_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_cols<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
-    k_cols<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(Z + (size_t)i * G * G, tw, T + (size_t)i * (G / 2) * G,
-                                                            partial + (size_t)i * (G / CC::S));
+    k_cols<G, S><<<dim3(G / S, n), CC::NT, CC::smem, s>>>(Z + (size_t)i * G * G, tw, T + (size_t)i * (G / 2) * G,
+                                                           partial + (size_t)i * (G / S));
     note_launch();
     k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
-                                                         partial + (size_t)i * (G / CC::S), N,
-                                                         dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
-                                                         status ? status + i : nullptr);
+                                                               partial + (size_t)i * (G / S), G / S, N,
+                                                               dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
+                                                               status ? status + i : nullptr);
     note_launch();
   }
+}
+
+template <int G>
+void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float *gc, float2 *T, float *partial,
+                    float *dirty, float *beam, int32_t *status, cudaStream_t s, int variant) {
+  constexpr int S0 = ColCfg<G>::S, S1 = S0 >= 2 ? S0 / 2 : S0;
+  if (variant == 1 && S1 != S0)
+    launch_dirty_GS<G, S1>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s);
+  else
+    launch_dirty_GS<G, S0>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s);
 }
 
 template <int G>
@@ -246,7 +257,7 @@ void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W,
         entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S), wp);
     note_launch();
     k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
-                                                         partial + (size_t)i * (G / CC::S), N,
+                                                         partial + (size_t)i * (G / CC::S), G / CC::S, N,
                                                          dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
                                                          status ? status + i : nullptr);
     note_launch();
@@ -274,12 +285,17 @@ int dirty_strip_width(int G) {
   }
 }
 
+int dirty_min_strip_width(int G) {
+  const int S = dirty_strip_width(G);
+  return S >= 2 ? S / 2 : S;
+}
+
 void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T, float *partial,
-                  float *dirty, float *beam, int32_t *status, cudaStream_t s) {
+                  float *dirty, float *beam, int32_t *status, cudaStream_t s, int variant) {
   if (B <= 0) return;
   switch (G) {
 #define MUSER_CASE(g) \
-  case g: launch_dirty_G<g>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s); break;
+  case g: launch_dirty_G<g>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s, variant); break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
     MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240) MUSER_CASE(20480)
 #undef MUSER_CASE

@@ -897,3 +897,33 @@ def test_mixed_stream_by_size_class(m):
 def dataclasses_copy(o):
     import dataclasses
     return dataclasses.replace(o, **{f.name: getattr(o, f.name).clone() for f in dataclasses.fields(o)})
+
+
+# ------------------------------------------------------------------------------ autotuner
+def test_autotune_grid_and_dirty_shapes(m):
+    """muser_autotune picks a gridding band height and a column-strip width; every candidate
+    shape gives the oracle's grid, map and beam (only the order of float sums differs)."""
+    wl = WORKLOADS["small-N32-3frames"]()
+    cfg = cfg_for(m, wl)
+    rec, _, st, off, _ = gpu_records(m, wl, cfg, want_uvw=False)
+    rows = m.autotune(m.CALL_GRID, cfg, rec=rec, vis_off=off)
+    assert rows >= 1 and cfg.G % rows == 0 and rows * cfg.G * 8 <= 200 * 1024
+    var = m.autotune(m.CALL_DIRTY, cfg, B=4)
+    assert var in (0, 1)
+    ref = _dirty_both(m, wl)[5]
+    try:
+        for r in (1, 2, 8, 64):
+            if cfg.G % r or r * cfg.G * 8 > 200 * 1024:
+                continue
+            m.set_tuning(m.CALL_GRID, cfg, r)
+            for v in (0, 1):
+                m.set_tuning(m.CALL_DIRTY, cfg, v)
+                Z, s2 = m.grid(rec, off, cfg, status=st.clone())
+                D, Bm, _ = m.dirty(Z, cfg, status=s2)
+                for i, (Zo, Do, Bo, _) in enumerate(ref):
+                    assert np.abs(_np(Z)[i] - Zo).max() <= 1e-5 * np.abs(Zo).max(), (r, v)
+                    assert np.abs(_np(D)[i] - Do).max() <= 1e-4 * np.abs(Do).max(), (r, v)
+                    assert np.abs(_np(Bm)[i] - Bo).max() <= 1e-4, (r, v)
+    finally:
+        m.set_tuning(m.CALL_GRID, cfg, 0)
+        m.set_tuning(m.CALL_DIRTY, cfg, 0)
