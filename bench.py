@@ -300,6 +300,9 @@ def main():
     rec, _, st = m.uvw(wl.ant_enu, wl.pairs, ha, dec, wl.freq, cell, vis, cfg, flags=flags)
     off = torch.arange(B + 1, dtype=torch.int64, device="cuda") * wl.n_bl
     ws = m.Workspace()
+    # launch shapes of the separate calls, tuned on one chunk (muser_autotune)
+    tuned = {"grid_band_rows": m.autotune(m.CALL_GRID, cfg, rec=rec, vis_off=off[:min(B, 32) + 1]),
+             "dirty_column_variant": m.autotune(m.CALL_DIRTY, cfg, B=min(B, 32))}
     phase = {"grid": [], "dirty": [], "clean": [], "restore": []}
     clean_bytes, hbm_equiv_bytes = [], []
     N, G = wl.N, wl.G
@@ -364,6 +367,7 @@ def main():
              / (statistics.mean(phase["dirty"]) / 1e3) / 1e9,
              "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum()),
              "graph_replay_images_per_s": graph_value,
+             "autotuned": tuned,
              "center_ms_per_chunk": center_ms,
              "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3),
              "steer_ms_per_chunk_20_cycles": steer_ms, "steer_instance_cycles": steer_cycles,
