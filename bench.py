@@ -306,6 +306,12 @@ def main():
     phase = {"grid": [], "dirty": [], "clean": [], "restore": []}
     clean_bytes, hbm_equiv_bytes = [], []
     N, G = wl.N, wl.G
+    # one untimed pass over the first chunk so that no timed call waits for an allocation
+    n0 = min(args.chunk, B)
+    Z, stc = m.grid(rec, off[:n0 + 1], cfg, status=st[:n0].clone(), ws=ws)
+    D, Bm, stc = m.dirty(Z, cfg, status=stc, ws=ws)
+    del Z, D, Bm
+    torch.cuda.synchronize()
     for c0 in range(0, min(B, 2 * args.chunk), args.chunk):
         n = min(args.chunk, B - c0)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -376,6 +382,10 @@ def main():
              # passes of side 2N move 160 N^2 (half-planes where C or Y is zero)
              "steer_GBps": 192.0 * N * N * steer_cycles / (steer_ms / 1e3) / 1e9}
 
+    # the extra legs need the device memory of the main batch
+    del imager, out, o, vis_dev, ws, rec, st
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     if not args.no_extras and rank == 0:
         extra.update(plain_and_degrid(m, wl, cell, cfg, stream))
 
@@ -524,6 +534,8 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     res["plain_images_per_s"] = n_plain / (e0.elapsed_time(e1) / 1e3)
+    del ims
+    torch.cuda.empty_cache()
     # differentiable imaging: 512^2 sky, 780 baselines x 64 channels, chi2 + gradient per evaluation
     w4 = synth.config4_operator()
     cfg4 = m.Config(N=w4.N, G=w4.G, lat_rad=w4.lat)
@@ -555,6 +567,8 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     ev_bytes = 2 * (4.0 * N4 * N4 + 2 * 16.0 * G4 * G4 + 8.0 * w4.vis.size)
     res["grad_GBps"] = res["grad_evals_per_s"] * ev_bytes / 1e9
     res.update(fft_vs_cufft(m, wl, cell, cfg, stream))
+    del gd, obs, rec
+    torch.cuda.empty_cache()
     res["large_images"] = large_images(m, stream)
     res["w_projection"] = wproj_leg(m, stream)
     res["mixed_stream"] = mixed_stream(m, stream)
@@ -590,6 +604,7 @@ def wproj_leg(m, stream, n=296, P=128):
         torch.cuda.synchronize()
         res[f"{name}_images_per_s"] = wl.n_inst / (e0.elapsed_time(e1) / 1e3)
         del im
+        torch.cuda.empty_cache()
     res.update(w_planes=P, w_support=Ww, w_max_grid_units=w_max)
     return res
 
