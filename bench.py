@@ -185,7 +185,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=CHUNK)
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
-    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "wproj", "mixed"],
+    ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "large_clean", "wproj",
+                                       "mixed"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -421,6 +422,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     large: the large-image leg of the benchmark at one image side (`size`).
     wproj: the w-projection leg (MUSER-I band, about `n_inst` instances) with and without it.
     mixed: the mixed stream of `n_inst` (default 10,000) MUSER-I / MUSER-II instances.
+    large_clean: streaming CLEAN (`iters` iterations) of `n_inst` (default 16) instances at side `size`.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -432,6 +434,30 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         return
     if case == "wproj":
         print(json.dumps({"case": case, **wproj_leg(m, torch.cuda.current_stream(), n=n_inst or 296)}))
+        return
+    if case == "large_clean":
+        # streaming CLEAN of `n_inst` instances at a large image side (dirty maps built first)
+        wlL = synth.muser2_large_band(size, chans=list(range(n_inst or 16)))
+        cfgL = m.Config(N=size, G=4 * size, W=wlL.W, os=wlL.OS, max_iter=iters, gain=wlL.gain, lat_rad=wlL.lat)
+        cellL = m.pixel_size(wlL.freq, wlL.bmax, size, wlL.fov_min)
+        recL, _, stL = m.uvw(wlL.ant_enu, wlL.pairs, wlL.ha, wlL.dec, wlL.freq, cellL, wlL.vis, cfgL, flags=wlL.flags)
+        B = wlL.n_inst
+        offL = torch.arange(B + 1, dtype=torch.int64, device="cuda") * wlL.n_bl
+        D = torch.empty((B, size, size), dtype=torch.float32, device="cuda")
+        Bm = torch.empty((B, 2 * size, 2 * size), dtype=torch.float32, device="cuda")
+        for i in range(B):
+            Z, s2 = m.grid(recL, offL[i:i + 2], cfgL, status=stL[i:i + 1].clone())
+            d, b, _ = m.dirty(Z, cfgL, status=s2)
+            D[i], Bm[i] = d[0], b[0]
+            del Z, d, b
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        R, pos, flux, nc, _ = m.clean(D, Bm, cfgL)
+        e1.record()
+        torch.cuda.synchronize()
+        it = float(nc.double().sum())
+        print(json.dumps({"case": case, "N": size, "instances": B, "clean_ms": e0.elapsed_time(e1),
+                          "GBps": 12.0 * size * size * it / (e0.elapsed_time(e1) / 1e3) / 1e9}))
         return
     if case == "large":
         print(json.dumps({"case": case, **large_images(m, torch.cuda.current_stream(), sizes=(size,))}))
