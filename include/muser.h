@@ -87,8 +87,11 @@ typedef struct muser_config {
   int32_t gmm_bins;     /* histogram ranges for the GMM, 2..4096; 2000 in the paper (Sec. 4.1) */
   double lat_rad;       /* array latitude (Sec. 3.2.2) */
   int32_t batch_chunk;  /* muser_image: instances per internal chunk (0 = whole batch) */
-  int32_t clean_kernel; /* 0: residual held on chip for N = 256/512/1024 when the device allows
-                           (else streaming); 1: always stream the residual from memory */
+  int32_t clean_kernel; /* 0: residual held on chip for N = 256/512/1024 when the device allows;
+                           images of 640 pixels and more in batches of fewer instances than half the
+                           SMs streamed by clusters of 8 or 16 blocks per instance; otherwise one
+                           streaming block per instance.
+                           1: always one block per instance streaming the residual */
   int32_t w_planes;     /* w-projection (Alg. 1 dirty_image, Sec. 6.1): number of w-planes P, 0 = off
                            (2-D imaging), else 2..1024.  Imaging calls only (not muser_degrid). */
   float w_max;          /* largest |wg| the planes cover (wg = w (G cell)^2, record field wg);

@@ -351,10 +351,8 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_GMM: break;
     case MUSER_CALL_CLEAN:
       a.take<float>(2 * (size_t)B);
-      if (copies(*cfg)) {
-        a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
-        a.take<int>(1);
-      }
+      if (copies(*cfg)) a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
+      a.take<int>(1);
       break;
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
@@ -471,6 +469,10 @@ int muser_clean(float *residual, const float *beam, int B, const muser_config_t 
     launch_beam_copies(beam, B, N, 0, beam4, cstride, s);
     launch_hogbom(residual, beam, beam4, cstride, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
                   comp_flux, n_comp, status, s);
+  } else if (!clean_uses_copies(N) && cfg->clean_kernel == 0) {   // no on-chip kernel: clusters stream
+    int *next = a.take<int>(1);
+    launch_hogbom(residual, beam, nullptr, 0, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
+                  comp_flux, n_comp, status, s);
   } else {
     launch_hogbom_stream(residual, beam, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux,
                          n_comp, status, s);
@@ -566,7 +568,8 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     cudaStream_t hs = pp->clean[k];
     cudaStreamWaitEvent(hs, pp->prepped[k], 0);
     launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
-                  (size_t)Bc * 4 * N * N, w.next[k], n, N, cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
+                  (size_t)Bc * 4 * N * N, cfg->clean_kernel == 0 ? w.next[k] : nullptr, n, N,
+                  cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
                   cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                   comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);
     cudaEventRecord(pp->cleaned[k], hs);

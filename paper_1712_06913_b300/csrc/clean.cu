@@ -577,6 +577,162 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
   }
 }
 
+// ------------------------------------------------------------------ clustered streaming
+// k_hogbom_cstream (images whose residual does not fit on chip, N >= 640): clusters of CS
+// blocks share an instance; block `rank` streams rows [rank ceil(N/CS), ...) of the residual from
+// memory every iteration (16-byte residual accesses, 4-byte beam loads) and the block maxima meet
+// in the cluster exchange of k_hogbom_onchip.  Instances are claimed from a counter, so a batch of
+// fewer instances than SMs still streams on every SM.  The same operations as k_hogbom: the same
+// components and residuals.
+template <int CS, int MODE>
+__global__ void __launch_bounds__(kOnT, 1) k_hogbom_cstream(float *__restrict__ Rall, const float *__restrict__ beam,
+                                                            int N, int B, int *__restrict__ next,
+                                                            const float *__restrict__ thr, float gain, int cap,
+                                                            int32_t *__restrict__ pos, float *__restrict__ flux,
+                                                            int32_t *__restrict__ n_comp,
+                                                            int32_t *__restrict__ status) {
+  __shared__ Exchange<CS> xch;
+  __shared__ int claim[2], mine[2], stop_flag[2], any_abort[2];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int rows = (N + CS - 1) / CS;
+  const int r0 = min(N, rank * rows), r1 = min(N, r0 + rows);
+  const int qpr = N / 4, q0 = r0 * qpr, q1 = r1 * qpr;       // this block's quads
+  auto packed = [](const Peak &p) { return p.idx < 0x7fffffff ? pack_peak<MODE>(p.val, p.idx) : make_uint2(0u, 0u); };
+  if (tid == 0) {
+    xch.abort = 0;
+    mbar_init(&xch.bar[0], 1);
+    mbar_init(&xch.bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_arm(&xch.bar[0], CS * 8u);
+    mbar_arm(&xch.bar[1], CS * 8u);
+  }
+  __syncthreads();
+  int xk = 0, cpar = 0;
+  for (;;) {
+    if (rank == 0 && tid == 0) claim[cpar] = atomicAdd(next, 1);
+    if (tid == 0) stop_flag[cpar] = xch.abort;
+    cluster.sync();
+    if (tid < 32) {
+      const int f = tid < CS ? *cluster.map_shared_rank(stop_flag + cpar, tid) : 0;
+      const unsigned any = __ballot_sync(0xffffffffu, f != 0);
+      if (tid == 0) {
+        mine[cpar] = *cluster.map_shared_rank(claim + cpar, 0);
+        any_abort[cpar] = any != 0u;
+      }
+    }
+    __syncthreads();
+    const int inst = mine[cpar];
+    const bool aborted = any_abort[cpar] != 0;
+    cpar ^= 1;
+    if (inst >= B) break;                                   // same value in every block of the cluster
+    if (aborted || (status && (status[inst] & MUSER_ST_ALL_FLAGGED))) {
+      if (rank == 0 && tid == 0) {
+        n_comp[inst] = 0;
+        if (aborted && status) atomicOr(status + inst, MUSER_ST_TIMEOUT);
+      }
+      continue;
+    }
+    float4 *R4 = reinterpret_cast<float4 *>(Rall + (size_t)inst * N * N);
+    const float *Bm = beam + (size_t)inst * 4 * N * N;
+    const float t = thr ? thr[inst] : -CUDART_INF_F;
+    Peak lp{-CUDART_INF_F, 0.f, 0x7fffffff};
+    for (int q = q0 + tid; q < q1; q += kOnT) {
+      const float4 r = R4[q];
+      consider(lp, r.x, 4 * q, MODE);
+      consider(lp, r.y, 4 * q + 1, MODE);
+      consider(lp, r.z, 4 * q + 2, MODE);
+      consider(lp, r.w, 4 * q + 3, MODE);
+    }
+    Peak p = cluster_argmax<CS, MODE>(packed(lp), xch, xk++);
+    int it = 0;
+    while (!xch.abort && it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
+      const float f = gain * p.val;
+      if (rank == 0 && tid == 0) {
+        pos[(size_t)inst * cap + it] = p.idx;
+        flux[(size_t)inst * cap + it] = f;
+      }
+      const int py = p.idx / N, px = p.idx % N;
+      const float *Bw = Bm + (size_t)(N - py) * (2 * N) + (N - px);
+      Peak np{-CUDART_INF_F, 0.f, 0x7fffffff};
+#pragma unroll 2
+      for (int q = q0 + tid; q < q1; q += kOnT) {
+        const int y = q / qpr, x = (q - y * qpr) * 4;
+        const float *b = Bw + (size_t)y * (2 * N) + x;
+        float4 r = R4[q];
+        r.x -= f * __ldg(b);
+        r.y -= f * __ldg(b + 1);
+        r.z -= f * __ldg(b + 2);
+        r.w -= f * __ldg(b + 3);
+        R4[q] = r;
+        consider(np, r.x, 4 * q, MODE);
+        consider(np, r.y, 4 * q + 1, MODE);
+        consider(np, r.z, 4 * q + 2, MODE);
+        consider(np, r.w, 4 * q + 3, MODE);
+      }
+      p = cluster_argmax<CS, MODE>(packed(np), xch, xk++);
+      it++;
+    }
+    if (xch.abort && tid == 0 && status) atomicOr(status + inst, MUSER_ST_TIMEOUT);
+    if (rank == 0 && tid == 0) {
+      n_comp[inst] = it;
+      if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
+        atomicOr(status + inst, MUSER_ST_ITER_CAP);
+    }
+  }
+  if (xch.abort) __nanosleep(100000);
+  cluster.sync();   // peers may still read our claim and flags until here
+}
+
+struct CstreamPlan {
+  int usable = -1, clusters = 0;
+};
+
+template <int CS, int MODE>
+bool launch_cstream_mode(float *R, const float *beam, int N, int B, int *next, const float *thr, float gain, int cap,
+                         int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  static CstreamPlan plan;
+  auto k = k_hogbom_cstream<CS, MODE>;
+  cudaLaunchConfig_t lc = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  lc.blockDim = dim3(kOnT);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = s;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  if (plan.usable < 0) {
+    plan.usable = 0;
+    if (CS <= 8 || cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      int nclusters = 0;
+      lc.gridDim = dim3(CS);
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k, &lc) == cudaSuccess && nclusters > 0) {
+        plan.usable = 1;
+        plan.clusters = nclusters;
+      }
+    }
+    cudaGetLastError();
+  }
+  if (!plan.usable) return false;
+  const int nc = plan.clusters < B ? plan.clusters : B;
+  cudaMemsetAsync(next, 0, sizeof(int), s);
+  lc.gridDim = dim3(nc * CS);
+  cudaLaunchKernelEx(&lc, k, R, beam, N, B, next, thr, gain, cap, pos, flux, n_comp, status);
+  note_launch();
+  return true;
+}
+
+template <int CS>
+bool launch_cstream(float *R, const float *beam, int N, int B, int *next, const float *thr, float gain, int cap,
+                    int mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
+  return mode ? launch_cstream_mode<CS, 1>(R, beam, N, B, next, thr, gain, cap, pos, flux, n_comp, status, s)
+              : launch_cstream_mode<CS, 0>(R, beam, N, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
+}
+
 struct OnchipPlan {
   int usable = -1;       // -1 not yet queried, 0 cannot run, 1 can run
   int clusters = 0;      // resident clusters of the on-chip kernel
@@ -732,6 +888,20 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
       done = launch_onchip<1024, 16>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
   }
   if (done) return;
+  // images too large for the chip: one streaming block per instance fills the SMs when the batch
+  // has at least half as many instances as SMs (two chunks of muser_image overlap); smaller
+  // batches stream in clusters of blocks instead
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
+  if (next && !clean_uses_copies(N) && N >= 640 && N % 4 == 0 && 2 * B < sms) {
+    done = N >= 2560 ? launch_cstream<16>(R, beam, N, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s)
+                     : launch_cstream<8>(R, beam, N, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (done) return;
+  }
   launch_hogbom_stream(R, beam, B, N, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
 }
 

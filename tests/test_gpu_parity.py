@@ -927,3 +927,21 @@ def test_autotune_grid_and_dirty_shapes(m):
     finally:
         m.set_tuning(m.CALL_GRID, cfg, 0)
         m.set_tuning(m.CALL_DIRTY, cfg, 0)
+
+
+@pytest.mark.parametrize("name", ["N640", "N1280"])
+def test_clean_clustered_streaming_equals_single_block(m, name):
+    """Images without the on-chip kernel: clusters of blocks streaming one instance give the
+    components and residuals of one block per instance (the same operations), and follow the
+    oracle."""
+    import torch
+    wl = FIVE_CASES[name]()
+    cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
+    cfg.max_iter = 120
+    R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
+    cfg.clean_kernel = 1
+    R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
+    assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
+    assert float((R1 - R2).abs().max()) == 0.0
+    Do, Bo = ref[0][1], ref[0][2]
+    lockstep(Do, Bo, _np(p1)[0], _np(f1)[0], cfg.gain)
