@@ -379,9 +379,9 @@ def main():
              "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3),
              "steer_ms_per_chunk_20_cycles": steer_ms, "steer_instance_cycles": steer_cycles,
              "steer_us_per_instance_cycle": steer_ms * 1e3 / max(steer_cycles, 1),
-             # per instance-cycle: peak, selection and update read/write 32 N^2 bytes, the four FFT
-             # passes of side 2N move 160 N^2 (half-planes where C or Y is zero)
-             "steer_GBps": 192.0 * N * N * steer_cycles / (steer_ms / 1e3) / 1e9}
+             # per instance-cycle: selection 4 N^2 and update 20 N^2 bytes; the four FFT passes of
+             # side 2N move 148.8 N^2 (half-planes where C or Y is zero, half beam spectrum)
+             "steer_GBps": 172.8 * N * N * steer_cycles / (steer_ms / 1e3) / 1e9}
 
     # the extra legs need the device memory of the main batch
     del imager, out, o, vis_dev, ws, rec, st
@@ -521,7 +521,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         cyc = int(nc.sum())
         print(json.dumps({"case": case, "instances": n_inst, "steer_ms": e0.elapsed_time(e1), "instance_cycles": cyc,
                           "us_per_instance_cycle": e0.elapsed_time(e1) * 1e3 / max(cyc, 1),
-                          "GBps": 192.0 * N * N * cyc / (e0.elapsed_time(e1) / 1e3) / 1e9}))
+                          "GBps": 172.8 * N * N * cyc / (e0.elapsed_time(e1) / 1e3) / 1e9}))
     if case == "clean":
         ws.buf = None
         torch.cuda.empty_cache()
