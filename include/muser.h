@@ -70,7 +70,7 @@ enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
 enum {
   MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
   MUSER_CALL_RESTORE = 5, MUSER_CALL_IMAGE = 6, MUSER_CALL_DEGRID = 7, MUSER_CALL_CHI2 = 8,
-  MUSER_CALL_CENTER = 9, MUSER_CALL_STEER = 10
+  MUSER_CALL_CENTER = 9, MUSER_CALL_STEER = 10, MUSER_CALL_GRAD = 11
 };
 
 /* Imaging parameters (host struct, passed by pointer). */
@@ -285,6 +285,21 @@ MUSER_API int muser_center(const float *residual, const float *mu_a, const float
 MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr,
                           float clip, float *model, int32_t *n_cycles, void *ws, size_t ws_bytes, int32_t *status,
                           muser_stream_t stream);
+
+/* One step of gradient-descent imaging with the chi-square data term (the operator of
+ * muser_degrid; its gradient as for muser_chi2 + MUSER_ADJOINT):
+ *   v = A img;  loss = sum_k w_k |v_k - obs_k|^2 / sigma^2;  grad = Re A^H (2 w (v - obs) / sigma^2);
+ *   img -= eta grad.
+ * One call: the two forward transform passes, the interpolation with the chi-square term fused
+ * (the predicted visibilities are not stored), the adjoint's tap gathers and transform passes, and
+ * the update in the last pass's epilogue.  img [N][N] (in/out), obs [n_vis] complex64, loss (device
+ * float, out), grad [N][N] (out, nullable).  flags: 0 builds the plan (as muser_degrid without
+ * MUSER_REUSE_PLAN) in ws, MUSER_REUSE_PLAN reuses the plan a previous muser_degrid or
+ * muser_grad_step built in the same ws for the same records.  ws: muser_workspace_size(
+ * MUSER_CALL_GRAD, 1, n_vis, cfg) bytes (it holds the muser_degrid workspace at its start).  W <= 8. */
+MUSER_API int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_t n_vis, const float *obs,
+                              float inv_sigma2, float eta, float *loss, float *grad, const muser_config_t *cfg,
+                              void *ws, size_t ws_bytes, muser_stream_t stream);
 
 /* Launch-shape autotuner.  Times the candidates of one call's launch shape on the given batch
  * and keeps the fastest for later calls of this process with the same grid size (and

@@ -14,7 +14,7 @@ MUSER_OK, MUSER_ERR_ARG, MUSER_ERR_CUDA, MUSER_ERR_TIMEOUT, MUSER_ERR_UNSUPPORTE
  ST_NO_DISK) = 1, 2, 4, 8, 16, 32, 64, 128
 FORWARD, ADJOINT, REUSE_PLAN = 0, 1, 4
 (CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2, CALL_CENTER,
- CALL_STEER) = range(1, 11)
+ CALL_STEER, CALL_GRAD) = range(1, 12)
 
 _ERRNAMES = {1: "MUSER_ERR_ARG", 2: "MUSER_ERR_CUDA", 3: "MUSER_ERR_TIMEOUT", 4: "MUSER_ERR_UNSUPPORTED",
              5: "MUSER_ERR_WORKSPACE"}
@@ -57,6 +57,7 @@ SIGNATURES = {
     "muser_chi2": (I32, [P, P, P, I64, F32, P, P, P, SZ, P]),
     "muser_center": (I32, [P, P, P, P, I32, CFG, P, P, P, P, SZ, P, P]),
     "muser_steer": (I32, [P, P, I32, CFG, P, F32, P, P, P, SZ, P, P]),
+    "muser_grad_step": (I32, [I32, P, P, I64, P, F32, F32, P, P, CFG, P, SZ, P]),
     "muser_autotune": (I32, [I32, P, P, I32, I64, CFG, P, P]),
     "muser_set_tuning": (I32, [I32, CFG, I32]),
 }

@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import CALL_CENTER, CALL_CHI2, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
+from ._lib import CALL_CENTER, CALL_CHI2, CALL_GRAD, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GRID, CALL_IMAGE, check
 
 RECORD_FLOATS = 8          # 32-byte record viewed as float32[8]
 
@@ -491,7 +491,8 @@ class DegridPlan:
         self.n = rec.shape[0]
         self.c = cfg.c()
         self.ws = Workspace()
-        self.w, self.wb = self.ws.get(workspace_size(CALL_DEGRID, 1, self.n, cfg))
+        # the gradient-step workspace holds the operator's at its start: one plan serves both
+        self.w, self.wb = self.ws.get(workspace_size(CALL_GRAD, 1, self.n, cfg))
         self.cws = Workspace()
         self.cw, self.cwb = self.cws.get(workspace_size(CALL_CHI2, 1, self.n, None))
         self.planned = False
@@ -515,6 +516,14 @@ class DegridPlan:
         check(self.lib.muser_degrid(self._flag(_lib.ADJOINT), _p(out), _p(self.rec), self.n, _p(vis),
                                     ctypes.byref(self.c), self.w, self.wb, _stream()))
         return out
+
+    def grad_step(self, img, obs, inv_sigma2: float, eta: float, loss, grad=None):
+        """img -= eta grad chi2(img) in place (one library call, muser_grad_step); loss [1] (device)
+        receives chi2 at the incoming img, grad (optional [N, N]) the gradient."""
+        check(self.lib.muser_grad_step(_lib.REUSE_PLAN if self.planned else 0, _p(img), _p(self.rec), self.n,
+                                       _p(obs), float(inv_sigma2), float(eta), _p(loss), _p(grad),
+                                       ctypes.byref(self.c), self.w, self.wb, _stream()))
+        self.planned = True
 
     def chi2(self, pred, obs, inv_sigma2: float):
         """(loss, residual seed) of predicted visibilities against obs (see muser_chi2)."""

@@ -86,6 +86,21 @@ class GradientImaging:
         return lam
 
     def step(self):
+        """One step.  In a single process one library call does it all (muser_grad_step: forward,
+        chi-square, adjoint and update); across ranks the loss and gradient go through the
+        autograd functions and are summed over ranks before the update."""
+        import torch
+        if _dist.rank_world()[1] == 1 and self.cfg.W <= 8:
+            if not hasattr(self, "_loss_buf"):
+                self._loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
+            with torch.no_grad():
+                self.plan.grad_step(self.x, self.obs, self.inv_s2, self.eta, self._loss_buf)
+            self.loss = self._loss_buf[0]
+            return self.loss
+        return self.step_autograd()
+
+    def step_autograd(self):
+        """The same step through Degrid/Chi2 and loss.backward()."""
         import torch
         self.x.grad = None
         loss = chi2_loss(self.x, self.plan, self.obs, self.inv_s2)

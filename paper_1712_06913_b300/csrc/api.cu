@@ -342,7 +342,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
   if (B < 0 || n_vis_total < 0) return SIZE_MAX;
   if (call_id == MUSER_CALL_CHI2) return align_up(sizeof(float) * chi2_blocks(n_vis_total));
   if (!cfg) return SIZE_MAX;
-  const Mode mode = call_id == MUSER_CALL_DEGRID ? DEGRID : IMAGING;
+  const Mode mode = (call_id == MUSER_CALL_DEGRID || call_id == MUSER_CALL_GRAD) ? DEGRID : IMAGING;
   if (check_cfg(cfg, mode) != MUSER_OK) return SIZE_MAX;
   SizeArena a;
   switch (call_id) {
@@ -357,6 +357,14 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
     case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
+    case MUSER_CALL_GRAD: {
+      DegridWs<SizeArena> w;
+      w.carve(a, n_vis_total, *cfg);
+      a.take<float2>((size_t)n_vis_total);
+      a.take<float>((size_t)grad_interp_blocks(n_vis_total));
+      a.take<unsigned>(1);
+      break;
+    }
     case MUSER_CALL_CENTER: { CenterWs<SizeArena> w; w.carve(a, B, *cfg, true); break; }
     case MUSER_CALL_STEER: { SteerWs<SizeArena> w; w.carve(a, B, *cfg); break; }
     default: return SIZE_MAX;
@@ -613,6 +621,39 @@ int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64
     launch_degrid_adjoint((const float2 *)vis, cfg->N, cfg->G, w.tw, w.gc, K2, w.cell_off, w.taps, w.long_cells,
                           w.pieces, w.counts, w.partial, w.X, w.T, img, s);
   return check_launch("muser_degrid");
+}
+
+int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_t n_vis, const float *obs,
+                    float inv_sigma2, float eta, float *loss, float *grad, const muser_config_t *cfg, void *ws,
+                    size_t ws_bytes, muser_stream_t stream) {
+  MUSER_TRY(check_cfg(cfg, DEGRID));
+  if ((flags & ~MUSER_REUSE_PLAN) != 0) return fail(MUSER_ERR_ARG, "flags: 0 or MUSER_REUSE_PLAN");
+  if (n_vis < 1 || n_vis >= (int64_t)1 << 30) return fail(MUSER_ERR_ARG, "n_vis must be in [1, 2^30)");
+  if (cfg->W > 8) return fail(MUSER_ERR_UNSUPPORTED, "muser_grad_step needs W <= 8");
+  if (!img || !rec || !obs || !loss) return fail(MUSER_ERR_ARG, "muser_grad_step: required pointer is NULL");
+  if (!aligned(obs, 8)) return fail(MUSER_ERR_ARG, "obs must be 8-byte aligned");
+  const size_t need = muser_workspace_size(MUSER_CALL_GRAD, 1, n_vis, cfg);
+  MUSER_TRY(check_ws(ws, ws_bytes, need));
+  Arena a(ws, ws_bytes);
+  DegridWs<Arena> w;
+  w.carve(a, n_vis, *cfg);
+  float2 *resid = a.take<float2>((size_t)n_vis);
+  float *partial = a.take<float>((size_t)grad_interp_blocks(n_vis));
+  unsigned *ticket = a.take<unsigned>(1);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Pswf &P = pswf_coefficients(cfg->W);
+  const float K2 = (float)(P.K * P.K);
+  if (!(flags & MUSER_REUSE_PLAN)) {
+    launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
+    fft::launch_twiddles(w.tw, cfg->G, s);
+    launch_degrid_plan((const Rec *)rec, n_vis, cfg->G, cfg->W, cfg->os, w.tab, w.cnt, w.cell_off, w.sums, w.taps,
+                       w.long_cells, w.pieces, w.counts, s);
+  }
+  cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
+  launch_grad_step(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T, w.X,
+                   (const float2 *)obs, inv_sigma2, resid, partial, ticket, loss, w.cell_off, w.taps, w.long_cells,
+                   w.pieces, w.counts, w.partial, eta, grad, s);
+  return check_launch("muser_grad_step");
 }
 
 int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2,

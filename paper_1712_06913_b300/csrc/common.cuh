@@ -225,6 +225,15 @@ int chi2_blocks(int64_t n_vis);
 
 // centring (center.cu): Cc [B][N/2+1][N/2+1], dlm [B][2], shift [B][2] (nullable); scratch
 // thr, r2 [B] f32, masked [B] i32, F [B][2N][2N] c64, U [B][N/2+1][2N] c64, tw [2N] twiddles.
+// One gradient step of chi2 imaging (degrid.cu): forward operator, the chi-square seed and loss
+// fused into the interpolation, adjoint, img -= eta grad fused into the adjoint's row pass.
+// The plan (cell_off, taps, long_cells, pieces, counts) is the one launch_degrid_plan built.
+int grad_interp_blocks(int64_t n_vis);
+void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os, const float *tab,
+                      const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
+                      float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
+                      const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
+                      const int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s);
 // Steer clean (steer.cu): scratch FB [B][2N][N + 1] c64, F [B][2N][2N] c64, U [B][N][2N] c64, Y [B][N][N] f32,
 // state [B][steer_state_bytes()], tw [2N] twiddles.
 size_t steer_state_bytes();

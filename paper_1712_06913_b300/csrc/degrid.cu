@@ -119,95 +119,148 @@ __global__ void __launch_bounds__(256) k_interp(const float2 *__restrict__ X, co
   vis[r] = acc;
 }
 
-// FORWARD pass 3 for W <= 8: eight lanes per record, lane tv sums its row of taps; the
-// eight partial sums are combined with shuffles (more loads in flight than one thread per
-// record).
-__global__ void __launch_bounds__(256) k_interp8(const float2 *__restrict__ X, const Rec *__restrict__ rec, int64_t n,
-                                                 int G, int W, const float *__restrict__ tab, int ntab, float os,
-                                                 float invK2, float2 *__restrict__ vis) {
-  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-  const int tv = threadIdx.x & 7;
+// FORWARD pass 3 for W <= 8: eight lanes per record.  Interpolated visibility (before the 1/K^2
+// scale) of the record handled by this 8-lane group: lane t < W takes column t of the footprint,
+// looks up cu(t) and cv(t) once and gathers its W cells down the column, so each load instruction
+// of the group reads W consecutive cells of one grid row; the column sum uses the cv of every lane
+// (shuffles), the group sum the columns (shuffles).
+__device__ __forceinline__ float2 interp8_value(const float2 *__restrict__ X, const Rec &R, bool ok, int t, int G,
+                                                int W, const float *__restrict__ tab, int ntab, float os) {
   const int h = (W - 1) / 2;
-  Rec R;
-  bool ok = false;
-  if (r < n) {
-    R = rec[r];
-    ok = record_ok(R, G, h);
+  const bool act = ok && t < W;
+  float cu = 0.f, cv = 0.f;
+  float2 xs[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) xs[k] = make_float2(0.f, 0.f);
+  if (act) {
+    cu = kernel_lookup(tab, ntab, os, (float)(t - h) + R.fu);
+    cv = kernel_lookup(tab, ntab, os, (float)(t - h) + R.fv);
+    const float2 *col = X + (size_t)(R.kv - h) * G + (R.ku - h + t);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+      if (k < W) xs[k] = __ldg(col + (size_t)k * G);
   }
-  float2 acc = make_float2(0.f, 0.f);
-  if (ok && tv < W) {
-    const float cv = kernel_lookup(tab, ntab, os, (float)(tv - h) + R.fv);
-    const float2 *row = X + (size_t)(R.kv + tv - h) * G + (R.ku - h);
-    for (int tu = 0; tu < W; tu++) {
-      const float c = cv * kernel_lookup(tab, ntab, os, (float)(tu - h) + R.fu);
-      const float2 x = __ldg(row + tu);
-      acc.x += c * x.x;
-      acc.y += c * x.y;
-    }
+  const int base = threadIdx.x & 24;           // first lane of this group within the warp
+  float2 ca = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const float c = __shfl_sync(0xffffffffu, cv, base + k);
+    ca.x += c * xs[k].x;
+    ca.y += c * xs[k].y;
   }
+  float2 acc = make_float2(cu * ca.x, cu * ca.y);
 #pragma unroll
   for (int o = 1; o < 8; o <<= 1) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
+  return acc;
+}
+
+__global__ void __launch_bounds__(256) k_interp8(const float2 *__restrict__ X, const Rec *__restrict__ rec, int64_t n,
+                                                 int G, int W, const float *__restrict__ tab, int ntab, float os,
+                                                 float invK2, float2 *__restrict__ vis) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int tv = threadIdx.x & 7;
+  Rec R;
+  bool ok = false;
+  if (r < n) {
+    R = rec[r];
+    ok = record_ok(R, G, (W - 1) / 2);
+  }
+  const float2 acc = interp8_value(X, R, ok, tv, G, W, tab, ntab, os);
   if (r < n && tv == 0) vis[r] = ok ? make_float2(acc.x * invK2, acc.y * invK2) : make_float2(0.f, 0.f);
 }
 
-// ADJOINT gather: Z[c] = sum of its taps' weight x vis.  Short lists: one thread per cell;
-// lists longer than kLongList: skipped here, summed by a warp in k_adj_gather_long.
-constexpr int kLongList = 32;
-
-__global__ void k_adj_gather(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
-                             const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
-  const int a = cell_off[c], e = cell_off[c + 1];
-  if (e - a > kLongList) return;
-  float2 z = make_float2(0.f, 0.f);
-  int j = a;
-  for (; j + 4 <= e; j += 4) {                  // four gathers in flight, added in list order
-    int2 t[4];
-    float2 v[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
-#pragma unroll
-    for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const float w = __int_as_float(t[k].y);
-      z.x += w * v[k].x;
-      z.y += w * v[k].y;
+// k_interp8 with the chi-square data term fused (one gradient step): the predicted visibility v
+// of record r is not stored; instead resid[r] = 2 w (v - obs) / sigma^2 (the adjoint's input) and
+// the block's sum of w |v - obs|^2 / sigma^2 goes to partial[block].  The last block to finish
+// (ticket counter) adds the partials in block order into loss and re-arms the counter.
+constexpr int kInterpThreads = 256;
+__global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *__restrict__ X, const Rec *__restrict__ rec,
+                                                                 int64_t n, int G, int W, const float *__restrict__ tab,
+                                                                 int ntab, float os, float invK2,
+                                                                 const float2 *__restrict__ obs, float inv_s2,
+                                                                 float2 *__restrict__ resid, float *__restrict__ partial,
+                                                                 unsigned *__restrict__ ticket, float *__restrict__ loss) {
+  __shared__ float red[kInterpThreads / 32];
+  __shared__ bool last;
+  const int tv = threadIdx.x & 7;
+  const int64_t per = (int64_t)gridDim.x * (kInterpThreads / 8);   // records per sweep of the grid
+  float l = 0.f;
+  for (int64_t r0 = (int64_t)blockIdx.x * (kInterpThreads / 8); r0 < n; r0 += per) {   // uniform per block
+    const int64_t r = r0 + (threadIdx.x >> 3);
+    Rec R;
+    bool ok = false;
+    if (r < n) {
+      R = rec[r];
+      ok = record_ok(R, G, (W - 1) / 2);
+    }
+    const float2 acc = interp8_value(X, R, ok, tv, G, W, tab, ntab, os);
+    if (r < n && tv == 0) {
+      const float w = ok ? R.w : 0.f;
+      const float2 o = obs[r];
+      const float dx = acc.x * invK2 - o.x, dy = acc.y * invK2 - o.y;
+      if (w > 0.f) l += w * (dx * dx + dy * dy);
+      resid[r] = w > 0.f ? make_float2(2.f * w * dx * inv_s2, 2.f * w * dy * inv_s2) : make_float2(0.f, 0.f);
     }
   }
-  for (; j < e; j++) {
-    const int2 t = __ldg(taps + j);
-    const float w = __int_as_float(t.y);
-    const float2 v = __ldg(vis + t.x);
-    z.x += w * v.x;
-    z.y += w * v.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < kInterpThreads / 32; k++) t += red[k];
+    partial[blockIdx.x] = t * inv_s2;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
-  Z[c] = z;
+  __syncthreads();
+  if (last) {                      // the whole block adds the partials, in a fixed order
+    __threadfence();
+    float t = 0.f;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kInterpThreads) t += __ldcg(partial + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float u = 0.f;
+      for (int k = 0; k < kInterpThreads / 32; k++) u += red[k];
+      *loss = u;
+      *ticket = 0u;
+    }
+  }
 }
 
+// ADJOINT gather: Z[c] = sum of its taps' weight x vis.  Lists of at most kLongList taps: one
+// thread per cell; longer lists are cut into pieces of kPiece taps.
+constexpr int kLongList = 32;
 constexpr int kPiece = 512;
+constexpr int kPieceBlocks = 592;
 
-// One warp per piece of a long list: its partial sum (lanes stride the piece, then a fixed
-// shuffle tree).
-__global__ void k_adj_pieces(const int2 *__restrict__ taps, const float2 *__restrict__ vis,
-                             const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
-                             float2 *__restrict__ partial) {
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  const int np = *n_pieces;
-  for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < np; k += nw) {
-    const int4 pc = pieces[k];                 // {cell, first tap, end tap, -}
+// One launch for both: the first kPieceBlocks blocks take one piece of a long list per warp
+// (lanes stride the piece, then a fixed shuffle tree) into partial[piece] -- they start first,
+// being the longest -- and the others gather the short lists (one thread per cell, four gathers
+// in flight, added in list order).
+__global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
+                                    const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z, int nbg,
+                                    const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
+                                    float2 *__restrict__ partial) {
+  if ((int)blockIdx.x >= kPieceBlocks) {
+    const int64_t c = (int64_t)(blockIdx.x - kPieceBlocks) * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int a = cell_off[c], e = cell_off[c + 1];
+    if (e - a > kLongList) return;
     float2 z = make_float2(0.f, 0.f);
-    int j = pc.y + lane;
-    for (; j + 96 < pc.z; j += 128) {           // four gathers per lane in flight, added in order
+    int j = a;
+    for (; j + 4 <= e; j += 4) {
       int2 t[4];
       float2 v[4];
 #pragma unroll
-      for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + 32 * k);
+      for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
 #pragma unroll
       for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
 #pragma unroll
@@ -215,6 +268,37 @@ __global__ void k_adj_pieces(const int2 *__restrict__ taps, const float2 *__rest
         const float w = __int_as_float(t[k].y);
         z.x += w * v[k].x;
         z.y += w * v[k].y;
+      }
+    }
+    for (; j < e; j++) {
+      const int2 t = __ldg(taps + j);
+      const float w = __int_as_float(t.y);
+      const float2 v = __ldg(vis + t.x);
+      z.x += w * v.x;
+      z.y += w * v.y;
+    }
+    Z[c] = z;
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int nw = kPieceBlocks * (blockDim.x >> 5);
+  const int np = *n_pieces;
+  for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < np; k += nw) {
+    const int4 pc = pieces[k];
+    float2 z = make_float2(0.f, 0.f);
+    int j = pc.y + lane;
+    for (; j + 96 < pc.z; j += 128) {
+      int2 t[4];
+      float2 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) t[q] = __ldg(taps + j + 32 * q);
+#pragma unroll
+      for (int q = 0; q < 4; q++) v[q] = __ldg(vis + t[q].x);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const float w = __int_as_float(t[q].y);
+        z.x += w * v[q].x;
+        z.y += w * v[q].y;
       }
     }
     for (; j < pc.z; j += 32) {
@@ -279,9 +363,11 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_adj_cols(const float2 *__rest
 
 // ADJOINT pass 2: rows, central N columns, real part, grid correction and 1/K^2.
 template <int G>
+// img = grad; or, in a gradient step (upd), img -= eta grad and grad (if given) = grad
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
                                                            const float *__restrict__ gc, float invK2,
-                                                           float *__restrict__ img) {
+                                                           float *__restrict__ img, int upd, float eta,
+                                                           float *__restrict__ grad) {
   using C = RowCfg<G>;
   constexpr int N = G / 2, S = C::S, NT = C::NT, LO = G / 2 - N / 2;
   __shared__ float2 sm[C::Layout::size];
@@ -293,23 +379,38 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(const float2 *__rest
   } load{T, r0};
   struct Store {
     const float *gc;
-    float *img;
-    int r0;
-    float invK2;
+    float *img, *grad;
+    int r0, upd;
+    float invK2, eta;
     __device__ void operator()(int x, int s, float2 v) const {
       if (x < LO || x >= LO + N) return;
       const int y = r0 + s + LO;
       float f = invK2 / (__ldg(gc + x) * __ldg(gc + y));
       if ((x + y) & 1) f = -f;
-      img[(size_t)(r0 + s) * N + (x - LO)] = v.x * f;
+      const size_t k = (size_t)(r0 + s) * N + (x - LO);
+      const float g = v.x * f;
+      if (!upd) {
+        img[k] = g;
+        return;
+      }
+      img[k] -= eta * g;
+      if (grad) grad[k] = g;
     }
-  } store{gc, img, r0, invK2};
+  } store{gc, img, grad, r0, upd, invK2, eta};
   fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
 }
 
+// GradStep: the chi-square term of a gradient step fused into the interpolation (obs set)
+struct GradStep {
+  const float2 *obs = nullptr;
+  float inv_s2 = 0.f;
+  float *partial = nullptr, *loss = nullptr;
+  unsigned *ticket = nullptr;
+};
+
 template <int G>
 void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const float *tab, const float2 *tw,
-               const float *gc, float K2, float2 *T1, float2 *X, float2 *vis, cudaStream_t s) {
+               const float *gc, float K2, float2 *T1, float2 *X, float2 *vis, cudaStream_t s, const GradStep &gs) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, tw, gc, T1);
@@ -317,6 +418,13 @@ void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const
   cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(T1, tw, X);
   note_launch();
+  if (gs.obs) {              // gradient step: vis receives the residual seed (W <= 8 checked by the caller)
+    k_interp8_chi2<<<grad_interp_blocks(n), kInterpThreads, 0, s>>>(
+        X, rec, n, G, W, tab, table_len(W, os), (float)os, 1.f / K2, gs.obs, gs.inv_s2, vis, gs.partial, gs.ticket,
+        gs.loss);
+    note_launch();
+    return;
+  }
   if (n > 0 && W <= 8) {
     k_interp8<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
                                                                1.f / K2, vis);
@@ -329,13 +437,14 @@ void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const
 }
 
 template <int G>
-void adjoint_G(const float2 *Z, const float2 *tw, const float *gc, float K2, float2 *T, float *img, cudaStream_t s) {
+void adjoint_G(const float2 *Z, const float2 *tw, const float *gc, float K2, float2 *T, float *img, cudaStream_t s,
+               int upd, float eta, float *grad) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_adj_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(Z, tw, T);
   note_launch();
-  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(T, tw, gc, 1.f / K2, img);
+  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(T, tw, gc, 1.f / K2, img, upd, eta, grad);
   note_launch();
 }
 
@@ -502,7 +611,7 @@ void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int 
                            float2 *vis, cudaStream_t s) {
   switch (G) {
 #define MUSER_CASE(g) \
-  case g: forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, vis, s); break;
+  case g: forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, vis, s, GradStep{}); break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
 #undef MUSER_CASE
     default: break;
@@ -549,15 +658,51 @@ void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, co
                            const int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
                            cudaStream_t s) {
   const int64_t ncell = (int64_t)G * G;
-  k_adj_gather<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(cell_off, taps, vis, ncell, Z);
-  note_launch();
-  k_adj_pieces<<<592, 256, 0, s>>>(taps, vis, pieces, counts + 1, partial);
+  const int nbg = (int)((ncell + 255) / 256);
+  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, nbg, pieces, counts + 1,
+                                                         partial);
   note_launch();
   k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, partial, Z);
   note_launch();
   switch (G) {
 #define MUSER_CASE(g) \
-  case g: adjoint_G<g>(Z, tw, gc, K2, T, img, s); break;
+  case g: adjoint_G<g>(Z, tw, gc, K2, T, img, s, 0, 0.f, nullptr); break;
+    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+#undef MUSER_CASE
+    default: break;
+  }
+}
+
+// grid of the fused interpolation: at most four blocks per SM of a B300 (the blocks' loss
+// tickets meet on one counter), each sweeping records
+int grad_interp_blocks(int64_t n_vis) {
+  const int64_t b = (n_vis * 8 + kInterpThreads - 1) / kInterpThreads;
+  return (int)(b < 1 ? 1 : (b > 592 ? 592 : b));
+}
+
+void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os, const float *tab,
+                      const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
+                      float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
+                      const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
+                      const int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s) {
+  GradStep gs;
+  gs.obs = obs;
+  gs.inv_s2 = inv_s2;
+  gs.partial = partial;
+  gs.loss = loss;
+  gs.ticket = ticket;
+  const int64_t ncell = (int64_t)G * G;
+  switch (G) {
+#define MUSER_CASE(g)                                                                                \
+  case g:                                                                                            \
+    forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, resid, s, gs);                      \
+    k_adj_gather_pieces<<<(int)((ncell + 255) / 256) + kPieceBlocks, 256, 0, s>>>(                 \
+        cell_off, taps, resid, ncell, X, (int)((ncell + 255) / 256), pieces, counts + 1, apartial);   \
+    note_launch();                                                                                   \
+    k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, apartial, X);                                 \
+    note_launch();                                                                                   \
+    adjoint_G<g>(X, tw, gc, K2, T1, img, s, 1, eta, grad);                                           \
+    break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
 #undef MUSER_CASE
     default: break;

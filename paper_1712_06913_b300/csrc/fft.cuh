@@ -296,13 +296,14 @@ __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, L
 // rows: S rows per block, 16 values per thread per stage (32 above G = 10240, so that a row
 // still fits in 1024 threads).  ColCfg / RowCfg (S = min(G, 16384 / G) columns,
 // min(max(1, 4096 / G), G / 2) rows; 20480 / G and 5120 / G for G = 5 * 2^m) fill the SMs when
-// many instances are transformed at once; ColCfg1 / RowCfg1 (max(4, 4096 / G) columns,
+// many instances are transformed at once; ColCfg1 / RowCfg1 (max(4, 4096 / G) columns with 16
+// values per thread,
 // max(1, 2048 / G) rows) give one transform 4 times as many blocks.  Row kernels whose strip
 // exceeds 48 KB (G >= 8192) take their shared memory dynamically (RowStrip::dyn).
-template <int G, int S_>
+template <int G, int S_, int E = 32>
 struct ColStrip {
   static constexpr int S = S_;
-  static constexpr int NT = S * G / 32;
+  static constexpr int NT = S * G / E;       // E values per thread per stage
   using Layout = Interleaved<G, S>;
   static constexpr size_t smem = sizeof(float2) * Layout::size;
 };
@@ -321,7 +322,7 @@ using ColCfg = ColStrip<G, cmin(G, (G % 5 ? 16384 : 20480) / G)>;
 template <int G>
 using RowCfg = RowStrip<G, cmin(cmax(1, (G % 5 ? 4096 : 5120) / G), G / 2)>;
 template <int G>
-using ColCfg1 = ColStrip<G, cmin(G, cmax(4, 4096 / G))>;
+using ColCfg1 = ColStrip<G, cmin(G, cmax(4, 4096 / G)), 16>;
 template <int G>
 using RowCfg1 = RowStrip<G, cmin(cmax(1, 2048 / G), G / 2)>;
 

@@ -464,6 +464,35 @@ def test_gradient_descent_imaging_vs_oracle_and_graph_replay(m):
     assert float((gd3.x.detach() - x_replay).abs().max()) <= 1e-6 * float(x_replay.abs().max())
 
 
+@pytest.mark.parametrize("N", [32, 64])
+def test_fused_gradient_step_equals_autograd_step(m, N):
+    """muser_grad_step (forward, chi-square fused into the interpolation, adjoint, update in the
+    adjoint's epilogue) equals the step through the autograd functions: same loss, gradient
+    and updated image up to the order of float sums."""
+    import torch
+    from paper_1712_06913_b300.autograd import GradientImaging
+    wl, cfg, rec, ro = _op_case(m, N)
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    x0 = torch.tensor(np.random.default_rng(N).normal(size=(N, N)), dtype=torch.float32, device="cuda")
+    a = GradientImaging(rec, obs, 0.5, cfg, x0=x0, eta=1e-4)
+    b = GradientImaging(rec, obs, 0.5, cfg, x0=x0, eta=1e-4)
+    la = float(a.step())                       # fused (single process)
+    lb = float(b.step_autograd())
+    assert la == pytest.approx(lb, rel=1e-5)
+    xa, xb = a.x.detach(), b.x.detach()
+    assert float((xa - xb).abs().max()) <= 1e-6 * float(xb.abs().max())
+    # the gradient output of the fused call against the oracle's FP64 gradient at x0
+    plan = a.plan
+    grad = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    x = x0.clone()
+    plan.grad_step(x, obs, 1.0 / 0.25, 0.0, loss, grad)
+    assert torch.equal(x, x0)                   # eta = 0 leaves the image
+    c_o, g_o = oop.chi2_grad(x0.cpu().numpy().astype(np.float64), ro, ro["vis"], 0.5, N, cfg.G, KER)
+    assert float(loss[0]) == pytest.approx(c_o, rel=1e-4)
+    assert np.linalg.norm(_np(grad) - g_o) <= 1e-4 * np.linalg.norm(g_o)
+
+
 # ------------------------------------------------------------------------------ disk centring (Sec. 4.2)
 def _centring_case(off_px, N=128, seed=110):
     wl0 = synth.small_workload(n_ant=31, N=N, config_id=seed, bmax=600.0, snr=0)
