@@ -315,6 +315,12 @@ MUSER_API int muser_autotune(int call_id, const muser_vis_record_t *rec, const i
                              int64_t n_vis_total, const muser_config_t *cfg, int32_t *choice, muser_stream_t stream);
 MUSER_API int muser_set_tuning(int call_id, const muser_config_t *cfg, int value);
 
+/* Self-test of the library's bounded waits (failure detection without a fault): one warp waits
+ * on a shared-memory mbarrier that nothing completes, with the try_wait loop of the CLEAN
+ * clusters' exchange, for at most limit_cycles SM clock cycles (<= 2^31, about one second), then
+ * writes MUSER_ST_TIMEOUT to status[0] (device int) and returns; the context stays usable. */
+MUSER_API int muser_selftest_wait(long long limit_cycles, int32_t *status, muser_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

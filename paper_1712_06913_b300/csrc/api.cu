@@ -799,4 +799,12 @@ int muser_autotune(int call_id, const muser_vis_record_t *rec, const int64_t *vi
   return check_launch("muser_autotune");
 }
 
+int muser_selftest_wait(long long limit_cycles, int32_t *status, muser_stream_t stream) {
+  if (!status) return fail(MUSER_ERR_ARG, "muser_selftest_wait: status is NULL");
+  if (limit_cycles < 0 || limit_cycles > (1ll << 31))
+    return fail(MUSER_ERR_ARG, "limit_cycles must be in [0, 2^31] (about one second)");
+  launch_wait_selftest(limit_cycles, status, (cudaStream_t)stream);
+  return check_launch("muser_selftest_wait");
+}
+
 }  // extern "C"

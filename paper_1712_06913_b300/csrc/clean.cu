@@ -685,6 +685,21 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_cstream(float *__restrict__ 
   cluster.sync();   // peers may still read our claim and flags until here
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that no one completes, with the
+// same try_wait loop as the cluster exchange but a caller-given bound; when the bound runs out it
+// reports MUSER_ST_TIMEOUT and returns, leaving the context usable.
+__global__ void k_wait_selftest(long long limit, int32_t *__restrict__ status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);                     // one arrival expected; none comes
+    const long long t0 = clock64();
+    bool done = false;
+    while (!(done = mbar_try_wait(&bar, 0u)))
+      if (clock64() - t0 > limit) break;
+    status[0] = done ? 0 : MUSER_ST_TIMEOUT;
+  }
+}
+
 struct CstreamPlan {
   int usable = -1, clusters = 0;
 };
@@ -915,6 +930,11 @@ void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float
                                           flux + (size_t)i * cap, n_comp + i, status ? status + i : nullptr);
     note_launch();
   }
+}
+
+void launch_wait_selftest(long long limit_cycles, int32_t *status, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(limit_cycles, status);
+  note_launch();
 }
 
 }  // namespace muser

@@ -246,7 +246,7 @@ constexpr int kPieceBlocks = 592;
 // being the longest -- and the others gather the short lists (one thread per cell, four gathers
 // in flight, added in list order).
 __global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
-                                    const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z, int nbg,
+                                    const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z,
                                     const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
                                     float2 *__restrict__ partial) {
   if ((int)blockIdx.x >= kPieceBlocks) {
@@ -659,8 +659,7 @@ void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, co
                            cudaStream_t s) {
   const int64_t ncell = (int64_t)G * G;
   const int nbg = (int)((ncell + 255) / 256);
-  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, nbg, pieces, counts + 1,
-                                                         partial);
+  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, pieces, counts + 1, partial);
   note_launch();
   k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, partial, Z);
   note_launch();
@@ -697,7 +696,7 @@ void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, i
   case g:                                                                                            \
     forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, resid, s, gs);                      \
     k_adj_gather_pieces<<<(int)((ncell + 255) / 256) + kPieceBlocks, 256, 0, s>>>(                 \
-        cell_off, taps, resid, ncell, X, (int)((ncell + 255) / 256), pieces, counts + 1, apartial);   \
+        cell_off, taps, resid, ncell, X, pieces, counts + 1, apartial);                               \
     note_launch();                                                                                   \
     k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, apartial, X);                                 \
     note_launch();                                                                                   \

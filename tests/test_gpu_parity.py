@@ -974,3 +974,22 @@ def test_clean_clustered_streaming_equals_single_block(m, name):
     assert float((R1 - R2).abs().max()) == 0.0
     Do, Bo = ref[0][1], ref[0][2]
     lockstep(Do, Bo, _np(p1)[0], _np(f1)[0], cfg.gain)
+
+
+# ------------------------------------------------------------------------------ failure detection
+def test_bounded_wait_runs_out_and_context_stays_usable(m):
+    """A wait that nothing completes (the exchange's try_wait loop, on an mbarrier no one
+    arrives at) gives up after its bound and reports MUSER_ST_TIMEOUT; the next calls work."""
+    import ctypes
+    import time
+    import torch
+    from paper_1712_06913_b300 import _lib
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    _lib.check(_lib.load().muser_selftest_wait(1 << 27, ctypes.c_void_p(st.data_ptr()),
+                                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    torch.cuda.synchronize()
+    assert int(st[0]) == m.ST_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    # the context is usable: a CLEAN right after follows the oracle
+    test_clean_threshold_and_abs_mode(m)
