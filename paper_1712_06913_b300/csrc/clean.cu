@@ -330,19 +330,25 @@ __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o
 // kernels share a batch without any other coordination.
 //
 // Per block, a band of kTmPix / N rows of the residual (CS blocks per instance).
-template <int N, int CS, int MODE>
+// NQ quads per thread: the first kTmQuads in tensor memory, the rest (EXT: the 320, 640 and 1280
+// pixel images, 25 quads = 102400 pixels per block) in shared memory, [quad - kTmQuads][thread].
+template <int N, int CS, int MODE, int NQ = kTmQuads>
 __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ Rall, const float *__restrict__ beam4,
                                                            size_t cstride, int B, int *__restrict__ next,
                                                            const float *__restrict__ thr, float gain, int cap,
                                                            int32_t *__restrict__ pos, float *__restrict__ flux,
                                                            int32_t *__restrict__ n_comp,
                                                            int32_t *__restrict__ status) {
-  static_assert(N * N == CS * kTmPix, "one band per block");
-  static_assert((4 * kOnT) % N == 0, "a quad step spans whole rows");
+  constexpr bool EXT = NQ > kTmQuads;
+  constexpr int SQ = NQ - kTmQuads, kSB = 3;              // shared-memory quads, beam loads in flight
+  static_assert(N * N == CS * NQ * 4 * kOnT, "one band per block");
+  static_assert(EXT || (4 * kOnT) % N == 0, "a quad step spans whole rows");
+  static_assert(!EXT || (SQ % kSB == 0 && N % 4 == 0), "whole batches of shared-memory quads");
   __shared__ Exchange<CS> xch;
   __shared__ int claim[2], mine[2], stop_flag[2], any_abort[2];
   __shared__ uint32_t tm_base;
-  constexpr int ROWS = kTmPix / N;
+  extern __shared__ float4 xs4[];                           // EXT: [SQ][kOnT] residual quads
+  constexpr int ROWS = NQ * 4 * kOnT / N;
   constexpr int QSTEP = 4 * kOnT / N;                    // rows advanced per quad step
   const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -422,6 +428,14 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
         cb.quad(b, 4 * i + 4);
         tm_st8(tm + 4 * i, u);
       }
+      if constexpr (EXT) {
+#pragma unroll
+        for (int i = kTmQuads; i < NQ; i++) {
+          const float4 a = R4[tid + i * kOnT];
+          xs4[(i - kTmQuads) * kOnT + tid] = a;
+          cb.quad(a, 4 * i);
+        }
+      }
     }
     tm_wait_st();
     Peak p = cluster_argmax<CS, MODE>(packed(cb.value(), cb.o), xch, xk++);
@@ -438,6 +452,16 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       const int off = N - px;
       const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
       const float4 *bt = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
+      // beam quad of the thread's quad i: a fixed stride when a quad step spans whole rows, else
+      // from the band pixel's row and column
+      auto beam_q = [&](int i) -> const float4 * {
+        if constexpr (EXT) {
+          const int b = 4 * (tid + i * kOnT), r = b / N, c = b - r * N;
+          return reinterpret_cast<const float4 *>(Wa + (size_t)r * (2 * N) + c);
+        } else {
+          return bt + i * QSTEP * (2 * N / 4);
+        }
+      };
       cb = Cand<MODE>();
       // kTmBatch aligned beam loads in flight, then the residual read, updated and written back
       // eight cells at a time
@@ -445,7 +469,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       for (int i0 = 0; i0 < kTmQuads; i0 += kTmBatch) {   // not unrolled: keeps the batches apart
         float4 bb[kTmBatch];
 #pragma unroll
-        for (int k = 0; k < kTmBatch; k++) bb[k] = __ldg(bt + (i0 + k) * QSTEP * (2 * N / 4));
+        for (int k = 0; k < kTmBatch; k++) bb[k] = __ldg(beam_q(i0 + k));
 #pragma unroll
         for (int k = 0; k < kTmBatch; k += 2) {
           const int i = i0 + k;
@@ -462,6 +486,24 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
           tm_st8(tm + 4 * i, u);
           cb.quad(v[0], v[1], v[2], v[3], 4 * i);
           cb.quad(v[4], v[5], v[6], v[7], 4 * i + 4);
+        }
+      }
+      if constexpr (EXT) {                                  // the shared-memory quads, after the others
+#pragma unroll 1
+        for (int i0 = kTmQuads; i0 < NQ; i0 += kSB) {
+          float4 bb[kSB];
+#pragma unroll
+          for (int k = 0; k < kSB; k++) bb[k] = __ldg(beam_q(i0 + k));
+#pragma unroll
+          for (int k = 0; k < kSB; k++) {
+            float4 v = xs4[(i0 + k - kTmQuads) * kOnT + tid];
+            v.x -= f * bb[k].x;
+            v.y -= f * bb[k].y;
+            v.z -= f * bb[k].z;
+            v.w -= f * bb[k].w;
+            xs4[(i0 + k - kTmQuads) * kOnT + tid] = v;
+            cb.quad(v, 4 * (i0 + k));
+          }
         }
       }
       tm_wait_st();
@@ -485,6 +527,10 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
                                        __uint_as_float(u[3]));
       R4[tid + (i + 1) * kOnT] = make_float4(__uint_as_float(u[4]), __uint_as_float(u[5]), __uint_as_float(u[6]),
                                              __uint_as_float(u[7]));
+    }
+    if constexpr (EXT) {
+#pragma unroll
+      for (int i = kTmQuads; i < NQ; i++) R4[tid + i * kOnT] = xs4[(i - kTmQuads) * kOnT + tid];
     }
   }
   tm_fence_before();
@@ -782,15 +828,16 @@ SideStream *side_stream() {
 }
 
 // Launch the queue workers if the device can host the on-chip clusters; false -> fallback.
-template <int N, int CS, int MODE>
+template <int N, int CS, int MODE, int NQ = kTmQuads>
 bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
                         int cap, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
   static OnchipPlan plan;          // per process: the library runs on one device model
-  auto k = k_hogbom_onchip<N, CS, MODE>;
-  // the residual lives in tensor memory; the kernel still asks for more than half of an SM's
-  // shared memory so that no two of its blocks (each allocating all 512 columns) share an SM
-  const size_t smem = (size_t)116 * 1024;
-  auto ks = k_hogbom_stream_q<N, MODE>;
+  constexpr bool EXT = NQ > kTmQuads;
+  auto k = k_hogbom_onchip<N, CS, MODE, NQ>;
+  // the residual lives in tensor memory (and, EXT, partly in shared memory); the kernel asks for
+  // more than half of an SM's shared memory so that no two of its blocks (each allocating all
+  // 512 columns) share an SM
+  const size_t smem = EXT ? (size_t)(NQ - kTmQuads) * kOnT * sizeof(float4) : (size_t)116 * 1024;
   cudaLaunchConfig_t lc = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -822,7 +869,7 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   // Streaming workers (one instance each, the last ns of the batch) only when the clusters'
   // share is at least 40 waves, long enough to hide a streaming instance (which takes about
   // 40 times as long as a cluster's at N = 1024).
-  const int ns = (plan.leftover > 0 && B - plan.leftover >= 40 * plan.clusters) ? plan.leftover : 0;
+  const int ns = (!EXT && plan.leftover > 0 && B - plan.leftover >= 40 * plan.clusters) ? plan.leftover : 0;
   const int Bc = B - ns;
   const int nc = plan.clusters < Bc ? plan.clusters : Bc;
   cudaMemsetAsync(next, 0, sizeof(int), s);
@@ -837,21 +884,24 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   lc.gridDim = dim3(nc * CS);
   cudaLaunchKernelEx(&lc, k, R, beam4, cstride, Bc, next, thr, gain, cap, pos, flux, n_comp, status);
   note_launch();
-  if (side) {
-    cudaStreamWaitEvent(side->s, side->fork, 0);
-    ks<<<ns, kOnT, 0, side->s>>>(R, beam4, cstride, Bc, thr, gain, cap, pos, flux, n_comp, status);
-    note_launch();
-    cudaEventRecord(side->join, side->s);
-    cudaStreamWaitEvent(s, side->join, 0);
+  if constexpr (!EXT) {
+    if (side) {
+      cudaStreamWaitEvent(side->s, side->fork, 0);
+      k_hogbom_stream_q<N, MODE><<<ns, kOnT, 0, side->s>>>(R, beam4, cstride, Bc, thr, gain, cap, pos, flux, n_comp,
+                                                            status);
+      note_launch();
+      cudaEventRecord(side->join, side->s);
+      cudaStreamWaitEvent(s, side->join, 0);
+    }
   }
   return true;
 }
 
-template <int N, int CS>
+template <int N, int CS, int NQ = kTmQuads>
 bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
                    int cap, int mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
-  return mode ? launch_onchip_mode<N, CS, 1>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s)
-              : launch_onchip_mode<N, CS, 0>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
+  return mode ? launch_onchip_mode<N, CS, 1, NQ>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s)
+              : launch_onchip_mode<N, CS, 0, NQ>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
 }
 
 // dst copy k (k = first..3) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
@@ -876,6 +926,9 @@ int hogbom_onchip_clusters(int N) {
     case 256: return 1;
     case 512: return 4;
     case 1024: return 16;
+    case 320: return 1;
+    case 640: return 4;
+    case 1280: return 16;
     default: return 0;
   }
 }
@@ -901,6 +954,14 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
       done = launch_onchip<512, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 1024)
       done = launch_onchip<1024, 16>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    // 102400-pixel bands: 65536 pixels in tensor memory, 36864 in shared memory
+    if (N == 320)
+      done = launch_onchip<320, 1, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (N == 640)
+      done = launch_onchip<640, 4, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+    if (N == 1280)
+      done = launch_onchip<1280, 16, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+                                         s);
   }
   if (done) return;
   // images too large for the chip: one streaming block per instance fills the SMs when the batch

@@ -192,7 +192,7 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
 void launch_wait_selftest(long long limit_cycles, int32_t *status, cudaStream_t s);
 // copies k = first..3 of beam [B][2N][2N] into beam4 (copy 0 at beam4 is written only if first == 0)
 void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4, size_t cstride, cudaStream_t s);
-inline bool clean_uses_copies(int N) { return N == 256 || N == 512 || N == 1024; }
+inline bool clean_uses_copies(int N) { return N == 256 || N == 512 || N == 1024 || N == 320 || N == 640 || N == 1280; }
 void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float *thr, float gain, int cap,
                           int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s);
 int hogbom_onchip_clusters(int N);   // blocks per instance of the on-chip kernel (0: not available)

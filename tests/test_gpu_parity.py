@@ -790,6 +790,30 @@ def test_image_five_end_to_end(m, name, cap):
             assert np.abs(_np(out.residual)[i] - o["R"]).max() <= 1e-4 * np.abs(o["D"]).max()
 
 
+def test_clean_clustered_streaming_2560_equals_single_block(m):
+    """2560^2 in a batch smaller than half the SMs: clusters of 16 blocks stream one instance and
+    give the components and residuals of one streaming block per instance, bit for bit."""
+    import torch
+    N = 2560
+    rng = np.random.default_rng(2560)
+    yy, xx = np.mgrid[-N:N, -N:N].astype(np.float32)
+    Bo = np.exp(-(xx * xx + yy * yy) / np.float32(2 * 6.0 ** 2)) + np.float32(0.03) * np.cos(xx / np.float32(5)) * \
+        np.cos(yy / np.float32(9))
+    Bo = (Bo / Bo[N, N]).astype(np.float32)
+    del yy, xx
+    Do = rng.normal(size=(2, N, N)).astype(np.float32)
+    Do[0, 100, 2000] += 30.0
+    Do[1, 1500, 7] += 20.0
+    D = torch.tensor(Do, device="cuda")
+    Bm = torch.tensor(np.stack([Bo, Bo]), device="cuda")
+    cfg = m.Config(N=N, G=4 * N, max_iter=30)
+    R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
+    cfg.clean_kernel = 1
+    R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
+    assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
+    assert float((R1 - R2).abs().max()) == 0.0
+
+
 def test_clean_5120_streaming(m):
     """CLEAN at 5120^2 (streaming residual, one block per instance): a seeded map and beam of
     that size, 40 Hogbom steps against the oracle."""
@@ -958,11 +982,11 @@ def test_autotune_grid_and_dirty_shapes(m):
         m.set_tuning(m.CALL_DIRTY, cfg, 0)
 
 
-@pytest.mark.parametrize("name", ["N640", "N1280"])
-def test_clean_clustered_streaming_equals_single_block(m, name):
-    """Images without the on-chip kernel: clusters of blocks streaming one instance give the
-    components and residuals of one block per instance (the same operations), and follow the
-    oracle."""
+@pytest.mark.parametrize("name", ["N320x2", "N640", "N1280"])
+def test_clean_extended_onchip_equals_single_block(m, name):
+    """320, 640 and 1280 pixel images: bands of 102400 pixels on chip (65536 in tensor memory,
+    36864 in shared memory; clusters of 1, 4 and 16 blocks) give the components and residuals of
+    one streaming block per instance (the same operations), and follow the oracle."""
     import torch
     wl = FIVE_CASES[name]()
     cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
