@@ -914,7 +914,7 @@ __global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, f
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       if (k < first) continue;
-      beam4[k * cstride + row * W + x] = x + k < W ? src[x + k] : 0.f;
+      __stcs(beam4 + k * cstride + row * W + x, x + k < W ? src[x + k] : 0.f);   // read by a later CLEAN
     }
   }
 }

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
   struct Load {
     const float2 *Ti;
     int y0;
-    __device__ float2 operator()(int i, int s) const { return Ti[(size_t)(y0 + s) * G + i]; }
+    __device__ float2 operator()(int i, int s) const { return __ldcs(Ti + (size_t)(y0 + s) * G + i); }   // last use
   } load{Ti, y0};
   struct Store {
     const float *gc;
