@@ -292,7 +292,8 @@ __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, L
   stages<L, S, NT, SIGN, SFAST, Layout, 0, 1, SYNC0>(sm, tw, load, store);
 }
 
-// Column strips: S columns of a G x G array per block, 32 complex values per thread per stage;
+// Column strips: S columns of a G x G array per block, 16 complex values per thread per stage
+// (32 for G = 5 * 2^m, whose strips hold 20480 values);
 // rows: S rows per block, 16 values per thread per stage (32 above G = 10240, so that a row
 // still fits in 1024 threads).  ColCfg / RowCfg (S = min(G, 16384 / G) columns,
 // min(max(1, 4096 / G), G / 2) rows; 20480 / G and 5120 / G for G = 5 * 2^m) fill the SMs when
@@ -304,6 +305,7 @@ template <int G, int S_, int E = 32>
 struct ColStrip {
   static constexpr int S = S_;
   static constexpr int NT = S * G / E;       // E values per thread per stage
+  static_assert(NT <= 1024, "a strip fits one block");
   using Layout = Interleaved<G, S>;
   static constexpr size_t smem = sizeof(float2) * Layout::size;
 };
@@ -318,7 +320,7 @@ struct RowStrip {
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 template <int G>
-using ColCfg = ColStrip<G, cmin(G, (G % 5 ? 16384 : 20480) / G)>;
+using ColCfg = ColStrip<G, cmin(G, (G % 5 ? 16384 : 20480) / G), (G % 5 ? 16 : 32)>;   // at most 1024 threads
 template <int G>
 using RowCfg = RowStrip<G, cmin(cmax(1, (G % 5 ? 4096 : 5120) / G), G / 2)>;
 template <int G>
