@@ -99,7 +99,10 @@ typedef struct muser_config {
   int32_t w_support;    /* w-kernel support in cells, odd, W..63 (used when w_planes > 0); the chirp
                            of plane wg spreads a sample over |wg| xi cells at field radius xi
                            (xi = 1/8 at the map's edge, 1/4 at the beam's) */
-  int32_t reserved[3];  /* must be zero */
+  int32_t clean_variant;/* muser_image: 0 Hogbom CLEAN (max_iter iterations), 1 Steer clean as
+                           muser_steer (max_iter major cycles, selection level steer_clip) */
+  float steer_clip;     /* Steer selection level, (0, 1] (used when clean_variant = 1) */
+  int32_t reserved[1];  /* must be zero */
 } muser_config_t;
 
 /* One gridding record per visibility, 32 bytes (written by muser_uvw).
@@ -217,11 +220,14 @@ MUSER_API int muser_restore(const float *residual, const float *beam, const int3
                   const int32_t *n_comp, int B, const muser_config_t *cfg, float *clean_img,
                   float *beam_params, void *ws, size_t ws_bytes, int32_t *status, muser_stream_t stream);
 
-/* The whole hot path for a batch (Alg. 1 without the w-term step): muser_uvw ->
+/* The whole hot path for a batch (Alg. 1; the w-term step when cfg->w_planes > 0): muser_uvw ->
  * muser_grid -> muser_dirty -> [muser_gmm if thr_mode 1] -> muser_clean -> muser_restore,
  * in chunks of cfg->batch_chunk instances.  Arguments as for muser_uvw, plus outputs
  * clean_img[B][N][N], residual[B][N][N], comp_pos/comp_flux[B][max_iter], n_comp[B],
  * thr_out[B] (threshold used, NULL = not written), beam_params[B][3] (NULL = not written).
+ * With cfg->clean_variant = 1 the CLEAN is Steer clean (as muser_steer: max_iter major cycles at
+ * selection level steer_clip; n_comp = cycles run; comp_pos/comp_flux are not written and may be
+ * NULL) and the restore adds the model map convolved with the clean beam.
  * status[B] is zeroed by the call. */
 MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
                 const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,

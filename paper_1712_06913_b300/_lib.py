@@ -32,7 +32,7 @@ class Config(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("gain", ctypes.c_float), ("gmm_bins", ctypes.c_int32),
                 ("lat_rad", ctypes.c_double), ("batch_chunk", ctypes.c_int32), ("clean_kernel", ctypes.c_int32),
                 ("w_planes", ctypes.c_int32), ("w_max", ctypes.c_float), ("w_support", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("clean_variant", ctypes.c_int32), ("steer_clip", ctypes.c_float), ("reserved", ctypes.c_int32 * 1)]
 
 
 P = ctypes.c_void_p

@@ -38,11 +38,14 @@ class Config:
     w_planes: int = 0           # w-projection planes (0: 2-D imaging)
     w_max: float = 0.0          # largest |wg| = |w| (G cell)^2 the planes cover
     w_support: int = 15         # w-kernel support (cells, odd)
+    clean_variant: int = 0      # muser_image: 0 Hogbom, 1 Steer (max_iter major cycles)
+    steer_clip: float = 0.9     # Steer selection level
 
     def c(self) -> _lib.Config:
         return _lib.Config(self.N, self.G, self.W, self.os, self.weight_mode, self.peak_mode, self.thr_mode,
                            self.max_iter, self.gain, self.gmm_bins, self.lat_rad, self.batch_chunk,
-                           self.clean_kernel, self.w_planes, self.w_max, self.w_support)
+                           self.clean_kernel, self.w_planes, self.w_max, self.w_support, self.clean_variant,
+                           self.steer_clip)
 
 
 def _p(t):

@@ -63,8 +63,10 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (cfg->gmm_bins < 2 || cfg->gmm_bins > 4096) return fail(MUSER_ERR_ARG, "gmm_bins must be in [2, 4096]");
   if (cfg->batch_chunk < 0) return fail(MUSER_ERR_ARG, "batch_chunk must be >= 0");
   if (cfg->clean_kernel != 0 && cfg->clean_kernel != 1) return fail(MUSER_ERR_ARG, "clean_kernel must be 0 or 1");
-  for (int i = 0; i < 3; i++)
-    if (cfg->reserved[i] != 0) return fail(MUSER_ERR_ARG, "reserved fields must be zero");
+  if (cfg->reserved[0] != 0) return fail(MUSER_ERR_ARG, "reserved fields must be zero");
+  if (cfg->clean_variant != 0 && cfg->clean_variant != 1) return fail(MUSER_ERR_ARG, "clean_variant must be 0 or 1");
+  if (cfg->clean_variant == 1 && !(cfg->steer_clip > 0.f && cfg->steer_clip <= 1.f))
+    return fail(MUSER_ERR_ARG, "steer_clip must be in (0, 1]");
   if (cfg->w_planes != 0) {
     if (mode != IMAGING) return fail(MUSER_ERR_UNSUPPORTED, "w-projection applies to imaging calls only");
     if (cfg->w_planes < 2 || cfg->w_planes > 1024) return fail(MUSER_ERR_ARG, "w_planes must be 0 or in [2, 1024]");
@@ -134,6 +136,10 @@ struct ImageWs {
   int32_t *bin_off, *entries;   // per-strip sample lists of the fused gridding
   float *beam[2], *mu_a[2], *mu_b[2], *params;
   int *next[2];
+  // Steer clean (clean_variant 1): model maps and transform scratch per chunk parity
+  float *model[2] = {nullptr, nullptr}, *sY[2] = {nullptr, nullptr};
+  float2 *sFB[2] = {nullptr, nullptr}, *sF[2] = {nullptr, nullptr}, *sU[2] = {nullptr, nullptr}, *tw2 = nullptr;
+  void *sstate[2] = {nullptr, nullptr};
   DirtyWs<A> d;
   void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
     const int S = dirty_strip_width(c.G);
@@ -150,6 +156,18 @@ struct ImageWs {
     }
     for (int k = 0; k < 2; k++) next[k] = (int *)a.template take<int>(1);
     params = (float *)a.template take<float>((size_t)Bc * 3);
+    if (c.clean_variant == 1) {
+      const size_t N = c.N, P = 2 * N;
+      tw2 = (float2 *)a.template take<float2>(P);
+      for (int k = 0; k < 2; k++) {
+        model[k] = (float *)a.template take<float>((size_t)Bc * N * N);
+        sY[k] = (float *)a.template take<float>((size_t)Bc * N * N);
+        sFB[k] = (float2 *)a.template take<float2>((size_t)Bc * P * (P / 2 + 1));
+        sF[k] = (float2 *)a.template take<float2>((size_t)Bc * P * P);
+        sU[k] = (float2 *)a.template take<float2>((size_t)Bc * N * P);
+        sstate[k] = (void *)a.template take<unsigned char>((size_t)Bc * steer_state_bytes());
+      }
+    }
   }
 };
 
@@ -257,7 +275,7 @@ struct SizeArena {
   }
 };
 
-bool copies(const muser_config_t &c) { return c.clean_kernel == 0 && clean_uses_copies(c.N); }
+bool copies(const muser_config_t &c) { return c.clean_kernel == 0 && c.clean_variant == 0 && clean_uses_copies(c.N); }
 
 
 int chunk_of(int B, const muser_config_t &c) { return (c.batch_chunk > 0 && c.batch_chunk < B) ? c.batch_chunk : B; }
@@ -517,8 +535,9 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   if (B == 0) return MUSER_OK;
   if (n_bl == 0) return fail(MUSER_ERR_ARG, "n_bl must be > 0");
   if (!ant_enu || !bl_pairs || !ha || !dec || !freq_hz || !cell_rad || !vis || !clean_img || !residual || !n_comp ||
-      !status || (cfg->max_iter > 0 && (!comp_pos || !comp_flux)))
+      !status || (cfg->clean_variant == 0 && cfg->max_iter > 0 && (!comp_pos || !comp_flux)))
     return fail(MUSER_ERR_ARG, "muser_image: required pointer is NULL");
+  if (cfg->clean_variant == 1 && cfg->N < 32) return fail(MUSER_ERR_UNSUPPORTED, "Steer clean needs N >= 32");
   if (!aligned(vis, 8) || !aligned(residual, 16)) return fail(MUSER_ERR_ARG, "vis / residual misaligned");
   const int Bc = chunk_of(B, *cfg);
   if ((int64_t)Bc * n_bl >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "chunk too large: lower batch_chunk");
@@ -540,6 +559,7 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   const WProj wp = make_wproj(w.wtab, *cfg);
   const int Wf = w_footprint(*cfg);
   fft::launch_twiddles(w.d.tw, G, s);
+  if (w.tw2) fft::launch_twiddles(w.tw2, 2 * N, s);
   // chunk c up to its CLEAN input, on the caller's stream
   auto prepare = [&](int c) {
     const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
@@ -565,6 +585,11 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   auto restore = [&](int c) {
     const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
     cudaStreamWaitEvent(s, pp->cleaned[k], 0);
+    if (cfg->clean_variant == 1) {
+      launch_restore_map(residual + (size_t)c0 * N * N, w.beam[k], w.model[k], n, N, clean_img + (size_t)c0 * N * N,
+                         beam_params ? beam_params + (size_t)c0 * 3 : w.params, status + c0, s);
+      return;
+    }
     launch_restore(residual + (size_t)c0 * N * N, w.beam[k], comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                    comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, n, N, cap,
                    clean_img + (size_t)c0 * N * N, beam_params ? beam_params + (size_t)c0 * 3 : w.params,
@@ -575,11 +600,17 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     const int c0 = c * Bc, n = B - c0 < Bc ? B - c0 : Bc, k = c & 1;
     cudaStream_t hs = pp->clean[k];
     cudaStreamWaitEvent(hs, pp->prepped[k], 0);
-    launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
-                  (size_t)Bc * 4 * N * N, cfg->clean_kernel == 0 ? w.next[k] : nullptr, n, N,
-                  cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap,
-                  cfg->peak_mode, comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
-                  comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);
+    if (cfg->clean_variant == 1) {          // Steer: n_comp counts major cycles, the model is a map
+      launch_steer(residual + (size_t)c0 * N * N, w.beam[k], n, N, cfg->gain, cap,
+                   cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->steer_clip, w.model[k], n_comp + c0, w.tw2,
+                   w.sFB[k], w.sF[k], w.sU[k], w.sY[k], w.sstate[k], status + c0, hs);
+    } else {
+      launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
+                    (size_t)Bc * 4 * N * N, cfg->clean_kernel == 0 ? w.next[k] : nullptr, n, N,
+                    cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap, cfg->peak_mode,
+                    comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
+                    comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);
+    }
     cudaEventRecord(pp->cleaned[k], hs);
     // the caller's stream: next chunk's preparation (set k ^ 1, free once chunk c - 1 was
     // restored, earlier on this stream), then this chunk's restore

@@ -198,6 +198,9 @@ void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float
 int hogbom_onchip_clusters(int N);   // blocks per instance of the on-chip kernel (0: not available)
 void launch_gmm(const float *dirty, int B, int N, int bins, float *mu_a, float *mu_b, int32_t *status,
                 cudaStream_t s);
+// restore from a model map [B][N][N] (Steer clean): beam fit, then clean = R + model * clean beam
+void launch_restore_map(const float *R, const float *beam, const float *model, int B, int N, float *clean,
+                        float *params, int32_t *status, cudaStream_t s);
 void launch_restore(const float *R, const float *beam, const int32_t *pos, const float *flux,
                     const int32_t *n_comp, int B, int N, int cap, float *clean, float *params, int32_t *status,
                     cudaStream_t s);

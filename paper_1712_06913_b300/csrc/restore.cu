@@ -177,7 +177,105 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
   }
 }
 
+// Restore from a model map (Steer clean): clean(q) = R(q) + sum_p model(p) CB(q - p).  Per tile,
+// the non-zero model pixels of its halo (the tile grown by the truncation radius) are compacted
+// in row-major order, a chunk of 256 at a time, and added as in k_restore.
+__global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ Rall, const float *__restrict__ model,
+                                                     int N, const float *__restrict__ params, float *__restrict__ clean) {
+  __shared__ int cp[256];
+  __shared__ float cf[256];
+  __shared__ int wcount[8];
+  __shared__ int nsurv;
+  const int inst = blockIdx.y;
+  const int tiles_x = N / 32 > 0 ? N / 32 : 1;
+  const int tw = N < 32 ? N : 32;
+  const int ty0 = (blockIdx.x / tiles_x) * tw, tx0 = (blockIdx.x % tiles_x) * tw;
+  const float *R = Rall + (size_t)inst * N * N;
+  const float *M = model + (size_t)inst * N * N;
+  float *C = clean + (size_t)inst * N * N;
+  const float sxx = params[inst * 3], sxy = params[inst * 3 + 1], syy = params[inst * 3 + 2];
+  const float det = sxx * syy - sxy * sxy;
+  const bool ok = det > 0.f;
+  const float ixx = ok ? syy / det : 0.f, ixy = ok ? -sxy / det : 0.f, iyy = ok ? sxx / det : 0.f;
+  const int rx = ok ? (int)ceilf(sqrtf(kTrunc * sxx)) : 0, ry = ok ? (int)ceilf(sqrtf(kTrunc * syy)) : 0;
+  float acc[4];
+  int py[4], px[4];
+  const int npx = tw * tw;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int p = threadIdx.x + k * 256;
+    py[k] = ty0 + (p < npx ? p / tw : 0);
+    px[k] = tx0 + (p < npx ? p % tw : 0);
+    acc[k] = 0.f;
+  }
+  const int hy0 = max(0, ty0 - ry), hy1 = min(N - 1, ty0 + tw - 1 + ry);
+  const int hx0 = max(0, tx0 - rx), hx1 = min(N - 1, tx0 + tw - 1 + rx);
+  const int hw = hx1 - hx0 + 1, nh = ok ? (hy1 - hy0 + 1) * hw : 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int h0 = 0; h0 < nh; h0 += 256) {
+    __syncthreads();
+    const int h = h0 + threadIdx.x;
+    int cpos = 0;
+    float cflux = 0.f;
+    if (h < nh) {
+      cpos = (hy0 + h / hw) * N + hx0 + h % hw;
+      cflux = M[cpos];
+    }
+    const bool hit = cflux != 0.f;
+    const unsigned mask = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) wcount[wid] = __popc(mask);
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < wid; w++) base += wcount[w];
+    if (hit) {
+      const int slot = base + __popc(mask & ((1u << lane) - 1u));
+      cp[slot] = cpos;
+      cf[slot] = cflux;
+    }
+    if (threadIdx.x == 255) {
+      int tot = 0;
+      for (int w = 0; w < 8; w++) tot += wcount[w];
+      nsurv = tot;
+    }
+    __syncthreads();
+    const int m = nsurv;
+    for (int k2 = 0; k2 < m; k2++) {
+      const int cy = cp[k2] / N, cx = cp[k2] % N;
+      const float f = cf[k2];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float dx = (float)(px[k] - cx), dy = (float)(py[k] - cy);
+        const float qq = ixx * dx * dx + 2.f * ixy * dx * dy + iyy * dy * dy;
+        if (qq <= kTrunc) acc[k] += f * expf(-0.5f * qq);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int p = threadIdx.x + k * 256;
+    if (p < npx) {
+      const size_t q = (size_t)py[k] * N + px[k];
+      C[q] = R[q] + acc[k];
+    }
+  }
+}
+
 }  // namespace
+
+void launch_restore_map(const float *R, const float *beam, const float *model, int B, int N, float *clean,
+                        float *params, int32_t *status, cudaStream_t s) {
+  if (B <= 0) return;
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    k_beam_fit<<<n, kFitThreads, 0, s>>>(beam + (size_t)i * 4 * N * N, N, params + (size_t)i * 3,
+                                         status ? status + i : nullptr);
+    note_launch();
+    const int tiles = N >= 32 ? (N / 32) * (N / 32) : 1;
+    k_restore_map<<<dim3(tiles, n), 256, 0, s>>>(R + (size_t)i * N * N, model + (size_t)i * N * N, N,
+                                                 params + (size_t)i * 3, clean + (size_t)i * N * N);
+    note_launch();
+  }
+}
 
 void launch_restore(const float *R, const float *beam, const int32_t *pos, const float *flux, const int32_t *n_comp,
                     int B, int N, int cap, float *clean, float *params, int32_t *status, cudaStream_t s) {

@@ -1017,3 +1017,29 @@ def test_bounded_wait_runs_out_and_context_stays_usable(m):
     assert time.perf_counter() - t0 < 10.0
     # the context is usable: a CLEAN right after follows the oracle
     test_clean_threshold_and_abs_mode(m)
+
+
+def test_image_with_steer_clean_end_to_end(m):
+    """muser_image with Steer clean (clean_variant 1): cycles, residual and the restored image
+    (residual + model map convolved with the fitted clean beam) against the oracle's dirty map,
+    Steer cycles and restore of the model's pixels."""
+    from oracle import restore as orest
+    wl = synth.small_workload(n_ant=10, N=64, n_frame=2, config_id=263, bmax=300.0)
+    cfg = cfg_for(m, wl, max_iter=12)
+    cfg.clean_variant, cfg.steer_clip = 1, 0.9
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    out = m.image(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    ro = oracle_records(wl)
+    for i in range(wl.n_inst):
+        ri = geometry.instance_slice(ro, i, wl.n_bl)
+        Do, Bo, _ = imaging.dirty_and_beam(imaging.grid(ri, wl.G, KER), wl.N, KER)
+        Ro, Mo, co, gap = _oracle_steer_chain(Do, Bo, cfg.gain, 0.9, 12)
+        assert gap > 3e-5, "the oracle run has a near-tie at its selection level"
+        assert int(_np(out.n_comp)[i]) == co == 12
+        peak = float(np.abs(Do).max())
+        assert np.abs(_np(out.residual)[i] - Ro).max() <= 1e-4 * peak
+        S = orest.clean_beam(Bo)
+        np.testing.assert_allclose(_np(out.beam_params)[i], S, rtol=1e-5)
+        nz = np.flatnonzero(Mo)
+        Io = orest.restore(Ro, nz, Mo.ravel()[nz], S)
+        assert np.abs(_np(out.clean)[i] - Io).max() <= 1e-4 * np.abs(Io).max()
