@@ -6,7 +6,7 @@ package loads the library and raises ImportError if it is missing: there is no
 fallback implementation.
 """
 from . import _lib
-from ._lib import (ADJOINT, CALL_CENTER, CALL_CHI2, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GMM, CALL_GRID, CALL_IMAGE,
+from ._lib import (ADJOINT, CALL_CENTER, CALL_CHI2, CALL_GRAD, CALL_STEER, CALL_CLEAN, CALL_DEGRID, CALL_DIRTY, CALL_GMM, CALL_GRID, CALL_IMAGE,
                    CALL_RESTORE, FORWARD, MuserError, ST_ALL_FLAGGED, ST_BEAM_FIT, ST_DROPPED, ST_GMM_DEGENERATE,
                    ST_ITER_CAP, ST_NO_DISK, ST_NONFINITE, ST_TIMEOUT)
 from .api import (Config, DegridPlan, Imager, ImageResult, MixedImager, Source, Workspace, autotune, center, chi2, clean,

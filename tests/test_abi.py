@@ -26,7 +26,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_record_and_config_layout():
     import paper_1712_06913_b300 as m
-    # 10 int32/float fields, a double at offset 40, batch_chunk, clean_kernel and 6 reserved int32
+    # 10 int32/float fields, a double at offset 40, batch_chunk, clean_kernel, w-projection (3),
+    # the CLEAN variant (2) and 1 reserved int32
     assert ctypes.sizeof(m._lib.Config) == 80
     assert m._lib.Config.lat_rad.offset == 40 and m._lib.Config.batch_chunk.offset == 48
     assert m.api.RECORD_FLOATS * 4 == 32
@@ -45,3 +46,57 @@ def test_host_pixel_size_and_workspace_queries():
         m.workspace_size(m.CALL_DIRTY, 1, 0, m.Config(N=256, G=512))       # imaging needs G = 4N
     with pytest.raises(m.MuserError):
         m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=256, G=1024))    # degridding needs G = 2N
+
+
+def test_config_validation_of_the_widened_calls():
+    """Image sides, w-projection and CLEAN-variant fields are checked on the host (no GPU)."""
+    import paper_1712_06913_b300 as m
+    ok = [m.Config(N=n, G=4 * n) for n in (16, 1024, 160, 320, 1280, 2560, 5120)]
+    for c in ok:
+        assert m.workspace_size(m.CALL_DIRTY, 1, 0, c) > 0
+    bad = [m.Config(N=n, G=4 * n) for n in (100, 80, 2048, 10240, 96)]
+    for c in bad:
+        with pytest.raises(m.MuserError):
+            m.workspace_size(m.CALL_DIRTY, 1, 0, c)
+    with pytest.raises(m.MuserError):                                   # 5 * 2^a sides: imaging only
+        m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=320, G=640))
+    # w-projection
+    assert m.workspace_size(m.CALL_GRID, 2, 100, m.Config(N=64, G=256, w_planes=16, w_max=5.0, w_support=15)) > \
+        m.workspace_size(m.CALL_GRID, 2, 100, m.Config(N=64, G=256))
+    for kw in (dict(w_planes=1, w_max=5.0), dict(w_planes=16, w_max=0.0), dict(w_planes=16, w_max=5.0, w_support=14),
+               dict(w_planes=16, w_max=5.0, w_support=5), dict(w_planes=16, w_max=5.0, w_support=65)):
+        with pytest.raises(m.MuserError):
+            m.workspace_size(m.CALL_GRID, 1, 10, m.Config(N=64, G=256, **kw))
+    with pytest.raises(m.MuserError):                                   # no w-projection in the operator
+        m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=64, G=128, w_planes=8, w_max=1.0))
+    # CLEAN variant
+    assert m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256, clean_variant=1)) > \
+        m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256))
+    for kw in (dict(clean_variant=2), dict(clean_variant=1, steer_clip=0.0), dict(clean_variant=1, steer_clip=1.5)):
+        with pytest.raises(m.MuserError):
+            m.workspace_size(m.CALL_IMAGE, 1, 10, m.Config(N=64, G=256, **kw))
+    # gradient step workspace holds the operator's
+    c = m.Config(N=64, G=128)
+    assert m.workspace_size(m.CALL_GRAD, 1, 500, c) > m.workspace_size(m.CALL_DEGRID, 1, 500, c)
+
+
+def test_call_argument_errors_without_a_gpu():
+    """Argument errors are returned before any device work (the library loads without a GPU)."""
+    import paper_1712_06913_b300 as m
+    lib = m._lib.load()
+    c = m.Config(N=64, G=256).c()
+    null = ctypes.c_void_p(0)
+    # muser_steer: clip outside (0, 1]
+    rc = lib.muser_steer(null, null, 1, ctypes.byref(c), null, 1.5, null, null, null, 0, null, null)
+    assert rc != 0 and b"clip" in lib.muser_last_error()
+    # muser_grad_step: bad flags, missing pointers
+    cd = m.Config(N=64, G=128).c()
+    assert lib.muser_grad_step(3, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
+    assert lib.muser_grad_step(0, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
+    # muser_set_tuning: band rows must divide G; column variant 0 or 1
+    assert lib.muser_set_tuning(m.CALL_GRID, ctypes.byref(c), 3) != 0
+    assert lib.muser_set_tuning(m.CALL_DIRTY, ctypes.byref(c), 2) != 0
+    assert lib.muser_set_tuning(m.CALL_CLEAN, ctypes.byref(c), 0) != 0
+    # muser_selftest_wait: bound above about one second
+    st = ctypes.c_void_p(16)
+    assert lib.muser_selftest_wait(1 << 40, st, null) != 0
