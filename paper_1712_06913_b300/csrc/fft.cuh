@@ -226,7 +226,7 @@ struct Plan {
 // One stage and (recursively) the following ones.  SFAST: work items enumerate the
 // sequence index fastest (column strips, coalesced global rows) or the butterfly index
 // fastest (rows).  NT threads; a stage whose S * L / R items are not a multiple of NT leaves
-// the last round's surplus threads idle (the radix 5 Q stages).
+// the surplus threads of the last sweep over the items idle (the radix 5 Q stages).
 template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, bool SYNC0, class Load, class Store>
 __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
   constexpr int R = Plan<L>::template radix<STAGE>();
