@@ -597,6 +597,7 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     torch.cuda.empty_cache()
     res["large_images"] = large_images(m, stream)
     res["w_projection"] = wproj_leg(m, stream)
+    res["steer_image"] = steer_image_leg(m, wl, cell, cfg, stream)
     res["mixed_stream"] = mixed_stream(m, stream)
     return res
 
@@ -686,6 +687,29 @@ def mixed_stream(m, stream, n_total=10000, n_plain=8):
            "batched_images_per_s": n_total / t_batched, "plain_images_per_s": n_total / t_plain,
            "plain_sample": f"{n_plain} instances per class, one muser_image call each"}
     del mix
+    torch.cuda.empty_cache()
+    return res
+
+
+def steer_image_leg(m, wl, cell, cfg, stream, n=296, cycles=20):
+    """Alg. 1 with the paper's production clean: one chunk of the MUSER-II batch through
+    muser_image with Steer clean (clean_variant 1, `cycles` major cycles at clip 0.9; restore
+    from the model map): images/s."""
+    import torch
+    chans = list(range(min(n, wl.n_chan)))
+    c = m.Config(**{**cfg.__dict__, "batch_chunk": 0, "max_iter": cycles, "clean_variant": 1, "steer_clip": 0.9})
+    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha[:1], wl.dec[:1], wl.freq[chans], cell[chans], wl.vis[:1, chans], c,
+                  flags=wl.flags[:1, chans])
+    im.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = im.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res = {"instances": len(chans), "major_cycles": cycles, "images_per_s": len(chans) / (e0.elapsed_time(e1) / 1e3),
+           "cycles_run_mean": float(out.n_comp.float().mean())}
+    del im, out
     torch.cuda.empty_cache()
     return res
 
