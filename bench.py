@@ -186,7 +186,7 @@ def main():
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
     ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "large_clean", "wproj",
-                                       "mixed"],
+                                       "mixed", "center"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -422,7 +422,8 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     large: the large-image leg of the benchmark at one image side (`size`).
     wproj: the w-projection leg (MUSER-I band, about `n_inst` instances) with and without it.
     mixed: the mixed stream of `n_inst` (default 10,000) MUSER-I / MUSER-II instances.
-    large_clean: streaming CLEAN (`iters` iterations) of `n_inst` (default 16) instances at side `size`.
+    large_clean: CLEAN (`iters` iterations) of `n_inst` (default 16) instances at side `size`.
+    center: disk centring of `n_inst` (default 32) MUSER-II dirty maps.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -434,6 +435,26 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         return
     if case == "wproj":
         print(json.dumps({"case": case, **wproj_leg(m, torch.cuda.current_stream(), n=n_inst or 296)}))
+        return
+    if case == "center":
+        # disk centring (muser_center) of `n_inst` (default 32) MUSER-II dirty maps
+        wlc = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst or 32)))
+        cfgc = m.Config(N=wlc.N, G=wlc.G, W=wlc.W, os=wlc.OS, max_iter=0, gain=wlc.gain, lat_rad=wlc.lat)
+        cellc = m.pixel_size(wlc.freq, wlc.bmax, wlc.N, wlc.fov_min)
+        recc, _, stc = m.uvw(wlc.ant_enu, wlc.pairs, wlc.ha, wlc.dec, wlc.freq, cellc, wlc.vis, cfgc, flags=wlc.flags)
+        offc = torch.arange(wlc.n_inst + 1, dtype=torch.int64, device="cuda") * wlc.n_bl
+        Zc, s2 = m.grid(recc, offc, cfgc, status=stc)
+        Dc, _, s2 = m.dirty(Zc, cfgc, status=s2)
+        del Zc
+        mu_a, mu_b, _ = m.gmm(Dc, cfgc)
+        cells = torch.tensor(cellc, dtype=torch.float64, device="cuda")
+        m.center(Dc, mu_a, mu_b, cells, cfgc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m.center(Dc, mu_a, mu_b, cells, cfgc)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "instances": wlc.n_inst, "center_ms": e0.elapsed_time(e1)}))
         return
     if case == "large_clean":
         # streaming CLEAN of `n_inst` instances at a large image side (dirty maps built first)

@@ -7,13 +7,17 @@
 //   Cc(s) = sum_p M(p) S(p - s),  |s_x|, |s_y| <= N/4
 // through zero-padded FFTs of side P = 2N (no wrap-around for these shifts): one forward
 // transform of Z = M + i S gives both spectra (two-real trick: FM = (F(k) + F(-k)*) / 2,
-// FS = (F(k) - F(-k)*) / 2i), H = FM FS*, and Cc(s) = Re IFFT(H)(s) / P^2.
+// FS = (F(k) - F(-k)*) / 2i), H = FM FS*, and Cc(s) = Re IFFT(H)(s) / P^2.  Cc is real, so
+// H(-k) = H(k)* and only the half spectrum k_x in [0, P/2] is formed and transformed back.
 //   pass 1 (columns of Z; only the N columns and rows where Z can be non-zero are read),
-//   pass 2 (rows; columns >= N of pass 1 are known zeros), pairing H(k), H(-k) in place,
-//   pass 3 (inverse columns, only the N/2 + 1 output rows of the shift window),
-//   pass 4 (inverse rows of those, only the N/2 + 1 columns of the window) -> Cc.
-// Then one block per instance takes the best shift (largest Cc; ties to the smallest |s|,
-// then the lowest row-major index), refines each axis with a 3-point parabola (offset
+//   pass 2 (rows k_y and P - k_y in one block, columns >= N of pass 1 are known zeros; the
+//           block pairs F(k) with F(-k) in shared memory and writes H for k_x <= P/2),
+//   pass 3 (inverse columns k_x <= P/2, only the N/2 + 1 output rows of the shift window),
+//   pass 4 (inverse rows of those, k_x > P/2 as the conjugate of column P - k_x; only the
+//           N/2 + 1 columns of the window) -> Cc.
+// Pass 4 also keeps each block's best shift (largest Cc; ties to the smallest |s|, then the
+// lowest row-major index); one block per instance then takes the best of those and
+// refines each axis with a 3-point parabola (offset
 // clipped to +-1/2, none when the curvature is not negative) and returns
 // (dl, dm) = (s_x, s_y) * cell.
 #include "fft.cuh"
@@ -63,32 +67,6 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_ctr_cols(const float *__restr
   if (__syncthreads_or(load.any) && threadIdx.x == 0) atomicOr(masked + inst, 1);
 }
 
-// pass 2: rows of F in place (columns >= N are zero after pass 1 and are not read).
-template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_rows(const float2 *__restrict__ tw, float2 *__restrict__ F) {
-  using C = RowCfg<P>;
-  constexpr int N = P / 2, S = C::S, NT = C::NT;
-  extern __shared__ float4 smem4[];
-  float2 *sm = reinterpret_cast<float2 *>(smem4);
-  const int inst = blockIdx.y, y0 = blockIdx.x * S;
-  float2 *Fi = F + (size_t)inst * P * P;
-  struct Load {
-    const float2 *Fi;
-    int y0;
-    __device__ float2 operator()(int i, int s) const {
-      return i < N ? Fi[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
-    }
-  } load{Fi, y0};
-  struct Store {
-    float2 *Fi;
-    int y0;
-    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)(y0 + s) * P + o] = v; }
-  } store{Fi, y0};
-  // every load of the block happens before its first store (the stages exchange through
-  // shared memory), so the rows can be transformed in place
-  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
-}
-
 // H = FM FS* from a = F(k), b = F(-k):  FM = (a + b*) / 2,  FS = (a - b*) / 2i.
 __device__ __forceinline__ float2 pair_product(float2 a, float2 b) {
   const float2 fm = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
@@ -96,34 +74,53 @@ __device__ __forceinline__ float2 pair_product(float2 a, float2 b) {
   return make_float2(fm.x * fs.x + fm.y * fs.y, fm.y * fs.x - fm.x * fs.y);
 }
 
-// H(k) and H(-k) = H(k)* in place, one thread per pair: rows 1 .. P/2 - 1 (their partners
-// are rows P - 1 .. P/2 + 1).
+// Row strips of pass 2: pairs of rows (q, P - q), at least one pair per block.
 template <int P>
-__global__ void k_ctr_pair(float2 *__restrict__ F) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= (int64_t)(P / 2 - 1) * P) return;
-  float2 *Fi = F + (size_t)blockIdx.y * P * P;
-  const int ky = 1 + (int)(j / P), kx = (int)(j % P);
-  const int nky = P - ky, nkx = (P - kx) % P;
-  const float2 h = pair_product(Fi[(size_t)ky * P + kx], Fi[(size_t)nky * P + nkx]);
-  Fi[(size_t)ky * P + kx] = h;
-  Fi[(size_t)nky * P + nkx] = make_float2(h.x, -h.y);
-}
+using PairRowCfg = fft::RowStrip<P, fft::cmax(2, RowCfg<P>::S)>;
 
-// rows 0 and P/2 pair within themselves (kx with P - kx; kx = 0 and P/2 with themselves).
+// pass 2: slot 2j holds row q = blockIdx.x * S/2 + j (q in [0, P/2]) and slot 2j + 1 row
+// (P - q) mod P; rows 0 and P/2 are their own partners.  The final FFT stage stores into the
+// block's shared memory (its loads are complete by then), then H(k_x, q) and H(k_x, P - q),
+// k_x in [0, P/2], go to F in place (every row a block writes is one it alone read).
 template <int P>
-__global__ void k_ctr_pair_rows(float2 *__restrict__ F) {
-  float2 *Fi = F + (size_t)blockIdx.y * P * P;
-  const int row = blockIdx.x * (P / 2);
-  for (int kx = threadIdx.x; kx <= P / 2; kx += blockDim.x) {
+__global__ void __launch_bounds__(PairRowCfg<P>::NT) k_ctr_rows_pair(const float2 *__restrict__ tw,
+                                                                    float2 *__restrict__ F) {
+  using C = PairRowCfg<P>;
+  using L = typename C::Layout;
+  constexpr int N = P / 2, S = C::S, NT = C::NT, NP = S / 2;
+  static_assert(S % 2 == 0, "row pairs");
+  extern __shared__ float4 smem4[];
+  float2 *sm = reinterpret_cast<float2 *>(smem4);
+  const int inst = blockIdx.y, q0 = blockIdx.x * NP;
+  float2 *Fi = F + (size_t)inst * P * P;
+  struct Load {
+    const float2 *Fi;
+    int q0;
+    __device__ float2 operator()(int i, int s) const {
+      const int q = q0 + (s >> 1);
+      if (i >= N || q > P / 2) return make_float2(0.f, 0.f);
+      const int row = (s & 1) ? (P - q) % P : q;
+      return Fi[(size_t)row * P + i];
+    }
+  } load{Fi, q0};
+  struct Store {
+    float2 *sm;
+    __device__ void operator()(int o, int s, float2 v) const { sm[L::at(o, s)] = v; }
+  } store{sm};
+  fft::run<P, S, NT, -1, false, L>(sm, tw, load, store);
+  __syncthreads();
+  for (int it = threadIdx.x; it < NP * (P / 2 + 1); it += NT) {
+    const int j = it / (P / 2 + 1), kx = it % (P / 2 + 1), q = q0 + j;
+    if (q > P / 2) continue;
     const int nkx = (P - kx) % P;
-    const float2 h = pair_product(Fi[(size_t)row * P + kx], Fi[(size_t)row * P + nkx]);
-    Fi[(size_t)row * P + kx] = h;
-    if (nkx != kx) Fi[(size_t)row * P + nkx] = make_float2(h.x, -h.y);
+    Fi[(size_t)q * P + kx] = pair_product(sm[L::at(kx, 2 * j)], sm[L::at(nkx, 2 * j + 1)]);
+    if (q != 0 && q != P / 2)
+      Fi[(size_t)(P - q) * P + kx] = pair_product(sm[L::at(kx, 2 * j + 1)], sm[L::at(nkx, 2 * j)]);
   }
 }
 
-// pass 3: inverse columns; output rows s_y in [-N/4, N/4] (mod P) -> U[s_y + N/4][P].
+// pass 3: inverse columns k_x in [0, P/2]; output rows s_y in [-N/4, N/4] (mod P) ->
+// U[s_y + N/4][k_x] (row stride P).
 template <int P>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_ctr_icols(const float2 *__restrict__ F, const float2 *__restrict__ tw,
                                                             float2 *__restrict__ U) {
@@ -137,23 +134,57 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_ctr_icols(const float2 *__res
   struct Load {
     const float2 *Fi;
     int x0;
-    __device__ float2 operator()(int i, int s) const { return Fi[(size_t)i * P + x0 + s]; }
+    __device__ float2 operator()(int i, int s) const {
+      return x0 + s <= P / 2 ? Fi[(size_t)i * P + x0 + s] : make_float2(0.f, 0.f);
+    }
   } load{Fi, x0};
   struct Store {
     float2 *Ui;
     int x0;
     __device__ void operator()(int o, int s, float2 v) const {
       const int sy = o <= SM ? o : o - P;
-      if (sy >= -SM && sy <= SM) Ui[(size_t)(sy + SM) * P + x0 + s] = v;
+      if (sy >= -SM && sy <= SM && x0 + s <= P / 2) Ui[(size_t)(sy + SM) * P + x0 + s] = v;
     }
   } store{Ui, x0};
   fft::run<P, S, NT, +1, true, typename C::Layout>(sm, tw, load, store);
 }
 
-// pass 4: inverse rows of U; output columns s_x in [-N/4, N/4] -> Cc[s_y + N/4][s_x + N/4].
+// Shift candidates are ordered by (value, -|s|^2, -row-major index): a total order, so any
+// partition of the window reduces to the same best shift.
+struct Best {
+  float v;
+  int d2, idx;
+};
+__device__ __forceinline__ bool better(const Best &a, const Best &b) {
+  return a.v > b.v || (a.v == b.v && (a.d2 < b.d2 || (a.d2 == b.d2 && a.idx < b.idx)));
+}
+__device__ __forceinline__ Best warp_best(Best b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Best c{__shfl_xor_sync(0xffffffffu, b.v, o), __shfl_xor_sync(0xffffffffu, b.d2, o),
+           __shfl_xor_sync(0xffffffffu, b.idx, o)};
+    if (better(c, b)) b = c;
+  }
+  return b;
+}
+// best of a block (blockDim.x a multiple of 32); the result is valid in thread 0
+__device__ Best block_best(Best b) {
+  __shared__ Best red[32];
+  b = warp_best(b);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    b = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : Best{-CUDART_INF_F, 0x7fffffff, 0x7fffffff};
+    b = warp_best(b);
+  }
+  return b;
+}
+
+// pass 4: inverse rows of U (U(k_x) = U(P - k_x)* for k_x > P/2, H being Hermitian); output
+// columns s_x in [-N/4, N/4] -> Cc[s_y + N/4][s_x + N/4].
 template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_irows(const float2 *__restrict__ U, const float2 *__restrict__ tw,
-                                                            float *__restrict__ Cc) {
+                                                            float *__restrict__ Cc, float2 *__restrict__ F) {
   using C = RowCfg<P>;
   constexpr int N = P / 2, SM = N / 4, W = 2 * SM + 1, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
@@ -165,28 +196,34 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_irows(const float2 *__res
     const float2 *Ui;
     int y0;
     __device__ float2 operator()(int i, int s) const {
-      return y0 + s < W ? Ui[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
+      if (y0 + s >= W) return make_float2(0.f, 0.f);
+      if (i <= P / 2) return Ui[(size_t)(y0 + s) * P + i];
+      const float2 u = Ui[(size_t)(y0 + s) * P + (P - i)];
+      return make_float2(u.x, -u.y);
     }
   } load{Ui, y0};
   struct Store {
     float *Ci;
     int y0;
-    __device__ void operator()(int o, int s, float2 v) const {
-      const int sx = o <= SM ? o : o - P;
-      if (y0 + s < W && sx >= -SM && sx <= SM) Ci[(size_t)(y0 + s) * W + (sx + SM)] = v.x * (1.f / ((float)P * (float)P));
+    Best b;
+    __device__ void operator()(int o, int s, float2 v) {
+      const int sx = o <= SM ? o : o - P, row = y0 + s;
+      if (row < W && sx >= -SM && sx <= SM) {
+        const float c = v.x * (1.f / ((float)P * (float)P));
+        const int idx = row * W + (sx + SM), sy = row - SM;
+        Ci[idx] = c;
+        const Best cand{c, sx * sx + sy * sy, idx};
+        if (better(cand, b)) b = cand;
+      }
     }
-  } store{Ci, y0};
+  } store{Ci, y0, Best{-CUDART_INF_F, 0x7fffffff, 0x7fffffff}};
   fft::run<P, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+  // the best shift among this block's rows, kept at the start of the instance's spectrum
+  // buffer (free once pass 3 has read it)
+  const Best b = block_best(store.b);
+  if (threadIdx.x == 0) reinterpret_cast<Best *>(F + (size_t)inst * P * P)[blockIdx.x] = b;
 }
 
-// best shift of one instance (block of 1024 threads): (value, -|s|^2, -index) maximised.
-struct Best {
-  float v;
-  int d2, idx;
-};
-__device__ __forceinline__ bool better(const Best &a, const Best &b) {
-  return a.v > b.v || (a.v == b.v && (a.d2 < b.d2 || (a.d2 == b.d2 && a.idx < b.idx)));
-}
 
 __device__ float parabola(float cm, float c0, float cp) {
   const float den = cm - 2.f * c0 + cp;
@@ -195,51 +232,34 @@ __device__ float parabola(float cm, float c0, float cp) {
   return d < -0.5f ? -0.5f : (d > 0.5f ? 0.5f : d);
 }
 
-__global__ void __launch_bounds__(1024) k_ctr_pick(const float *__restrict__ Cc, int W, const double *__restrict__ cell,
-                                                   const int32_t *__restrict__ masked, double *__restrict__ dlm,
-                                                   float *__restrict__ shift, int32_t *__restrict__ status) {
-  __shared__ Best red[32];
+// the best shift of each instance from pass 4's per-block candidates, refined by parabolas
+__global__ void __launch_bounds__(256) k_ctr_pick(const float *__restrict__ Cc, int W, int nblk, int64_t part_stride,
+                                                  const float2 *__restrict__ F, const double *__restrict__ cell,
+                                                  const int32_t *__restrict__ masked, double *__restrict__ dlm,
+                                                  float *__restrict__ shift, int32_t *__restrict__ status) {
   const int inst = blockIdx.x, SM = W / 2;
   const float *Ci = Cc + (size_t)inst * W * W;
+  const Best *part = reinterpret_cast<const Best *>(F + (size_t)inst * part_stride);
   Best b{-CUDART_INF_F, 0x7fffffff, 0x7fffffff};
-  for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
-    const int sy = i / W - SM, sx = i % W - SM;
-    const Best c{Ci[i], sx * sx + sy * sy, i};
-    if (better(c, b)) b = c;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    Best c{__shfl_xor_sync(0xffffffffu, b.v, o), __shfl_xor_sync(0xffffffffu, b.d2, o),
-           __shfl_xor_sync(0xffffffffu, b.idx, o)};
-    if (better(c, b)) b = c;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = b;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    b = red[threadIdx.x];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      Best c{__shfl_xor_sync(0xffffffffu, b.v, o), __shfl_xor_sync(0xffffffffu, b.d2, o),
-             __shfl_xor_sync(0xffffffffu, b.idx, o)};
-      if (better(c, b)) b = c;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+    if (better(part[i], b)) b = part[i];
+  b = block_best(b);
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    if (masked[inst] && b.idx < W * W) {
+      const int iy = b.idx / W, ix = b.idx % W;
+      const float dx = (ix > 0 && ix < W - 1) ? parabola(Ci[b.idx - 1], Ci[b.idx], Ci[b.idx + 1]) : 0.f;
+      const float dy = (iy > 0 && iy < W - 1) ? parabola(Ci[b.idx - W], Ci[b.idx], Ci[b.idx + W]) : 0.f;
+      sx = (double)(ix - SM) + dx;
+      sy = (double)(iy - SM) + dy;
+    } else if (status) {
+      atomicOr(status + inst, MUSER_ST_NO_DISK);
     }
-    if (threadIdx.x == 0) {
-      double sx = 0.0, sy = 0.0;
-      if (masked[inst] && b.idx < W * W) {
-        const int iy = b.idx / W, ix = b.idx % W;
-        const float dx = (ix > 0 && ix < W - 1) ? parabola(Ci[b.idx - 1], Ci[b.idx], Ci[b.idx + 1]) : 0.f;
-        const float dy = (iy > 0 && iy < W - 1) ? parabola(Ci[b.idx - W], Ci[b.idx], Ci[b.idx + W]) : 0.f;
-        sx = (double)(ix - SM) + dx;
-        sy = (double)(iy - SM) + dy;
-      } else if (status) {
-        atomicOr(status + inst, MUSER_ST_NO_DISK);
-      }
-      dlm[2 * inst] = sx * cell[inst];
-      dlm[2 * inst + 1] = sy * cell[inst];
-      if (shift) {
-        shift[2 * inst] = (float)sx;
-        shift[2 * inst + 1] = (float)sy;
-      }
+    dlm[2 * inst] = sx * cell[inst];
+    dlm[2 * inst + 1] = sy * cell[inst];
+    if (shift) {
+      shift[2 * inst] = (float)sx;
+      shift[2 * inst + 1] = (float)sy;
     }
   }
 }
@@ -262,12 +282,13 @@ void center_P(const float *R, const float *mu_a, const float *mu_b, const double
               int32_t *status, cudaStream_t s) {
   using CC = ColCfg<P>;
   using RC = RowCfg<P>;
-  constexpr int N = P / 2, W = N / 2 + 1;
+  using PC = PairRowCfg<P>;
+  constexpr int N = P / 2, W = N / 2 + 1, NP = PC::S / 2, H = P / 2 + 1;
   k_ctr_params<<<(B + 255) / 256, 256, 0, s>>>(mu_a, mu_b, cell, B, thr, r2, masked);
   note_launch();
   cudaFuncSetAttribute(k_ctr_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_ctr_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  cudaFuncSetAttribute(k_ctr_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
+  cudaFuncSetAttribute(k_ctr_rows_pair<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PC::smem);
   cudaFuncSetAttribute(k_ctr_irows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
@@ -275,19 +296,15 @@ void center_P(const float *R, const float *mu_a, const float *mu_b, const double
     k_ctr_cols<P><<<dim3((N + CC::S - 1) / CC::S, n), CC::NT, CC::smem, s>>>(R + (size_t)i * N * N, thr + i, r2 + i, tw, Fi,
                                                                 masked + i);
     note_launch();
-    k_ctr_rows<P><<<dim3(P / RC::S, n), RC::NT, RC::smem, s>>>(tw, Fi);
+    k_ctr_rows_pair<P><<<dim3((H + NP - 1) / NP, n), PC::NT, PC::smem, s>>>(tw, Fi);
     note_launch();
-    k_ctr_pair<P><<<dim3((unsigned)(((int64_t)(P / 2 - 1) * P + 255) / 256), n), 256, 0, s>>>(Fi);
-    note_launch();
-    k_ctr_pair_rows<P><<<dim3(2, n), 256, 0, s>>>(Fi);
-    note_launch();
-    k_ctr_icols<P><<<dim3(P / CC::S, n), CC::NT, CC::smem, s>>>(Fi, tw, U + (size_t)i * W * P);
+    k_ctr_icols<P><<<dim3((H + CC::S - 1) / CC::S, n), CC::NT, CC::smem, s>>>(Fi, tw, U + (size_t)i * W * P);
     note_launch();
     k_ctr_irows<P><<<dim3((W + RC::S - 1) / RC::S, n), RC::NT, RC::smem, s>>>(U + (size_t)i * W * P, tw,
-                                                                        Cc + (size_t)i * W * W);
+                                                                        Cc + (size_t)i * W * W, Fi);
     note_launch();
   }
-  k_ctr_pick<<<B, 1024, 0, s>>>(Cc, W, cell, masked, dlm, shift, status);
+  k_ctr_pick<<<B, 256, 0, s>>>(Cc, W, (W + RC::S - 1) / RC::S, (int64_t)P * P, F, cell, masked, dlm, shift, status);
   note_launch();
 }
 

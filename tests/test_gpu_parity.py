@@ -503,7 +503,8 @@ def _centring_case(off_px, N=128, seed=110):
     return wl, cell
 
 
-@pytest.mark.parametrize("off_px,N", [((5.0, -3.0), 128), ((-11.4, 7.6), 128), ((7.3, 4.2), 160)])
+@pytest.mark.parametrize("off_px,N", [((5.0, -3.0), 128), ((-11.4, 7.6), 128), ((7.3, 4.2), 160),
+                                      ((-9.6, 12.2), 256), ((3.3, -6.8), 320)])
 def test_center_correlation_and_shift_vs_oracle(m, off_px, N):
     """muser_center on the oracle's pre-cleaned residual: the disk correlation over all
     shifts within 1e-5 of its peak, the best shift and its parabolic refinement equal."""
@@ -535,6 +536,36 @@ def test_center_correlation_and_shift_vs_oracle(m, off_px, N):
     assert abs(gs[0] - sx) <= 1e-3 and abs(gs[1] - sy) <= 1e-3, (gs, sx, sy)
     np.testing.assert_allclose(_np(dlm)[0], [gs[0] * cell, gs[1] * cell], rtol=1e-6)
     assert int(_np(st)[0]) & m.ST_NO_DISK == 0
+
+
+@pytest.mark.parametrize("N,off", [(1024, (17.0, -23.0)), (1280, (-31.0, 8.0))])
+def test_center_synthetic_disk_large(m, N, off):
+    """Sides whose row pass holds one row pair per block (P = 2N = 2048, 2560): a disk of
+    radius 0.3 N shifted by whole pixels plus noise and bright spots, against the oracle's
+    correlation over all shifts and its best shift."""
+    import torch
+    from oracle import centering
+    rng = np.random.default_rng(N)
+    r = 0.3 * N + 0.37
+    cell = 16 * np.pi / 180 / 60 / r
+    y, x = np.mgrid[0:N, 0:N]
+    R = np.where((x - N // 2 - off[0]) ** 2 + (y - N // 2 - off[1]) ** 2 <= r * r, 1.0, 0.0)
+    R += 0.2 * rng.standard_normal((N, N))
+    R[rng.integers(0, N, 40), rng.integers(0, N, 40)] += 3.0
+    R32 = R.astype(np.float32)
+    thr = np.float32(0.5) * (np.float32(0.0) + np.float32(1.0))
+    M = np.where(R32 > thr, R32, np.float32(0)).astype(np.float64)
+    S = centering.disk_model(N, r)
+    Cc = centering.correlation(M, S, N // 4)
+    cfg = m.Config(N=N, G=4 * N)
+    dlm, shift, corr, st = m.center(torch.tensor(R32[None], device="cuda"), torch.zeros(1, device="cuda"),
+                                    torch.ones(1, device="cuda"), np.array([cell]), cfg, want_corr=True)
+    Cg = _np(corr)[0]
+    assert np.abs(Cg - Cc).max() <= 1e-5 * np.abs(Cc).max()
+    sx, sy = centering.best_shift(Cc, N // 4)
+    gs = _np(shift)[0]
+    assert abs(gs[0] - sx) <= 1e-3 and abs(gs[1] - sy) <= 1e-3, (gs, sx, sy)
+    assert abs(sx - off[0]) <= 0.5 and abs(sy - off[1]) <= 0.5
 
 
 def test_image_centred_end_to_end(m):
