@@ -13,8 +13,8 @@
 //   pass 2 (rows k_y and P - k_y in one block, columns >= N of pass 1 are known zeros; the
 //           block pairs F(k) with F(-k) in shared memory and writes H for k_x <= P/2),
 //   pass 3 (inverse columns k_x <= P/2, only the N/2 + 1 output rows of the shift window),
-//   pass 4 (inverse rows of those, k_x > P/2 as the conjugate of column P - k_x; only the
-//           N/2 + 1 columns of the window) -> Cc.
+//   pass 4 (inverse rows of those, two real output rows per transform, k_x > P/2 as the
+//           conjugate of column P - k_x; only the N/2 + 1 columns of the window) -> Cc.
 // Pass 4 also keeps each block's best shift (largest Cc; ties to the smallest |s|, then the
 // lowest row-major index); one block per instance then takes the best of those and
 // refines each axis with a 3-point parabola (offset
@@ -181,7 +181,9 @@ __device__ Best block_best(Best b) {
 }
 
 // pass 4: inverse rows of U (U(k_x) = U(P - k_x)* for k_x > P/2, H being Hermitian); output
-// columns s_x in [-N/4, N/4] -> Cc[s_y + N/4][s_x + N/4].
+// columns s_x in [-N/4, N/4] -> Cc[s_y + N/4][s_x + N/4].  Every output row is real, so slot s
+// transforms two window rows at once (row a + i row b; the real and imaginary parts of the
+// result are the two rows).
 template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_irows(const float2 *__restrict__ U, const float2 *__restrict__ tw,
                                                             float *__restrict__ Cc, float2 *__restrict__ F) {
@@ -189,31 +191,39 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_ctr_irows(const float2 *__res
   constexpr int N = P / 2, SM = N / 4, W = 2 * SM + 1, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
-  const int inst = blockIdx.y, y0 = blockIdx.x * S;
+  const int inst = blockIdx.y, y0 = blockIdx.x * 2 * S;
   const float2 *Ui = U + (size_t)inst * W * P;
   float *Ci = Cc + (size_t)inst * W * W;
   struct Load {
     const float2 *Ui;
     int y0;
+    __device__ float2 u(int row, int i) const {
+      if (row >= W) return make_float2(0.f, 0.f);
+      if (i <= P / 2) return Ui[(size_t)row * P + i];
+      const float2 v = Ui[(size_t)row * P + (P - i)];
+      return make_float2(v.x, -v.y);
+    }
     __device__ float2 operator()(int i, int s) const {
-      if (y0 + s >= W) return make_float2(0.f, 0.f);
-      if (i <= P / 2) return Ui[(size_t)(y0 + s) * P + i];
-      const float2 u = Ui[(size_t)(y0 + s) * P + (P - i)];
-      return make_float2(u.x, -u.y);
+      const float2 a = u(y0 + 2 * s, i), b = u(y0 + 2 * s + 1, i);
+      return make_float2(a.x - b.y, a.y + b.x);
     }
   } load{Ui, y0};
   struct Store {
     float *Ci;
     int y0;
     Best b;
+    __device__ void put(int row, int sx, float c) {
+      const int idx = row * W + (sx + SM), sy = row - SM;
+      Ci[idx] = c;
+      const Best cand{c, sx * sx + sy * sy, idx};
+      if (better(cand, b)) b = cand;
+    }
     __device__ void operator()(int o, int s, float2 v) {
-      const int sx = o <= SM ? o : o - P, row = y0 + s;
+      const int sx = o <= SM ? o : o - P, row = y0 + 2 * s;
       if (row < W && sx >= -SM && sx <= SM) {
-        const float c = v.x * (1.f / ((float)P * (float)P));
-        const int idx = row * W + (sx + SM), sy = row - SM;
-        Ci[idx] = c;
-        const Best cand{c, sx * sx + sy * sy, idx};
-        if (better(cand, b)) b = cand;
+        constexpr float inv = 1.f / ((float)P * (float)P);
+        put(row, sx, v.x * inv);
+        if (row + 1 < W) put(row + 1, sx, v.y * inv);
       }
     }
   } store{Ci, y0, Best{-CUDART_INF_F, 0x7fffffff, 0x7fffffff}};
@@ -300,11 +310,12 @@ void center_P(const float *R, const float *mu_a, const float *mu_b, const double
     note_launch();
     k_ctr_icols<P><<<dim3((H + CC::S - 1) / CC::S, n), CC::NT, CC::smem, s>>>(Fi, tw, U + (size_t)i * W * P);
     note_launch();
-    k_ctr_irows<P><<<dim3((W + RC::S - 1) / RC::S, n), RC::NT, RC::smem, s>>>(U + (size_t)i * W * P, tw,
-                                                                        Cc + (size_t)i * W * W, Fi);
+    k_ctr_irows<P><<<dim3((W + 2 * RC::S - 1) / (2 * RC::S), n), RC::NT, RC::smem, s>>>(U + (size_t)i * W * P, tw,
+                                                                                Cc + (size_t)i * W * W, Fi);
     note_launch();
   }
-  k_ctr_pick<<<B, 256, 0, s>>>(Cc, W, (W + RC::S - 1) / RC::S, (int64_t)P * P, F, cell, masked, dlm, shift, status);
+  k_ctr_pick<<<B, 256, 0, s>>>(Cc, W, (W + 2 * RC::S - 1) / (2 * RC::S), (int64_t)P * P, F, cell, masked, dlm, shift,
+                               status);
   note_launch();
 }
 
