@@ -42,6 +42,24 @@ CHUNK = 296
 
 
 # ----------------------------------------------------------------------------- helpers
+
+def steer_bytes(N):
+    """Bytes one Steer major cycle moves per instance: R in and the column pass's half spectrum
+    (N + 1 rows of N) out; the row pass reads that, the beam's half spectrum (N + 1 rows of 2N)
+    and writes N + 1 rows of N; the inverse column pass reads them and writes Y; the update
+    reads R, Y and the model and writes R and the model."""
+    H = N + 1
+    return 4.0 * N * N + 8.0 * H * N + (8.0 * H * N + 8.0 * H * 2 * N + 8.0 * H * N) + (8.0 * H * N + 4.0 * N * N) \
+        + 20.0 * N * N
+
+
+def center_bytes(N):
+    """Bytes one disk-centring instance moves: residual in, forward columns out and back in,
+    half spectrum (P/2 + 1 columns) out and back in, window columns out and back in, window out."""
+    P, W = 2 * N, N // 2 + 1
+    H = P // 2 + 1
+    return 4.0 * N * N + 2 * 8.0 * N * P + 2 * 8.0 * H * P + 2 * 8.0 * W * H + 4.0 * W * W
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -377,11 +395,12 @@ def main():
              "autotuned": tuned,
              "center_ms_per_chunk": center_ms,
              "center_instances_per_s": min(B, args.chunk) / (center_ms / 1e3),
+             "center_GBps": min(B, args.chunk) * center_bytes(N) / (center_ms / 1e3) / 1e9,
              "steer_ms_per_chunk_20_cycles": steer_ms, "steer_instance_cycles": steer_cycles,
              "steer_us_per_instance_cycle": steer_ms * 1e3 / max(steer_cycles, 1),
              # per instance-cycle: selection 4 N^2 and update 20 N^2 bytes; the four FFT passes of
              # side 2N move 148.8 N^2 (half-planes where C or Y is zero, half beam spectrum)
-             "steer_GBps": 172.8 * N * N * steer_cycles / (steer_ms / 1e3) / 1e9}
+             "steer_GBps": steer_bytes(N) * steer_cycles / (steer_ms / 1e3) / 1e9}
 
     # the extra legs need the device memory of the main batch
     del imager, out, o, vis_dev, ws, rec, st
@@ -491,12 +510,21 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         cell4 = np.full(w4.n_chan, 60 * synth.ARCMIN / w4.N)
         rec, _, _ = m.uvw(w4.ant_enu, w4.pairs, w4.ha, w4.dec, w4.freq, cell4, w4.vis, cfg4, flags=w4.flags)
         obs = torch.tensor(w4.vis.reshape(-1), dtype=torch.complex64, device="cuda")
-        gd = GradientImaging(rec, obs, float(np.sqrt(np.mean(np.abs(w4.vis) ** 2)) / 30.0), cfg4, eta=1e-9)
-        t0 = time.perf_counter()
-        for _ in range(10):
-            gd.step()
+        gd = GradientImaging(rec, obs, float(np.sqrt(np.mean(np.abs(w4.vis) ** 2)) / 30.0), cfg4)
+        gd.capture()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        print(json.dumps({"case": case, "steps": 10, "s": time.perf_counter() - t0}))
+        e0.record()
+        gd.replay(200)
+        e1.record()
+        torch.cuda.synchronize()
+        graph_us = e0.elapsed_time(e1) * 1e3 / 200
+        e0.record()
+        for _ in range(20):
+            gd.step()
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"case": case, "graph_us_per_eval": graph_us, "eager_us_per_eval": e0.elapsed_time(e1) * 1e3 / 20}))
         return
     n_inst = n_inst or (148 if case == "clean" else 8)
     wl = synth.config3_muser2_uneven(n_frame=1, chans=list(range(n_inst)))
@@ -542,7 +570,8 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         cyc = int(nc.sum())
         print(json.dumps({"case": case, "instances": n_inst, "steer_ms": e0.elapsed_time(e1), "instance_cycles": cyc,
                           "us_per_instance_cycle": e0.elapsed_time(e1) * 1e3 / max(cyc, 1),
-                          "GBps": 172.8 * N * N * cyc / (e0.elapsed_time(e1) / 1e3) / 1e9}))
+                          "GBps": steer_bytes(N) * cyc / (e0.elapsed_time(e1) / 1e3) / 1e9}))
+        return
     if case == "clean":
         ws.buf = None
         torch.cuda.empty_cache()

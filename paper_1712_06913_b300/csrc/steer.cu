@@ -6,17 +6,20 @@
 // (clip = 1 keeps the peak alone and a = gain: one Hogbom step.)
 //
 // Y comes from circular convolutions of side P = 2N: C (N x N at the origin) with the beam
-// (2N x 2N): Y(q) = (C (*) Bm)(q + (N, N)), nothing wraps.  The beam spectrum FB is computed
-// once per call.  Per cycle (every instance of the batch at once; an instance that has stopped
-// returns from every kernel at once):
+// (2N x 2N): Y(q) = (C (*) Bm)(q + (N, N)), nothing wraps.  C and the beam are real, so their
+// spectra are Hermitian and only the rows k_y in [0, P/2] are formed; the beam spectrum FB is
+// computed once per call.  Per cycle (every instance of the batch at once; an instance that has
+// stopped returns from every kernel at once):
 //   k_st_decide max R (gathered by the previous update) -> m, threshold, active flag;
-//   k_st_cols   forward column pass of C (only the N columns and rows where C can be non-zero);
-//   k_st_rows   forward row pass, multiplied by FB on the way out;
-//   k_st_icols  inverse column pass, output rows N .. 2N - 1 only;
-//   k_st_irows  inverse row pass, output columns N .. 2N - 1 only -> Y (/ P^2), block maxima of Y;
+//   k_st_cols   forward column pass of C (only the N columns and rows where C can be non-zero),
+//               output rows k_y <= P/2;
+//   k_st_rows   per row k_y <= P/2: forward transform along x, times FB, inverse transform along
+//               k_x, in one block; output columns N .. 2N - 1 only;
+//   k_st_icols  inverse column pass with the Hermitian extension U(-k_y) = U(k_y)*, two real
+//               columns per transform, output rows N .. 2N - 1 only -> Y (/ P^2), block maxima
+//               of Y;
 //   k_st_update R -= a Y, model += a C (C re-derived from the same R and threshold), block
 //               maxima of the new R for the next cycle.
-// The beam is real, so FB(-v, -u) = conj FB(v, u): only the columns u <= P/2 are stored.
 #include "fft.cuh"
 
 namespace muser {
@@ -42,13 +45,8 @@ struct SteerState {      // per instance
 };
 
 template <int P>
-struct HalfSpec {        // FB stored as [P][P/2 + 1]
+struct HalfSpec {        // FB stored as [P/2 + 1][P]: rows k_y <= P/2, every k_x
   static constexpr int H = P / 2 + 1;
-  __device__ static float2 get(const float2 *__restrict__ F, int v, int u) {
-    if (u <= P / 2) return F[(size_t)v * H + u];
-    const float2 c = F[(size_t)(v == 0 ? 0 : P - v) * H + (P - u)];
-    return make_float2(c.x, -c.y);
-  }
 };
 
 // block max of a float over the block's threads -> atomicMax on an ordered int
@@ -83,11 +81,14 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_beam_cols(const float *__r
   struct Store {
     float2 *Fi;
     int x0;
-    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)o * P + x0 + s] = v; }
+    __device__ void operator()(int o, int s, float2 v) const {
+      if (o <= P / 2) Fi[(size_t)o * P + x0 + s] = v;
+    }
   } store{Fi, x0};
   fft::run<P, S, NT, -1, true, typename C::Layout>(sm, tw, load, store);
 }
 
+// rows k_y <= P/2 of the column spectra -> FB[k_y][k_x]
 template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_beam_rows(const float2 *__restrict__ tw, const float2 *__restrict__ FB,
                                                                 float2 *__restrict__ FBh) {
@@ -100,14 +101,16 @@ __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_beam_rows(const float2 *__
   struct Load {
     const float2 *Fi;
     int y0;
-    __device__ float2 operator()(int i, int s) const { return Fi[(size_t)(y0 + s) * P + i]; }
+    __device__ float2 operator()(int i, int s) const {
+      return y0 + s <= P / 2 ? Fi[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
+    }
   } load{Fi, y0};
   float2 *Hi = FBh + (size_t)inst * P * HalfSpec<P>::H;
   struct Store {
     float2 *Hi;
     int y0;
     __device__ void operator()(int o, int s, float2 v) const {
-      if (o <= P / 2) Hi[(size_t)(y0 + s) * HalfSpec<P>::H + o] = v;
+      if (y0 + s <= P / 2) Hi[(size_t)(y0 + s) * P + o] = v;
     }
   } store{Hi, y0};
   fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
@@ -143,7 +146,8 @@ __global__ void k_st_decide(SteerState *__restrict__ st, int B, int cap, const f
   S.mnext = ordered(-CUDART_INF_F);
 }
 
-// forward column pass of C = R [R >= tau] (columns and rows < N)
+// forward column pass of C = R [R >= tau] (columns and rows < N); rows k_y <= P/2 of the
+// spectrum -> F[k_y][x]
 template <int P>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restrict__ R, const SteerState *__restrict__ st,
                                                           const float2 *__restrict__ tw, float2 *__restrict__ F) {
@@ -169,97 +173,107 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restri
   struct Store {
     float2 *Fi;
     int x0;
-    __device__ void operator()(int o, int s, float2 v) const { Fi[(size_t)o * P + x0 + s] = v; }
+    __device__ void operator()(int o, int s, float2 v) const {
+      if (o <= P / 2) Fi[(size_t)o * P + x0 + s] = v;
+    }
   } store{Fi, x0};
   fft::run<P, S, NT, -1, true, typename C::Layout>(sm, tw, load, store);
 }
 
-// forward row pass (columns >= N of pass 1 are zero), times the beam spectrum, in place
+// row k_y <= P/2: forward transform along x (columns >= N of pass 1 are zero), times FB, inverse
+// transform along k_x; output columns N .. 2N - 1 -> U[k_y][x - N].  The forward transform's
+// last stage stores the product into the block's own shared memory (its loads are complete by
+// then), which the inverse transform reads.
 template <int P>
 __global__ void __launch_bounds__(RowCfg<P>::NT) k_st_rows(const SteerState *__restrict__ st, const float2 *__restrict__ tw,
-                                                          const float2 *__restrict__ FB, float2 *__restrict__ F) {
+                                                          const float2 *__restrict__ FB, const float2 *__restrict__ F,
+                                                          float2 *__restrict__ U) {
   using C = RowCfg<P>;
+  using L = typename C::Layout;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
   const int inst = blockIdx.y, y0 = blockIdx.x * S;
   if (!st[inst].active) return;
-  float2 *Fi = F + (size_t)inst * P * P;
+  const float2 *Fi = F + (size_t)inst * P * P;
   const float2 *Bi = FB + (size_t)inst * P * HalfSpec<P>::H;
   struct Load {
     const float2 *Fi;
     int y0;
     __device__ float2 operator()(int i, int s) const {
-      return i < N ? Fi[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
+      return i < N && y0 + s <= P / 2 ? Fi[(size_t)(y0 + s) * P + i] : make_float2(0.f, 0.f);
     }
   } load{Fi, y0};
-  struct Store {
-    float2 *Fi;
+  struct Mul {
+    float2 *sm;
     const float2 *Bi;
     int y0;
     __device__ void operator()(int o, int s, float2 v) const {
-      Fi[(size_t)(y0 + s) * P + o] = cmul(v, HalfSpec<P>::get(Bi, y0 + s, o));
+      const float2 b = y0 + s <= P / 2 ? Bi[(size_t)(y0 + s) * P + o] : make_float2(0.f, 0.f);
+      sm[L::at(o, s)] = cmul(v, b);
     }
-  } store{Fi, Bi, y0};
-  fft::run<P, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
+  } mul{sm, Bi, y0};
+  fft::run<P, S, NT, -1, false, L>(sm, tw, load, mul);
+  __syncthreads();
+  struct Back {
+    const float2 *sm;
+    __device__ float2 operator()(int i, int s) const { return sm[L::at(i, s)]; }
+  } back{sm};
+  float2 *Ui = U + (size_t)inst * HalfSpec<P>::H * N;
+  struct Store {
+    float2 *Ui;
+    int y0;
+    __device__ void operator()(int o, int s, float2 v) const {
+      if (o >= N && y0 + s <= P / 2) Ui[(size_t)(y0 + s) * N + (o - N)] = v;
+    }
+  } store{Ui, y0};
+  fft::run<P, S, NT, +1, false, L, true>(sm, tw, back, store);
 }
 
-// inverse column pass, output rows N .. 2N - 1 -> U[row - N][P]
+// inverse column pass over k_y: U(-k_y) = U(k_y)* (Y is real; the imaginary parts of rows 0 and
+// P/2 are rounding and dropped), columns 2s and 2s + 1 of the strip in slot s as
+// U_a + i U_b; output rows N .. 2N - 1 -> Y (real and imaginary parts / P^2), and max Y.
 template <int P>
-__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_icols(const SteerState *__restrict__ st, const float2 *__restrict__ F,
-                                                           const float2 *__restrict__ tw, float2 *__restrict__ U) {
+__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_icols(SteerState *__restrict__ st, const float2 *__restrict__ U,
+                                                           const float2 *__restrict__ tw, float *__restrict__ Y) {
   using C = ColCfg<P>;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
-  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  const int inst = blockIdx.y, x0 = blockIdx.x * 2 * S;
   if (!st[inst].active) return;
-  const float2 *Fi = F + (size_t)inst * P * P;
-  float2 *Ui = U + (size_t)inst * N * P;
-  struct Load {
-    const float2 *Fi;
-    int x0;
-    __device__ float2 operator()(int i, int s) const { return Fi[(size_t)i * P + x0 + s]; }
-  } load{Fi, x0};
-  struct Store {
-    float2 *Ui;
-    int x0;
-    __device__ void operator()(int o, int s, float2 v) const {
-      if (o >= N) Ui[(size_t)(o - N) * P + x0 + s] = v;
-    }
-  } store{Ui, x0};
-  fft::run<P, S, NT, +1, true, typename C::Layout>(sm, tw, load, store);
-}
-
-// inverse row pass, output columns N .. 2N - 1 -> Y (real part / P^2), and max Y
-template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_irows(SteerState *__restrict__ st, const float2 *__restrict__ U,
-                                                           const float2 *__restrict__ tw, float *__restrict__ Y) {
-  using C = RowCfg<P>;
-  constexpr int N = P / 2, S = C::S, NT = C::NT;
-  extern __shared__ float4 smem4[];
-  float2 *sm = reinterpret_cast<float2 *>(smem4);
-  const int inst = blockIdx.y, y0 = blockIdx.x * S;
-  if (!st[inst].active) return;
-  const float2 *Ui = U + (size_t)inst * N * P;
+  const float2 *Ui = U + (size_t)inst * HalfSpec<P>::H * N;
   float *Yi = Y + (size_t)inst * N * N;
   struct Load {
     const float2 *Ui;
-    int y0;
-    __device__ float2 operator()(int i, int s) const { return Ui[(size_t)(y0 + s) * P + i]; }
-  } load{Ui, y0};
+    int x0;
+    __device__ float2 u(int i, int x) const {
+      if (x >= N) return make_float2(0.f, 0.f);
+      if (i == 0 || i == P / 2) return make_float2(Ui[(size_t)i * N + x].x, 0.f);
+      if (i < P / 2) return Ui[(size_t)i * N + x];
+      const float2 v = Ui[(size_t)(P - i) * N + x];
+      return make_float2(v.x, -v.y);
+    }
+    __device__ float2 operator()(int i, int s) const {
+      const float2 a = u(i, x0 + 2 * s), b = u(i, x0 + 2 * s + 1);
+      return make_float2(a.x - b.y, a.y + b.x);
+    }
+  } load{Ui, x0};
   struct Store {
     float *Yi;
-    int y0;
+    int x0;
     float mx;
     __device__ void operator()(int o, int s, float2 v) {
-      if (o < N) return;
-      const float y = v.x * (1.f / ((float)P * (float)P));
-      Yi[(size_t)(y0 + s) * N + (o - N)] = y;
-      mx = fmaxf(mx, y);
+      const int x = x0 + 2 * s;
+      if (o < N || x >= N) return;
+      constexpr float inv = 1.f / ((float)P * (float)P);
+      const float ya = v.x * inv, yb = v.y * inv;
+      Yi[(size_t)(o - N) * N + x] = ya;
+      Yi[(size_t)(o - N) * N + x + 1] = yb;
+      mx = fmaxf(mx, fmaxf(ya, yb));
     }
-  } store{Yi, y0, -CUDART_INF_F};
-  fft::run<P, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+  } store{Yi, x0, -CUDART_INF_F};
+  fft::run<P, S, NT, +1, true, typename C::Layout>(sm, tw, load, store);
   block_max_to(store.mx, &st[inst].ymax);
 }
 
@@ -316,13 +330,12 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
   cudaFuncSetAttribute(k_st_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   cudaFuncSetAttribute(k_st_beam_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   cudaFuncSetAttribute(k_st_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
-  cudaFuncSetAttribute(k_st_irows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   cudaMemsetAsync(model, 0, sizeof(float) * (size_t)B * N * N, s);
   k_st_init<<<(B + 255) / 256, 256, 0, s>>>(st, B, status);
   note_launch();
   k_st_beam_cols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(beam, tw, F);    // F: scratch here
   note_launch();
-  k_st_beam_rows<P><<<dim3(P / RC::S, B), RC::NT, RC::smem, s>>>(tw, F, FB);
+  k_st_beam_rows<P><<<dim3((N + RC::S) / RC::S, B), RC::NT, RC::smem, s>>>(tw, F, FB);
   note_launch();
   const int mb = N * N / 4 / 1024 < 1 ? 1 : (N * N / 4 / 1024 > 64 ? 64 : N * N / 4 / 1024);
   k_st_max<<<dim3(mb, B), 1024, 0, s>>>(R, N, st);
@@ -332,11 +345,9 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
     note_launch();
     k_st_cols<P><<<dim3((N + CC::S - 1) / CC::S, B), CC::NT, CC::smem, s>>>(R, st, tw, F);
     note_launch();
-    k_st_rows<P><<<dim3(P / RC::S, B), RC::NT, RC::smem, s>>>(st, tw, FB, F);
+    k_st_rows<P><<<dim3((N + RC::S) / RC::S, B), RC::NT, RC::smem, s>>>(st, tw, FB, F, U);
     note_launch();
-    k_st_icols<P><<<dim3(P / CC::S, B), CC::NT, CC::smem, s>>>(st, F, tw, U);
-    note_launch();
-    k_st_irows<P><<<dim3(N / RC::S, B), RC::NT, RC::smem, s>>>(st, U, tw, Y);
+    k_st_icols<P><<<dim3((N + 2 * CC::S - 1) / (2 * CC::S), B), CC::NT, CC::smem, s>>>(st, U, tw, Y);
     note_launch();
     k_st_update<<<dim3((N * N + 1023) / 1024 < 64 ? (N * N + 1023) / 1024 : 64, B), 1024, 0, s>>>(R, Y, model, N,
                                                                                                  gain, st);
