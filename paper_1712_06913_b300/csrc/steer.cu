@@ -12,7 +12,7 @@
 // stopped returns from every kernel at once):
 //   k_st_decide max R (gathered by the previous update) -> m, threshold, active flag;
 //   k_st_cols   forward column pass of C (only the N columns and rows where C can be non-zero),
-//               output rows k_y <= P/2;
+//               two real columns per transform, output rows k_y <= P/2;
 //   k_st_rows   per row k_y <= P/2: forward transform along x, times FB, inverse transform along
 //               k_x, in one block; output columns N .. 2N - 1 only;
 //   k_st_icols  inverse column pass with the Hermitian extension U(-k_y) = U(k_y)*, two real
@@ -147,15 +147,18 @@ __global__ void k_st_decide(SteerState *__restrict__ st, int B, int cap, const f
 }
 
 // forward column pass of C = R [R >= tau] (columns and rows < N); rows k_y <= P/2 of the
-// spectrum -> F[k_y][x]
+// spectrum -> F[k_y][x].  C is real: slot s transforms columns x0 + 2s and x0 + 2s + 1 at once
+// as Z = C_a + i C_b, stores Z in the block's shared memory (the last stage's loads are complete
+// by then) and splits it, C_a^(k) = (Z(k) + Z(-k)*) / 2, C_b^(k) = (Z(k) - Z(-k)*) / 2i.
 template <int P>
 __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restrict__ R, const SteerState *__restrict__ st,
                                                           const float2 *__restrict__ tw, float2 *__restrict__ F) {
   using C = ColCfg<P>;
+  using L = typename C::Layout;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
-  const int inst = blockIdx.y, x0 = blockIdx.x * S;
+  const int inst = blockIdx.y, x0 = blockIdx.x * 2 * S;
   if (!st[inst].active) return;
   const float *Ri = R + (size_t)inst * N * N;
   struct Load {
@@ -163,29 +166,35 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restri
     float tau;
     int x0;
     __device__ float2 operator()(int i, int s) const {
-      const int x = x0 + s;
+      const int x = x0 + 2 * s;
       if (i >= N || x >= N) return make_float2(0.f, 0.f);
-      const float r = Ri[(size_t)i * N + x];
-      return make_float2(r >= tau ? r : 0.f, 0.f);
+      const float2 r = *reinterpret_cast<const float2 *>(Ri + (size_t)i * N + x);
+      return make_float2(r.x >= tau ? r.x : 0.f, r.y >= tau ? r.y : 0.f);
     }
   } load{Ri, st[inst].tau, x0};
+  struct Keep {
+    float2 *sm;
+    __device__ void operator()(int o, int s, float2 v) const { sm[L::at(o, s)] = v; }
+  } keep{sm};
+  fft::run<P, S, NT, -1, true, L>(sm, tw, load, keep);
+  __syncthreads();
   float2 *Fi = F + (size_t)inst * P * P;
-  struct Store {
-    float2 *Fi;
-    int x0;
-    __device__ void operator()(int o, int s, float2 v) const {
-      if (o <= P / 2) Fi[(size_t)o * P + x0 + s] = v;
-    }
-  } store{Fi, x0};
-  fft::run<P, S, NT, -1, true, typename C::Layout>(sm, tw, load, store);
+  for (int it = threadIdx.x; it < (P / 2 + 1) * S; it += NT) {
+    const int s = it % S, o = it / S, x = x0 + 2 * s;
+    if (x >= N) continue;
+    const float2 z = sm[L::at(o, s)], zm = sm[L::at((P - o) % P, s)];
+    const float4 ab = make_float4(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y), 0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+    *reinterpret_cast<float4 *>(Fi + (size_t)o * P + x) = ab;
+  }
 }
 
 // row k_y <= P/2: forward transform along x (columns >= N of pass 1 are zero), times FB, inverse
 // transform along k_x; output columns N .. 2N - 1 -> U[k_y][x - N].  The forward transform's
 // last stage stores the product into the block's own shared memory (its loads are complete by
-// then), which the inverse transform reads.
+// then), which the inverse transform reads.  For P = 2^m the kernel is held to 64 registers so
+// that 1024 threads fit per SM (the radix-5Q first stage of P = 5 * 2^m would spill).
 template <int P>
-__global__ void __launch_bounds__(RowCfg<P>::NT) k_st_rows(const SteerState *__restrict__ st, const float2 *__restrict__ tw,
+__global__ void __launch_bounds__(RowCfg<P>::NT, P % 5 ? fft::cmax(1, 1024 / RowCfg<P>::NT) : 1) k_st_rows(const SteerState *__restrict__ st, const float2 *__restrict__ tw,
                                                           const float2 *__restrict__ FB, const float2 *__restrict__ F,
                                                           float2 *__restrict__ U) {
   using C = RowCfg<P>;
@@ -343,7 +352,7 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
   for (int c = 0; c < cap; c++) {
     k_st_decide<<<(B + 255) / 256, 256, 0, s>>>(st, B, cap, thr, clip);
     note_launch();
-    k_st_cols<P><<<dim3((N + CC::S - 1) / CC::S, B), CC::NT, CC::smem, s>>>(R, st, tw, F);
+    k_st_cols<P><<<dim3((N + 2 * CC::S - 1) / (2 * CC::S), B), CC::NT, CC::smem, s>>>(R, st, tw, F);
     note_launch();
     k_st_rows<P><<<dim3((N + RC::S) / RC::S, B), RC::NT, RC::smem, s>>>(st, tw, FB, F, U);
     note_launch();
