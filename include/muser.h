@@ -272,7 +272,8 @@ MUSER_API int muser_chi2(const float *pred, const float *obs, const muser_vis_re
  * dlm_out[B][2] f64; shift_out[B][2] f32 pixels (NULL = not written); corr_out[B][N/2+1][N/2+1]
  * f32 (NULL = not written).  Pass dlm_out to muser_uvw / muser_image to phase-correct the
  * visibilities (exp(+2 pi i (u dl + v dm))) and re-image.  The RA offset is dl / cos(dec).
- * Instances whose mask is empty get MUSER_ST_NO_DISK and offset 0.  N <= 1024. */
+ * Instances whose mask is empty get MUSER_ST_NO_DISK and offset 0.  N = 2^a in [32, 1024] or
+ * 5 * 2^a in [160, 5120]. */
 MUSER_API int muser_center(const float *residual, const float *mu_a, const float *mu_b, const double *cell_rad, int B,
                            const muser_config_t *cfg, float *corr_out, double *dlm_out, float *shift_out, void *ws,
                            size_t ws_bytes, int32_t *status, muser_stream_t stream);
@@ -285,9 +286,10 @@ MUSER_API int muser_center(const float *residual, const float *mu_a, const float
  * With clip = 1 every cycle is one Hogbom step.  Y is computed with FFTs of side 2N.
  * residual[B][N][N] (in: dirty map, out: residual), beam[B][2N][2N], thr[B] (NULL: no
  * threshold, or the GMM sky level when cfg->thr_mode = 1), model[B][N][N] (out, zeroed by the
- * call), n_cycles[B] (out).  0 < clip <= 1.  Every instance runs in the same launches: a batch
- * enqueues 6 kernels per cycle up to cfg->max_iter cycles, and an instance that has stopped
- * returns from them at once.  N <= 1024. */
+ * call), n_cycles[B] (out); residual 16-byte aligned.  0 < clip <= 1.  Every instance runs in
+ * the same launches: a batch enqueues 5 kernels per cycle up to cfg->max_iter cycles, and an
+ * instance that has stopped returns from them at once.  N = 2^a in [32, 1024] or 5 * 2^a in
+ * [160, 5120]. */
 MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser_config_t *cfg, const float *thr,
                           float clip, float *model, int32_t *n_cycles, void *ws, size_t ws_bytes, int32_t *status,
                           muser_stream_t stream);

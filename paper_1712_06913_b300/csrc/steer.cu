@@ -206,6 +206,12 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, P % 5 ? fft::cmax(1, 1024 / Row
   if (!st[inst].active) return;
   const float2 *Fi = F + (size_t)inst * P * P;
   const float2 *Bi = FB + (size_t)inst * P * HalfSpec<P>::H;
+  // the block's rows of FB are needed only after the forward transform: start moving them
+  // into L2 now (one bulk prefetch of 8 P bytes per row; rows are 16-byte aligned)
+  if (threadIdx.x < S && y0 + (int)threadIdx.x <= P / 2)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(Bi + (size_t)(y0 + threadIdx.x) * P),
+                 "r"((unsigned)(P * sizeof(float2)))
+                 : "memory");
   struct Load {
     const float2 *Fi;
     int y0;
@@ -256,16 +262,13 @@ __global__ void __launch_bounds__(ColCfg<P>::NT) k_st_icols(SteerState *__restri
   struct Load {
     const float2 *Ui;
     int x0;
-    __device__ float2 u(int i, int x) const {
-      if (x >= N) return make_float2(0.f, 0.f);
-      if (i == 0 || i == P / 2) return make_float2(Ui[(size_t)i * N + x].x, 0.f);
-      if (i < P / 2) return Ui[(size_t)i * N + x];
-      const float2 v = Ui[(size_t)(P - i) * N + x];
-      return make_float2(v.x, -v.y);
-    }
     __device__ float2 operator()(int i, int s) const {
-      const float2 a = u(i, x0 + 2 * s), b = u(i, x0 + 2 * s + 1);
-      return make_float2(a.x - b.y, a.y + b.x);
+      const int x = x0 + 2 * s;                // even: (U_a, U_b) is one aligned 16-byte load
+      if (x >= N) return make_float2(0.f, 0.f);
+      float4 ab = *reinterpret_cast<const float4 *>(Ui + (size_t)(i <= P / 2 ? i : P - i) * N + x);
+      if (i == 0 || i == P / 2) ab.y = ab.w = 0.f;
+      else if (i > P / 2) ab.y = -ab.y, ab.w = -ab.w;
+      return make_float2(ab.x - ab.w, ab.y + ab.z);   // U_a + i U_b
     }
   } load{Ui, x0};
   struct Store {

@@ -89,6 +89,10 @@ def test_call_argument_errors_without_a_gpu():
     # muser_steer: clip outside (0, 1]
     rc = lib.muser_steer(null, null, 1, ctypes.byref(c), null, 1.5, null, null, null, 0, null, null)
     assert rc != 0 and b"clip" in lib.muser_last_error()
+    # muser_steer: residual not 16-byte aligned (checked before any device work)
+    fake = [ctypes.c_void_p(a) for a in (0x10004, 0x20000, 0x30000, 0x40000)]
+    rc = lib.muser_steer(fake[0], fake[1], 1, ctypes.byref(c), null, 0.9, fake[2], fake[3], null, 0, null, null)
+    assert rc != 0 and b"aligned" in lib.muser_last_error()
     # muser_grad_step: bad flags, missing pointers
     cd = m.Config(N=64, G=128).c()
     assert lib.muser_grad_step(3, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
