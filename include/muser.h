@@ -286,7 +286,7 @@ MUSER_API int muser_center(const float *residual, const float *mu_a, const float
  * With clip = 1 every cycle is one Hogbom step.  Y is computed with FFTs of side 2N.
  * residual[B][N][N] (in: dirty map, out: residual), beam[B][2N][2N], thr[B] (NULL: no
  * threshold, or the GMM sky level when cfg->thr_mode = 1), model[B][N][N] (out, zeroed by the
- * call), n_cycles[B] (out); residual 16-byte aligned.  0 < clip <= 1.  Every instance runs in
+ * call), n_cycles[B] (out); residual and model 16-byte aligned.  0 < clip <= 1.  Every instance runs in
  * the same launches: a batch enqueues 5 kernels per cycle up to cfg->max_iter cycles, and an
  * instance that has stopped returns from them at once.  N = 2^a in [32, 1024] or 5 * 2^a in
  * [160, 5120]. */

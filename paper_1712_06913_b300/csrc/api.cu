@@ -727,7 +727,7 @@ int muser_steer(float *residual, const float *beam, int B, const muser_config_t 
   if (cfg->N < 32) return fail(MUSER_ERR_UNSUPPORTED, "muser_steer needs N >= 32");
   if (!(clip > 0.f && clip <= 1.f)) return fail(MUSER_ERR_ARG, "clip must be in (0, 1]");
   if (!residual || !beam || !model || !n_cycles) return fail(MUSER_ERR_ARG, "muser_steer: required pointer is NULL");
-  if (!aligned(residual, 16)) return fail(MUSER_ERR_ARG, "residual must be 16-byte aligned");
+  if (!aligned(residual, 16) || !aligned(model, 16)) return fail(MUSER_ERR_ARG, "residual and model must be 16-byte aligned");
   const size_t need = muser_workspace_size(MUSER_CALL_STEER, B, 0, cfg);
   MUSER_TRY(check_ws(ws, ws_bytes, need));
   Arena a(ws, ws_bytes);

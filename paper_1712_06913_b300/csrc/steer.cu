@@ -302,13 +302,23 @@ __global__ void k_st_update(float *__restrict__ R, const float *__restrict__ Y, 
   }
   const float a = gain * S.m / ym, tau = S.tau;
   const size_t base = (size_t)inst * N * N;
+  // four pixels per 16-byte access (N^2 is a multiple of 4 and every image starts 16-byte aligned)
+  float4 *R4 = reinterpret_cast<float4 *>(R + base), *M4 = reinterpret_cast<float4 *>(model + base);
+  const float4 *Y4 = reinterpret_cast<const float4 *>(Y + base);
   float mx = -CUDART_INF_F;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N; i += gridDim.x * blockDim.x) {
-    const float r = R[base + i];
-    if (r >= tau) model[base + i] += a * r;
-    const float rn = r - a * Y[base + i];
-    R[base + i] = rn;
-    mx = fmaxf(mx, rn);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * N / 4; i += gridDim.x * blockDim.x) {
+    const float4 r = R4[i], y = Y4[i];
+    if (r.x >= tau || r.y >= tau || r.z >= tau || r.w >= tau) {
+      float4 mo = M4[i];
+      if (r.x >= tau) mo.x += a * r.x;
+      if (r.y >= tau) mo.y += a * r.y;
+      if (r.z >= tau) mo.z += a * r.z;
+      if (r.w >= tau) mo.w += a * r.w;
+      M4[i] = mo;
+    }
+    const float4 rn = make_float4(r.x - a * y.x, r.y - a * y.y, r.z - a * y.z, r.w - a * y.w);
+    R4[i] = rn;
+    mx = fmaxf(mx, fmaxf(fmaxf(rn.x, rn.y), fmaxf(rn.z, rn.w)));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) S.cycles++;
   block_max_to(mx, &S.mnext);
@@ -361,8 +371,8 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
     note_launch();
     k_st_icols<P><<<dim3((N + 2 * CC::S - 1) / (2 * CC::S), B), CC::NT, CC::smem, s>>>(st, U, tw, Y);
     note_launch();
-    k_st_update<<<dim3((N * N + 1023) / 1024 < 64 ? (N * N + 1023) / 1024 : 64, B), 1024, 0, s>>>(R, Y, model, N,
-                                                                                                 gain, st);
+    k_st_update<<<dim3((N * N / 4 + 1023) / 1024 < 64 ? (N * N / 4 + 1023) / 1024 : 64, B), 1024, 0, s>>>(
+        R, Y, model, N, gain, st);
     note_launch();
   }
   k_st_finish<<<(B + 255) / 256, 256, 0, s>>>(st, B, n_cycles);
