@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
     ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "large_clean", "wproj",
-                                       "mixed", "center"],
+                                       "mixed", "center", "band2"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -443,6 +443,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     mixed: the mixed stream of `n_inst` (default 10,000) MUSER-I / MUSER-II instances.
     large_clean: CLEAN (`iters` iterations) of `n_inst` (default 16) instances at side `size`.
     center: disk centring of `n_inst` (default 32) MUSER-II dirty maps.
+    band2: the whole MUSER-I band (2048 instances of 512^2) with the GMM iteration estimate.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -454,6 +455,9 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         return
     if case == "wproj":
         print(json.dumps({"case": case, **wproj_leg(m, torch.cuda.current_stream(), n=n_inst or 296)}))
+        return
+    if case == "band2":
+        print(json.dumps({"case": case, **config2_band(m, torch.cuda.current_stream())}))
         return
     if case == "center":
         # disk centring (muser_center) of `n_inst` (default 32) MUSER-II dirty maps
@@ -648,6 +652,7 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     res["large_images"] = large_images(m, stream)
     res["w_projection"] = wproj_leg(m, stream)
     res["steer_image"] = steer_image_leg(m, wl, cell, cfg, stream)
+    res["config2_band"] = config2_band(m, stream)
     res["mixed_stream"] = mixed_stream(m, stream)
     return res
 
@@ -683,6 +688,33 @@ def wproj_leg(m, stream, n=296, P=128):
         del im
         torch.cuda.empty_cache()
     res.update(w_planes=P, w_support=Ww, w_max_grid_units=w_max)
+    return res
+
+
+def config2_band(m, stream):
+    """The whole MUSER-I band as one batch: 64 channels x 32 frames = 2048 instances of 512^2
+    (G 2048) through muser_image with the paper's iteration estimate (CLEAN down to the GMM sky
+    level of each dirty map, at most 1000 iterations): images/s and the iterations run."""
+    import torch
+    import synth
+    wl = synth.config2_muser1_band()
+    cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=wl.max_iter, gain=wl.gain, lat_rad=wl.lat,
+                   thr_mode=wl.thr_mode)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    im.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = im.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    nc = out.n_comp.float()
+    res = {"workload": f"MUSER-I band, {wl.n_inst} instances of 512^2 (G 2048), GMM threshold, cap 1000",
+           "images_per_s": wl.n_inst / (e0.elapsed_time(e1) / 1e3),
+           "iterations_mean": float(nc.mean()), "iterations_max": int(nc.max())}
+    del im, out
+    torch.cuda.empty_cache()
     return res
 
 
