@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
     ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "large_clean", "wproj",
-                                       "mixed", "center", "band2"],
+                                       "mixed", "center", "band2", "plain1"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -444,6 +444,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     large_clean: CLEAN (`iters` iterations) of `n_inst` (default 16) instances at side `size`.
     center: disk centring of `n_inst` (default 32) MUSER-II dirty maps.
     band2: the whole MUSER-I band (2048 instances of 512^2) with the GMM iteration estimate.
+    plain1: one 256^2 image (one frame, one channel, 200 iterations) per call, device and end to end.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -458,6 +459,9 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         return
     if case == "band2":
         print(json.dumps({"case": case, **config2_band(m, torch.cuda.current_stream())}))
+        return
+    if case == "plain1":
+        print(json.dumps({"case": case, **config1_latency(m, torch.cuda.current_stream())}))
         return
     if case == "center":
         # disk centring (muser_center) of `n_inst` (default 32) MUSER-II dirty maps
@@ -653,6 +657,7 @@ def plain_and_degrid(m, wl, cell, cfg, stream):
     res["w_projection"] = wproj_leg(m, stream)
     res["steer_image"] = steer_image_leg(m, wl, cell, cfg, stream)
     res["config2_band"] = config2_band(m, stream)
+    res["config1_plain"] = config1_latency(m, stream)
     res["mixed_stream"] = mixed_stream(m, stream)
     return res
 
@@ -714,6 +719,43 @@ def config2_band(m, stream):
            "images_per_s": wl.n_inst / (e0.elapsed_time(e1) / 1e3),
            "iterations_mean": float(nc.mean()), "iterations_max": int(nc.max())}
     del im, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def config1_latency(m, stream, reps=20):
+    """Config 1 (one frame, 780 baselines, 1 channel, 256^2, 200 iterations) as a plain
+    pipeline: ms per image on the device (inputs resident), and end to end on the host clock
+    (pinned visibilities to the device, muser_image, clean image back, synchronised)."""
+    import time
+    import torch
+    import synth
+    wl = synth.config1_plain_frame()
+    cfg = m.Config(N=wl.N, G=wl.G, W=wl.W, os=wl.OS, max_iter=wl.max_iter, gain=wl.gain, lat_rad=wl.lat)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    for _ in range(3):
+        im.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        im.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dev_ms = e0.elapsed_time(e1) / reps
+    vis_h = torch.from_numpy(wl.vis.astype("complex64")).pin_memory()
+    img_h = torch.empty(im.out.clean.shape, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        im.vis.copy_(vis_h, non_blocking=True)
+        out = im.run()
+        img_h.copy_(out.clean, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / reps
+    res = {"workload": "one frame, 780 baselines, 1 channel at 1.7 GHz, 256^2 (G 1024), 200 iterations",
+           "device_ms_per_image": dev_ms, "e2e_ms_per_image": e2e_ms}
+    del im
     torch.cuda.empty_cache()
     return res
 
