@@ -188,18 +188,25 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *_
   const int tv = threadIdx.x & 7;
   const int64_t per = (int64_t)gridDim.x * (kInterpThreads / 8);   // records per sweep of the grid
   float l = 0.f;
-  for (int64_t r0 = (int64_t)blockIdx.x * (kInterpThreads / 8); r0 < n; r0 += per) {   // uniform per block
-    const int64_t r = r0 + (threadIdx.x >> 3);
-    Rec R;
-    bool ok = false;
-    if (r < n) {
-      R = rec[r];
-      ok = record_ok(R, G, (W - 1) / 2);
+  // the record and observation of the next sweep are loaded before this sweep's gathers
+  int64_t r = (int64_t)blockIdx.x * (kInterpThreads / 8) + (threadIdx.x >> 3);
+  Rec Rn;
+  float2 on = make_float2(0.f, 0.f);
+  if (r < n) {
+    Rn = rec[r];
+    if (tv == 0) on = obs[r];
+  }
+  for (int64_t r0 = (int64_t)blockIdx.x * (kInterpThreads / 8); r0 < n; r0 += per, r += per) {   // uniform per block
+    const Rec R = Rn;
+    const float2 o = on;
+    if (r + per < n) {
+      Rn = rec[r + per];
+      if (tv == 0) on = obs[r + per];
     }
+    const bool ok = r < n && record_ok(R, G, (W - 1) / 2);
     const float2 acc = interp8_value(X, R, ok, tv, G, W, tab, ntab, os);
     if (r < n && tv == 0) {
       const float w = ok ? R.w : 0.f;
-      const float2 o = obs[r];
       const float dx = acc.x * invK2 - o.x, dy = acc.y * invK2 - o.y;
       if (w > 0.f) l += w * (dx * dx + dy * dy);
       resid[r] = w > 0.f ? make_float2(2.f * w * dx * inv_s2, 2.f * w * dy * inv_s2) : make_float2(0.f, 0.f);
