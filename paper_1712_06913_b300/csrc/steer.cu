@@ -27,6 +27,10 @@ namespace muser {
 namespace {
 
 using fft::ColCfg;
+// Column strips of the per-cycle passes: half as wide as ColCfg's for P = 2^m (two blocks of 512
+// threads per SM instead of one of 1024, whose barriers stall the whole SM), ColCfg's otherwise.
+template <int P>
+using StCol = fft::ColStrip<P, (P % 5 == 0 || ColCfg<P>::S < 2) ? ColCfg<P>::S : ColCfg<P>::S / 2, (P % 5 ? 16 : 32)>;
 using fft::RowCfg;
 
 // order-preserving float <-> int for atomicMax on a float
@@ -151,9 +155,9 @@ __global__ void k_st_decide(SteerState *__restrict__ st, int B, int cap, const f
 // as Z = C_a + i C_b, stores Z in the block's shared memory (the last stage's loads are complete
 // by then) and splits it, C_a^(k) = (Z(k) + Z(-k)*) / 2, C_b^(k) = (Z(k) - Z(-k)*) / 2i.
 template <int P>
-__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_cols(const float *__restrict__ R, const SteerState *__restrict__ st,
+__global__ void __launch_bounds__(StCol<P>::NT) k_st_cols(const float *__restrict__ R, const SteerState *__restrict__ st,
                                                           const float2 *__restrict__ tw, float2 *__restrict__ F) {
-  using C = ColCfg<P>;
+  using C = StCol<P>;
   using L = typename C::Layout;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
@@ -249,9 +253,9 @@ __global__ void __launch_bounds__(RowCfg<P>::NT, P % 5 ? fft::cmax(1, 1024 / Row
 // P/2 are rounding and dropped), columns 2s and 2s + 1 of the strip in slot s as
 // U_a + i U_b; output rows N .. 2N - 1 -> Y (real and imaginary parts / P^2), and max Y.
 template <int P>
-__global__ void __launch_bounds__(ColCfg<P>::NT) k_st_icols(SteerState *__restrict__ st, const float2 *__restrict__ U,
+__global__ void __launch_bounds__(StCol<P>::NT) k_st_icols(SteerState *__restrict__ st, const float2 *__restrict__ U,
                                                            const float2 *__restrict__ tw, float *__restrict__ Y) {
-  using C = ColCfg<P>;
+  using C = StCol<P>;
   constexpr int N = P / 2, S = C::S, NT = C::NT;
   extern __shared__ float4 smem4[];
   float2 *sm = reinterpret_cast<float2 *>(smem4);
@@ -345,11 +349,12 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
              int32_t *n_cycles, const float2 *tw, float2 *FB, float2 *F, float2 *U, float *Y, SteerState *st,
              const int32_t *status, cudaStream_t s) {
   using CC = ColCfg<P>;
+  using SC = StCol<P>;
   using RC = RowCfg<P>;
   constexpr int N = P / 2;
   cudaFuncSetAttribute(k_st_beam_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  cudaFuncSetAttribute(k_st_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  cudaFuncSetAttribute(k_st_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_st_cols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC::smem);
+  cudaFuncSetAttribute(k_st_icols<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SC::smem);
   cudaFuncSetAttribute(k_st_beam_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   cudaFuncSetAttribute(k_st_rows<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
   cudaMemsetAsync(model, 0, sizeof(float) * (size_t)B * N * N, s);
@@ -365,11 +370,11 @@ void steer_P(float *R, const float *beam, int B, float gain, int cap, const floa
   for (int c = 0; c < cap; c++) {
     k_st_decide<<<(B + 255) / 256, 256, 0, s>>>(st, B, cap, thr, clip);
     note_launch();
-    k_st_cols<P><<<dim3((N + 2 * CC::S - 1) / (2 * CC::S), B), CC::NT, CC::smem, s>>>(R, st, tw, F);
+    k_st_cols<P><<<dim3((N + 2 * SC::S - 1) / (2 * SC::S), B), SC::NT, SC::smem, s>>>(R, st, tw, F);
     note_launch();
     k_st_rows<P><<<dim3((N + RC::S) / RC::S, B), RC::NT, RC::smem, s>>>(st, tw, FB, F, U);
     note_launch();
-    k_st_icols<P><<<dim3((N + 2 * CC::S - 1) / (2 * CC::S), B), CC::NT, CC::smem, s>>>(st, U, tw, Y);
+    k_st_icols<P><<<dim3((N + 2 * SC::S - 1) / (2 * SC::S), B), SC::NT, SC::smem, s>>>(st, U, tw, Y);
     note_launch();
     k_st_update<<<dim3((N * N / 4 + 1023) / 1024 < 64 ? (N * N / 4 + 1023) / 1024 : 64, B), 1024, 0, s>>>(
         R, Y, model, N, gain, st);
