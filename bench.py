@@ -204,7 +204,7 @@ def main():
     ap.add_argument("--frames", type=int, default=8, help="frames per rank (8 = the full workload)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/degrid/cpu-baseline legs")
     ap.add_argument("--case", choices=["clean", "dirty", "grid", "grad", "image0", "steer", "large", "large_clean", "wproj",
-                                       "mixed", "center", "band2", "plain1"],
+                                       "mixed", "center", "band2", "plain1", "steerimg"],
                     default=None,
                     help="small single-kernel case of the same workload (for ncu captures)")
     ap.add_argument("--instances", type=int, default=0, help="instances of a --case (default 148 / 8)")
@@ -445,6 +445,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
     center: disk centring of `n_inst` (default 32) MUSER-II dirty maps.
     band2: the whole MUSER-I band (2048 instances of 512^2) with the GMM iteration estimate.
     plain1: one 256^2 image (one frame, one channel, 200 iterations) per call, device and end to end.
+    steerimg: muser_image with Steer clean on four 296-instance chunks of the MUSER-II workload.
     dirty: 8 instances, gridding + FFT to dirty map and beam.
     grid:  8 instances, gridding only.
     """
@@ -459,6 +460,12 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         return
     if case == "band2":
         print(json.dumps({"case": case, **config2_band(m, torch.cuda.current_stream())}))
+        return
+    if case == "steerimg":
+        wls = synth.config3_muser2_uneven(n_frame=4, chans=list(range(296)))
+        cfgs = m.Config(N=wls.N, G=wls.G, W=wls.W, os=wls.OS, gain=wls.gain, lat_rad=wls.lat)
+        cells = m.pixel_size(wls.freq, wls.bmax, wls.N, wls.fov_min)
+        print(json.dumps({"case": case, **steer_image_leg(m, wls, cells, cfgs, torch.cuda.current_stream())}))
         return
     if case == "plain1":
         print(json.dumps({"case": case, **config1_latency(m, torch.cuda.current_stream())}))
@@ -815,15 +822,16 @@ def mixed_stream(m, stream, n_total=10000, n_plain=8):
     return res
 
 
-def steer_image_leg(m, wl, cell, cfg, stream, n=296, cycles=20):
-    """Alg. 1 with the paper's production clean: one chunk of the MUSER-II batch through
-    muser_image with Steer clean (clean_variant 1, `cycles` major cycles at clip 0.9; restore
-    from the model map): images/s."""
+def steer_image_leg(m, wl, cell, cfg, stream, n=296, frames=4, cycles=20):
+    """Alg. 1 with the paper's production clean: `frames` chunks of `n` instances of the MUSER-II
+    batch through muser_image with Steer clean (clean_variant 1, `cycles` major cycles at clip
+    0.9; restore from the model map; chunk c + 1 prepared while chunk c is cleaned): images/s."""
     import torch
     chans = list(range(min(n, wl.n_chan)))
-    c = m.Config(**{**cfg.__dict__, "batch_chunk": 0, "max_iter": cycles, "clean_variant": 1, "steer_clip": 0.9})
-    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha[:1], wl.dec[:1], wl.freq[chans], cell[chans], wl.vis[:1, chans], c,
-                  flags=wl.flags[:1, chans])
+    c = m.Config(**{**cfg.__dict__, "batch_chunk": len(chans), "max_iter": cycles, "clean_variant": 1,
+                    "steer_clip": 0.9})
+    im = m.Imager(wl.ant_enu, wl.pairs, wl.ha[:frames], wl.dec[:frames], wl.freq[chans], cell[chans],
+                  wl.vis[:frames, chans], c, flags=wl.flags[:frames, chans])
     im.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -831,8 +839,8 @@ def steer_image_leg(m, wl, cell, cfg, stream, n=296, cycles=20):
     out = im.run()
     e1.record(stream)
     torch.cuda.synchronize()
-    res = {"instances": len(chans), "major_cycles": cycles, "images_per_s": len(chans) / (e0.elapsed_time(e1) / 1e3),
-           "cycles_run_mean": float(out.n_comp.float().mean())}
+    res = {"instances": im.B, "chunks": frames, "major_cycles": cycles,
+           "images_per_s": im.B / (e0.elapsed_time(e1) / 1e3), "cycles_run_mean": float(out.n_comp.float().mean())}
     del im, out
     torch.cuda.empty_cache()
     return res
