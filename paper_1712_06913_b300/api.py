@@ -132,12 +132,19 @@ def record_fields(rec: torch.Tensor):
     return vis, rec[:, 2], rec[:, 3], k[0::2].to(torch.int64), k[1::2].to(torch.int64), rec[:, 5], rec[:, 6]
 
 
-def grid(rec, vis_off, cfg: Config, status=None, ws: Workspace = None):
-    """uv grids Z [B, G, G] complex64 from CSR records."""
+def grid(rec, vis_off, cfg: Config, status=None, ws: Workspace = None, out=None, n_vis=None):
+    """uv grids Z [B, G, G] complex64 from CSR records.  `out`: a contiguous complex64 tensor of
+    that shape to write into (else one is allocated); `n_vis`: vis_off[B] when the caller knows
+    it (else it is read back from the device)."""
     vo = _dev(vis_off, torch.int64)
     B = vo.numel() - 1
-    n = int(vo[-1].item()) if B > 0 else 0
-    Z = torch.empty((B, cfg.G, cfg.G), dtype=torch.complex64, device="cuda")
+    n = int(n_vis) if n_vis is not None else (int(vo[-1].item()) if B > 0 else 0)
+    if out is not None:
+        if tuple(out.shape) != (B, cfg.G, cfg.G) or out.dtype != torch.complex64 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex64 tensor of shape (B, G, G)")
+        Z = out
+    else:
+        Z = torch.empty((B, cfg.G, cfg.G), dtype=torch.complex64, device="cuda")
     st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
     c = cfg.c()
     w, wb = (ws or _default_ws).get(workspace_size(CALL_GRID, B, n, cfg))
@@ -145,12 +152,19 @@ def grid(rec, vis_off, cfg: Config, status=None, ws: Workspace = None):
     return Z, st
 
 
-def dirty(Z, cfg: Config, status=None, ws: Workspace = None):
-    """(dirty [B, N, N], beam [B, 2N, 2N], status) from grids."""
+def dirty(Z, cfg: Config, status=None, ws: Workspace = None, out=None):
+    """(dirty [B, N, N], beam [B, 2N, 2N], status) from grids.  `out`: a pair (D, Bm) of
+    contiguous float32 tensors of those shapes to write into (else they are allocated)."""
     B = Z.shape[0]
     N = cfg.N
-    D = torch.empty((B, N, N), dtype=torch.float32, device="cuda")
-    Bm = torch.empty((B, 2 * N, 2 * N), dtype=torch.float32, device="cuda")
+    if out is not None:
+        D, Bm = out
+        if (tuple(D.shape) != (B, N, N) or tuple(Bm.shape) != (B, 2 * N, 2 * N) or D.dtype != torch.float32
+                or Bm.dtype != torch.float32 or not D.is_contiguous() or not Bm.is_contiguous()):
+            raise ValueError("out must be contiguous float32 tensors of shapes (B, N, N) and (B, 2N, 2N)")
+    else:
+        D = torch.empty((B, N, N), dtype=torch.float32, device="cuda")
+        Bm = torch.empty((B, 2 * N, 2 * N), dtype=torch.float32, device="cuda")
     st = status if status is not None else torch.zeros(max(B, 1), dtype=torch.int32, device="cuda")
     c = cfg.c()
     w, wb = (ws or _default_ws).get(workspace_size(CALL_DIRTY, B, 0, cfg))
