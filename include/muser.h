@@ -75,11 +75,15 @@ enum {
 
 /* Imaging parameters (host struct, passed by pointer). */
 typedef struct muser_config {
-  int32_t N;            /* image side, power of two, 16..1024 (Table 2 sizes 256..1024) */
+  int32_t N;            /* image side: 2^a in 16..1024, or for imaging 5 * 2^a in 160..5120 (Table 2) */
   int32_t G;            /* uv-grid side: 4N for imaging (beam of 2N, Sec. 3.2.1), 2N for degrid */
   int32_t W;            /* spheroidal support in cells, odd, 3..9 (7 in every workload) */
   int32_t os;           /* kernel table samples per cell, 16..4096 (1024) */
-  int32_t weight_mode;  /* 0 natural, 1 uniform (Alg. 1 weighting mode) */
+  int32_t weight_mode;  /* 0 natural; 1 uniform (Alg. 1 weighting mode), imaging calls only: each
+                           kept sample weighted by 1 / cnt, cnt = samples (with their -uv mirrors)
+                           in its cell of the unpadded N x N grid, the cell decided in FP32 as
+                           floor((float(k - G/2) - f) / (G/N) + N/2 + 1/2) per axis, the mirror's
+                           as N - cell; muser_grid applies it to a copy of the records */
   int32_t peak_mode;    /* CLEAN peak: 0 largest signed value, 1 largest |value| */
   int32_t thr_mode;     /* CLEAN threshold: 0 fixed thr[] (or -inf), 1 GMM sky level mu_a (Sec. 4.3) */
   int32_t max_iter;     /* CLEAN iteration cap (>= 0) */

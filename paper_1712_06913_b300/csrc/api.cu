@@ -55,7 +55,9 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (n2 && (G < 64 || G > 4096)) return fail(MUSER_ERR_UNSUPPORTED, "G must be in [64, 4096]");
   if (cfg->W < 3 || cfg->W > 9 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "W must be odd in [3, 9]");
   if (cfg->os < 16 || cfg->os > 4096) return fail(MUSER_ERR_ARG, "os must be in [16, 4096]");
-  if (cfg->weight_mode != 0) return fail(MUSER_ERR_UNSUPPORTED, "only natural weighting (weight_mode 0) is implemented");
+  if (cfg->weight_mode != 0 && cfg->weight_mode != 1) return fail(MUSER_ERR_ARG, "weight_mode must be 0 or 1");
+  if (cfg->weight_mode != 0 && mode == DEGRID)
+    return fail(MUSER_ERR_UNSUPPORTED, "the degridding operator uses natural weights (weight_mode 0)");
   if (cfg->peak_mode != 0 && cfg->peak_mode != 1) return fail(MUSER_ERR_ARG, "peak_mode must be 0 or 1");
   if (cfg->thr_mode != 0 && cfg->thr_mode != 1) return fail(MUSER_ERR_ARG, "thr_mode must be 0 or 1");
   if (cfg->max_iter < 0) return fail(MUSER_ERR_ARG, "max_iter must be >= 0");
@@ -96,10 +98,16 @@ struct GridWs {
   float *tab;
   float2 *wtab;
   int32_t *bin_off, *entries;
+  Rec *urec = nullptr;          // uniform weighting: the records with their weights
+  int32_t *ucnt = nullptr;      // uniform weighting: per-instance N-grid cell counts
   void carve(A &a, int B, int64_t n_vis, const muser_config_t &c, bool mirror) {
     const int rows = grid_band_rows(c.G), nb = c.G / rows;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     wtab = carve_wtab(a, c);
+    if (c.weight_mode == 1) {
+      urec = (Rec *)a.template take<Rec>((size_t)n_vis);
+      ucnt = (int32_t *)a.template take<int32_t>((size_t)B * uniform_count_len(c.N));
+    }
     // sized for bands of one row, the narrowest muser_autotune may choose
     bin_off = (int32_t *)a.template take<int32_t>((size_t)B * (c.G + 1));
     entries = (int32_t *)a.template take<int32_t>((size_t)n_vis * (mirror ? 2 : 1) *
@@ -136,6 +144,7 @@ struct ImageWs {
   int32_t *bin_off, *entries;   // per-strip sample lists of the fused gridding
   float *beam[2], *mu_a[2], *mu_b[2], *params;
   int *next[2];
+  int32_t *ucnt = nullptr;      // uniform weighting: per-instance N-grid cell counts of a chunk
   // Steer clean (clean_variant 1): model maps and transform scratch per chunk parity
   float *model[2] = {nullptr, nullptr}, *sY[2] = {nullptr, nullptr};
   float2 *sFB[2] = {nullptr, nullptr}, *sF[2] = {nullptr, nullptr}, *sU[2] = {nullptr, nullptr}, *tw2 = nullptr;
@@ -146,6 +155,7 @@ struct ImageWs {
     rec = (Rec *)a.template take<Rec>((size_t)Bc * n_bl);
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     wtab = carve_wtab(a, c);
+    if (c.weight_mode == 1) ucnt = (int32_t *)a.template take<int32_t>((size_t)Bc * uniform_count_len(c.N));
     bin_off = (int32_t *)a.template take<int32_t>((size_t)Bc * (c.G / S + 1));
     entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(w_footprint(c), c.G, S, c.G));
     d.carve(a, Bc, c);
@@ -429,8 +439,14 @@ int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, int B, int
   launch_pswf_table(w.tab, cfg->W, cfg->os, nullptr, 0, s);
   if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
                           cfg->W, s);
+  const Rec *r = (const Rec *)rec;
+  if (cfg->weight_mode == 1) {            // uniform weights on a copy of the caller's records
+    cudaMemcpyAsync(w.urec, rec, sizeof(Rec) * (size_t)n_vis_total, cudaMemcpyDeviceToDevice, s);
+    launch_uniform_weights(w.urec, vis_off, 0, B, cfg->N, cfg->G, w.ucnt, s);
+    r = w.urec;
+  }
   const int rows = tuned_band_rows(cfg->G, w_footprint(*cfg));
-  launch_grid((const Rec *)rec, vis_off, 0, B, cfg->G, w_footprint(*cfg), cfg->os, w.tab, true, nullptr,
+  launch_grid(r, vis_off, 0, B, cfg->G, w_footprint(*cfg), cfg->os, w.tab, true, nullptr,
               rows > 0 ? rows : grid_band_rows(cfg->G), cfg->G, (float2 *)Z, w.bin_off, w.entries, status, false, s,
               make_wproj(w.wtab, *cfg));
   return check_launch("muser_grid");
@@ -567,6 +583,7 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     float *R = residual + (size_t)c0 * N * N;
     launch_uvw(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_chan, freq_hz, cell_rad, (const float2 *)vis, flags, dlm, c0, n, G,
                Wf, cfg->lat_rad, w.rec, nullptr, status, s);
+    if (cfg->weight_mode == 1) launch_uniform_weights(w.rec, nullptr, n_bl, n, N, G, w.ucnt, s);
     launch_dirty_gridded(w.rec, n_bl, n, N, G, Wf, cfg->os, w.tab, w.bin_off, w.entries, w.d.tw, w.d.gc, w.d.T,
                          w.d.partial, R, w.beam[k], st, s, wp);
     if (cfg->thr_mode == 1) {

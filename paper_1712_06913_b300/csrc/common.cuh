@@ -148,6 +148,11 @@ __host__ __device__ inline int tiles_per_sample(int W, int tr, int tc, int G) {
 // written, so Z need not be cleared.  sorted: bin_off/entries already hold this record set's
 // tile lists (same rec, offsets, G, W, tr, tc, mirror), so the sort is skipped.
 // W is the footprint (the w-kernel support when wp.tab is set).
+// uniform weighting (weights.cu): w of every kept record -> 1 / (samples in its N-grid cell);
+// cnt: B x uniform_count_len(N) int32 of scratch
+size_t uniform_count_len(int N);
+void launch_uniform_weights(Rec *rec, const int64_t *vis_off, int64_t stride, int B, int N, int G, int32_t *cnt,
+                            cudaStream_t s);
 void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, int os,
                  const float *tab, bool mirror, const float2 *vals, int tr, int tc, float2 *Z, int32_t *bin_off,
                  int32_t *entries, int32_t *status, bool sorted, cudaStream_t s, WProj wp = WProj{nullptr, 0, 0, 0.f});

@@ -69,6 +69,15 @@ def test_config_validation_of_the_widened_calls():
             m.workspace_size(m.CALL_GRID, 1, 10, m.Config(N=64, G=256, **kw))
     with pytest.raises(m.MuserError):                                   # no w-projection in the operator
         m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=64, G=128, w_planes=8, w_max=1.0))
+    # uniform weighting: imaging calls only; its scratch (records copy, cell counts) is sized in
+    assert m.workspace_size(m.CALL_GRID, 2, 100, m.Config(N=64, G=256, weight_mode=1)) > \
+        m.workspace_size(m.CALL_GRID, 2, 100, m.Config(N=64, G=256)) + 2 * (64 * 64 + 64) * 4
+    assert m.workspace_size(m.CALL_IMAGE, 2, 100, m.Config(N=64, G=256, weight_mode=1)) > \
+        m.workspace_size(m.CALL_IMAGE, 2, 100, m.Config(N=64, G=256))
+    with pytest.raises(m.MuserError):
+        m.workspace_size(m.CALL_GRID, 1, 10, m.Config(N=64, G=256, weight_mode=2))
+    with pytest.raises(m.MuserError):
+        m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=64, G=128, weight_mode=1))
     # CLEAN variant
     assert m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256, clean_variant=1)) > \
         m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256))

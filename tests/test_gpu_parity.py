@@ -130,6 +130,48 @@ def test_grid_and_dirty_into_caller_buffers(m):
         m.dirty(Z, cfg, out=(Db[:B], Bb[:B, :N]))
 
 
+@pytest.mark.parametrize("name", ["small-N64", "small-N32-3frames", "plain-N256"])
+def test_uniform_weighting_grid_and_dirty(m, name):
+    """weight_mode 1 (Alg. 1's uniform weighting): grids, maps and beams of muser_grid /
+    muser_dirty against the oracle's 1 / (samples per N-grid cell) weights; the caller's
+    records keep their weights (muser_grid weights a copy)."""
+    import dataclasses
+    wl = WORKLOADS[name]()
+    cfg = dataclasses.replace(cfg_for(m, wl), weight_mode=1)
+    rec, _, st, off, _ = gpu_records(m, wl, cfg, want_uvw=False)
+    w_before = m.record_fields(rec)[5].clone()
+    Z, st = m.grid(rec, off, cfg, status=st)
+    D, Bm, st = m.dirty(Z, cfg, status=st)
+    assert bool((m.record_fields(rec)[5] == w_before).all())
+    ro = oracle_records(wl)
+    Zg, Dg, Bg = _np(Z), _np(D), _np(Bm)
+    for i in range(wl.n_inst):
+        ri = geometry.instance_slice(ro, i, wl.n_bl)
+        Zo, Do, Bo, norm = pipeline.dirty(ri, wl.N, wl.G, KER, weight_mode=1)
+        assert np.abs(Zg[i] - Zo).max() <= 1e-5 * np.abs(Zo).max(), i
+        assert np.abs(Dg[i] - Do).max() <= 1e-4 * np.abs(Do).max(), i
+        assert np.abs(Bg[i] - Bo).max() <= 1e-4, i
+    # natural and uniform weighting give different beams (the weights did change)
+    Zn, _ = m.grid(rec, off, dataclasses.replace(cfg, weight_mode=0))
+    assert float((Zn - Z).abs().max()) > 1e-3 * float(Z.abs().max())
+
+
+def test_uniform_weighting_image_end_to_end(m):
+    """muser_image with weight_mode 1 on the plain frame: the CLEAN components in lockstep with
+    the oracle's uniformly weighted dirty map and beam."""
+    import dataclasses
+    wl = synth.config1_plain_frame()
+    cfg = dataclasses.replace(cfg_for(m, wl), weight_mode=1)
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    out = m.image(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    ro = oracle_records(wl)
+    o = pipeline.image_instance(geometry.instance_slice(ro, 0, wl.n_bl), wl.N, wl.G, gain=wl.gain, cap=wl.max_iter,
+                                weight_mode=1)
+    assert int(_np(out.n_comp)[0]) == wl.max_iter
+    lockstep(o["D"], o["Bm"], _np(out.comp_pos)[0], _np(out.comp_flux)[0], wl.gain)
+    np.testing.assert_allclose(_np(out.beam_params)[0], o["S"], rtol=1e-4)
+
+
 def test_dirty_full_size_instance(m):
     """One MUSER-II instance at the largest workload size (N = 1024, G = 4096)."""
     wl = synth.config3_muser2_uneven(n_frame=1, chans=[5, 300])
