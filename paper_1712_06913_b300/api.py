@@ -472,6 +472,64 @@ def image_centred(ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=N
     return out, dlm, shift
 
 
+class CentredImager:
+    """image_centred on device-resident inputs, enqueued with no host synchronisation and
+    replayable from one CUDA graph: uvw -> grid -> dirty -> GMM -> CLEAN down to the disk level
+    mu_b -> disk offset (muser_center) -> phase-corrected muser_image with the sky threshold.
+    `run()` launches it all; `capture()` records it once; `replay()` re-runs the graph (copy new
+    visibilities into `self.vis` first).  Outputs: `self.imager.out` (ImageResult), `self.dlm`
+    [B, 2] rad and `self.shift` [B, 2] px.  The first pass holds every instance's G x G grid."""
+
+    def __init__(self, ant_enu, pairs, ha, dec, freq, cell, vis, cfg: Config, flags=None, pre_cap=1000):
+        self.pre = Config(**{**cfg.__dict__, "thr_mode": 0, "max_iter": pre_cap})
+        self.ant, self.pairs = _dev(ant_enu, torch.float64), _dev(pairs, torch.int32)
+        self.ha, self.dec = _dev(ha, torch.float64), _dev(dec, torch.float64)
+        self.freq, self.cell = _dev(freq, torch.float64), _dev(cell, torch.float64)
+        self.vis = _dev(vis, torch.complex64)
+        self.flags = _dev(flags, torch.uint8) if flags is not None else None
+        F, C, self.nb = len(self.ha), len(self.freq), self.pairs.shape[0]
+        self.B = F * C
+        self.off = torch.arange(self.B + 1, dtype=torch.int64, device="cuda") * self.nb
+        self.cell_b = self.cell.repeat(F)            # instance f * C + c
+        self.dlm = torch.zeros((self.B, 2), dtype=torch.float64, device="cuda")
+        self.shift = torch.zeros((self.B, 2), dtype=torch.float32, device="cuda")
+        self.imager = Imager(self.ant, self.pairs, self.ha, self.dec, self.freq, self.cell, self.vis,
+                             Config(**{**cfg.__dict__, "thr_mode": 1}), flags=self.flags, dlm=self.dlm)
+        self.ws = Workspace()
+        self.graph = None
+
+    def run(self):
+        pre = self.pre
+        rec, _, st = uvw(self.ant, self.pairs, self.ha, self.dec, self.freq, self.cell, self.vis, pre, flags=self.flags)
+        Z, st = grid(rec, self.off, pre, status=st, ws=self.ws, n_vis=self.B * self.nb)
+        D, Bm, st = dirty(Z, pre, status=st, ws=self.ws)
+        del Z
+        mu_a, mu_b, st = gmm(D, pre, status=st)
+        R, _, _, _, st = clean(D, Bm, pre, thr=mu_b, status=st, ws=self.ws)
+        dlm, shift, _, st = center(R, mu_a, mu_b, self.cell_b, pre, status=st, ws=self.ws)
+        self.dlm.copy_(dlm)
+        self.shift.copy_(shift)
+        return self.imager.run()
+
+    def capture(self):
+        """One eager run on a side stream (the library's streams, plans and workspaces), then
+        the whole pipeline recorded in one CUDA graph."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self
+
+    def replay(self):
+        self.graph.replay()
+        return self.imager.out
+
+
 def degrid(direction, rec, cfg: Config, img=None, vis=None, ws: Workspace = None, reuse_plan=False):
     """FORWARD: img [N, N] f32 -> vis [n] complex64.  ADJOINT: vis -> img (real part of A^H vis).
 
