@@ -630,6 +630,8 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__
 // in the cluster exchange of k_hogbom_onchip.  Instances are claimed from a counter, so a batch of
 // fewer instances than SMs still streams on every SM.  The same operations as k_hogbom: the same
 // components and residuals.
+constexpr int kCsBatch = 4;
+
 template <int CS, int MODE>
 __global__ void __launch_bounds__(kOnT, 1) k_hogbom_cstream(float *__restrict__ Rall, const float *__restrict__ beam,
                                                             int N, int B, int *__restrict__ next,
@@ -702,20 +704,37 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_cstream(float *__restrict__ 
       const int py = p.idx / N, px = p.idx % N;
       const float *Bw = Bm + (size_t)(N - py) * (2 * N) + (N - px);
       Peak np{-CUDART_INF_F, 0.f, 0x7fffffff};
-#pragma unroll 2
-      for (int q = q0 + tid; q < q1; q += kOnT) {
-        const int y = q / qpr, x = (q - y * qpr) * 4;
-        const float *b = Bw + (size_t)y * (2 * N) + x;
-        float4 r = R4[q];
-        r.x -= f * __ldg(b);
-        r.y -= f * __ldg(b + 1);
-        r.z -= f * __ldg(b + 2);
-        r.w -= f * __ldg(b + 3);
-        R4[q] = r;
-        consider(np, r.x, 4 * q, MODE);
-        consider(np, r.y, 4 * q + 1, MODE);
-        consider(np, r.z, 4 * q + 2, MODE);
-        consider(np, r.w, 4 * q + 3, MODE);
+      // kCsBatch quads per thread in flight: their residual and beam loads first, then the
+      // updates (the candidate order does not matter: ties go to the lower index)
+#pragma unroll 1
+      for (int qb = q0 + tid; qb < q1; qb += kCsBatch * kOnT) {
+        float4 rr[kCsBatch], bb[kCsBatch];
+#pragma unroll
+        for (int k = 0; k < kCsBatch; k++) {
+          const int q = qb + k * kOnT;
+          if (q < q1) {
+            const int y = q / qpr, x = (q - y * qpr) * 4;
+            const float *b = Bw + (size_t)y * (2 * N) + x;
+            rr[k] = R4[q];
+            bb[k] = make_float4(__ldg(b), __ldg(b + 1), __ldg(b + 2), __ldg(b + 3));
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kCsBatch; k++) {
+          const int q = qb + k * kOnT;
+          if (q < q1) {
+            float4 r = rr[k];
+            r.x -= f * bb[k].x;
+            r.y -= f * bb[k].y;
+            r.z -= f * bb[k].z;
+            r.w -= f * bb[k].w;
+            R4[q] = r;
+            consider(np, r.x, 4 * q, MODE);
+            consider(np, r.y, 4 * q + 1, MODE);
+            consider(np, r.z, 4 * q + 2, MODE);
+            consider(np, r.w, 4 * q + 3, MODE);
+          }
+        }
       }
       p = cluster_argmax<CS, MODE>(packed(np), xch, xk++);
       it++;
