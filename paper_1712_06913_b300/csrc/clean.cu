@@ -112,20 +112,36 @@ __global__ void __launch_bounds__(kCleanThreads) k_hogbom(float *__restrict__ Ra
     // beam element for residual pixel (y, x): Bm[(y - py + N) * 2N + (x - px + N)]
     const float *Bw = Bm + (size_t)(N - py) * (2 * N) + (N - px);
     Peak np{-CUDART_INF_F, 0.f, 0x7fffffff};
-#pragma unroll 2
-    for (int q = threadIdx.x; q < nq; q += kCleanThreads) {
-      const int y = q / qpr, x = (q - y * qpr) * 4;
-      const float *b = Bw + (size_t)y * (2 * N) + x;
-      float4 r = R4[q];
-      r.x -= f * __ldg(b);
-      r.y -= f * __ldg(b + 1);
-      r.z -= f * __ldg(b + 2);
-      r.w -= f * __ldg(b + 3);
-      R4[q] = r;
-      consider(np, r.x, 4 * q, mode);
-      consider(np, r.y, 4 * q + 1, mode);
-      consider(np, r.z, 4 * q + 2, mode);
-      consider(np, r.w, 4 * q + 3, mode);
+    // four quads per thread in flight: their residual and beam loads first, then the updates
+#pragma unroll 1
+    for (int qb = threadIdx.x; qb < nq; qb += 4 * kCleanThreads) {
+      float4 rr[4], bb[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int q = qb + k * kCleanThreads;
+        if (q < nq) {
+          const int y = q / qpr, x = (q - y * qpr) * 4;
+          const float *b = Bw + (size_t)y * (2 * N) + x;
+          rr[k] = R4[q];
+          bb[k] = make_float4(__ldg(b), __ldg(b + 1), __ldg(b + 2), __ldg(b + 3));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const int q = qb + k * kCleanThreads;
+        if (q < nq) {
+          float4 r = rr[k];
+          r.x -= f * bb[k].x;
+          r.y -= f * bb[k].y;
+          r.z -= f * bb[k].z;
+          r.w -= f * bb[k].w;
+          R4[q] = r;
+          consider(np, r.x, 4 * q, mode);
+          consider(np, r.y, 4 * q + 1, mode);
+          consider(np, r.z, 4 * q + 2, mode);
+          consider(np, r.w, 4 * q + 3, mode);
+        }
+      }
     }
     p = block_argmax(np, sh);
     it++;
