@@ -853,7 +853,7 @@ def steer_image_leg(m, wl, cell, cfg, stream, n=296, frames=4, cycles=20):
     return res
 
 
-LARGE = {1280: (148, 148), 2560: (148, 74), 5120: (64, 32)}     # N: (instances, chunk)
+LARGE = {1280: (148, 80), 2560: (148, 74), 5120: (64, 32)}      # N: (instances, chunk)
 
 
 def large_images(m, stream, sizes=(1280, 2560, 5120)):
