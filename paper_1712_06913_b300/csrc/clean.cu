@@ -6,7 +6,8 @@
 //
 // k_hogbom_onchip (N = 256, 512, 1024): the residual never leaves the chip.  Each block of
 //   1024 threads keeps a band of 65536 residual pixels in its SM's tensor memory (256 KB).
-//   N = 256 needs one block per instance, N = 512 a cluster of 4 blocks and N = 1024 a cluster
+//   N = 256 needs one block per instance (a batch of at most 32 instances takes clusters of 4
+//   blocks with 16384-pixel bands instead), N = 512 a cluster of 4 blocks and N = 1024 a cluster
 //   of 16, whose block maxima are exchanged through distributed shared memory (st.async onto
 //   each block's mbarrier) once per iteration.  An iteration then moves only the beam window
 //   (4 N^2 bytes, mostly from L2) instead of 12 N^2 bytes.
@@ -357,6 +358,9 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
                                                            int32_t *__restrict__ status) {
   constexpr bool EXT = NQ > kTmQuads;
   constexpr int SQ = NQ - kTmQuads, kSB = 3;              // shared-memory quads, beam loads in flight
+  constexpr int TQ = NQ < kTmQuads ? NQ : kTmQuads;       // quads in tensor memory (fewer: small bands)
+  constexpr int TB = TQ < kTmBatch ? TQ : kTmBatch;       // beam loads in flight
+  static_assert(TQ % TB == 0 && TB % 2 == 0, "whole batches of column groups");
   static_assert(N * N == CS * NQ * 4 * kOnT, "one band per block");
   static_assert(EXT || (4 * kOnT) % N == 0, "a quad step spans whole rows");
   static_assert(!EXT || (SQ % kSB == 0 && N % 4 == 0), "whole batches of shared-memory quads");
@@ -436,7 +440,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
     {
       const float4 *R4 = reinterpret_cast<const float4 *>(Rb);
 #pragma unroll
-      for (int i = 0; i < kTmQuads; i += 2) {
+      for (int i = 0; i < TQ; i += 2) {
         const float4 a = R4[tid + i * kOnT], b = R4[tid + (i + 1) * kOnT];
         const uint32_t u[8] = {__float_as_uint(a.x), __float_as_uint(a.y), __float_as_uint(a.z), __float_as_uint(a.w),
                                __float_as_uint(b.x), __float_as_uint(b.y), __float_as_uint(b.z), __float_as_uint(b.w)};
@@ -479,15 +483,15 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
         }
       };
       cb = Cand<MODE>();
-      // kTmBatch aligned beam loads in flight, then the residual read, updated and written back
+      // TB aligned beam loads in flight, then the residual read, updated and written back
       // eight cells at a time
 #pragma unroll 1
-      for (int i0 = 0; i0 < kTmQuads; i0 += kTmBatch) {   // not unrolled: keeps the batches apart
-        float4 bb[kTmBatch];
+      for (int i0 = 0; i0 < TQ; i0 += TB) {   // not unrolled: keeps the batches apart
+        float4 bb[TB];
 #pragma unroll
-        for (int k = 0; k < kTmBatch; k++) bb[k] = __ldg(beam_q(i0 + k));
+        for (int k = 0; k < TB; k++) bb[k] = __ldg(beam_q(i0 + k));
 #pragma unroll
-        for (int k = 0; k < kTmBatch; k += 2) {
+        for (int k = 0; k < TB; k += 2) {
           const int i = i0 + k;
           uint32_t u[8];
           tm_ld8(tm + 4 * i, u);
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
     // tensor memory -> residual band
     float4 *R4 = reinterpret_cast<float4 *>(Rb);
 #pragma unroll
-    for (int i = 0; i < kTmQuads; i += 2) {
+    for (int i = 0; i < TQ; i += 2) {
       uint32_t u[8];
       tm_ld8(tm + 4 * i, u);
       tm_wait_ld();
@@ -983,7 +987,12 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
   if (B <= 0) return;
   bool done = false;
   if (beam4 && next) {
-    if (N == 256)
+    // 256^2: one block per instance fills the SMs with many instances; a batch of a few
+    // instances runs faster in clusters of 4 blocks (16384-pixel bands, 4 quads per thread)
+    if (N == 256 && B <= 32)
+      done = launch_onchip<256, 4, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+                                       s);
+    if (N == 256 && !done)
       done = launch_onchip<256, 1>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 512)
       done = launch_onchip<512, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
