@@ -7,8 +7,9 @@
 // k_hogbom_onchip (N = 256, 512, 1024): the residual never leaves the chip.  Each block of
 //   1024 threads keeps a band of 65536 residual pixels in its SM's tensor memory (256 KB).
 //   N = 256 needs one block per instance (a batch of at most 32 instances takes clusters of 4
-//   blocks with 16384-pixel bands instead), N = 512 a cluster of 4 blocks and N = 1024 a cluster
-//   of 16, whose block maxima are exchanged through distributed shared memory (st.async onto
+//   blocks with 16384-pixel bands instead), N = 512 a cluster of 4 blocks (at most 7 instances:
+//   16 blocks with 16384-pixel bands) and N = 1024 a cluster of 16, whose block maxima are
+//   exchanged through distributed shared memory (st.async onto
 //   each block's mbarrier) once per iteration.  An iteration then moves only the beam window
 //   (4 N^2 bytes, mostly from L2) instead of 12 N^2 bytes.
 // k_hogbom (any N, fallback): one block per instance streams the residual from HBM every
@@ -994,7 +995,11 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
                                        s);
     if (N == 256 && !done)
       done = launch_onchip<256, 1>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
-    if (N == 512)
+    // 512^2: clusters of 4 blocks; a batch of a few instances in clusters of 16 (4 quads per thread)
+    if (N == 512 && B <= 7)
+      done = launch_onchip<512, 16, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+                                        s);
+    if (N == 512 && !done)
       done = launch_onchip<512, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 1024)
       done = launch_onchip<1024, 16>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);

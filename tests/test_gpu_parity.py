@@ -204,7 +204,9 @@ ONCHIP_CASES = {
     # 6 instances: clusters of 4 blocks with 16384-pixel bands; 40: one block per instance
     "N256x6": lambda: synth.small_workload(n_ant=31, N=256, n_frame=6, config_id=230, bmax=2000.0),
     "N256x40": lambda: synth.small_workload(n_ant=31, N=256, n_frame=40, config_id=231, bmax=2000.0),
+    # 2 instances: clusters of 16 blocks with 16384-pixel bands; 12: clusters of 4
     "N512x2": lambda: synth.config2_muser1_band(n_frame=1, chans=[10, 50]),
+    "N512x12": lambda: synth.config2_muser1_band(n_frame=1, chans=list(range(4, 64, 5))),
     "N1024x2": lambda: synth.config3_muser2_uneven(n_frame=1, chans=[7, 400]),
 }
 
