@@ -1,36 +1,69 @@
-"""Build libmuser.so in-tree with nvcc for sm_103a (B300)."""
+"""Build libmuser.so in-tree with nvcc for sm_103a (B300).
+
+Each .cu file compiles to its own object (in parallel, under _build/), then one nvcc call
+links the shared library.  Device code never calls across files, so no relocatable device
+code is needed.
+"""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmuser.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
-         "-shared"]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]
 
 
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _headers():
+    return glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "muser.h")]
+
+
 def stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "muser.h")]
-    return any(os.path.getmtime(p) > t for p in deps)
+    return any(os.path.getmtime(p) > t for p in sources() + _headers())
+
+
+def _obj(src):
+    return os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+
+
+def _compile(src, extra, verbose, force):
+    o = _obj(src)
+    if not force and os.path.exists(o):
+        t = os.path.getmtime(o)
+        if all(os.path.getmtime(p) <= t for p in [src] + _headers()):
+            return o
+    cmd = [NVCC, *FLAGS, *extra, "-c", "-o", o + ".tmp", src]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.run(cmd, check=True)
+    os.replace(o + ".tmp", o)
+    return o
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not stale():
         return LIB
-    cmd = [NVCC, *FLAGS, *extra, "-o", LIB + ".tmp", *sources()]
+    os.makedirs(OBJ, exist_ok=True)
+    srcs = sources()
+    # an extra flag set changes every object: rebuild them all
+    rebuild = force or bool(extra)
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, list(extra), verbose, rebuild), srcs))
+    cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)

@@ -157,3 +157,38 @@ def test_wproj_screen_sign_flipped_is_caught(monkeypatch):
     monkeypatch.setattr(wproj, "kernel_tables", bad)
     _fails(pins.test_wproj_dirty_matches_direct_transform_with_w)
     _fails(pins.test_wproj_kernel_image_plane_is_screen_times_correction)
+
+
+def test_lipschitz_without_hessian_factor_two_is_caught(monkeypatch):
+    def bad(rec, N, G, ker, sigma, iters=20, seed=0, K=None):
+        rng = np.random.default_rng(seed)
+        x = rng.standard_normal((N, N))
+        x /= np.linalg.norm(x)
+        lam = 0.0
+        for _ in range(iters):                    # the factor 2 of d2 chi2 / dx2 dropped
+            y = operator.adjoint(operator.forward(x, rec, N, G, ker, K) * rec["w"], rec, N, G, ker, K).real / sigma ** 2
+            lam = float(np.linalg.norm(y))
+            x = y / lam
+        return lam
+    monkeypatch.setattr(operator, "lipschitz", bad)
+    _fails(pins.test_lipschitz_is_the_largest_hessian_eigenvalue)
+
+
+def test_uniform_weights_without_mirror_count_is_caught(monkeypatch):
+    def bad(rec, G, N):
+        keep = rec["w"] > 0
+        r = np.float32(G // N)
+
+        def cell(k, f):
+            t = np.float32(k - G // 2).astype(np.float32) - np.asarray(f, np.float32)
+            return np.floor((t / r).astype(np.float32) + np.float32(N // 2) + np.float32(0.5)).astype(np.int64)
+        cu = cell(rec["ku"][keep], rec["fu"][keep])
+        cv = cell(rec["kv"][keep], rec["fv"][keep])
+        keys = cv * N + cu                        # the -uv mirrors are not counted
+        uniq, counts = np.unique(keys, return_counts=True)
+        cnt = dict(zip(uniq.tolist(), counts.tolist()))
+        w = np.zeros(len(rec["w"]))
+        w[np.nonzero(keep)[0]] = [1.0 / cnt[int(k)] for k in keys]
+        return w
+    monkeypatch.setattr(imaging, "uniform_weights", bad)
+    _fails(pins.test_uniform_weights_from_fp64_uv_cells)

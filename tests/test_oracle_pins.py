@@ -215,6 +215,37 @@ def test_uniform_weights_matches_weighted_dft_and_sums_to_one_per_cell():
     assert np.abs(Bm - Bd).max() <= 4e-4
 
 
+def test_uniform_weights_from_fp64_uv_cells():
+    """Uniform weighting decided independently of the oracle's FP32 cell rule: the N-grid
+    cell of every sample is taken in FP64 straight from (u, v) (cell = floor(u N cell_rad +
+    N/2 + 1/2), the mirror at -u, -v), on inputs with no sample near a cell boundary.  Then
+    every occupied cell carries total weight 1 and all its samples the same weight 1/count
+    (Alg. 1 weighting mode; the count includes the -uv mirrors)."""
+    wl, rec = _tiny(N=32, n_ant=10, seed_cfg=104, bmax=200.0)
+    N, G = wl.N, wl.G
+    w = imaging.uniform_weights(rec, G, N)
+    keep = np.nonzero(rec["w"] > 0)[0]
+    cell = pipeline.cell_sizes(wl)[0]
+    u = rec["uvw"][keep, 0] * N * cell
+    v = rec["uvw"][keep, 1] * N * cell
+    for t in (u, v):
+        frac = t - np.floor(t)
+        assert np.all(np.abs(frac - 0.5) > 1e-6), "seeded input has a sample on an N-grid cell boundary"
+    cu = np.floor(u + N / 2 + 0.5).astype(int)
+    cv = np.floor(v + N / 2 + 0.5).astype(int)
+    mu = np.floor(-u + N / 2 + 0.5).astype(int)
+    mv = np.floor(-v + N / 2 + 0.5).astype(int)
+    members = {}
+    for j, i in enumerate(keep):
+        members.setdefault((cv[j], cu[j]), []).append(w[i])
+        members.setdefault((mv[j], mu[j]), []).append(w[i])
+    assert any(len(ws) > 1 for ws in members.values())
+    for key, ws in members.items():
+        ws = np.asarray(ws)
+        assert np.all(ws == ws[0]), key
+        assert ws.sum() == pytest.approx(1.0, abs=1e-12), key
+
+
 # ----------------------------------------------------------------------------- GMM
 def test_gmm_recovers_known_mixture():
     rng = np.random.default_rng(5)
@@ -461,6 +492,42 @@ def test_gradient_descent_decreases_chi2():
     x, hist = operator.gradient_descent(rec, rec["vis"], 0.5, N, G, KER, steps=15)
     assert np.all(np.diff(hist) <= 1e-9 * hist[0])
     assert hist[-1] < 0.5 * hist[0]
+
+
+def _hessian_from_gradients(rec, N, G, sigma):
+    """Dense Hessian of chi2 on a tiny image, column j = grad(e_j) - grad(0) (chi2 is
+    quadratic, so this is exact up to rounding; the gradient itself is pinned by finite
+    differences of chi2 above)."""
+    g0 = operator.chi2_grad(np.zeros((N, N)), rec, rec["vis"], sigma, N, G, KER)[1].ravel()
+    H = np.zeros((N * N, N * N))
+    for j in range(N * N):
+        e = np.zeros(N * N)
+        e[j] = 1.0
+        H[:, j] = operator.chi2_grad(e.reshape(N, N), rec, rec["vis"], sigma, N, G, KER)[1].ravel() - g0
+    return H
+
+
+def _tiny_operator(N=8):
+    wl = synth.small_workload(n_ant=7, N=N, config_id=122, bmax=20.0, freq=np.linspace(1.0e9, 1.6e9, 3))
+    G = 2 * N
+    cell = np.full(wl.n_chan, geometry.pixel_size(wl.freq.max(), wl.bmax, N, 60 * synth.ARCMIN))
+    uvw = geometry.uvw(wl.ant_enu, wl.pairs, wl.lat, wl.ha, wl.dec, wl.freq)
+    rec = geometry.grid_records(uvw, wl.vis, wl.flags, cell, G, 7)
+    assert (rec["w"] > 0).sum() >= 40
+    return rec, G
+
+
+def test_lipschitz_is_the_largest_hessian_eigenvalue():
+    """The step size of gradient imaging, eta = 1/L: L from power iteration equals the largest
+    eigenvalue of the dense chi2 Hessian (numpy eigvalsh) on an 8 x 8 image."""
+    N, sigma = 8, 0.7
+    rec, G = _tiny_operator(N)
+    H = _hessian_from_gradients(rec, N, G, sigma)
+    assert np.abs(H - H.T).max() <= 1e-9 * np.abs(H).max()      # a Hessian is symmetric
+    ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+    assert ev[0] >= -1e-9 * ev[-1]                              # and positive semi-definite
+    L = operator.lipschitz(rec, N, G, KER, sigma, iters=120)
+    assert L == pytest.approx(ev[-1], rel=1e-10)
 
 
 # ----------------------------------------------------------------------------- w-projection
