@@ -10,8 +10,10 @@ restore, batched in chunks of 296 instances (2 x 148 SMs).  Synthetic, seeded in
 Reported (one JSON line on rank 0):
   value      CLEANed images/s, inputs resident on the device (muser_image per step)
   e2e        the same with the visibilities copied from pinned host memory every step and
-             the CLEAN model (component lists, counts, status) read back
-  roofline   the dominant kernel (CLEAN) against the measured HBM copy bandwidth
+             the restored images, component lists, counts and status read back (on a copy
+             stream, overlapping the next step)
+  roofline   the dominant kernel (CLEAN): its streaming-model bytes per second against the
+             measured HBM copy bandwidth, with the DRAM and L2 fractions it actually reaches
   cpu_baseline  the FP64 oracle on a bounded sample on this host's cores
   extra      plain one-image-per-call throughput, gridding GB/s, gradient evaluations/s
 
@@ -59,6 +61,19 @@ def center_bytes(N):
     P, W = 2 * N, N // 2 + 1
     H = P // 2 + 1
     return 4.0 * N * N + 2 * 8.0 * N * P + 2 * 8.0 * H * P + 2 * 8.0 * W * H + 4.0 * W * W
+
+STATUS_BITS = ("ALL_FLAGGED", "NONFINITE", "DROPPED", "GMM_DEGENERATE", "ITER_CAP", "BEAM_FIT", "TIMEOUT", "NO_DISK")
+
+
+def status_histogram(status):
+    """Instances per status bit (MUSER_ST_*), plus those with no bit set."""
+    import numpy as np
+    st = np.asarray(status)
+    out = {name: int(((st >> b) & 1).sum()) for b, name in enumerate(STATUS_BITS)}
+    out["none"] = int((st == 0).sum())
+    out["unknown_bits"] = int((st & ~((1 << len(STATUS_BITS)) - 1) != 0).sum())
+    return out
+
 
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -280,30 +295,60 @@ def main():
     status = out.status.cpu().numpy()
     gpu_launches = launches1 - launches0   # counted by the library as it enqueues its kernels
 
-    # ---- end to end: pinned host visibilities in, CLEAN model out, every step
+    # ---- end to end: pinned host visibilities in; restored images, CLEAN model and status out,
+    # every step.  Two output sets alternate, so that step k's results stream to the host on a
+    # copy stream while step k + 1 is imaged.
     vis_host = torch.from_numpy(np.ascontiguousarray(vis.astype(np.complex64))).pin_memory()
     vis_dev = torch.empty_like(vis_host, device="cuda")
+    outs = [out, imager.new_output()]
+    clean_bytes_all = out.clean.numel() * 4
+    avail = 0                              # room for every restored image in pinned host memory?
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    avail = int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    n_img = B if avail > 3 * clean_bytes_all else max(1, min(B, int(avail // (3 * 4 * wl.N * wl.N))))
+    clean_host = torch.empty((n_img, wl.N, wl.N), dtype=torch.float32).pin_memory()
     pos_host = torch.empty(out.comp_pos.shape, dtype=torch.int32).pin_memory()
     flux_host = torch.empty(out.comp_flux.shape, dtype=torch.float32).pin_memory()
     nc_host = torch.empty(B, dtype=torch.int32).pin_memory()
     st_host = torch.empty(B, dtype=torch.int32).pin_memory()
     h2d = vis_host.numel() * 8
-    d2h = pos_host.numel() * 4 + flux_host.numel() * 4 + 2 * B * 4
+    d2h = clean_host.numel() * 4 + pos_host.numel() * 4 + flux_host.numel() * 4 + 2 * B * 4
+    copy_stream = torch.cuda.Stream()
+    imaged = [torch.cuda.Event() for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
     for k in range(args.steps):
+        j = k & 1
+        if k >= 2:
+            stream.wait_event(copied[j])    # this output set's copy from step k - 2 is done
         vis_dev.copy_(vis_host, non_blocking=True)
-        o = imager.run(vis_dev)
-        pos_host.copy_(o.comp_pos, non_blocking=True)
-        flux_host.copy_(o.comp_flux, non_blocking=True)
-        nc_host.copy_(o.n_comp, non_blocking=True)
-        st_host.copy_(o.status, non_blocking=True)
+        o = imager.run(vis_dev, out=outs[j])
+        imaged[j].record(stream)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(imaged[j])
+            clean_host.copy_(o.clean[:n_img], non_blocking=True)
+            pos_host.copy_(o.comp_pos, non_blocking=True)
+            flux_host.copy_(o.comp_flux, non_blocking=True)
+            nc_host.copy_(o.n_comp, non_blocking=True)
+            st_host.copy_(o.status, non_blocking=True)
+            copied[j].record(copy_stream)
+    stream.wait_stream(copy_stream)
     e1.record(stream)
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     e2e_value = B * world * args.steps / (e2e_ms / 1e3)
     assert np.array_equal(nc_host.numpy(), n_comp)
+    e2e_images = ("every restored image" if n_img == B else
+                  f"restored images of the first {n_img} of {B} instances (host memory)")
+    del outs
+    imager.out = out
 
     # ---- the same batch replayed from one CUDA graph (every chunk, both streams)
     imager.capture()
@@ -380,24 +425,35 @@ def main():
     del Z, Zbuf, Dbuf, Bbuf
     torch.cuda.empty_cache()
     clean_ms = statistics.mean(phase["clean"])
-    achieved = statistics.mean(clean_bytes) / (clean_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
     tr = recorded_traffic()
-    roofline = {"kernel": "muser_clean: k_beam_shift + k_hogbom_onchip", "bound": "hbm", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                "bytes_per_launch": statistics.mean(clean_bytes),
-                "launch_ms": clean_ms,
-                "traffic": (statistics.mean(clean_bytes) * tr["dram_per_algorithmic"]) if tr else None,
-                "traffic_source": (f"ncu dram bytes of {tr['case']}, scaled to this launch by algorithmic "
+    # algorithmic bytes of the CLEAN call by the streaming-residual model: every iteration reads the
+    # residual and one beam window and writes the residual (12 N^2), plus the residual's first read
+    stream_model = statistics.mean(hbm_equiv_bytes)
+    achieved = stream_model / (clean_ms / 1e3) / 1e9
+    traffic = statistics.mean(clean_bytes) * tr["dram_per_algorithmic"] if tr else None
+    roofline = {"kernel": "muser_clean: k_beam_shift + k_hogbom_onchip", "bound": "latency",
+                "bound_detail": ("the residual stays on chip, so DRAM is not the limit: an iteration is the "
+                                 "beam-window loads, the tensor-memory pass and the 16-block cluster exchange "
+                                 "one after the other (SM time and exchange latency)"),
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": peak_kind,
+                "bytes_model": "12 N^2 per iteration (residual read + beam window read + residual write) + 4 N^2",
+                "bytes_per_launch": stream_model, "launch_ms": clean_ms,
+                "traffic": traffic,
+                "traffic_source": (f"ncu dram bytes of {tr['case']}, scaled to this launch by on-chip-design "
                                    "bytes") if tr else None,
-                "note": "beam windows are served mostly from L2, so achieved bytes/s can exceed the HBM copy rate",
-                "hbm_equivalent_GBps": statistics.mean(hbm_equiv_bytes) / (clean_ms / 1e3) / 1e9}
+                "dram_GBps": traffic / (clean_ms / 1e3) / 1e9 if tr else None,
+                "dram_frac": traffic / (clean_ms / 1e3) / 1e9 / peak if tr else None,
+                "l2_frac": tr.get("lts_throughput") if tr else None,
+                "onchip_design_GBps": statistics.mean(clean_bytes) / (clean_ms / 1e3) / 1e9,
+                "onchip_design_bytes": "4 N^2 beam window per iteration + 8 N^2 residual in/out + 64 N^2 beam copies"}
     grid_bytes = args.chunk * (32.0 * wl.n_bl + 8.0 * G * G)
     extra = {"phase_ms_per_chunk": {k: statistics.mean(v) for k, v in phase.items()},
              "gridding_GBps": grid_bytes / (statistics.mean(phase["grid"]) / 1e3) / 1e9,
              "dirty_fft_GBps": args.chunk * (8.0 * G * G + 4.0 * G * G * 2 + 4.0 * N * N + 16.0 * N * N)
              / (statistics.mean(phase["dirty"]) / 1e3) / 1e9,
-             "n_comp_min": int(n_comp.min()), "status_nonzero": int((status != 0).sum()),
+             "n_comp_min": int(n_comp.min()), "status_bits": status_histogram(status),
              "graph_replay_images_per_s": graph_value,
              "autotuned": tuned,
              "center_ms_per_chunk": center_ms,
@@ -429,7 +485,8 @@ def main():
                                  "copies) and 283 GB of column-pass output stream through HBM"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "images/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                        "d2h_bytes_per_step": d2h,
+                        "copies": "visibilities H2D; " + e2e_images + ", component lists, counts and status D2H"},
                 "gpu_launches": gpu_launches, "clocks": clk, "extra": extra}
         print(json.dumps(line), flush=True)
     if world > 1:

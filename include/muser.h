@@ -182,21 +182,23 @@ MUSER_API int muser_grid(const muser_vis_record_t *rec, const int64_t *vis_off, 
 MUSER_API int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam, void *ws,
                 size_t ws_bytes, int32_t *status, muser_stream_t stream);
 
-/* Size of the library-owned scratch array used by muser_dirty_noalloc (16 MiB). */
-#define MUSER_NOALLOC_SCRATCH_BYTES (16u << 20)
+/* Size of the library-owned scratch array used by muser_dirty_noalloc (16 MiB + 64 KiB). */
+#define MUSER_NOALLOC_SCRATCH_BYTES ((16u << 20) + (64u << 10))
 
 /* muser_dirty without a workspace, for callers that cannot allocate device memory (for
  * example a host application whose device memory belongs to another allocator or a fixed
  * budget, or code that must not call cudaMalloc/cudaFree because they synchronise the
  * device).  The paper has no counterpart: this is a deployment variant of muser_dirty.
- * Same arguments, results and status bits as muser_dirty, minus ws/ws_bytes.  Scratch
- * comes from one static device array of MUSER_NOALLOC_SCRATCH_BYTES inside the library,
- * held by every GPU that loads the library until exit.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress, with that device current): make it
- * before any stream capture.  All calls share the array, so calls that may overlap on the
- * GPU (other streams or host threads) race and must be serialised.  A batch whose scratch
- * exceeds the array, about B * (G/2) * G * 8 bytes, returns MUSER_ERR_ARG; no device memory
- * is ever allocated. */
+ * It is muser_dirty (same arguments minus ws/ws_bytes, same checks, kernels, tuned launch
+ * shape, results and status bits) with its workspace taken from one static device array of
+ * MUSER_NOALLOC_SCRATCH_BYTES inside the library, held by every GPU that loads the library
+ * until exit.  A batch fits when muser_workspace_size(MUSER_CALL_DIRTY, B, 0, cfg) is at most
+ * that size: one instance at N = 512, four at N = 256, two at N = 320; none at N = 1024.
+ * Larger batches return MUSER_ERR_ARG; no device memory is ever allocated.  The first call on a
+ * device (and the first in a new context of it, e.g. after cudaDeviceReset) looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current): make it before any
+ * stream capture.  All calls share the array, so calls that may overlap on the GPU (other
+ * streams or host threads) race and must be serialised. */
 MUSER_API int muser_dirty_noalloc(const float *Z, int B, const muser_config_t *cfg, float *dirty, float *beam,
                                   int32_t *status, muser_stream_t stream);
 
@@ -312,6 +314,38 @@ MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser
 MUSER_API int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_t n_vis, const float *obs,
                               float inv_sigma2, float eta, float *loss, float *grad, const muser_config_t *cfg,
                               void *ws, size_t ws_bytes, muser_stream_t stream);
+
+/* Step size of gradient imaging (Sec. 3.2.3 operator, transposed; the descent x <- x - eta grad chi2
+ * with eta = 1/L): L = largest eigenvalue of the chi-square Hessian H = 2 Re(A^H W A) / sigma^2,
+ * W = diag(w_k), found by power iteration.
+ *
+ * muser_normal_apply:  u = H v for one real image v[N][N] (device, read) into u[N][N] (device, written;
+ *   may alias v).  A is muser_degrid's operator on rec[n_vis]; the weights w_k are the records'.
+ * muser_normalize:  norm[0] = ||u||_2 over n floats, v = u / norm[0] (v = 0 if u = 0); v may alias u;
+ *   all device.  One block: meant for the power iteration's N x N directions, not for bulk data.
+ * muser_lipschitz:  v[N][N] (device, in: any non-zero start vector, out: the last unit direction);
+ *   v <- v / ||v||, then `iters` times: u = H v, L[0] = ||u||, v = u / L[0].  L (device float, out).
+ * Under several ranks (channels split across processes) H is the sum of the ranks' Hessians: call
+ * muser_normal_apply, sum u over the ranks, then muser_normalize, `iters` times.
+ * flags (normal_apply, lipschitz): 0 builds the operator's plan in ws, MUSER_REUSE_PLAN reuses the plan
+ * an earlier muser_degrid / muser_grad_step / muser_normal_apply / muser_lipschitz built in the same ws
+ * for the same records.  ws: muser_workspace_size(MUSER_CALL_GRAD, 1, n_vis, cfg) bytes.
+ * inv_sigma2 = 1 / sigma^2 > 0.  Errors: MUSER_ERR_ARG for bad sizes, flags, pointers or sigma. */
+MUSER_API int muser_normal_apply(int flags, const float *v, float *u, const muser_vis_record_t *rec, int64_t n_vis,
+                                 float inv_sigma2, const muser_config_t *cfg, void *ws, size_t ws_bytes,
+                                 muser_stream_t stream);
+MUSER_API int muser_normalize(const float *u, int64_t n, float *v, float *norm, muser_stream_t stream);
+MUSER_API int muser_lipschitz(int flags, float *v, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2,
+                              int iters, float *L, const muser_config_t *cfg, void *ws, size_t ws_bytes,
+                              muser_stream_t stream);
+
+/* The descent update and other scaled sums of gradient imaging: y[i] += alpha * s * x[i] for
+ * i < n, with s = alpha_dev[0] (a device float, e.g. the incoming gradient of a loss) or 1 when
+ * alpha_dev is NULL.  x, y device floats (y in/out; complex data as 2n floats).  The multi-rank step
+ * is muser_grad_step with eta = 0 and a gradient output, a sum over ranks, then
+ * muser_axpy(img, grad, N*N, -eta, NULL).  alpha must be finite. */
+MUSER_API int muser_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev,
+                         muser_stream_t stream);
 
 /* Launch-shape autotuner.  Times the candidates of one call's launch shape on the given batch
  * and keeps the fastest for later calls of this process with the same grid size (and

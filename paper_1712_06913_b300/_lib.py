@@ -58,6 +58,10 @@ SIGNATURES = {
     "muser_center": (I32, [P, P, P, P, I32, CFG, P, P, P, P, SZ, P, P]),
     "muser_steer": (I32, [P, P, I32, CFG, P, F32, P, P, P, SZ, P, P]),
     "muser_grad_step": (I32, [I32, P, P, I64, P, F32, F32, P, P, CFG, P, SZ, P]),
+    "muser_normal_apply": (I32, [I32, P, P, P, I64, F32, CFG, P, SZ, P]),
+    "muser_normalize": (I32, [P, I64, P, P, P]),
+    "muser_lipschitz": (I32, [I32, P, P, I64, F32, I32, P, CFG, P, SZ, P]),
+    "muser_axpy": (I32, [P, P, I64, F32, P, P]),
     "muser_selftest_wait": (I32, [ctypes.c_longlong, P, P]),
     "muser_autotune": (I32, [I32, P, P, I32, I64, CFG, P, P]),
     "muser_set_tuning": (I32, [I32, CFG, I32]),

@@ -275,8 +275,16 @@ class Imager:
         self.F, self.C, self.nb = len(self.ha), len(self.freq), self.pairs.shape[0]
         B, N, cap = self.F * self.C, cfg.N, cfg.max_iter
         self.B = B
-        dev = "cuda"
-        self.out = ImageResult(
+        self.out = self.new_output()
+        self.ws = Workspace()
+        self.ws_bytes = workspace_size(CALL_IMAGE, B, self.nb, cfg)
+        self.c = cfg.c()
+
+    def new_output(self):
+        """A fresh set of output tensors for this batch shape (e.g. a second set, so that one
+        batch's results can be copied out while the next batch is imaged)."""
+        B, N, cap, dev = self.B, self.cfg.N, self.cfg.max_iter, "cuda"
+        return ImageResult(
             clean=torch.empty((B, N, N), dtype=torch.float32, device=dev),
             residual=torch.empty((B, N, N), dtype=torch.float32, device=dev),
             comp_pos=torch.zeros((B, max(cap, 1)), dtype=torch.int32, device=dev),
@@ -285,14 +293,12 @@ class Imager:
             thr=torch.empty(B, dtype=torch.float32, device=dev),
             beam_params=torch.empty((B, 3), dtype=torch.float32, device=dev),
             status=torch.empty(B, dtype=torch.int32, device=dev))
-        self.ws = Workspace()
-        self.ws_bytes = workspace_size(CALL_IMAGE, B, self.nb, cfg)
-        self.c = cfg.c()
 
-    def run(self, vis=None):
-        """Launch the whole batch on the current stream (no host synchronisation)."""
+    def run(self, vis=None, out=None):
+        """Launch the whole batch on the current stream (no host synchronisation), writing
+        `out` (default: self.out)."""
         V = self.vis if vis is None else vis
-        o = self.out
+        o = self.out if out is None else out
         w, wb = self.ws.get(self.ws_bytes)
         check(_lib.load().muser_image(
             _p(self.ant), self.ant.shape[0], _p(self.pairs), self.nb, _p(self.ha), _p(self.dec), self.F,
@@ -600,6 +606,25 @@ class DegridPlan:
                                        ctypes.byref(self.c), self.w, self.wb, _stream()))
         self.planned = True
 
+    def normal_apply(self, v, inv_sigma2: float, out=None):
+        """u = 2 Re A^H (w A v) / sigma^2, the chi-square Hessian applied to v (muser_normal_apply)."""
+        v = v.contiguous()
+        u = torch.empty((self.cfg.N, self.cfg.N), dtype=torch.float32, device="cuda") if out is None else out
+        check(self.lib.muser_normal_apply(_lib.REUSE_PLAN if self.planned else 0, _p(v), _p(u), _p(self.rec), self.n,
+                                          float(inv_sigma2), ctypes.byref(self.c), self.w, self.wb, _stream()))
+        self.planned = True
+        return u
+
+    def lipschitz(self, v, inv_sigma2: float, iters: int, L=None):
+        """Power iteration on the chi-square Hessian from the start direction v (updated in place to
+        the last unit direction): L [1] (device) = its largest eigenvalue (muser_lipschitz)."""
+        L = torch.empty(1, dtype=torch.float32, device="cuda") if L is None else L
+        check(self.lib.muser_lipschitz(_lib.REUSE_PLAN if self.planned else 0, _p(v), _p(self.rec), self.n,
+                                       float(inv_sigma2), int(iters), _p(L), ctypes.byref(self.c), self.w, self.wb,
+                                       _stream()))
+        self.planned = True
+        return L
+
     def chi2(self, pred, obs, inv_sigma2: float):
         """(loss, residual seed) of predicted visibilities against obs (see muser_chi2)."""
         loss = torch.empty(1, dtype=torch.float32, device="cuda")
@@ -617,3 +642,22 @@ def chi2(pred, obs, rec, inv_sigma2: float, want_resid=True, ws: Workspace = Non
     check(_lib.load().muser_chi2(_p(pred.contiguous()), _p(obs.contiguous()), _p(rec), n, float(inv_sigma2), _p(resid),
                                  _p(loss), w, wb, _stream()))
     return loss[0], resid
+
+
+def normalize(u, v=None, norm=None):
+    """norm [1] (device) = |u|_2 and v = u / norm (muser_normalize); v may be u itself."""
+    v = torch.empty_like(u) if v is None else v
+    norm = torch.empty(1, dtype=torch.float32, device="cuda") if norm is None else norm
+    check(_lib.load().muser_normalize(_p(u), u.numel(), _p(v), _p(norm), _stream()))
+    return v, norm
+
+
+def axpy(y, x, alpha: float, alpha_dev=None):
+    """y += alpha * (alpha_dev[0] if given else 1) * x in place (muser_axpy); complex tensors are
+    taken as pairs of floats."""
+    if y.is_complex():
+        y, x = torch.view_as_real(y), torch.view_as_real(x)
+    if not (y.is_contiguous() and x.is_contiguous() and y.numel() == x.numel()):
+        raise ValueError("axpy: x and y must be contiguous and of one size")
+    check(_lib.load().muser_axpy(_p(y), _p(x), y.numel(), float(alpha), _p(alpha_dev), _stream()))
+    return y

@@ -4,7 +4,10 @@ Degrid.forward  = muser_degrid(FORWARD):  sky image x [N, N] -> predicted visibi
 Degrid.backward = muser_degrid(ADJOINT):  grad_x = Re A^H grad_v.  For a real loss, torch
 passes grad_v = dL/dRe v + i dL/dIm v, and dL/dx = Re(A^H grad_v) because A is linear.
 Chi2.forward    = muser_chi2: sum_k w_k |v_k - obs_k|^2 / sigma^2; its backward returns the
-kernel's residual seed 2 w (v - obs) / sigma^2 times the incoming gradient.
+kernel's residual seed 2 w (v - obs) / sigma^2 times the incoming gradient (muser_axpy).
+
+Every step of the arithmetic is a library call; this module only allocates tensors and passes
+them on (and, across ranks, sums tensors with torch.distributed).
 """
 from __future__ import annotations
 
@@ -38,7 +41,9 @@ class Chi2(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_loss):
         (resid,) = ctx.saved_tensors
-        return resid * grad_loss, None, None, None
+        out = torch.zeros_like(resid)
+        api.axpy(out, resid, 1.0, grad_loss.detach().reshape(1).float().contiguous())
+        return out, None, None, None
 
 
 def chi2_loss(img, plan, obs, inv_sigma2):
@@ -72,35 +77,50 @@ class GradientImaging:
         self.graph = None
 
     def lipschitz(self, iters=20, seed=0):
-        """Largest eigenvalue of the chi2 Hessian 2 Re(A^H W A)/sigma^2 by power iteration."""
+        """Largest eigenvalue of the chi2 Hessian 2 Re(A^H W A)/sigma^2 by power iteration from a
+        seeded random start direction (muser_lipschitz; across ranks the Hessian products are summed
+        before each normalisation).  Returns L as a Python float."""
         import torch
         g = torch.Generator(device="cuda").manual_seed(seed)
         v = torch.randn((self.cfg.N, self.cfg.N), generator=g, device="cuda")
-        v /= torch.linalg.norm(v)
-        lam = 0.0
-        for _ in range(iters):
-            y = self.plan.forward(v)
-            u = _dist.all_sum_(self.plan.adjoint(y) * (2.0 * self.inv_s2))
-            lam = float(torch.linalg.norm(u))
-            v = u / lam
-        return lam
+        if _dist.rank_world()[1] == 1:
+            L = self.plan.lipschitz(v, self.inv_s2, iters)
+        else:
+            L = torch.empty(1, dtype=torch.float32, device="cuda")
+            api.normalize(v, v, L)
+            u = torch.empty_like(v)
+            for _ in range(iters):
+                self.plan.normal_apply(v, self.inv_s2, out=u)
+                _dist.all_sum_(u)
+                api.normalize(u, v, L)
+        return float(L[0])
+
+    def _buffers(self):
+        import torch
+        if not hasattr(self, "_loss_buf"):
+            self._loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
+            self._grad_buf = torch.zeros((self.cfg.N, self.cfg.N), dtype=torch.float32, device="cuda")
 
     def step(self):
         """One step.  In a single process one library call does it all (muser_grad_step: forward,
-        chi-square, adjoint and update); across ranks the loss and gradient go through the
-        autograd functions and are summed over ranks before the update."""
+        chi-square, adjoint and update).  Across ranks each rank's call returns its loss and gradient
+        (eta = 0 leaves the image), both are summed over ranks, and muser_axpy applies the update."""
         import torch
-        if _dist.rank_world()[1] == 1 and self.cfg.W <= 8:
-            if not hasattr(self, "_loss_buf"):
-                self._loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
-            with torch.no_grad():
+        self._buffers()
+        single = _dist.rank_world()[1] == 1
+        with torch.no_grad():
+            if single:
                 self.plan.grad_step(self.x, self.obs, self.inv_s2, self.eta, self._loss_buf)
-            self.loss = self._loss_buf[0]
-            return self.loss
-        return self.step_autograd()
+            else:
+                self.plan.grad_step(self.x, self.obs, self.inv_s2, 0.0, self._loss_buf, self._grad_buf)
+                _dist.all_sum_(self._grad_buf)
+                _dist.all_sum_(self._loss_buf)
+                api.axpy(self.x.data, self._grad_buf, -self.eta)
+        self.loss = self._loss_buf[0]
+        return self.loss
 
     def step_autograd(self):
-        """The same step through Degrid/Chi2 and loss.backward()."""
+        """The same step through Degrid/Chi2 and loss.backward(), the update by muser_axpy."""
         import torch
         self.x.grad = None
         loss = chi2_loss(self.x, self.plan, self.obs, self.inv_s2)
@@ -110,7 +130,7 @@ class GradientImaging:
             if _dist.rank_world()[1] > 1:
                 _dist.all_sum_(self.x.grad)
                 loss = _dist.all_sum_(loss.clone())
-            self.x.add_(self.x.grad, alpha=-self.eta)
+            api.axpy(self.x.data, self.x.grad.contiguous(), -self.eta)
         self.loss = loss
         return self.loss
 

@@ -237,7 +237,26 @@ struct DegridWs {
     long_cells = (int4 *)a.template take<int4>((size_t)np);
     pieces = (int4 *)a.template take<int4>((size_t)np);
     partial = (float2 *)a.template take<float2>((size_t)np);
-    counts = (int32_t *)a.template take<int32_t>(2);
+    counts = (int32_t *)a.template take<int32_t>(2 + (size_t)np);   // {long cells, pieces}, tickets
+  }
+};
+
+// Gradient imaging (muser_grad_step, muser_normal_apply, muser_lipschitz): the operator's
+// workspace first (so that one plan serves muser_degrid too), then the chi-square seed, the
+// interpolation's loss partials and ticket, and one N x N direction of the power iteration.
+template <class A>
+struct GradWs {
+  DegridWs<A> d;
+  float2 *resid;
+  float *partial;
+  unsigned *ticket;
+  float *hv;
+  void carve(A &a, int64_t n_vis, const muser_config_t &c) {
+    d.carve(a, n_vis, c);
+    resid = (float2 *)a.template take<float2>((size_t)n_vis);
+    partial = (float *)a.template take<float>((size_t)grad_interp_blocks(n_vis));
+    ticket = (unsigned *)a.template take<unsigned>(1);
+    hv = (float *)a.template take<float>((size_t)c.N * c.N);
   }
 };
 
@@ -300,6 +319,15 @@ int check_ws(void *ws, size_t ws_bytes, size_t need) {
   return MUSER_OK;
 }
 
+// The operator's plan in w: kernel table, grid correction, twiddles and the adjoint's tap lists.
+template <class A>
+void plan_operator(DegridWs<A> &w, const Rec *rec, int64_t n_vis, const muser_config_t &c, cudaStream_t s) {
+  launch_pswf_table(w.tab, c.W, c.os, w.gc, c.G, s);
+  fft::launch_twiddles(w.tw, c.G, s);
+  launch_degrid_plan(rec, n_vis, c.G, c.W, c.os, w.tab, w.cnt, w.cell_off, w.sums, w.taps, w.long_cells, w.pieces,
+                     w.counts, s);
+}
+
 __global__ void k_fill(float *p, int n, float v) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -314,6 +342,17 @@ __global__ void k_copy(float *dst, const float *src, int n) {
     int _rc = (x);               \
     if (_rc != MUSER_OK) return _rc; \
   } while (0)
+
+int check_normal_args(const char *who, int flags, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2,
+                      const muser_config_t *cfg) {
+  MUSER_TRY(check_cfg(cfg, DEGRID));
+  if ((flags & ~MUSER_REUSE_PLAN) != 0) return fail(MUSER_ERR_ARG, std::string(who) + ": flags must be 0 or MUSER_REUSE_PLAN");
+  if (n_vis < 1 || n_vis >= (int64_t)1 << 30) return fail(MUSER_ERR_ARG, std::string(who) + ": n_vis must be in [1, 2^30)");
+  if (!rec) return fail(MUSER_ERR_ARG, std::string(who) + ": rec is NULL");
+  if (!(inv_sigma2 > 0.f) || !isfinite(inv_sigma2))
+    return fail(MUSER_ERR_ARG, std::string(who) + ": inv_sigma2 must be positive and finite");
+  return MUSER_OK;
+}
 
 }  // namespace
 
@@ -385,14 +424,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_RESTORE: break;
     case MUSER_CALL_IMAGE: { ImageWs<SizeArena> w; w.carve(a, chunk_of(B, *cfg), (int)n_vis_total, *cfg); break; }
     case MUSER_CALL_DEGRID: { DegridWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
-    case MUSER_CALL_GRAD: {
-      DegridWs<SizeArena> w;
-      w.carve(a, n_vis_total, *cfg);
-      a.take<float2>((size_t)n_vis_total);
-      a.take<float>((size_t)grad_interp_blocks(n_vis_total));
-      a.take<unsigned>(1);
-      break;
-    }
+    case MUSER_CALL_GRAD: { GradWs<SizeArena> w; w.carve(a, n_vis_total, *cfg); break; }
     case MUSER_CALL_CENTER: { CenterWs<SizeArena> w; w.carve(a, B, *cfg, true); break; }
     case MUSER_CALL_STEER: { SteerWs<SizeArena> w; w.carve(a, B, *cfg); break; }
     default: return SIZE_MAX;
@@ -656,12 +688,7 @@ int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64
   cudaStream_t s = (cudaStream_t)stream;
   const Pswf &P = pswf_coefficients(cfg->W);
   const float K2 = (float)(P.K * P.K);
-  if (!reuse) {           // plan: kernel table, grid correction, twiddles and the adjoint's tap lists
-    launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
-    fft::launch_twiddles(w.tw, cfg->G, s);
-    launch_degrid_plan((const Rec *)rec, n_vis, cfg->G, cfg->W, cfg->os, w.tab, w.cnt, w.cell_off, w.sums, w.taps,
-                       w.long_cells, w.pieces, w.counts, s);
-  }
+  if (!reuse) plan_operator(w, (const Rec *)rec, n_vis, *cfg, s);
   if (dir == MUSER_FORWARD)
     launch_degrid_forward(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T,
                           w.X, (float2 *)vis, s);
@@ -683,25 +710,73 @@ int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_
   const size_t need = muser_workspace_size(MUSER_CALL_GRAD, 1, n_vis, cfg);
   MUSER_TRY(check_ws(ws, ws_bytes, need));
   Arena a(ws, ws_bytes);
-  DegridWs<Arena> w;
+  GradWs<Arena> w;
   w.carve(a, n_vis, *cfg);
-  float2 *resid = a.take<float2>((size_t)n_vis);
-  float *partial = a.take<float>((size_t)grad_interp_blocks(n_vis));
-  unsigned *ticket = a.take<unsigned>(1);
   cudaStream_t s = (cudaStream_t)stream;
   const Pswf &P = pswf_coefficients(cfg->W);
   const float K2 = (float)(P.K * P.K);
-  if (!(flags & MUSER_REUSE_PLAN)) {
-    launch_pswf_table(w.tab, cfg->W, cfg->os, w.gc, cfg->G, s);
-    fft::launch_twiddles(w.tw, cfg->G, s);
-    launch_degrid_plan((const Rec *)rec, n_vis, cfg->G, cfg->W, cfg->os, w.tab, w.cnt, w.cell_off, w.sums, w.taps,
-                       w.long_cells, w.pieces, w.counts, s);
-  }
-  cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
-  launch_grad_step(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T, w.X,
-                   (const float2 *)obs, inv_sigma2, resid, partial, ticket, loss, w.cell_off, w.taps, w.long_cells,
-                   w.pieces, w.counts, w.partial, eta, grad, s);
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
+  cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), s);
+  launch_grad_step(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc, K2, w.d.T,
+                   w.d.X, (const float2 *)obs, inv_sigma2, w.resid, w.partial, w.ticket, loss, w.d.cell_off, w.d.taps,
+                   w.d.long_cells, w.d.pieces, w.d.counts, w.d.partial, eta, grad, s);
   return check_launch("muser_grad_step");
+}
+
+int muser_normal_apply(int flags, const float *v, float *u, const muser_vis_record_t *rec, int64_t n_vis,
+                       float inv_sigma2, const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream) {
+  MUSER_TRY(check_normal_args("muser_normal_apply", flags, rec, n_vis, inv_sigma2, cfg));
+  if (!v || !u) return fail(MUSER_ERR_ARG, "muser_normal_apply: v and u are required");
+  MUSER_TRY(check_ws(ws, ws_bytes, muser_workspace_size(MUSER_CALL_GRAD, 1, n_vis, cfg)));
+  Arena a(ws, ws_bytes);
+  GradWs<Arena> w;
+  w.carve(a, n_vis, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Pswf &P = pswf_coefficients(cfg->W);
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
+  launch_normal_apply(v, u, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc,
+                      (float)(P.K * P.K), w.d.T, w.d.X, w.resid, inv_sigma2, w.d.cell_off, w.d.taps, w.d.long_cells,
+                      w.d.pieces, w.d.counts, w.d.partial, s);
+  return check_launch("muser_normal_apply");
+}
+
+int muser_normalize(const float *u, int64_t n, float *v, float *norm, muser_stream_t stream) {
+  if (n < 1) return fail(MUSER_ERR_ARG, "muser_normalize: n must be >= 1");
+  if (!u || !v || !norm) return fail(MUSER_ERR_ARG, "muser_normalize: required pointer is NULL");
+  launch_normalize(u, n, v, norm, (cudaStream_t)stream);
+  return check_launch("muser_normalize");
+}
+
+int muser_lipschitz(int flags, float *v, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2, int iters,
+                    float *L, const muser_config_t *cfg, void *ws, size_t ws_bytes, muser_stream_t stream) {
+  MUSER_TRY(check_normal_args("muser_lipschitz", flags, rec, n_vis, inv_sigma2, cfg));
+  if (!v || !L) return fail(MUSER_ERR_ARG, "muser_lipschitz: v and L are required");
+  if (iters < 1 || iters > 100000) return fail(MUSER_ERR_ARG, "muser_lipschitz: iters must be in [1, 100000]");
+  MUSER_TRY(check_ws(ws, ws_bytes, muser_workspace_size(MUSER_CALL_GRAD, 1, n_vis, cfg)));
+  Arena a(ws, ws_bytes);
+  GradWs<Arena> w;
+  w.carve(a, n_vis, *cfg);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Pswf &P = pswf_coefficients(cfg->W);
+  const int64_t NN = (int64_t)cfg->N * cfg->N;
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
+  launch_normalize(v, NN, v, L, s);
+  for (int k = 0; k < iters; k++) {
+    launch_normal_apply(v, w.hv, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc,
+                        (float)(P.K * P.K), w.d.T, w.d.X, w.resid, inv_sigma2, w.d.cell_off, w.d.taps, w.d.long_cells,
+                        w.d.pieces, w.d.counts, w.d.partial, s);
+    launch_normalize(w.hv, NN, v, L, s);
+  }
+  return check_launch("muser_lipschitz");
+}
+
+int muser_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev, muser_stream_t stream) {
+  if (n < 0) return fail(MUSER_ERR_ARG, "muser_axpy: negative n");
+  if (n == 0) return MUSER_OK;
+  if (!y || !x) return fail(MUSER_ERR_ARG, "muser_axpy: required pointer is NULL");
+  if (!isfinite(alpha)) return fail(MUSER_ERR_ARG, "muser_axpy: alpha must be finite");
+  launch_axpy(y, x, n, alpha, alpha_dev, (cudaStream_t)stream);
+  return check_launch("muser_axpy");
 }
 
 int muser_chi2(const float *pred, const float *obs, const muser_vis_record_t *rec, int64_t n_vis, float inv_sigma2,

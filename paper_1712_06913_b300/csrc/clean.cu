@@ -18,8 +18,6 @@
 // iteration k (warp shuffles, then shared memory, then the cluster).
 #include <cooperative_groups.h>
 
-#include <mutex>
-
 #include "common.cuh"
 
 namespace muser {
@@ -342,10 +340,8 @@ __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o
 // Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
 // 16-byte aligned in copy (N - px) mod 4 and each residual quad takes one aligned 16-byte load.
 //
-// Both kernels below are persistent workers drawing instances from one atomic counter
-// (`next`): the on-chip clusters and, on SMs that cannot host a whole cluster, streaming
-// blocks (launched on a second stream).  An instance is claimed by one worker, so the two
-// kernels share a batch without any other coordination.
+// The kernel below is a persistent worker: its clusters draw instances from one atomic counter
+// (`next`) until the batch is exhausted.
 //
 // Per block, a band of kTmPix / N rows of the residual (CS blocks per instance).
 // NQ quads per thread: the first kTmQuads in tensor memory, the rest (EXT: the 320, 640 and 1280
@@ -565,86 +561,6 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
   }
 }
 
-// Streaming worker on SMs that cannot host a whole cluster: block w images instance
-// first + w with the residual in global memory, in batches of 4 quads (4 residual + 4 aligned
-// beam 16-byte loads in flight per thread).  One instance per block, assigned statically:
-// a streaming instance takes far longer than a cluster's, so only as many are given out as
-// the clusters' share of the batch can hide.
-constexpr int kSqBatch = 4;
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(kOnT, 1) k_hogbom_stream_q(float *__restrict__ Rall, const float *__restrict__ beam4,
-                                                             size_t cstride, int first,
-                                                             const float *__restrict__ thr, float gain, int cap,
-                                                             int32_t *__restrict__ pos, float *__restrict__ flux,
-                                                             int32_t *__restrict__ n_comp,
-                                                             int32_t *__restrict__ status) {
-  constexpr int NQT = N * N / 4 / kOnT;                   // quads per thread
-  constexpr int QSTEP = 4 * kOnT / N;                     // rows advanced per quad step
-  static_assert(NQT % kSqBatch == 0 && (4 * kOnT) % N == 0, "whole batches of whole rows");
-  __shared__ Exchange<1> xch;
-  const int tid = threadIdx.x;
-  const int qr = (4 * tid) / N, qc = (4 * tid) % N;
-  int xk = 0;
-  {
-    const int inst = first + blockIdx.x;
-    if (status && (status[inst] & MUSER_ST_ALL_FLAGGED)) {
-      if (tid == 0) n_comp[inst] = 0;
-      return;
-    }
-    float4 *R4 = reinterpret_cast<float4 *>(Rall + (size_t)inst * N * N);
-    const float *Bm = beam4 + (size_t)inst * 4 * N * N;
-    const float t = thr ? thr[inst] : -CUDART_INF_F;
-    auto packed = [&](float v, int o) {
-      return o >= 0 ? pack_peak<MODE>(v, 4 * (tid + (o >> 2) * kOnT) + (o & 3)) : make_uint2(0u, 0u);
-    };
-    Cand<MODE> cb;
-    for (int i = 0; i < NQT; i++) cb.quad(R4[tid + i * kOnT], 4 * i);
-    Peak p = cluster_argmax<1, MODE>(packed(cb.value(), cb.o), xch, xk++);
-    int it = 0;
-    while (it < cap && p.idx < N * N && (MODE ? fabsf(p.val) : p.val) > t) {
-      const float f = gain * p.val;
-      if (tid == 0) {
-        pos[(size_t)inst * cap + it] = p.idx;
-        flux[(size_t)inst * cap + it] = f;
-      }
-      const int py = p.idx / N, px = p.idx % N;
-      const int off = N - px;
-      const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(N - py) * (2 * N) + (off & ~3);
-      const float4 *bq = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
-      cb = Cand<MODE>();
-#pragma unroll 1
-      for (int i0 = 0; i0 < NQT; i0 += kSqBatch) {
-        float4 rr[kSqBatch], bb[kSqBatch];
-#pragma unroll
-        for (int k = 0; k < kSqBatch; k++) {
-          rr[k] = R4[tid + (i0 + k) * kOnT];
-          bb[k] = __ldg(bq + (size_t)(i0 + k) * QSTEP * (2 * N / 4));
-        }
-#pragma unroll
-        for (int k = 0; k < kSqBatch; k++) {
-          const int i = i0 + k;
-          float4 v = rr[k];
-          v.x -= f * bb[k].x;
-          v.y -= f * bb[k].y;
-          v.z -= f * bb[k].z;
-          v.w -= f * bb[k].w;
-          R4[tid + i * kOnT] = v;
-          cb.quad(v, 4 * i);
-        }
-      }
-      p = cluster_argmax<1, MODE>(packed(cb.value(), cb.o), xch, xk++);
-      it++;
-    }
-    if (tid == 0) {
-      n_comp[inst] = it;
-      if (it == cap && cap > 0 && (MODE ? fabsf(p.val) : p.val) > t && status)
-        atomicOr(status + inst, MUSER_ST_ITER_CAP);
-    }
-  }
-}
-
-// ------------------------------------------------------------------ clustered streaming
 // k_hogbom_cstream (images whose residual does not fit on chip, N >= 640): clusters of CS
 // blocks share an instance; block `rank` streams rows [rank ceil(N/CS), ...) of the residual from
 // memory every iteration (16-byte residual accesses, 4-byte beam loads) and the block maxima meet
@@ -837,37 +753,9 @@ bool launch_cstream(float *R, const float *beam, int N, int B, int *next, const 
 struct OnchipPlan {
   int usable = -1;       // -1 not yet queried, 0 cannot run, 1 can run
   int clusters = 0;      // resident clusters of the on-chip kernel
-  int leftover = 0;      // SMs that cannot host a whole cluster
 };
 
-// Second stream and fork/join events per device, for the streaming workers (`busy` is held
-// from the fork to the join, so that calls from several host threads do not interleave).
-struct SideStream {
-  std::mutex busy;
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-};
-
-SideStream *side_stream() {
-  static std::mutex mu;
-  static SideStream tab[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  SideStream &x = tab[dev];
-  if (!x.s) {
-    if (cudaStreamCreateWithFlags(&x.s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      x.s = nullptr;
-      return nullptr;
-    }
-  }
-  return &x;
-}
-
-// Launch the queue workers if the device can host the on-chip clusters; false -> fallback.
+// Launch the persistent clusters if the device can host them; false -> fallback.
 template <int N, int CS, int MODE, int NQ = kTmQuads>
 bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
                         int cap, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
@@ -891,49 +779,23 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
   lc.numAttrs = 1;
   if (plan.usable < 0) {
     plan.usable = 0;
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
         (CS <= 8 || cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)) {
       int nclusters = 0;
       lc.gridDim = dim3(CS);
       if (cudaOccupancyMaxActiveClusters(&nclusters, k, &lc) == cudaSuccess && nclusters > 0) {
         plan.usable = 1;
         plan.clusters = nclusters;
-        plan.leftover = sms - nclusters * CS;
       }
     }
     cudaGetLastError();   // clear a failed query
   }
   if (!plan.usable) return false;
-  // Streaming workers (one instance each, the last ns of the batch) only when the clusters'
-  // share is at least 40 waves, long enough to hide a streaming instance (which takes about
-  // 40 times as long as a cluster's at N = 1024).
-  const int ns = (!EXT && plan.leftover > 0 && B - plan.leftover >= 40 * plan.clusters) ? plan.leftover : 0;
-  const int Bc = B - ns;
-  const int nc = plan.clusters < Bc ? plan.clusters : Bc;
+  const int nc = plan.clusters < B ? plan.clusters : B;
   cudaMemsetAsync(next, 0, sizeof(int), s);
-  // Clusters first (they need whole GPCs), then the streaming workers on the SMs left over.
-  SideStream *side = ns > 0 ? side_stream() : nullptr;
-  if (ns > 0 && !side) return false;
-  std::unique_lock<std::mutex> forked;
-  if (side) {
-    forked = std::unique_lock<std::mutex>(side->busy);
-    cudaEventRecord(side->fork, s);
-  }
   lc.gridDim = dim3(nc * CS);
-  cudaLaunchKernelEx(&lc, k, R, beam4, cstride, Bc, next, thr, gain, cap, pos, flux, n_comp, status);
+  cudaLaunchKernelEx(&lc, k, R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status);
   note_launch();
-  if constexpr (!EXT) {
-    if (side) {
-      cudaStreamWaitEvent(side->s, side->fork, 0);
-      k_hogbom_stream_q<N, MODE><<<ns, kOnT, 0, side->s>>>(R, beam4, cstride, Bc, thr, gain, cap, pos, flux, n_comp,
-                                                            status);
-      note_launch();
-      cudaEventRecord(side->join, side->s);
-      cudaStreamWaitEvent(s, side->join, 0);
-    }
-  }
   return true;
 }
 

@@ -216,8 +216,9 @@ void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int 
                            float2 *vis, cudaStream_t s);
 // Adjoint plan: tap lists by cell (cell_off [G*G + 1], taps [n_vis * W * W] {record, weight}),
 // the cells with long lists (long_cells {cell, first piece, pieces}) and their pieces
-// ({cell, first tap, end tap}; at most degrid_plan_pieces of each), counts {long cells,
-// pieces}; built with cnt [G*G] and scan scratch sums [degrid_plan_scan_blocks(G)].
+// ({cell, first tap, end tap, long-cell index}; at most degrid_plan_pieces of each), counts
+// {long cells, pieces, then one ticket per long cell} (2 + degrid_plan_pieces entries); built
+// with cnt [G*G] and scan scratch sums [degrid_plan_scan_blocks(G)].
 void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, const float *tab, int32_t *cnt,
                         int32_t *cell_off, int32_t *sums, int2 *taps, int4 *long_cells, int4 *pieces,
                         int32_t *counts, cudaStream_t s);
@@ -226,7 +227,7 @@ int64_t degrid_plan_pieces(int64_t n_vis, int G, int W);
 // partial: degrid_plan_pieces entries; Z: G x G scratch.
 void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
                            const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                           const int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
+                           int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
                            cudaStream_t s);
 
 void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t n_vis, float inv_sigma2,
@@ -238,12 +239,21 @@ int chi2_blocks(int64_t n_vis);
 // One gradient step of chi2 imaging (degrid.cu): forward operator, the chi-square seed and loss
 // fused into the interpolation, adjoint, img -= eta grad fused into the adjoint's row pass.
 // The plan (cell_off, taps, long_cells, pieces, counts) is the one launch_degrid_plan built.
+// Gradient imaging's step size and updates (degrid.cu): u = 2 Re A^H (w A v) / sigma^2 (the
+// chi-square Hessian applied to v; y: n_vis scratch, the rest as launch_grad_step); norm = |u|,
+// v = u / norm (one block); y += alpha (alpha_dev ? *alpha_dev : 1) x.
+void launch_normal_apply(const float *v, float *u, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
+                         const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
+                         float2 *y, float inv_s2, const int32_t *cell_off, const int2 *taps, const int4 *long_cells,
+                         const int4 *pieces, int32_t *counts, float2 *apartial, cudaStream_t s);
+void launch_normalize(const float *u, int64_t n, float *v, float *norm, cudaStream_t s);
+void launch_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev, cudaStream_t s);
 int grad_interp_blocks(int64_t n_vis);
 void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os, const float *tab,
                       const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
                       float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
                       const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                      const int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s);
+                      int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s);
 // Steer clean (steer.cu): scratch FB [B][2N][N + 1] c64, F [B][2N][2N] c64, U [B][N][2N] c64, Y [B][N][N] f32,
 // state [B][steer_state_bytes()], tw [2N] twiddles.
 size_t steer_state_bytes();

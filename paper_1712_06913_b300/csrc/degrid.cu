@@ -13,7 +13,8 @@
 //             (every tap of every record, grouped by cell): one thread per cell; lists longer
 //             than kLongList (short baselines at every channel crowd a few cells near the uv
 //             centre with thousands of taps) are cut into pieces of kPiece taps, one warp per
-//             piece, and a cell's pieces are added in order.  The order of a list is fixed when
+//             piece, and the warp that finishes a cell's last piece adds the cell's pieces in
+//             order (a per-cell ticket; the tickets reset themselves).  The order of a list is fixed when
 //             the plan is built, so every adjoint with one plan sums in the same order, without
 //             atomics;
 //     pass 1 (columns, outputs pruned to the central N rows), pass 2 (rows, central N
@@ -251,11 +252,14 @@ constexpr int kPieceBlocks = 592;
 // One launch for both: the first kPieceBlocks blocks take one piece of a long list per warp
 // (lanes stride the piece, then a fixed shuffle tree) into partial[piece] -- they start first,
 // being the longest -- and the others gather the short lists (one thread per cell, four gathers
-// in flight, added in list order).
+// in flight, added in list order).  A piece {cell, first tap, end tap, long-cell index} counts
+// itself on its cell's ticket; the warp that completes the cell adds its pieces' partial sums in
+// piece order (the same sum whichever warp comes last) and resets the ticket for the next call.
 __global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
                                     const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z,
                                     const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
-                                    float2 *__restrict__ partial) {
+                                    float2 *__restrict__ partial, const int4 *__restrict__ long_cells,
+                                    int32_t *__restrict__ tickets) {
   if ((int)blockIdx.x >= kPieceBlocks) {
     const int64_t c = (int64_t)(blockIdx.x - kPieceBlocks) * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -320,24 +324,26 @@ __global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const 
       z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
       z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
     }
-    if (lane == 0) partial[k] = z;
-  }
-}
-
-// One thread per long cell: its pieces' partial sums in order.
-__global__ void k_adj_long(const int4 *__restrict__ long_cells, const int32_t *__restrict__ n_long,
-                           const float2 *__restrict__ partial, float2 *__restrict__ Z) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nl = *n_long;
-  for (int k = i; k < nl; k += gridDim.x * blockDim.x) {
-    const int4 lc = long_cells[k];             // {cell, first piece, pieces, -}
-    float2 z = make_float2(0.f, 0.f);
-    for (int q = 0; q < lc.z; q++) {
-      const float2 v = partial[lc.y + q];
-      z.x += v.x;
-      z.y += v.y;
+    int last = 0;
+    int4 lc = make_int4(0, 0, 0, 0);
+    if (lane == 0) {
+      partial[k] = z;
+      __threadfence();                               // the partial is visible before the ticket
+      lc = long_cells[pc.w];                         // {cell, first piece, pieces, -}
+      last = atomicAdd(tickets + pc.w, 1) == lc.z - 1;
+      if (last) {
+        __threadfence();                             // the other pieces' partials, seen after theirs
+        float2 s = make_float2(0.f, 0.f);
+        for (int q = 0; q < lc.z; q++) {
+          const float2 v = __ldcg(partial + lc.y + q);
+          s.x += v.x;
+          s.y += v.y;
+        }
+        Z[lc.x] = s;
+        tickets[pc.w] = 0;                           // ready for the next adjoint with this plan
+      }
     }
-    Z[lc.x] = z;
+    __syncwarp();
   }
 }
 
@@ -568,7 +574,7 @@ __global__ void k_long_cells(const int32_t *__restrict__ cell_off, int64_t ncell
   const int i = atomicAdd(counts, 1);
   const int p0 = atomicAdd(counts + 1, np);
   long_cells[i] = make_int4((int)c, p0, np, 0);
-  for (int q = 0; q < np; q++) pieces[p0 + q] = make_int4((int)c, a + q * kPiece, min(e, a + (q + 1) * kPiece), 0);
+  for (int q = 0; q < np; q++) pieces[p0 + q] = make_int4((int)c, a + q * kPiece, min(e, a + (q + 1) * kPiece), i);
 }
 
 constexpr int kChi2Threads = 256;
@@ -611,6 +617,53 @@ __global__ void k_chi2_final(const float *__restrict__ partial, int n, float *__
   }
 }
 
+// Power iteration and descent updates of gradient imaging (the step size eta = 1/L, L the
+// largest eigenvalue of the chi-square Hessian 2 Re(A^H W A) / sigma^2, and x <- x - eta grad).
+
+// Seed of the Hessian applied to a direction: y_k = 2 w_k (A v)_k / sigma^2, 0 where w = 0.
+__global__ void k_hess_seed(float2 *__restrict__ y, const Rec *__restrict__ rec, int64_t n, float inv_s2) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const float w = rec[r].w;
+    const float2 p = y[r];
+    const float a = 2.f * w * inv_s2;
+    y[r] = w > 0.f ? make_float2(a * p.x, a * p.y) : make_float2(0.f, 0.f);
+  }
+}
+
+// norm[0] = ||u||_2, v = u / norm (v = 0 when u = 0); one block, sums in a fixed order
+// (per-thread FP32 partials, combined in FP64), so repeated calls give identical results.
+constexpr int kNormThreads = 1024;
+__global__ void __launch_bounds__(kNormThreads) k_normalize(const float *__restrict__ u, int64_t n,
+                                                            float *__restrict__ v, float *__restrict__ norm) {
+  __shared__ double red[kNormThreads / 32];
+  __shared__ float scale;
+  float acc = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += kNormThreads) acc = fmaf(u[i], u[i], acc);
+  double d = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kNormThreads / 32; w++) t += red[w];
+    const double nrm = sqrt(t);
+    norm[0] = (float)nrm;
+    scale = nrm > 0.0 ? (float)(1.0 / nrm) : 0.f;
+  }
+  __syncthreads();
+  const float sc = scale;
+  for (int64_t i = threadIdx.x; i < n; i += kNormThreads) v[i] = u[i] * sc;
+}
+
+// y += alpha (alpha_dev ? alpha_dev[0] : 1) x
+__global__ void k_axpy(float *__restrict__ y, const float *__restrict__ x, int64_t n, float alpha,
+                       const float *__restrict__ alpha_dev) {
+  const float a = alpha * (alpha_dev ? alpha_dev[0] : 1.f);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fmaf(a, x[i], y[i]);
+}
+
 }  // namespace
 
 void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
@@ -647,7 +700,8 @@ void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, con
     k_tap_fill<<<rb, 256, 0, s>>>(rec, n_vis, G, W, tab, table_len(W, os), (float)os, cell_off, cnt, taps);
     note_launch();
   }
-  cudaMemsetAsync(counts, 0, 2 * sizeof(int32_t), s);
+  // counts: {long cells, pieces}, then one ticket per long cell (zero; the adjoint resets them)
+  cudaMemsetAsync(counts, 0, (2 + (size_t)degrid_plan_pieces(n_vis, G, W)) * sizeof(int32_t), s);
   k_long_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(cell_off, ncell, long_cells, counts, pieces);
   note_launch();
 }
@@ -662,13 +716,12 @@ int degrid_plan_scan_blocks(int G) { return (int)(((int64_t)G * G + 1 + kScanPer
 
 void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
                            const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                           const int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
+                           int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
                            cudaStream_t s) {
   const int64_t ncell = (int64_t)G * G;
   const int nbg = (int)((ncell + 255) / 256);
-  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, pieces, counts + 1, partial);
-  note_launch();
-  k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, partial, Z);
+  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, pieces, counts + 1, partial,
+                                                         long_cells, counts + 2);
   note_launch();
   switch (G) {
 #define MUSER_CASE(g) \
@@ -690,7 +743,7 @@ void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, i
                       const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
                       float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
                       const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                      const int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s) {
+                      int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s) {
   GradStep gs;
   gs.obs = obs;
   gs.inv_s2 = inv_s2;
@@ -703,9 +756,8 @@ void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, i
   case g:                                                                                            \
     forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, resid, s, gs);                      \
     k_adj_gather_pieces<<<(int)((ncell + 255) / 256) + kPieceBlocks, 256, 0, s>>>(                 \
-        cell_off, taps, resid, ncell, X, pieces, counts + 1, apartial);                               \
-    note_launch();                                                                                   \
-    k_adj_long<<<148, 256, 0, s>>>(long_cells, counts, apartial, X);                                 \
+        cell_off, taps, resid, ncell, X, pieces, counts + 1, apartial, long_cells,                    \
+        counts + 2);                                                          \
     note_launch();                                                                                   \
     adjoint_G<g>(X, tw, gc, K2, T1, img, s, 1, eta, grad);                                           \
     break;
@@ -727,6 +779,31 @@ void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t 
   k_chi2<<<n_part, kChi2Threads, 0, s>>>(pred, obs, rec, n_vis, inv_sigma2, resid, partial);
   note_launch();
   k_chi2_final<<<1, 256, 0, s>>>(partial, n_part, loss);
+  note_launch();
+}
+
+void launch_normal_apply(const float *v, float *u, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
+                         const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
+                         float2 *y, float inv_s2, const int32_t *cell_off, const int2 *taps, const int4 *long_cells,
+                         const int4 *pieces, int32_t *counts, float2 *apartial, cudaStream_t s) {
+  launch_degrid_forward(v, rec, n_vis, N, G, W, os, tab, tw, gc, K2, T1, X, y, s);
+  if (n_vis > 0) {
+    const int64_t b = (n_vis + 255) / 256;
+    k_hess_seed<<<(unsigned)(b < 1184 ? b : 1184), 256, 0, s>>>(y, rec, n_vis, inv_s2);
+    note_launch();
+  }
+  launch_degrid_adjoint(y, N, G, tw, gc, K2, cell_off, taps, long_cells, pieces, counts, apartial, X, T1, u, s);
+}
+
+void launch_normalize(const float *u, int64_t n, float *v, float *norm, cudaStream_t s) {
+  k_normalize<<<1, kNormThreads, 0, s>>>(u, n, v, norm);
+  note_launch();
+}
+
+void launch_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t b = (n + 255) / 256;
+  k_axpy<<<(unsigned)(b < 1184 ? b : 1184), 256, 0, s>>>(y, x, n, alpha, alpha_dev);
   note_launch();
 }
 

@@ -84,3 +84,48 @@ def identical_positions_unless_near_tie(D_o, Bm_o, pos_g, gain, cap, thr=-np.inf
         py, px = divmod(int(po), N)
         R -= gain * R.ravel()[int(po)] * Bm_o[N - py:2 * N - py, N - px:2 * N - px]
     return len(pos_o)
+
+
+def follow_oracle(D_o, Bm_o, pos_g, flux_g, n_g, gain, cap, thr=-np.inf, peak_mode=0, tol_pos=1e-5, tol_flux=1e-4,
+                  tie=1e-5):
+    """All CLEAN checks of a GPU component list against the FP64 oracle in one pass.
+
+    Replays the GPU's n_g components on the oracle residual (lockstep).  At every step the GPU
+    position must be an exact or near-tie argmax (within tol_pos * peak0) and its flux within
+    tol_flux * peak0 of gain * R[p]; until the first step where the oracle's own argmax differs,
+    the two lists are identical, and that step must be a genuine near tie (oracle top-2 gap
+    within tie * peak0) -- from there on only the lockstep checks apply.  Stopping: the GPU may
+    only continue while the oracle's peak is above thr - tol_flux * peak0, and it may stop before
+    the cap only once the oracle's peak is at or below thr + tol_flux * peak0 (so the counts differ
+    only when the oracle's final peak sits within that band of thr).
+
+    Returns (first step whose position differs from the oracle's own, or n_g; R after the replay;
+    the oracle's fluxes gain * R[p] of the replayed steps).
+    """
+    N = D_o.shape[0]
+    R = np.array(D_o, dtype=np.float64, copy=True)
+    flat = R.ravel()
+    peak0 = np.abs(R).max()
+    diverged = None
+    flux_o = np.zeros(int(n_g))
+    for j in range(int(n_g)):
+        key = flat if peak_mode == 0 else np.abs(flat)
+        po = int(np.argmax(key))
+        best = key[po]
+        p = int(pos_g[j])
+        assert 0 <= p < N * N, ("position out of range", j, p)
+        assert key[p] >= best - tol_pos * peak0, ("not a near-argmax", j, p, key[p], best)
+        assert best > thr - tol_flux * peak0, ("continued below the threshold", j, best, thr)
+        fo = gain * flat[p]
+        flux_o[j] = fo
+        assert abs(float(flux_g[j]) - fo) <= tol_flux * peak0, ("flux", j, float(flux_g[j]), fo)
+        if diverged is None and p != po:
+            top = np.partition(key, -2)[-2:]
+            assert top[1] - top[0] <= tie * peak0, ("positions differ without a near tie", j, p, po)
+            diverged = j
+        py, px = divmod(p, N)
+        R -= fo * Bm_o[N - py:2 * N - py, N - px:2 * N - px]
+    if int(n_g) < cap:
+        key = flat if peak_mode == 0 else np.abs(flat)
+        assert key.max() <= thr + tol_flux * peak0, ("stopped above the threshold", int(n_g), key.max(), thr)
+    return (int(n_g) if diverged is None else diverged), R, flux_o

@@ -113,3 +113,31 @@ def test_call_argument_errors_without_a_gpu():
     # muser_selftest_wait: bound above about one second
     st = ctypes.c_void_p(16)
     assert lib.muser_selftest_wait(1 << 40, st, null) != 0
+
+
+def test_gradient_imaging_calls_reject_bad_arguments_without_a_gpu():
+    """The step-size and update calls check their arguments before any device work."""
+    import paper_1712_06913_b300 as m
+    lib = m._lib.load()
+    cd = m.Config(N=64, G=128).c()
+    null = ctypes.c_void_p(0)
+    fake = ctypes.c_void_p(0x10000)
+    # muser_normalize: n < 1, missing pointers
+    assert lib.muser_normalize(fake, 0, fake, fake, null) == m._lib.MUSER_ERR_ARG
+    assert lib.muser_normalize(null, 10, fake, fake, null) == m._lib.MUSER_ERR_ARG
+    # muser_axpy: non-finite alpha, missing pointers; n = 0 is a no-op
+    assert lib.muser_axpy(fake, fake, 10, float("nan"), null, null) == m._lib.MUSER_ERR_ARG
+    assert lib.muser_axpy(null, fake, 10, 1.0, null, null) == m._lib.MUSER_ERR_ARG
+    assert lib.muser_axpy(null, null, 0, 1.0, null, null) == m._lib.MUSER_OK
+    # muser_lipschitz / muser_normal_apply: iterations, sigma, flags, records, workspace
+    assert lib.muser_lipschitz(0, fake, fake, 10, 1.0, 0, fake, ctypes.byref(cd), fake, 1 << 30, null) != 0
+    assert b"iters" in lib.muser_last_error()
+    assert lib.muser_lipschitz(0, fake, fake, 10, -1.0, 5, fake, ctypes.byref(cd), fake, 1 << 30, null) != 0
+    assert b"inv_sigma2" in lib.muser_last_error()
+    assert lib.muser_normal_apply(2, fake, fake, fake, 10, 1.0, ctypes.byref(cd), fake, 1 << 30, null) != 0
+    assert lib.muser_normal_apply(0, fake, fake, null, 10, 1.0, ctypes.byref(cd), fake, 1 << 30, null) != 0
+    assert lib.muser_normal_apply(0, fake, fake, fake, 10, 1.0, ctypes.byref(cd), fake, 16, null) == \
+        m._lib.MUSER_ERR_WORKSPACE
+    # imaging-side configurations are refused by the operator's calls (G = 2N)
+    ci = m.Config(N=64, G=256).c()
+    assert lib.muser_normal_apply(0, fake, fake, fake, 10, 1.0, ctypes.byref(ci), fake, 1 << 30, null) != 0

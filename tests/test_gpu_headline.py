@@ -1,0 +1,260 @@
+"""GPU (libmuser, sm_103a) against the FP64 oracle at the benchmark's own shapes and launch paths.
+
+The benchmark images MUSER-II 1024^2 instances through muser_image in chunks: gridding fused
+into the 4096-point column transform, CLEAN by clusters of 16 blocks that each claim several
+instances in turn from a counter, 1000 iterations, two chunks in flight on alternating CLEAN
+streams.  The tests below run that path (and the MUSER-I band with the GMM threshold, the mixed
+stream's 512^2 and 1024^2 classes, and the gradient step on the 512^2 sky) and check every
+instance with the oracle, in spawned worker processes.
+
+Tolerances (north star, SURVEY C): CLEAN positions identical to the oracle's own list up to the
+first genuine near tie (top-2 gap within 1e-5 of the peak), every position a near-argmax of the
+lockstep-replayed oracle residual, fluxes within 1e-4 of the peak; residual and restored image
+within 1e-4 of the peak; GMM levels within 1e-4 of the image range; gradient 1e-4 relative L2.
+"""
+import multiprocessing as mp
+import os
+import types
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry, operator as oop, pipeline
+
+import _oracle_jobs
+from _parity import KER, assert_no_ties, cfg_for, oracle_records
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    import paper_1712_06913_b300 as mod
+    torch.cuda.init()
+    return mod
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _pool_map(fn, jobs):
+    """Oracle jobs in spawned processes (never forked from a process that holds a CUDA context)."""
+    n = max(1, min(len(jobs), len(os.sched_getaffinity(0)), 16))
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(fn, jobs, chunksize=1)
+
+
+def _jobs(wl, ro, out, cap, thr_mode, restore_for=()):
+    pos, flux, nc = _np(out.comp_pos), _np(out.comp_flux), _np(out.n_comp)
+    res, clean, bp = _np(out.residual), _np(out.clean), _np(out.beam_params)
+    thr = _np(out.thr) if out.thr is not None else None
+    jobs = []
+    for i in range(wl.n_inst):
+        jobs.append({"inst": i, "rec": geometry.instance_slice(ro, i, wl.n_bl), "N": wl.N, "G": wl.G, "gain": wl.gain,
+                     "cap": cap, "thr_mode": thr_mode, "pos": pos[i], "flux": flux[i], "n_comp": int(nc[i]),
+                     "residual": res[i], "beam_params": bp[i], "clean": clean[i] if i in restore_for else None,
+                     "thr": float(thr[i]) if thr is not None else None})
+    return jobs
+
+
+def _image(m, wl, cfg, **kw):
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    return m.image(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags, **kw)
+
+
+# ------------------------------------------------------------------------------ config 3 (the headline)
+def test_headline_1024_chunks_and_repeated_claims_vs_oracle(m):
+    """32 MUSER-II instances (2 frames x 16 channels over 2-15 GHz, 0-30 % flagged) at N = 1024,
+    1000 iterations, chunks of 16 on the two CLEAN streams: every 16-block cluster claims two or
+    three instances in turn (a B300 holds 7 such clusters), so tensor-memory reuse, the claim
+    double buffer and the exchange parity carried from one instance to the next are all exercised;
+    every instance follows the oracle."""
+    chans = list(range(3, 528, 33))
+    wl = synth.config3_muser2_uneven(n_frame=2, chans=chans)
+    assert wl.n_inst == 32 and wl.N == 1024 and wl.max_iter == 1000
+    cfg = cfg_for(m, wl, batch_chunk=16)
+    out = _image(m, wl, cfg)
+    ro = oracle_records(wl)
+    assert_no_ties(ro, wl.G, wl.W)
+    assert np.all(_np(out.n_comp) == 1000)
+    st = _np(out.status)
+    assert np.all(st & ~(m.ST_ITER_CAP | m.ST_DROPPED) == 0), st
+    res = _pool_map(_oracle_jobs.check_image_instance, _jobs(wl, ro, out, 1000, 0, restore_for=(0, 15, 16, 31)))
+    # every step was checked in the workers; late in a 1000-iteration CLEAN the residual is flat
+    # enough that genuine near ties (within 1e-5 of the peak) part the two lists
+    assert len(res) == 32 and all(r["residual_err"] <= 1e-4 for r in res)
+
+
+# ------------------------------------------------------------------------------ config 2
+def test_muser1_band_512_gmm_threshold_vs_oracle(m):
+    """48 MUSER-I instances of 512^2 (one 25 ms frame, 48 channels over 0.4-2 GHz), CLEAN down to
+    each map's GMM sky level with at most 1000 iterations, one batch as the benchmark runs it (more
+    instances than resident clusters of 4 blocks, so clusters claim again): the level within 1e-4
+    of the range, the stop decision and every component in lockstep with the oracle."""
+    wl = synth.config2_muser1_band(n_frame=1, chans=list(range(0, 64, 4)) + list(range(1, 64, 2)))
+    assert wl.n_inst == 48 and wl.N == 512 and wl.thr_mode == 1
+    cfg = cfg_for(m, wl)
+    out = _image(m, wl, cfg)
+    ro = oracle_records(wl)
+    assert_no_ties(ro, wl.G, wl.W)
+    nc = _np(out.n_comp)
+    assert nc.min() >= 1 and nc.max() <= 1000
+    res = _pool_map(_oracle_jobs.check_image_instance, _jobs(wl, ro, out, 1000, 1, restore_for=(0, 47)))
+    assert len(res) == 48 and all(r["residual_err"] <= 1e-4 for r in res)
+
+
+# ------------------------------------------------------------------------------ config 5
+def test_mixed_stream_512_and_1024_classes_vs_oracle(m):
+    """The mixed stream's MUSER-I 512^2 class and MUSER-II 1024^2 class, 1000 iterations, through
+    the size-class batches of one MixedImager: one instance of each class against the oracle."""
+    w1, w2, _ = synth.config5_mixed_stream(n_total=40)
+    ch1, ch2 = [20, 50], [10, 300]
+    src1 = m.Source(w1.ant_enu, w1.pairs, w1.ha[:1], w1.dec[:1], w1.freq[ch1], w1.vis[:1][:, ch1],
+                    w1.flags[:1][:, ch1], bmax=w1.bmax, fov_min=w1.fov_min, n_max=512, max_iter=1000,
+                    lat_rad=w1.lat)
+    src2 = m.Source(w2.ant_enu, w2.pairs, w2.ha[:1], w2.dec[:1], w2.freq[ch2], w2.vis[:1][:, ch2],
+                    w2.flags[:1][:, ch2], bmax=w2.bmax, fov_min=w2.fov_min, n_max=1024, max_iter=1000,
+                    lat_rad=w2.lat)
+    mix = m.MixedImager([src1, src2])
+    assert [(si, im.cfg.N) for si, _, _, im in mix.classes] == [(0, 512), (1, 1024)]
+    outs = mix.run()
+    jobs = []
+    for k, (src, w, N) in enumerate(((src1, w1, 512), (src2, w2, 1024))):
+        wl = types.SimpleNamespace(ant_enu=src.ant_enu, pairs=src.pairs, lat=src.lat_rad, ha=src.ha, dec=src.dec,
+                                   freq=src.freq, vis=src.vis, flags=src.flags, bmax=src.bmax, fov_min=src.fov_min,
+                                   N=N, G=4 * N, W=7)
+        ro = pipeline.records(wl)
+        n_bl = len(src.pairs)
+        o = outs[k]
+        i = 1                                          # the second instance of the class
+        jobs.append({"inst": (k, i), "rec": geometry.instance_slice(ro, i, n_bl), "N": N, "G": 4 * N, "gain": 0.1,
+                     "cap": 1000, "thr_mode": 0, "pos": _np(o.comp_pos)[i], "flux": _np(o.comp_flux)[i],
+                     "n_comp": int(_np(o.n_comp)[i]), "residual": _np(o.residual)[i],
+                     "beam_params": _np(o.beam_params)[i], "clean": _np(o.clean)[i], "thr": None})
+    res = _pool_map(_oracle_jobs.check_image_instance, jobs)
+    assert all(r["n_comp"] == 1000 for r in res)
+
+
+# ------------------------------------------------------------------------------ config 4
+def _config4(m, chans=None):
+    w4 = synth.config4_operator()
+    if chans is not None:
+        w4 = types.SimpleNamespace(**{**w4.__dict__, "freq": w4.freq[chans], "vis": w4.vis[:, chans],
+                                      "flags": w4.flags[:, chans], "n_chan": len(chans)})
+    cfg = m.Config(N=w4.N, G=w4.G, lat_rad=w4.lat)
+    cell = np.full(len(w4.freq), 60 * synth.ARCMIN / w4.N)
+    rec, _, _ = m.uvw(w4.ant_enu, w4.pairs, w4.ha, w4.dec, w4.freq, cell, w4.vis, cfg, flags=w4.flags)
+    ro = geometry.grid_records(geometry.uvw(w4.ant_enu, w4.pairs, w4.lat, w4.ha, w4.dec, w4.freq), w4.vis,
+                               w4.flags, cell, w4.G, 7)
+    sigma = float(np.sqrt(np.mean(np.abs(w4.vis) ** 2) / 900.0))      # SNR 30
+    return w4, cfg, rec, ro, sigma
+
+
+def test_grad_step_512_sky_vs_oracle_gradient(m):
+    """muser_grad_step on the 512^2 sky with all 780 baselines x 64 channels (49,920 visibilities):
+    the loss within 1e-4 and the gradient within 1e-4 relative L2 of the oracle's FP64 values at a
+    random image; eta = 0 leaves the image unchanged."""
+    import torch
+    w4, cfg, rec, ro, sigma = _config4(m)
+    plan = m.DegridPlan(rec, cfg)
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    x0 = np.random.default_rng(512).uniform(0, 1e-3, size=(cfg.N, cfg.N))
+    x = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    grad = torch.empty_like(x)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    plan.grad_step(x, obs, 1.0 / sigma ** 2, 0.0, loss, grad)
+    assert torch.equal(x, torch.tensor(x0, dtype=torch.float32, device="cuda"))
+    c_o, g_o = oop.chi2_grad(x0.astype(np.float32).astype(np.float64), ro, ro["vis"], sigma, cfg.N, cfg.G, KER)
+    assert float(loss[0]) == pytest.approx(c_o, rel=1e-4)
+    assert np.linalg.norm(_np(grad) - g_o) <= 1e-4 * np.linalg.norm(g_o)
+
+
+def test_gradient_descent_512_sky_follows_oracle_trajectory(m):
+    """100 steps of gradient-descent imaging on the 512^2 sky from x = 0 with every 8th channel
+    (8 x 780 visibilities), each step one muser_grad_step call: the loss history and the final image
+    follow the oracle's FP64 descent with the same step 1/L.  Tolerance 1e-3: each FP32 step adds
+    an error of order 1e-6 of the image, and 100 non-expansive steps (eta = 1/L) sum at most 1e-4;
+    the loss history is checked at 1e-4 relative.  The library's L (muser_lipschitz, 50 iterations)
+    agrees with the oracle's power iteration."""
+    import torch
+    from paper_1712_06913_b300.autograd import GradientImaging
+    w4, cfg, rec, ro, sigma = _config4(m, chans=list(range(0, 64, 8)))
+    L_o = oop.lipschitz(ro, cfg.N, cfg.G, KER, sigma, iters=50)
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    gd = GradientImaging(rec, obs, sigma, cfg)
+    L_g = gd.lipschitz(iters=50)
+    assert L_g == pytest.approx(L_o, rel=1e-3)
+    gd.eta = 1.0 / L_o
+    hist = [float(gd.step()) for _ in range(100)]
+    x_o = np.zeros((cfg.N, cfg.N))
+    hist_o = []
+    for _ in range(100):
+        c, g = oop.chi2_grad(x_o, ro, ro["vis"], sigma, cfg.N, cfg.G, KER)
+        hist_o.append(c)
+        x_o = x_o - g / L_o
+    np.testing.assert_allclose(hist, hist_o, rtol=1e-4)
+    assert hist[-1] < 0.5 * hist[0]
+    assert np.linalg.norm(_np(gd.x) - x_o) <= 1e-3 * np.linalg.norm(x_o)
+
+
+# ------------------------------------------------------------------------------ step size and update calls
+def _small_operator(m, N=32, n_chan=3, seed=220):
+    wl = synth.small_workload(n_ant=7, N=N, config_id=seed, bmax=150.0, freq=np.linspace(1.0e9, 1.6e9, n_chan))
+    cfg = m.Config(N=N, G=2 * N, lat_rad=wl.lat)
+    cell = np.full(wl.n_chan, geometry.pixel_size(wl.freq.max(), wl.bmax, N, 60 * synth.ARCMIN))
+    rec, _, _ = m.uvw(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+    ro = geometry.grid_records(geometry.uvw(wl.ant_enu, wl.pairs, wl.lat, wl.ha, wl.dec, wl.freq), wl.vis,
+                               wl.flags, cell, 2 * N, 7)
+    return cfg, rec, ro
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_hessian_product_power_iteration_and_update_vs_oracle(m, N):
+    """muser_normal_apply is the chi-square Hessian's action (the oracle's grad(v) - grad(0)) to
+    1e-4 relative L2; muser_lipschitz converges to the oracle's largest eigenvalue; muser_normalize
+    and muser_axpy against FP64; the multi-rank step form (gradient with eta = 0, then muser_axpy)
+    equals the single fused step."""
+    import torch
+    cfg, rec, ro = _small_operator(m, N)
+    sigma = 0.5
+    plan = m.DegridPlan(rec, cfg)
+    rng = np.random.default_rng(N)
+    v0 = rng.normal(size=(N, N))
+    u = plan.normal_apply(torch.tensor(v0, dtype=torch.float32, device="cuda"), 1.0 / sigma ** 2)
+    V = ro["vis"]
+    g0 = oop.chi2_grad(np.zeros((N, N)), ro, V, sigma, N, cfg.G, KER)[1]
+    Hv = oop.chi2_grad(v0.astype(np.float32).astype(np.float64), ro, V, sigma, N, cfg.G, KER)[1] - g0
+    assert np.linalg.norm(_np(u) - Hv) <= 1e-4 * np.linalg.norm(Hv)
+    # power iteration, enough steps for both sides to settle on the top eigenvalue
+    v = torch.tensor(rng.normal(size=(N, N)), dtype=torch.float32, device="cuda")
+    L = plan.lipschitz(v, 1.0 / sigma ** 2, 200)
+    L_o = oop.lipschitz(ro, N, cfg.G, KER, sigma, iters=200)
+    assert float(L[0]) == pytest.approx(L_o, rel=1e-4)
+    assert float(torch.linalg.vector_norm(v.double())) == pytest.approx(1.0, rel=1e-5)
+    # normalize and axpy
+    a = rng.normal(size=1000).astype(np.float32)
+    ta = torch.tensor(a, device="cuda")
+    vv, nrm = m.normalize(ta)
+    assert float(nrm[0]) == pytest.approx(np.linalg.norm(a.astype(np.float64)), rel=1e-6)
+    np.testing.assert_allclose(_np(vv), a / np.linalg.norm(a.astype(np.float64)), rtol=1e-5, atol=1e-7)
+    y = rng.normal(size=1000).astype(np.float32)
+    ty = torch.tensor(y, device="cuda")
+    s = torch.tensor([0.25], device="cuda")
+    m.axpy(ty, ta, -2.0, s)
+    np.testing.assert_allclose(_np(ty), y.astype(np.float64) - 0.5 * a, rtol=1e-6, atol=1e-6)
+    # multi-rank form of a step on one process: gradient with eta = 0, then the update
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    x0 = torch.tensor(rng.normal(size=(N, N)), dtype=torch.float32, device="cuda")
+    eta = 0.3 / float(L[0])
+    xa, xb = x0.clone(), x0.clone()
+    la = torch.empty(1, device="cuda")
+    lb = torch.empty(1, device="cuda")
+    grad = torch.empty_like(x0)
+    plan.grad_step(xa, obs, 1.0 / sigma ** 2, eta, la)
+    plan.grad_step(xb, obs, 1.0 / sigma ** 2, 0.0, lb, grad)
+    m.axpy(xb, grad, -eta)
+    assert float(la[0]) == float(lb[0])
+    assert float((xa - xb).abs().max()) <= 1e-6 * float(xa.abs().max())
