@@ -214,30 +214,42 @@ ImagePipe *image_pipe() {
   return &x;
 }
 
+// The degridding operator's plan and scratch (see OpPlan); the kernel table and grid correction
+// are written by plan_operator.
 template <class A>
 struct DegridWs {
   float *tab, *gc;
-  float2 *tw, *T, *X;
-  int32_t *cnt, *cell_off, *sums, *counts;
-  int2 *taps;
-  int4 *long_cells, *pieces;
-  float2 *partial;
+  OpPlan p;
   void carve(A &a, int64_t n_vis, const muser_config_t &c) {
     const int G = c.G;
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     gc = (float *)a.template take<float>(G);
-    tw = (float2 *)a.template take<float2>(G);
-    T = (float2 *)a.template take<float2>((size_t)(G / 2) * G);
-    X = (float2 *)a.template take<float2>((size_t)G * G);
-    cnt = (int32_t *)a.template take<int32_t>((size_t)G * G);
-    cell_off = (int32_t *)a.template take<int32_t>((size_t)G * G + 1);
-    sums = (int32_t *)a.template take<int32_t>(degrid_plan_scan_blocks(G));
-    taps = (int2 *)a.template take<int2>((size_t)n_vis * c.W * c.W);
+    p.N = c.N;
+    p.G = G;
+    p.W = c.W;
+    p.os = c.os;
+    p.n_vis = n_vis;
+    p.tab = tab;
+    p.gc = gc;
+    p.tw = (float2 *)a.template take<float2>(G);
+    p.T = (float2 *)a.template take<float2>((size_t)(G / 2) * G);
+    p.X = (float2 *)a.template take<float2>((size_t)G * G);
+    p.Zs = (float2 *)a.template take<float2>((size_t)G * G);
+    p.cnt = (int32_t *)a.template take<int32_t>((size_t)G * G + 1);
+    p.cell_off = (int32_t *)a.template take<int32_t>((size_t)G * G + 1);
+    p.sums = (int32_t *)a.template take<int32_t>(degrid_plan_scan_blocks(G));
+    p.taps = (int2 *)a.template take<int2>((size_t)n_vis * c.W * c.W);
     const int64_t np = degrid_plan_pieces(n_vis, G, c.W);
-    long_cells = (int4 *)a.template take<int4>((size_t)np);
-    pieces = (int4 *)a.template take<int4>((size_t)np);
-    partial = (float2 *)a.template take<float2>((size_t)np);
-    counts = (int32_t *)a.template take<int32_t>(2 + (size_t)np);   // {long cells, pieces}, tickets
+    p.long_cells = (int4 *)a.template take<int4>((size_t)np);
+    p.pieces = (int4 *)a.template take<int4>((size_t)np);
+    p.partial = (float2 *)a.template take<float2>((size_t)np);
+    p.counts = (int32_t *)a.template take<int32_t>(4 + (size_t)np);   // {long cells, pieces, items, -}, tickets
+    p.items = (int4 *)a.template take<int4>((size_t)degrid_plan_items(n_vis, G, c.W));
+    p.order = (int32_t *)a.template take<int32_t>((size_t)n_vis);
+    p.srec = (Rec *)a.template take<Rec>((size_t)n_vis);
+    p.vs = (float2 *)a.template take<float2>((size_t)n_vis);
+    const Pswf &P = pswf_coefficients(c.W);
+    p.K2 = (float)(P.K * P.K);
   }
 };
 
@@ -319,13 +331,13 @@ int check_ws(void *ws, size_t ws_bytes, size_t need) {
   return MUSER_OK;
 }
 
-// The operator's plan in w: kernel table, grid correction, twiddles and the adjoint's tap lists.
+// The operator's plan in w: kernel table, grid correction, twiddles, the sorted records and the
+// adjoint's tap lists.
 template <class A>
-void plan_operator(DegridWs<A> &w, const Rec *rec, int64_t n_vis, const muser_config_t &c, cudaStream_t s) {
+void plan_operator(DegridWs<A> &w, const Rec *rec, const muser_config_t &c, cudaStream_t s) {
   launch_pswf_table(w.tab, c.W, c.os, w.gc, c.G, s);
-  fft::launch_twiddles(w.tw, c.G, s);
-  launch_degrid_plan(rec, n_vis, c.G, c.W, c.os, w.tab, w.cnt, w.cell_off, w.sums, w.taps, w.long_cells, w.pieces,
-                     w.counts, s);
+  fft::launch_twiddles(const_cast<float2 *>(w.p.tw), c.G, s);
+  launch_degrid_plan(rec, w.p, s);
 }
 
 __global__ void k_fill(float *p, int n, float v) {
@@ -686,15 +698,11 @@ int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64
   DegridWs<Arena> w;
   w.carve(a, n_vis, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
-  const Pswf &P = pswf_coefficients(cfg->W);
-  const float K2 = (float)(P.K * P.K);
-  if (!reuse) plan_operator(w, (const Rec *)rec, n_vis, *cfg, s);
+  if (!reuse) plan_operator(w, (const Rec *)rec, *cfg, s);
   if (dir == MUSER_FORWARD)
-    launch_degrid_forward(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.tab, w.tw, w.gc, K2, w.T,
-                          w.X, (float2 *)vis, s);
+    launch_degrid_forward(img, w.p, (float2 *)vis, s);
   else
-    launch_degrid_adjoint((const float2 *)vis, cfg->N, cfg->G, w.tw, w.gc, K2, w.cell_off, w.taps, w.long_cells,
-                          w.pieces, w.counts, w.partial, w.X, w.T, img, s);
+    launch_degrid_adjoint((const float2 *)vis, w.p, img, s);
   return check_launch("muser_degrid");
 }
 
@@ -713,13 +721,9 @@ int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_
   GradWs<Arena> w;
   w.carve(a, n_vis, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
-  const Pswf &P = pswf_coefficients(cfg->W);
-  const float K2 = (float)(P.K * P.K);
-  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, *cfg, s);
   cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), s);
-  launch_grad_step(img, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc, K2, w.d.T,
-                   w.d.X, (const float2 *)obs, inv_sigma2, w.resid, w.partial, w.ticket, loss, w.d.cell_off, w.d.taps,
-                   w.d.long_cells, w.d.pieces, w.d.counts, w.d.partial, eta, grad, s);
+  launch_grad_step(img, w.d.p, (const float2 *)obs, inv_sigma2, w.resid, w.partial, w.ticket, loss, eta, grad, s);
   return check_launch("muser_grad_step");
 }
 
@@ -732,11 +736,8 @@ int muser_normal_apply(int flags, const float *v, float *u, const muser_vis_reco
   GradWs<Arena> w;
   w.carve(a, n_vis, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
-  const Pswf &P = pswf_coefficients(cfg->W);
-  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
-  launch_normal_apply(v, u, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc,
-                      (float)(P.K * P.K), w.d.T, w.d.X, w.resid, inv_sigma2, w.d.cell_off, w.d.taps, w.d.long_cells,
-                      w.d.pieces, w.d.counts, w.d.partial, s);
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, *cfg, s);
+  launch_normal_apply(v, u, w.d.p, w.resid, inv_sigma2, s);
   return check_launch("muser_normal_apply");
 }
 
@@ -757,14 +758,11 @@ int muser_lipschitz(int flags, float *v, const muser_vis_record_t *rec, int64_t 
   GradWs<Arena> w;
   w.carve(a, n_vis, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
-  const Pswf &P = pswf_coefficients(cfg->W);
   const int64_t NN = (int64_t)cfg->N * cfg->N;
-  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, n_vis, *cfg, s);
+  if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, *cfg, s);
   launch_normalize(v, NN, v, L, s);
   for (int k = 0; k < iters; k++) {
-    launch_normal_apply(v, w.hv, (const Rec *)rec, n_vis, cfg->N, cfg->G, cfg->W, cfg->os, w.d.tab, w.d.tw, w.d.gc,
-                        (float)(P.K * P.K), w.d.T, w.d.X, w.resid, inv_sigma2, w.d.cell_off, w.d.taps, w.d.long_cells,
-                        w.d.pieces, w.d.counts, w.d.partial, s);
+    launch_normal_apply(v, w.hv, w.d.p, w.resid, inv_sigma2, s);
     launch_normalize(w.hv, NN, v, L, s);
   }
   return check_launch("muser_lipschitz");

@@ -210,56 +210,59 @@ void launch_restore(const float *R, const float *beam, const int32_t *pos, const
                     const int32_t *n_comp, int B, int N, int cap, float *clean, float *params, int32_t *status,
                     cudaStream_t s);
 
-// degridding (degrid.cu)
-void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                           const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
-                           float2 *vis, cudaStream_t s);
-// Adjoint plan: tap lists by cell (cell_off [G*G + 1], taps [n_vis * W * W] {record, weight}),
-// the cells with long lists (long_cells {cell, first piece, pieces}) and their pieces
-// ({cell, first tap, end tap, long-cell index}; at most degrid_plan_pieces of each), counts
-// {long cells, pieces, then one ticket per long cell} (2 + degrid_plan_pieces entries); built
-// with cnt [G*G] and scan scratch sums [degrid_plan_scan_blocks(G)].
-void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, const float *tab, int32_t *cnt,
-                        int32_t *cell_off, int32_t *sums, int2 *taps, int4 *long_cells, int4 *pieces,
-                        int32_t *counts, cudaStream_t s);
+// degridding (degrid.cu): the operator's plan and scratch, carved from a workspace.  The plan
+// sorts the caller's records by 8 x 8-cell tile (order[i] = caller index of sorted record i,
+// srec[i] its record) and lists every tap by grid cell (cell_off [G*G + 1], taps [n_vis W W]
+// {sorted record, weight}); short non-empty cells as items {cell, first tap, end tap}, long ones
+// ({cell, first piece, pieces}) cut into pieces ({cell, first tap, end tap, long-cell index});
+// counts {long cells, pieces, items, -} then one ticket per long cell.  Zs: the adjoint's grid,
+// zero where no tap falls.  Scratch: cnt [G*G], sums [degrid_plan_scan_blocks(G)], T (G/2 x G),
+// X (G x G), partial (pieces), vs (n_vis, the adjoint's input in sorted order).
+struct OpPlan {
+  int N = 0, G = 0, W = 0, os = 0;
+  float K2 = 1.f;
+  int64_t n_vis = 0;
+  const float *tab = nullptr, *gc = nullptr;
+  const float2 *tw = nullptr;
+  float2 *T = nullptr, *X = nullptr, *Zs = nullptr, *partial = nullptr, *vs = nullptr;
+  int32_t *cnt = nullptr, *cell_off = nullptr, *sums = nullptr, *counts = nullptr, *order = nullptr;
+  int2 *taps = nullptr;
+  int4 *long_cells = nullptr, *pieces = nullptr, *items = nullptr;
+  Rec *srec = nullptr;
+};
+void launch_degrid_plan(const Rec *rec, const OpPlan &p, cudaStream_t s);
 int degrid_plan_scan_blocks(int G);
 int64_t degrid_plan_pieces(int64_t n_vis, int G, int W);
-// partial: degrid_plan_pieces entries; Z: G x G scratch.
-void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
-                           const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                           int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
-                           cudaStream_t s);
+int64_t degrid_plan_items(int64_t n_vis, int G, int W);
+// FORWARD: vis in the caller's record order.  ADJOINT: vis in the caller's record order.
+void launch_degrid_forward(const float *img, const OpPlan &p, float2 *vis, cudaStream_t s);
+void launch_degrid_adjoint(const float2 *vis, const OpPlan &p, float *img, cudaStream_t s);
 
 void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t n_vis, float inv_sigma2,
                  float2 *resid, float *partial, int n_part, float *loss, cudaStream_t s);
 int chi2_blocks(int64_t n_vis);
 
-// centring (center.cu): Cc [B][N/2+1][N/2+1], dlm [B][2], shift [B][2] (nullable); scratch
-// thr, r2 [B] f32, masked [B] i32, F [B][2N][2N] c64, U [B][N/2+1][2N] c64, tw [2N] twiddles.
 // One gradient step of chi2 imaging (degrid.cu): forward operator, the chi-square seed and loss
-// fused into the interpolation, adjoint, img -= eta grad fused into the adjoint's row pass.
-// The plan (cell_off, taps, long_cells, pieces, counts) is the one launch_degrid_plan built.
-// Gradient imaging's step size and updates (degrid.cu): u = 2 Re A^H (w A v) / sigma^2 (the
-// chi-square Hessian applied to v; y: n_vis scratch, the rest as launch_grad_step); norm = |u|,
-// v = u / norm (one block); y += alpha (alpha_dev ? *alpha_dev : 1) x.
-void launch_normal_apply(const float *v, float *u, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                         const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
-                         float2 *y, float inv_s2, const int32_t *cell_off, const int2 *taps, const int4 *long_cells,
-                         const int4 *pieces, int32_t *counts, float2 *apartial, cudaStream_t s);
+// fused into the interpolation (resid [n_vis] in the plan's order, obs in the caller's), adjoint,
+// img -= eta grad fused into the adjoint's row pass.
+// Gradient imaging's step size and updates: u = 2 Re A^H (w A v) / sigma^2 (the chi-square
+// Hessian applied to v; y: n_vis scratch); norm = |u|, v = u / norm (one block);
+// y += alpha (alpha_dev ? *alpha_dev : 1) x.
+int grad_interp_blocks(int64_t n_vis);
+void launch_grad_step(float *img, const OpPlan &p, const float2 *obs, float inv_s2, float2 *resid, float *partial,
+                      unsigned *ticket, float *loss, float eta, float *grad, cudaStream_t s);
+void launch_normal_apply(const float *v, float *u, const OpPlan &p, float2 *y, float inv_s2, cudaStream_t s);
 void launch_normalize(const float *u, int64_t n, float *v, float *norm, cudaStream_t s);
 void launch_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev, cudaStream_t s);
-int grad_interp_blocks(int64_t n_vis);
-void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os, const float *tab,
-                      const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
-                      float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
-                      const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                      int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s);
+
 // Steer clean (steer.cu): scratch FB [B][2N][N + 1] c64, F [B][2N][2N] c64, U [B][N][2N] c64, Y [B][N][N] f32,
 // state [B][steer_state_bytes()], tw [2N] twiddles.
 size_t steer_state_bytes();
 void launch_steer(float *R, const float *beam, int B, int N, float gain, int cap, const float *thr, float clip,
                   float *model, int32_t *n_cycles, const float2 *tw, float2 *FB, float2 *F, float2 *U, float *Y,
                   void *state, const int32_t *status, cudaStream_t s);
+// centring (center.cu): Cc [B][N/2+1][N/2+1], dlm [B][2], shift [B][2] (nullable); scratch
+// thr, r2 [B] f32, masked [B] i32, F [B][2N][2N] c64, U [B][N/2+1][2N] c64, tw [2N] twiddles.
 void launch_center(const float *R, const float *mu_a, const float *mu_b, const double *cell, int B, int N,
                    const float2 *tw, float *thr, float *r2, int32_t *masked, float2 *F, float2 *U, float *Cc,
                    double *dlm, float *shift, int32_t *status, cudaStream_t s);

@@ -7,16 +7,20 @@
 //             vis = (1/K^2) sum_taps C(tu + fu) C(tv + fv) X[kv + tv][ku + tu]
 //     pass 1 (rows, only the N nonzero padded rows): T1[py'][ku]
 //     pass 2 (columns, only the N nonzero inputs):   X[kv][ku]
-//     pass 3: one thread per record gathers its W x W taps from X (L2 resident).
+//     pass 3: eight lanes per record gather its W x W taps from X (L2 resident).
 //   ADJOINT   Z = grid of vis (no Hermitian mirror), Z[cell] = sum over the taps on the cell of
 //             C(tu + fu) C(tv + fv) vis[record], gathered cell by cell from the plan's tap lists
-//             (every tap of every record, grouped by cell): one thread per cell; lists longer
-//             than kLongList (short baselines at every channel crowd a few cells near the uv
-//             centre with thousands of taps) are cut into pieces of kPiece taps, one warp per
-//             piece, and the warp that finishes a cell's last piece adds the cell's pieces in
-//             order (a per-cell ticket; the tickets reset themselves).  The order of a list is fixed when
+//             (every tap of every record, grouped by cell): one thread per non-empty cell; lists
+//             longer than kLongList (short baselines at every channel crowd a few cells near the
+//             uv centre with thousands of taps) are cut into pieces of kPiece taps, one warp per
+//             piece, and the warp that finishes a cell's last piece adds the cell's pieces (a
+//             per-cell ticket; the tickets reset themselves).  The order of a list is fixed when
 //             the plan is built, so every adjoint with one plan sums in the same order, without
-//             atomics;
+//             atomics;  cells no tap reaches stay zero in a grid the plan clears once;
+//   The plan also sorts the records by 8 x 8-cell tile of their nearest cell (an order of the
+//   caller's records): the interpolation and the gathers then visit neighbouring records
+//   together, whose footprints share grid cells (L1 reuse); inputs and outputs in the caller's
+//   record order go through the permutation.
 //     pass 1 (columns, outputs pruned to the central N rows), pass 2 (rows, central N
 //     columns), img = Re(...) (-1)^(x+y) / (K^2 gc(x) gc(y)).
 //   One instance per call: the passes use strips a quarter as wide as the batched imaging
@@ -93,7 +97,8 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_fwd_cols(const float2 *__rest
 
 __global__ void __launch_bounds__(256) k_interp(const float2 *__restrict__ X, const Rec *__restrict__ rec, int64_t n,
                                                 int G, int W, const float *__restrict__ tab, int ntab, float os,
-                                                float invK2, float2 *__restrict__ vis) {
+                                                float invK2, const int32_t *__restrict__ order,
+                                                float2 *__restrict__ vis) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const Rec R = rec[r];
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(256) k_interp(const float2 *__restrict__ X, co
     acc.x *= invK2;
     acc.y *= invK2;
   }
-  vis[r] = acc;
+  vis[order ? order[r] : r] = acc;
 }
 
 // FORWARD pass 3 for W <= 8: eight lanes per record.  Interpolated visibility (before the 1/K^2
@@ -160,7 +165,8 @@ __device__ __forceinline__ float2 interp8_value(const float2 *__restrict__ X, co
 
 __global__ void __launch_bounds__(256) k_interp8(const float2 *__restrict__ X, const Rec *__restrict__ rec, int64_t n,
                                                  int G, int W, const float *__restrict__ tab, int ntab, float os,
-                                                 float invK2, float2 *__restrict__ vis) {
+                                                 float invK2, const int32_t *__restrict__ order,
+                                                 float2 *__restrict__ vis) {
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   const int tv = threadIdx.x & 7;
   Rec R;
@@ -170,17 +176,20 @@ __global__ void __launch_bounds__(256) k_interp8(const float2 *__restrict__ X, c
     ok = record_ok(R, G, (W - 1) / 2);
   }
   const float2 acc = interp8_value(X, R, ok, tv, G, W, tab, ntab, os);
-  if (r < n && tv == 0) vis[r] = ok ? make_float2(acc.x * invK2, acc.y * invK2) : make_float2(0.f, 0.f);
+  if (r < n && tv == 0)
+    vis[order ? order[r] : r] = ok ? make_float2(acc.x * invK2, acc.y * invK2) : make_float2(0.f, 0.f);
 }
 
 // k_interp8 with the chi-square data term fused (one gradient step): the predicted visibility v
-// of record r is not stored; instead resid[r] = 2 w (v - obs) / sigma^2 (the adjoint's input) and
+// of (sorted) record r is not stored; instead resid[r] = 2 w (v - obs) / sigma^2 (the adjoint's
+// input, in the sorted order; obs in the caller's order, read through order) and
 // the block's sum of w |v - obs|^2 / sigma^2 goes to partial[block].  The last block to finish
 // (ticket counter) adds the partials in block order into loss and re-arms the counter.
 constexpr int kInterpThreads = 256;
 __global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *__restrict__ X, const Rec *__restrict__ rec,
                                                                  int64_t n, int G, int W, const float *__restrict__ tab,
                                                                  int ntab, float os, float invK2,
+                                                                 const int32_t *__restrict__ order,
                                                                  const float2 *__restrict__ obs, float inv_s2,
                                                                  float2 *__restrict__ resid, float *__restrict__ partial,
                                                                  unsigned *__restrict__ ticket, float *__restrict__ loss) {
@@ -195,14 +204,14 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *_
   float2 on = make_float2(0.f, 0.f);
   if (r < n) {
     Rn = rec[r];
-    if (tv == 0) on = obs[r];
+    if (tv == 0) on = obs[order[r]];
   }
   for (int64_t r0 = (int64_t)blockIdx.x * (kInterpThreads / 8); r0 < n; r0 += per, r += per) {   // uniform per block
     const Rec R = Rn;
     const float2 o = on;
     if (r + per < n) {
       Rn = rec[r + per];
-      if (tv == 0) on = obs[r + per];
+      if (tv == 0) on = obs[order[r + per]];
     }
     const bool ok = r < n && record_ok(R, G, (W - 1) / 2);
     const float2 acc = interp8_value(X, R, ok, tv, G, W, tab, ntab, os);
@@ -244,56 +253,60 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *_
 }
 
 // ADJOINT gather: Z[c] = sum of its taps' weight x vis.  Lists of at most kLongList taps: one
-// thread per cell; longer lists are cut into pieces of kPiece taps.
+// thread per non-empty cell; longer lists are cut into pieces of kPiece taps.
 constexpr int kLongList = 32;
 constexpr int kPiece = 512;
 constexpr int kPieceBlocks = 592;
+constexpr int kItemBlocks = 1184;
 
 // One launch for both: the first kPieceBlocks blocks take one piece of a long list per warp
 // (lanes stride the piece, then a fixed shuffle tree) into partial[piece] -- they start first,
-// being the longest -- and the others gather the short lists (one thread per cell, four gathers
-// in flight, added in list order).  A piece {cell, first tap, end tap, long-cell index} counts
-// itself on its cell's ticket; the warp that completes the cell adds its pieces' partial sums in
-// piece order (the same sum whichever warp comes last) and resets the ticket for the next call.
-__global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const int2 *__restrict__ taps,
-                                    const float2 *__restrict__ vis, int64_t ncell, float2 *__restrict__ Z,
-                                    const int4 *__restrict__ pieces, const int32_t *__restrict__ n_pieces,
-                                    float2 *__restrict__ partial, const int4 *__restrict__ long_cells,
-                                    int32_t *__restrict__ tickets) {
+// being the longest -- and the others gather the short lists (items {cell, first tap, end tap}
+// of the non-empty short cells in cell order, one thread per item, four gathers in flight,
+// added in list order).  A piece {cell, first tap, end tap, long-cell index} counts itself on
+// its cell's ticket; the warp that completes the cell adds its pieces' partial sums in a fixed
+// order (whichever warp comes last) and resets the ticket for the next call.  counts: {long
+// cells, pieces, short items, -}, then the tickets.
+__global__ void k_adj_gather(const int4 *__restrict__ items, const int2 *__restrict__ taps,
+                             const float2 *__restrict__ vis, float2 *__restrict__ Z, const int4 *__restrict__ pieces,
+                             int32_t *__restrict__ counts, float2 *__restrict__ partial,
+                             const int4 *__restrict__ long_cells) {
   if ((int)blockIdx.x >= kPieceBlocks) {
-    const int64_t c = (int64_t)(blockIdx.x - kPieceBlocks) * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int a = cell_off[c], e = cell_off[c + 1];
-    if (e - a > kLongList) return;
-    float2 z = make_float2(0.f, 0.f);
-    int j = a;
-    for (; j + 4 <= e; j += 4) {
-      int2 t[4];
-      float2 v[4];
+    const int ns = counts[2];
+    for (int i = (blockIdx.x - kPieceBlocks) * blockDim.x + threadIdx.x; i < ns; i += kItemBlocks * blockDim.x) {
+      const int4 it = items[i];
+      const int e = it.z;
+      float2 z = make_float2(0.f, 0.f);
+      int j = it.y;
+      for (; j + 4 <= e; j += 4) {
+        int2 t[4];
+        float2 v[4];
 #pragma unroll
-      for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
+        for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
 #pragma unroll
-      for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
+        for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const float w = __int_as_float(t[k].y);
-        z.x += w * v[k].x;
-        z.y += w * v[k].y;
+        for (int k = 0; k < 4; k++) {
+          const float w = __int_as_float(t[k].y);
+          z.x += w * v[k].x;
+          z.y += w * v[k].y;
+        }
       }
+      for (; j < e; j++) {
+        const int2 t = __ldg(taps + j);
+        const float w = __int_as_float(t.y);
+        const float2 v = __ldg(vis + t.x);
+        z.x += w * v.x;
+        z.y += w * v.y;
+      }
+      Z[it.x] = z;
     }
-    for (; j < e; j++) {
-      const int2 t = __ldg(taps + j);
-      const float w = __int_as_float(t.y);
-      const float2 v = __ldg(vis + t.x);
-      z.x += w * v.x;
-      z.y += w * v.y;
-    }
-    Z[c] = z;
     return;
   }
+  int32_t *tickets = counts + 4;
   const int lane = threadIdx.x & 31;
   const int nw = kPieceBlocks * (blockDim.x >> 5);
-  const int np = *n_pieces;
+  const int np = counts[1];
   for (int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < np; k += nw) {
     const int4 pc = pieces[k];
     float2 z = make_float2(0.f, 0.f);
@@ -331,15 +344,26 @@ __global__ void k_adj_gather_pieces(const int32_t *__restrict__ cell_off, const 
       __threadfence();                               // the partial is visible before the ticket
       lc = long_cells[pc.w];                         // {cell, first piece, pieces, -}
       last = atomicAdd(tickets + pc.w, 1) == lc.z - 1;
-      if (last) {
-        __threadfence();                             // the other pieces' partials, seen after theirs
-        float2 s = make_float2(0.f, 0.f);
-        for (int q = 0; q < lc.z; q++) {
-          const float2 v = __ldcg(partial + lc.y + q);
-          s.x += v.x;
-          s.y += v.y;
-        }
-        Z[lc.x] = s;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {                                      // this warp adds the cell's pieces
+      __threadfence();                               // the other pieces' partials, seen after theirs
+      lc.x = __shfl_sync(0xffffffffu, lc.x, 0);
+      lc.y = __shfl_sync(0xffffffffu, lc.y, 0);
+      lc.z = __shfl_sync(0xffffffffu, lc.z, 0);
+      float2 sum = make_float2(0.f, 0.f);
+      for (int q = lane; q < lc.z; q += 32) {        // lane-strided, then a fixed tree: one order
+        const float2 v = __ldcg(partial + lc.y + q);
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+      }
+      if (lane == 0) {
+        Z[lc.x] = sum;
         tickets[pc.w] = 0;                           // ready for the next adjoint with this plan
       }
     }
@@ -421,43 +445,51 @@ struct GradStep {
   unsigned *ticket = nullptr;
 };
 
+// FORWARD on the plan's sorted records: vis[order[i]] (caller order) or, with sorted_out,
+// vis[i]; in a gradient step vis receives the sorted residual seed.
 template <int G>
-void forward_G(const float *img, const Rec *rec, int64_t n, int W, int os, const float *tab, const float2 *tw,
-               const float *gc, float K2, float2 *T1, float2 *X, float2 *vis, cudaStream_t s, const GradStep &gs) {
+void forward_G(const float *img, const OpPlan &p, float2 *vis, bool sorted_out, cudaStream_t s, const GradStep &gs) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
-  k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, tw, gc, T1);
+  const int64_t n = p.n_vis;
+  const int ntab = table_len(p.W, p.os);
+  k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, p.tw, p.gc, p.T);
   note_launch();
   cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(T1, tw, X);
+  k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(p.T, p.tw, p.X);
   note_launch();
   if (gs.obs) {              // gradient step: vis receives the residual seed (W <= 8 checked by the caller)
     k_interp8_chi2<<<grad_interp_blocks(n), kInterpThreads, 0, s>>>(
-        X, rec, n, G, W, tab, table_len(W, os), (float)os, 1.f / K2, gs.obs, gs.inv_s2, vis, gs.partial, gs.ticket,
-        gs.loss);
+        p.X, p.srec, n, G, p.W, p.tab, ntab, (float)p.os, 1.f / p.K2, p.order, gs.obs, gs.inv_s2, vis, gs.partial,
+        gs.ticket, gs.loss);
     note_launch();
     return;
   }
-  if (n > 0 && W <= 8) {
-    k_interp8<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
-                                                               1.f / K2, vis);
+  const int32_t *ord = sorted_out ? nullptr : p.order;
+  if (n > 0 && p.W <= 8) {
+    k_interp8<<<(unsigned)((n * 8 + 255) / 256), 256, 0, s>>>(p.X, p.srec, n, G, p.W, p.tab, ntab, (float)p.os,
+                                                               1.f / p.K2, ord, vis);
     note_launch();
   } else if (n > 0) {
-    k_interp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(X, rec, n, G, W, tab, table_len(W, os), (float)os,
-                                                          1.f / K2, vis);
+    k_interp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.X, p.srec, n, G, p.W, p.tab, ntab, (float)p.os,
+                                                          1.f / p.K2, ord, vis);
     note_launch();
   }
 }
 
+// ADJOINT of sorted-order visibilities: gather into the plan's grid Zs, then the two passes.
 template <int G>
-void adjoint_G(const float2 *Z, const float2 *tw, const float *gc, float K2, float2 *T, float *img, cudaStream_t s,
-               int upd, float eta, float *grad) {
+void adjoint_G(const float2 *vis_sorted, const OpPlan &p, float *img, cudaStream_t s, int upd, float eta,
+               float *grad) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
-  cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  k_adj_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(Z, tw, T);
+  k_adj_gather<<<kPieceBlocks + kItemBlocks, 256, 0, s>>>(p.items, p.taps, vis_sorted, p.Zs, p.pieces, p.counts,
+                                                          p.partial, p.long_cells);
   note_launch();
-  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(T, tw, gc, 1.f / K2, img, upd, eta, grad);
+  cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  k_adj_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(p.Zs, p.tw, p.T);
+  note_launch();
+  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(p.T, p.tw, p.gc, 1.f / p.K2, img, upd, eta, grad);
   note_launch();
 }
 
@@ -560,6 +592,57 @@ __global__ void k_tap_fill(const Rec *__restrict__ rec, int64_t n, int G, int W,
       taps[p] = make_int2((int)r, __float_as_int(kernel_lookup(tab, ntab, os, (float)tu + R.fu) * cv));
     }
   }
+}
+
+// ---- record order: by 8 x 8-cell tile of the nearest cell; records that are not gridded last
+__device__ __forceinline__ int record_tile(const Rec &R, int G, int h) {
+  const int tg = G >> 3;
+  return record_ok(R, G, h) ? (R.kv >> 3) * tg + (R.ku >> 3) : tg * tg;
+}
+
+__global__ void k_rec_tile_count(const Rec *__restrict__ rec, int64_t n, int G, int W, int32_t *__restrict__ cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  atomicAdd(cnt + record_tile(rec[r], G, (W - 1) / 2), 1);
+}
+
+// toff: exclusive offsets of the tiles; cursor: zeroed counters.  order[i] = caller index of
+// sorted record i, srec[i] = its record.
+__global__ void k_rec_tile_fill(const Rec *__restrict__ rec, int64_t n, int G, int W, const int32_t *__restrict__ toff,
+                                int32_t *__restrict__ cursor, int32_t *__restrict__ order, Rec *__restrict__ srec) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const Rec R = rec[r];
+  const int t = record_tile(R, G, (W - 1) / 2);
+  const int i = toff[t] + atomicAdd(cursor + t, 1);
+  order[i] = (int32_t)r;
+  srec[i] = R;
+}
+
+// flag[c] = 1 for a cell with 1..kLongList taps (scanned afterwards into item positions)
+__global__ void k_short_flags(const int32_t *__restrict__ cell_off, int64_t ncell, int32_t *__restrict__ flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int len = cell_off[c + 1] - cell_off[c];
+  flag[c] = (len > 0 && len <= kLongList) ? 1 : 0;
+}
+
+// items in cell order from the scanned flags (pos); the last cell also writes their count
+__global__ void k_short_fill(const int32_t *__restrict__ cell_off, int64_t ncell, const int32_t *__restrict__ pos,
+                             int4 *__restrict__ items, int32_t *__restrict__ counts) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int a = cell_off[c], e = cell_off[c + 1];
+  const int sh = (e - a > 0 && e - a <= kLongList) ? 1 : 0;
+  if (sh) items[pos[c]] = make_int4((int)c, a, e, 0);
+  if (c == ncell - 1) counts[2] = pos[c] + sh;
+}
+
+// vs[i] = vis[order[i]]: the caller's visibilities in the plan's record order
+__global__ void k_permute(const float2 *__restrict__ vis, const int32_t *__restrict__ order, int64_t n,
+                          float2 *__restrict__ vs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    vs[i] = vis[order[i]];
 }
 
 // The cells whose lists are long, in no particular order, each with its run of pieces
@@ -666,44 +749,16 @@ __global__ void k_axpy(float *__restrict__ y, const float *__restrict__ x, int64
 
 }  // namespace
 
-void launch_degrid_forward(const float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                           const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
-                           float2 *vis, cudaStream_t s) {
-  switch (G) {
+#define MUSER_DEGRID_CASES(X) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+void launch_degrid_forward(const float *img, const OpPlan &p, float2 *vis, cudaStream_t s) {
+  switch (p.G) {
 #define MUSER_CASE(g) \
-  case g: forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, vis, s, GradStep{}); break;
-    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+  case g: forward_G<g>(img, p, vis, false, s, GradStep{}); break;
+    MUSER_DEGRID_CASES(MUSER_CASE)
 #undef MUSER_CASE
     default: break;
   }
-}
-
-void launch_degrid_plan(const Rec *rec, int64_t n_vis, int G, int W, int os, const float *tab, int32_t *cnt,
-                        int32_t *cell_off, int32_t *sums, int2 *taps, int4 *long_cells, int4 *pieces,
-                        int32_t *counts, cudaStream_t s) {
-  const int64_t ncell = (int64_t)G * G;
-  cudaMemsetAsync(cell_off, 0, sizeof(int32_t) * (size_t)(ncell + 1), s);
-  const unsigned rb = (unsigned)((n_vis + 255) / 256);
-  if (n_vis > 0) {
-    k_tap_count<<<rb, 256, 0, s>>>(rec, n_vis, G, W, cell_off);
-    note_launch();
-  }
-  const int nb = (int)((ncell + 1 + kScanPer - 1) / kScanPer);
-  k_scan_blocks<<<nb, kScanThreads, 0, s>>>(cell_off, ncell + 1, sums);
-  note_launch();
-  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb);
-  note_launch();
-  k_scan_add<<<nb, kScanThreads, 0, s>>>(cell_off, ncell + 1, sums);
-  note_launch();
-  if (n_vis > 0) {
-    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)ncell, s);
-    k_tap_fill<<<rb, 256, 0, s>>>(rec, n_vis, G, W, tab, table_len(W, os), (float)os, cell_off, cnt, taps);
-    note_launch();
-  }
-  // counts: {long cells, pieces}, then one ticket per long cell (zero; the adjoint resets them)
-  cudaMemsetAsync(counts, 0, (2 + (size_t)degrid_plan_pieces(n_vis, G, W)) * sizeof(int32_t), s);
-  k_long_cells<<<(unsigned)((ncell + 255) / 256), 256, 0, s>>>(cell_off, ncell, long_cells, counts, pieces);
-  note_launch();
 }
 
 int64_t degrid_plan_pieces(int64_t n_vis, int G, int W) {
@@ -712,21 +767,80 @@ int64_t degrid_plan_pieces(int64_t n_vis, int G, int W) {
   return taps / kPiece + longs + 1;
 }
 
+int64_t degrid_plan_items(int64_t n_vis, int G, int W) {
+  const int64_t taps = n_vis * W * W, ncell = (int64_t)G * G;
+  return (taps < ncell ? taps : ncell) + 1;
+}
+
 int degrid_plan_scan_blocks(int G) { return (int)(((int64_t)G * G + 1 + kScanPer - 1) / kScanPer); }
 
-void launch_degrid_adjoint(const float2 *vis, int N, int G, const float2 *tw, const float *gc, float K2,
-                           const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                           int32_t *counts, float2 *partial, float2 *Z, float2 *T, float *img,
-                           cudaStream_t s) {
-  const int64_t ncell = (int64_t)G * G;
-  const int nbg = (int)((ncell + 255) / 256);
-  k_adj_gather_pieces<<<nbg + kPieceBlocks, 256, 0, s>>>(cell_off, taps, vis, ncell, Z, pieces, counts + 1, partial,
-                                                         long_cells, counts + 2);
+namespace {
+// exclusive scan of a[0..n) in place (n <= G * G + 1 of the plan's scan scratch)
+void scan_excl(int32_t *a, int64_t n, int32_t *sums, cudaStream_t s) {
+  const int nb = (int)((n + kScanPer - 1) / kScanPer);
+  k_scan_blocks<<<nb, kScanThreads, 0, s>>>(a, n, sums);
   note_launch();
-  switch (G) {
+  k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb);
+  note_launch();
+  k_scan_add<<<nb, kScanThreads, 0, s>>>(a, n, sums);
+  note_launch();
+}
+}  // namespace
+
+void launch_degrid_plan(const Rec *rec, const OpPlan &p, cudaStream_t s) {
+  const int G = p.G, W = p.W;
+  const int64_t n_vis = p.n_vis, ncell = (int64_t)G * G, tiles = (int64_t)(G / 8) * (G / 8);
+  const unsigned rb = (unsigned)((n_vis + 255) / 256);
+  const unsigned cb = (unsigned)((ncell + 255) / 256);
+  // records sorted by tile: counts (cnt), offsets, fill with a cursor (cell_off as scratch)
+  cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * (size_t)(tiles + 1), s);
+  cudaMemsetAsync(p.cell_off, 0, sizeof(int32_t) * (size_t)(tiles + 1), s);
+  if (n_vis > 0) {
+    k_rec_tile_count<<<rb, 256, 0, s>>>(rec, n_vis, G, W, p.cnt);
+    note_launch();
+  }
+  scan_excl(p.cnt, tiles + 1, p.sums, s);
+  if (n_vis > 0) {
+    k_rec_tile_fill<<<rb, 256, 0, s>>>(rec, n_vis, G, W, p.cnt, p.cell_off, p.order, p.srec);
+    note_launch();
+  }
+  // tap lists by cell, over the sorted records (taps name sorted record indices)
+  cudaMemsetAsync(p.cell_off, 0, sizeof(int32_t) * (size_t)(ncell + 1), s);
+  if (n_vis > 0) {
+    k_tap_count<<<rb, 256, 0, s>>>(p.srec, n_vis, G, W, p.cell_off);
+    note_launch();
+  }
+  scan_excl(p.cell_off, ncell + 1, p.sums, s);
+  if (n_vis > 0) {
+    cudaMemsetAsync(p.cnt, 0, sizeof(int32_t) * (size_t)ncell, s);
+    k_tap_fill<<<rb, 256, 0, s>>>(p.srec, n_vis, G, W, p.tab, table_len(W, p.os), (float)p.os, p.cell_off, p.cnt,
+                                  p.taps);
+    note_launch();
+  }
+  // counts: {long cells, pieces, short items, -}, then one ticket per long cell (zero; the
+  // adjoint resets them after use)
+  cudaMemsetAsync(p.counts, 0, (4 + (size_t)degrid_plan_pieces(n_vis, G, W)) * sizeof(int32_t), s);
+  k_long_cells<<<cb, 256, 0, s>>>(p.cell_off, ncell, p.long_cells, p.counts, p.pieces);
+  note_launch();
+  k_short_flags<<<cb, 256, 0, s>>>(p.cell_off, ncell, p.cnt);
+  note_launch();
+  scan_excl(p.cnt, ncell, p.sums, s);
+  k_short_fill<<<cb, 256, 0, s>>>(p.cell_off, ncell, p.cnt, p.items, p.counts);
+  note_launch();
+  // the adjoint's grid: cells that no tap reaches stay zero
+  cudaMemsetAsync(p.Zs, 0, sizeof(float2) * (size_t)ncell, s);
+}
+
+void launch_degrid_adjoint(const float2 *vis, const OpPlan &p, float *img, cudaStream_t s) {
+  if (p.n_vis > 0) {
+    const int64_t b = (p.n_vis + 255) / 256;
+    k_permute<<<(unsigned)(b < 1184 ? b : 1184), 256, 0, s>>>(vis, p.order, p.n_vis, p.vs);
+    note_launch();
+  }
+  switch (p.G) {
 #define MUSER_CASE(g) \
-  case g: adjoint_G<g>(Z, tw, gc, K2, T, img, s, 0, 0.f, nullptr); break;
-    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+  case g: adjoint_G<g>(p.vs, p, img, s, 0, 0.f, nullptr); break;
+    MUSER_DEGRID_CASES(MUSER_CASE)
 #undef MUSER_CASE
     default: break;
   }
@@ -739,29 +853,21 @@ int grad_interp_blocks(int64_t n_vis) {
   return (int)(b < 1 ? 1 : (b > 592 ? 592 : b));
 }
 
-void launch_grad_step(float *img, const Rec *rec, int64_t n_vis, int N, int G, int W, int os, const float *tab,
-                      const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X, const float2 *obs,
-                      float inv_s2, float2 *resid, float *partial, unsigned *ticket, float *loss,
-                      const int32_t *cell_off, const int2 *taps, const int4 *long_cells, const int4 *pieces,
-                      int32_t *counts, float2 *apartial, float eta, float *grad, cudaStream_t s) {
+void launch_grad_step(float *img, const OpPlan &p, const float2 *obs, float inv_s2, float2 *resid, float *partial,
+                      unsigned *ticket, float *loss, float eta, float *grad, cudaStream_t s) {
   GradStep gs;
   gs.obs = obs;
   gs.inv_s2 = inv_s2;
   gs.partial = partial;
   gs.loss = loss;
   gs.ticket = ticket;
-  const int64_t ncell = (int64_t)G * G;
-  switch (G) {
-#define MUSER_CASE(g)                                                                                \
-  case g:                                                                                            \
-    forward_G<g>(img, rec, n_vis, W, os, tab, tw, gc, K2, T1, X, resid, s, gs);                      \
-    k_adj_gather_pieces<<<(int)((ncell + 255) / 256) + kPieceBlocks, 256, 0, s>>>(                 \
-        cell_off, taps, resid, ncell, X, pieces, counts + 1, apartial, long_cells,                    \
-        counts + 2);                                                          \
-    note_launch();                                                                                   \
-    adjoint_G<g>(X, tw, gc, K2, T1, img, s, 1, eta, grad);                                           \
+  switch (p.G) {
+#define MUSER_CASE(g)                                  \
+  case g:                                              \
+    forward_G<g>(img, p, resid, true, s, gs);          \
+    adjoint_G<g>(resid, p, img, s, 1, eta, grad);      \
     break;
-    MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
+    MUSER_DEGRID_CASES(MUSER_CASE)
 #undef MUSER_CASE
     default: break;
   }
@@ -782,17 +888,22 @@ void launch_chi2(const float2 *pred, const float2 *obs, const Rec *rec, int64_t 
   note_launch();
 }
 
-void launch_normal_apply(const float *v, float *u, const Rec *rec, int64_t n_vis, int N, int G, int W, int os,
-                         const float *tab, const float2 *tw, const float *gc, float K2, float2 *T1, float2 *X,
-                         float2 *y, float inv_s2, const int32_t *cell_off, const int2 *taps, const int4 *long_cells,
-                         const int4 *pieces, int32_t *counts, float2 *apartial, cudaStream_t s) {
-  launch_degrid_forward(v, rec, n_vis, N, G, W, os, tab, tw, gc, K2, T1, X, y, s);
-  if (n_vis > 0) {
-    const int64_t b = (n_vis + 255) / 256;
-    k_hess_seed<<<(unsigned)(b < 1184 ? b : 1184), 256, 0, s>>>(y, rec, n_vis, inv_s2);
-    note_launch();
+void launch_normal_apply(const float *v, float *u, const OpPlan &p, float2 *y, float inv_s2, cudaStream_t s) {
+  switch (p.G) {
+#define MUSER_CASE(g)                                                                      \
+  case g:                                                                                  \
+    forward_G<g>(v, p, y, true, s, GradStep{});                                            \
+    if (p.n_vis > 0) {                                                                     \
+      const int64_t b = (p.n_vis + 255) / 256;                                             \
+      k_hess_seed<<<(unsigned)(b < 1184 ? b : 1184), 256, 0, s>>>(y, p.srec, p.n_vis, inv_s2); \
+      note_launch();                                                                       \
+    }                                                                                      \
+    adjoint_G<g>(y, p, u, s, 0, 0.f, nullptr);                                             \
+    break;
+    MUSER_DEGRID_CASES(MUSER_CASE)
+#undef MUSER_CASE
+    default: break;
   }
-  launch_degrid_adjoint(y, N, G, tw, gc, K2, cell_off, taps, long_cells, pieces, counts, apartial, X, T1, u, s);
 }
 
 void launch_normalize(const float *u, int64_t n, float *v, float *norm, cudaStream_t s) {
