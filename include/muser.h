@@ -347,14 +347,21 @@ MUSER_API int muser_lipschitz(int flags, float *v, const muser_vis_record_t *rec
 MUSER_API int muser_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev,
                          muser_stream_t stream);
 
-/* Launch-shape autotuner.  Times the candidates of one call's launch shape on the given batch
- * and keeps the fastest for later calls of this process with the same grid size (and
- * footprint): MUSER_CALL_GRID chooses the rows of the full-width gridding bands (powers of two
- * dividing G, at most 200 KB of shared memory per band); MUSER_CALL_DIRTY the column-pass
- * strip width (variant 0: 16384/G columns, 20480/G for G = 5 2^m; variant 1: half as wide).
- * rec/vis_off as muser_grid (required for MUSER_CALL_GRID, ignored otherwise); the timed calls
- * run on `stream` with scratch the call allocates and frees itself.  Synchronous; not for use
- * inside a CUDA graph capture.  choice (host, nullable) receives the chosen value.
+/* Launch-shape autotuner (the batch shape's tuning, no counterpart in the paper).  Times the
+ * candidates of one call's launch shape on the given batch and keeps the fastest for later calls of
+ * this process with the same grid size (and footprint):
+ *  MUSER_CALL_GRID   the rows of muser_grid's full-width gridding bands (powers of two dividing G,
+ *                    at most 200 KB of shared memory per band); rec/vis_off as muser_grid;
+ *  MUSER_CALL_DIRTY  muser_dirty's column-pass strip width (variant 0: 16384/G columns, 20480/G for
+ *                    G = 5 2^m; variant 1: half as wide); rec/vis_off ignored;
+ *  MUSER_CALL_IMAGE  muser_image's gridding tile and FFT radix (G = 1024, 2048, 4096): variant bit 0
+ *                    halves the column strip the fused gridding fills (twice the blocks, each with
+ *                    half the shared memory), bit 1 runs the column and row transforms in radix-8
+ *                    stages instead of radix-16; timed on the preparation of one chunk (strip sort,
+ *                    gridding + column pass, row pass).  rec holds B instances of n_vis_total / B
+ *                    records each, as muser_uvw writes them; vis_off is ignored.
+ * The timed calls run on `stream` with scratch the call allocates and frees itself.  Synchronous;
+ * not for use inside a CUDA graph capture.  choice (host, nullable) receives the chosen value.
  * muser_set_tuning sets the value directly (0 = the built-in choice).  Results differ between
  * shapes only in the order of floating-point sums. */
 MUSER_API int muser_autotune(int call_id, const muser_vis_record_t *rec, const int64_t *vis_off, int B,

@@ -330,12 +330,16 @@ class Imager:
 
 
 def autotune(call_id, cfg: Config, rec=None, vis_off=None, B=1):
-    """Time the launch-shape candidates of muser_grid (band rows; needs rec, vis_off) or
-    muser_dirty (column-strip width) on one batch and keep the fastest; returns the choice."""
+    """Time the launch-shape candidates of muser_grid (band rows; needs rec, vis_off), muser_dirty
+    (column-strip width) or muser_image (gridding tile and FFT radix; needs rec of B instances with
+    the same number of records each) on one batch and keep the fastest; returns the choice."""
     vo = _dev(vis_off, torch.int64) if vis_off is not None else None
     if vo is not None:
         B = vo.numel() - 1
     n = int(vo[-1].item()) if vo is not None and B > 0 else 0
+    if call_id == CALL_IMAGE:
+        n = rec.shape[0] if rec is not None else 0
+        vo = None
     out = ctypes.c_int32(0)
     c = cfg.c()
     check(_lib.load().muser_autotune(call_id, _p(rec), _p(vo), B, n, ctypes.byref(c), ctypes.byref(out), _stream()))

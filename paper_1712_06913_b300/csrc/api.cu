@@ -151,7 +151,7 @@ struct ImageWs {
   void *sstate[2] = {nullptr, nullptr};
   DirtyWs<A> d;
   void carve(A &a, int Bc, int n_bl, const muser_config_t &c) {
-    const int S = dirty_strip_width(c.G);
+    const int S = image_strip_width(c.G, 1);     // sized for the narrowest strips a tuned shape may use
     rec = (Rec *)a.template take<Rec>((size_t)Bc * n_bl);
     tab = (float *)a.template take<float>(table_len(c.W, c.os));
     wtab = carve_wtab(a, c);
@@ -373,7 +373,17 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, int> g_band_rows;   // (G, footprint) -> rows
 std::map<int, int> g_dirty_variant;               // G -> column-pass variant
+std::map<int, int> g_image_variant;               // G -> muser_image's fused gridding / FFT variant
 }  // namespace
+int tuned_image_variant(int G) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_image_variant.find(G);
+  return it == g_image_variant.end() ? 0 : it->second;
+}
+void set_tuned_image_variant(int G, int variant) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_image_variant[G] = variant;
+}
 int tuned_band_rows(int G, int W) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_band_rows.find({G, W});
@@ -612,6 +622,7 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   std::lock_guard<std::mutex> enqueue(pp->busy);
   const int N = cfg->N, G = cfg->G, cap = cfg->max_iter;
   const int n_chunks = (B + Bc - 1) / Bc;
+  const int variant = tuned_image_variant(G);
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
   launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s);
   if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
@@ -629,7 +640,7 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
                Wf, cfg->lat_rad, w.rec, nullptr, status, s);
     if (cfg->weight_mode == 1) launch_uniform_weights(w.rec, nullptr, n_bl, n, N, G, w.ucnt, s);
     launch_dirty_gridded(w.rec, n_bl, n, N, G, Wf, cfg->os, w.tab, w.bin_off, w.entries, w.d.tw, w.d.gc, w.d.T,
-                         w.d.partial, R, w.beam[k], st, s, wp);
+                         w.d.partial, R, w.beam[k], st, s, wp, variant);
     if (cfg->thr_mode == 1) {
       launch_gmm(R, n, N, cfg->gmm_bins, w.mu_a[k], w.mu_b[k], st, s);
       if (thr_out) {
@@ -849,17 +860,91 @@ int muser_set_tuning(int call_id, const muser_config_t *cfg, int value) {
     set_tuned_dirty_variant(cfg->G, value);
     return MUSER_OK;
   }
-  return fail(MUSER_ERR_UNSUPPORTED, "muser_set_tuning: MUSER_CALL_GRID or MUSER_CALL_DIRTY");
+  if (call_id == MUSER_CALL_IMAGE) {
+    if (value < 0 || value > 3) return fail(MUSER_ERR_ARG, "muser_image variant must be in [0, 3]");
+    set_tuned_image_variant(cfg->G, value);
+    return MUSER_OK;
+  }
+  return fail(MUSER_ERR_UNSUPPORTED, "muser_set_tuning: MUSER_CALL_GRID, MUSER_CALL_DIRTY or MUSER_CALL_IMAGE");
 }
+
+namespace {
+// muser_autotune for MUSER_CALL_IMAGE: times muser_image's preparation of one chunk (strip sort,
+// fused gridding + column pass, row pass) for each variant on the caller's records, scratch from
+// cudaMalloc.  Returns the fastest variant, or -1 if scratch or a launch failed.
+int tune_image(const Rec *rec, int B, int n_bl, const muser_config_t &c0, cudaStream_t s) {
+  muser_config_t c = c0;
+  c.batch_chunk = 0;
+  c.max_iter = 0;
+  c.clean_variant = 0;
+  const size_t wsb = muser_workspace_size(MUSER_CALL_IMAGE, B, n_bl, &c);
+  const size_t outb = (size_t)B * 5 * c.N * c.N * sizeof(float);
+  void *ws = nullptr, *out = nullptr;
+  int32_t *st = nullptr;
+  bool ok = wsb != SIZE_MAX && cudaMalloc(&ws, wsb) == cudaSuccess && cudaMalloc(&out, outb) == cudaSuccess &&
+            cudaMalloc((void **)&st, sizeof(int32_t) * B) == cudaSuccess;
+  int best = -1;
+  if (ok) {
+    Arena a(ws, wsb);
+    ImageWs<Arena> w;
+    w.carve(a, B, n_bl, c);
+    launch_pswf_table(w.tab, c.W, c.os, w.d.gc, c.G, s);
+    if (w.wtab) launch_wtab(w.wtab, c.w_planes, table_len(c.w_support, c.os), c.os, c.w_support, c.w_max, c.W, s);
+    fft::launch_twiddles(w.d.tw, c.G, s);
+    float *D = (float *)out, *Bm = D + (size_t)B * c.N * c.N;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int v = 0; v < 4 && ok; v++) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 4; rep++) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        cudaMemsetAsync(st, 0, sizeof(int32_t) * B, s);
+        launch_dirty_gridded(rec, n_bl, B, c.N, c.G, w_footprint(c), c.os, w.tab, w.bin_off, w.entries, w.d.tw,
+                             w.d.gc, w.d.T, w.d.partial, D, Bm, st, s, make_wproj(w.wtab, c), v);
+      }
+      cudaEventRecord(e1, s);
+      ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      if (ok && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  cudaStreamSynchronize(s);
+  cudaGetLastError();
+  cudaFree(ws);
+  cudaFree(out);
+  cudaFree(st);
+  return ok ? best : -1;
+}
+}  // namespace
 
 int muser_autotune(int call_id, const muser_vis_record_t *rec, const int64_t *vis_off, int B, int64_t n_vis_total,
                    const muser_config_t *cfg, int32_t *choice, muser_stream_t stream) {
   MUSER_TRY(check_cfg(cfg, IMAGING));
   if (B < 1 || n_vis_total < 0) return fail(MUSER_ERR_ARG, "muser_autotune needs B >= 1");
-  if (call_id != MUSER_CALL_GRID && call_id != MUSER_CALL_DIRTY)
-    return fail(MUSER_ERR_UNSUPPORTED, "muser_autotune: MUSER_CALL_GRID or MUSER_CALL_DIRTY");
+  if (call_id != MUSER_CALL_GRID && call_id != MUSER_CALL_DIRTY && call_id != MUSER_CALL_IMAGE)
+    return fail(MUSER_ERR_UNSUPPORTED, "muser_autotune: MUSER_CALL_GRID, MUSER_CALL_DIRTY or MUSER_CALL_IMAGE");
   if (call_id == MUSER_CALL_GRID && (!rec || !vis_off)) return fail(MUSER_ERR_ARG, "muser_autotune: records needed");
   cudaStream_t s = (cudaStream_t)stream;
+  if (call_id == MUSER_CALL_IMAGE) {
+    if (!rec || n_vis_total % B != 0 || n_vis_total / B < 1)
+      return fail(MUSER_ERR_ARG, "muser_autotune(MUSER_CALL_IMAGE): rec must hold B instances of n_vis_total / B records");
+    const int64_t n_bl = n_vis_total / B;
+    if (n_vis_total >= (int64_t)1 << 30) return fail(MUSER_ERR_UNSUPPORTED, "too many records to tune on");
+    const int best = tune_image((const Rec *)rec, B, (int)n_bl, *cfg, s);
+    if (best < 0) {
+      muser_set_tuning(call_id, cfg, 0);
+      return fail(MUSER_ERR_CUDA, "muser_autotune: scratch allocation or a timed call failed");
+    }
+    muser_set_tuning(call_id, cfg, best);
+    if (choice) *choice = best;
+    return check_launch("muser_autotune");
+  }
   const int G = cfg->G;
   std::vector<int> cand;
   if (call_id == MUSER_CALL_GRID) {

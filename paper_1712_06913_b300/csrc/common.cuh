@@ -162,12 +162,15 @@ void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stri
 // imaging FFT (dirty.cu)
 int dirty_strip_width(int G);
 // Gridding fused into the column pass (the G x G grid never reaches HBM): sorts the dense
-// records [B][stride] into per-strip lists (bin_off [B][G/S + 1], entries [B][stride][2][tiles]),
-// then column pass and row pass as launch_dirty.
+// records [B][stride] into per-strip lists (bin_off [B][G/S + 1], entries [B][stride][2][tiles],
+// S = image_strip_width(G, variant)), then column pass and row pass as launch_dirty.  variant
+// (muser_image's tuned shape, G = 1024 / 2048 / 4096 only): bit 0 half-width strips, bit 1
+// radix-8 FFT stages.
 void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
                           int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
                           float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
-                          WProj wp = WProj{nullptr, 0, 0, 0.f});
+                          WProj wp = WProj{nullptr, 0, 0, 0.f}, int variant = 0);
+int image_strip_width(int G, int variant);
 // variant 0: column strips of dirty_strip_width(G); 1: half as wide (dirty_min_strip_width);
 // partial holds B x G / dirty_min_strip_width(G) floats.
 int dirty_min_strip_width(int G);
@@ -175,7 +178,9 @@ void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const 
                   float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s, int variant = 0);
 
 // Tuned launch shapes (muser_autotune): gridding band rows per (G, footprint), column-pass
-// variant per G.  0 = not tuned (the built-in choice).
+// variant per G, muser_image's fused gridding / FFT variant per G.  0 = not tuned (the built-in choice).
+int tuned_image_variant(int G);
+void set_tuned_image_variant(int G, int variant);
 int tuned_band_rows(int G, int W);
 void set_tuned_band_rows(int G, int W, int rows);
 int tuned_dirty_variant(int G);

@@ -68,14 +68,17 @@ __global__ void __launch_bounds__(fft::ColStrip<G, S_>::NT) k_cols(const float2 
   }
 }
 
-template <int G>
-__global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restrict__ rec, int64_t stride, int W,
-                                                            const float *__restrict__ tab, int ntab, float os,
-                                                            const int32_t *__restrict__ bin_off,
-                                                            const int32_t *__restrict__ entries,
-                                                            const float2 *__restrict__ tw, float2 *__restrict__ T,
-                                                            float *__restrict__ partial, WProj wp) {
-  using C = ColCfg<G>;
+// Column strips of S_ columns (ColCfg<G>::S, or half of it: twice the blocks, each with half the
+// shared memory) and FFT stages of radix MAXR (16, or 8: one stage more, fewer registers).
+template <int G, int S_, int MAXR>
+using GridStrip = fft::ColStrip<G, S_, (G % 5 ? 16 : 32)>;
+
+template <int G, int S_ = ColCfg<G>::S, int MAXR = 16>
+__global__ void __launch_bounds__(GridStrip<G, S_, MAXR>::NT) k_cols_grid(
+    const Rec *__restrict__ rec, int64_t stride, int W, const float *__restrict__ tab, int ntab, float os,
+    const int32_t *__restrict__ bin_off, const int32_t *__restrict__ entries, const float2 *__restrict__ tw,
+    float2 *__restrict__ T, float *__restrict__ partial, WProj wp) {
+  using C = GridStrip<G, S_, MAXR>;
   using Lay = typename C::Layout;
   constexpr int S = C::S, NT = C::NT, NS = G / S;
   extern __shared__ float4 smem4[];
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restri
       if (o >= G / 4 && o < 3 * G / 4) Ti[(size_t)(o - G / 4) * G + x0 + s] = v;
     }
   } store{Ti, x0};
-  fft::run<G, S, NT, +1, true, Lay, true>(sm, tw, load, store);
+  fft::run<G, S, NT, +1, true, Lay, true, MAXR>(sm, tw, load, store);
   float v = load.im_sum;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_cols_grid(const Rec *__restri
   }
 }
 
-template <int G>
+template <int G, int MAXR = 16>
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
                                                        const float *__restrict__ gc, const float *__restrict__ partial,
                                                        int nstrip, int N, float *__restrict__ dirty,
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
       if (y >= lo && y < lo + N && x >= lo && x < lo + N) D[(size_t)(y - lo) * N + (x - lo)] = v.x * f;
     }
   } store{gc, dirty + (size_t)inst * N * N, beam + (size_t)inst * 4 * N * N, y0, N, scale};
-  fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+  fft::run<G, S, NT, +1, false, typename C::Layout, false, MAXR>(sm, tw, load, store);
 }
 
 // the column pass with strips of S columns (the tuned alternative is S / 2)
@@ -240,28 +243,57 @@ void launch_dirty_G(const float2 *Z, int B, int N, const float2 *tw, const float
     launch_dirty_GS<G, S0>(Z, B, N, tw, gc, T, partial, dirty, beam, status, s);
 }
 
+template <int G, int S, int MAXR>
+void launch_dirty_gridded_GSR(const Rec *rec, int64_t stride, int B, int N, int W, int os, const float *tab,
+                              const int32_t *bin_off, const int32_t *entries, const float2 *tw, const float *gc,
+                              float2 *T, float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
+                              WProj wp) {
+  using CC = GridStrip<G, S, MAXR>;
+  using RC = RowCfg<G>;
+  cudaFuncSetAttribute(k_cols_grid<G, S, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
+  cudaFuncSetAttribute(k_rows<G, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
+  const int tps = tiles_per_sample(W, G, S, G);
+  for (int i = 0; i < B; i += 65535) {
+    const int n = B - i < 65535 ? B - i : 65535;
+    k_cols_grid<G, S, MAXR><<<dim3(G / S, n), CC::NT, CC::smem, s>>>(
+        rec + (size_t)i * stride, stride, W, tab, table_len(W, os), (float)os, bin_off + (size_t)i * (G / S + 1),
+        entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / S), wp);
+    note_launch();
+    k_rows<G, MAXR><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(
+        T + (size_t)i * (G / 2) * G, tw, gc, partial + (size_t)i * (G / S), G / S, N, dirty + (size_t)i * N * N,
+        beam + (size_t)i * 4 * N * N, status ? status + i : nullptr);
+    note_launch();
+  }
+}
+
+// variant (the launch shape muser_autotune picks for muser_image): bit 0 half-width column strips,
+// bit 1 radix-8 stages; for G = 1024, 2048 and 4096 (other sides take variant 0)
 template <int G>
 void launch_dirty_gridded_G(const Rec *rec, int64_t stride, int B, int N, int W, int os, const float *tab,
                             const int32_t *bin_off, const int32_t *entries, const float2 *tw, const float *gc,
                             float2 *T, float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s,
-                            WProj wp) {
-  using CC = ColCfg<G>;
-  using RC = RowCfg<G>;
-  cudaFuncSetAttribute(k_cols_grid<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
-  cudaFuncSetAttribute(k_rows<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::smem);
-  const int tps = tiles_per_sample(W, G, CC::S, G);
-  for (int i = 0; i < B; i += 65535) {
-    const int n = B - i < 65535 ? B - i : 65535;
-    k_cols_grid<G><<<dim3(G / CC::S, n), CC::NT, CC::smem, s>>>(
-        rec + (size_t)i * stride, stride, W, tab, table_len(W, os), (float)os, bin_off + (size_t)i * (G / CC::S + 1),
-        entries + (size_t)i * stride * 2 * tps, tw, T + (size_t)i * (G / 2) * G, partial + (size_t)i * (G / CC::S), wp);
-    note_launch();
-    k_rows<G><<<dim3(G / 2 / RC::S, n), RC::NT, RC::smem, s>>>(T + (size_t)i * (G / 2) * G, tw, gc,
-                                                         partial + (size_t)i * (G / CC::S), G / CC::S, N,
-                                                         dirty + (size_t)i * N * N, beam + (size_t)i * 4 * N * N,
-                                                         status ? status + i : nullptr);
-    note_launch();
+                            WProj wp, int variant) {
+  constexpr int S0 = ColCfg<G>::S;
+  constexpr bool TUNED = G == 1024 || G == 2048 || G == 4096;
+  if constexpr (TUNED) {
+    switch (variant & 3) {
+      case 1:
+        launch_dirty_gridded_GSR<G, S0 / 2, 16>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial,
+                                                dirty, beam, status, s, wp);
+        return;
+      case 2:
+        launch_dirty_gridded_GSR<G, S0, 8>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial, dirty,
+                                           beam, status, s, wp);
+        return;
+      case 3:
+        launch_dirty_gridded_GSR<G, S0 / 2, 8>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial,
+                                               dirty, beam, status, s, wp);
+        return;
+      default: break;
+    }
   }
+  launch_dirty_gridded_GSR<G, S0, 16>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial, dirty,
+                                      beam, status, s, wp);
 }
 
 }  // namespace
@@ -290,6 +322,11 @@ int dirty_min_strip_width(int G) {
   return S >= 2 ? S / 2 : S;
 }
 
+int image_strip_width(int G, int variant) {
+  const bool tuned = G == 1024 || G == 2048 || G == 4096;
+  return (tuned && (variant & 1)) ? dirty_min_strip_width(G) : dirty_strip_width(G);
+}
+
 void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const float *gc, float2 *T, float *partial,
                   float *dirty, float *beam, int32_t *status, cudaStream_t s, int variant) {
   if (B <= 0) return;
@@ -305,16 +342,17 @@ void launch_dirty(const float2 *Z, int B, int N, int G, const float2 *tw, const 
 
 void launch_dirty_gridded(const Rec *rec, int64_t stride, int B, int N, int G, int W, int os, const float *tab,
                           int32_t *bin_off, int32_t *entries, const float2 *tw, const float *gc, float2 *T,
-                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s, WProj wp) {
+                          float *partial, float *dirty, float *beam, int32_t *status, cudaStream_t s, WProj wp,
+                          int variant) {
   if (B <= 0) return;
-  const int S = dirty_strip_width(G);
+  const int S = image_strip_width(G, variant);
   if (S == 0) return;
   launch_grid_sort(rec, nullptr, stride, B, G, W, true, G, S, bin_off, entries, status, s);
   switch (G) {
 #define MUSER_CASE(g)                                                                                          \
   case g:                                                                                                      \
     launch_dirty_gridded_G<g>(rec, stride, B, N, W, os, tab, bin_off, entries, tw, gc, T, partial, dirty, beam, \
-                              status, s, wp);                                                                  \
+                              status, s, wp, variant);                                                         \
     break;
     MUSER_CASE(64) MUSER_CASE(128) MUSER_CASE(256) MUSER_CASE(512) MUSER_CASE(1024) MUSER_CASE(2048) MUSER_CASE(4096)
     MUSER_CASE(640) MUSER_CASE(1280) MUSER_CASE(2560) MUSER_CASE(5120) MUSER_CASE(10240) MUSER_CASE(20480)

@@ -211,26 +211,32 @@ struct Sequential {           // one sequence after another: for rows
   __device__ __forceinline__ static int at(int i, int s) { return s * PL + i + (i >> 4); }
 };
 
-template <int L>
+// Stages of radix MAXR (16 or 8) after one remainder stage; MAXR = 8 takes one stage more
+// (4096 = 8^4 against 16^3) with half the values per butterfly (fewer registers, more butterflies
+// per thread).
+template <int L, int MAXR = 16>
 struct Plan {
+  static_assert(MAXR == 16 || MAXR == 8, "radix 16 or 8");
+  static constexpr int LGR = MAXR == 16 ? 4 : 3;
   static constexpr bool F5 = L % 5 == 0;
   static constexpr int L2 = F5 ? L / 5 : L;            // the power-of-two factor
   static_assert(L2 > 0 && (L2 & (L2 - 1)) == 0, "L = 2^m or 5 * 2^m");
   static constexpr int LOG2L = ilog2(L2);
-  static constexpr int REM = LOG2L % 4;
-  static constexpr int NST = LOG2L / 4 + ((REM || F5) ? 1 : 0);
+  static constexpr int REM = LOG2L % LGR;
+  static constexpr int NST = LOG2L / LGR + ((REM || F5) ? 1 : 0);
   template <int STAGE>
-  static constexpr int radix() { return STAGE == 0 ? (F5 ? 5 << REM : (REM ? 1 << REM : 16)) : 16; }
+  static constexpr int radix() { return STAGE == 0 ? (F5 ? 5 << REM : (REM ? 1 << REM : MAXR)) : MAXR; }
 };
 
 // One stage and (recursively) the following ones.  SFAST: work items enumerate the
 // sequence index fastest (column strips, coalesced global rows) or the butterfly index
 // fastest (rows).  NT threads; a stage whose S * L / R items are not a multiple of NT leaves
 // the surplus threads of the last sweep over the items idle (the radix 5 Q stages).
-template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, bool SYNC0, class Load, class Store>
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, int STAGE, int LS, bool SYNC0, int MAXR, class Load,
+          class Store>
 __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
-  constexpr int R = Plan<L>::template radix<STAGE>();
-  constexpr bool FIRST = STAGE == 0, LAST = STAGE == Plan<L>::NST - 1;
+  constexpr int R = Plan<L, MAXR>::template radix<STAGE>();
+  constexpr bool FIRST = STAGE == 0, LAST = STAGE == Plan<L, MAXR>::NST - 1;
   constexpr int NB = L / R;
   constexpr int ITEMS = S * NB;
   static_assert(ITEMS % NT == 0 || R % 5 == 0, "work items must divide among threads");
@@ -281,15 +287,16 @@ __device__ __forceinline__ void stages(float2 *sm, const float2 *__restrict__ tw
   }
   if constexpr (!LAST) {
     __syncthreads();
-    stages<L, S, NT, SIGN, SFAST, Layout, STAGE + 1, LS * R, false>(sm, tw, load, store);
+    stages<L, S, NT, SIGN, SFAST, Layout, STAGE + 1, LS * R, false, MAXR>(sm, tw, load, store);
   }
 }
 
 // SYNC0: the Load functor reads the block's own shared memory (data placed there before the
 // call), so the first stage waits for every load before it stores.
-template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, bool SYNC0 = false, class Load, class Store>
+template <int L, int S, int NT, int SIGN, bool SFAST, class Layout, bool SYNC0 = false, int MAXR = 16, class Load,
+          class Store>
 __device__ __forceinline__ void run(float2 *sm, const float2 *__restrict__ tw, Load &load, Store &store) {
-  stages<L, S, NT, SIGN, SFAST, Layout, 0, 1, SYNC0>(sm, tw, load, store);
+  stages<L, S, NT, SIGN, SFAST, Layout, 0, 1, SYNC0, MAXR>(sm, tw, load, store);
 }
 
 // Column strips: S columns of a G x G array per block, 16 complex values per thread per stage

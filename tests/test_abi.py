@@ -110,6 +110,10 @@ def test_call_argument_errors_without_a_gpu():
     assert lib.muser_set_tuning(m.CALL_GRID, ctypes.byref(c), 3) != 0
     assert lib.muser_set_tuning(m.CALL_DIRTY, ctypes.byref(c), 2) != 0
     assert lib.muser_set_tuning(m.CALL_CLEAN, ctypes.byref(c), 0) != 0
+    # muser_image's tuned shape: variants 0..3
+    assert lib.muser_set_tuning(m.CALL_IMAGE, ctypes.byref(c), 4) != 0
+    assert lib.muser_set_tuning(m.CALL_IMAGE, ctypes.byref(c), 2) == 0
+    assert lib.muser_set_tuning(m.CALL_IMAGE, ctypes.byref(c), 0) == 0
     # muser_selftest_wait: bound above about one second
     st = ctypes.c_void_p(16)
     assert lib.muser_selftest_wait(1 << 40, st, null) != 0

@@ -258,3 +258,47 @@ def test_hessian_product_power_iteration_and_update_vs_oracle(m, N):
     m.axpy(xb, grad, -eta)
     assert float(la[0]) == float(lb[0])
     assert float((xa - xb).abs().max()) <= 1e-6 * float(xa.abs().max())
+
+
+# ------------------------------------------------------------------------------ muser_image's tuned shapes
+@pytest.mark.parametrize("name,N", [("N256", 256), ("N1024", 1024)])
+def test_image_variants_follow_oracle_and_autotune(m, name, N):
+    """Every gridding-tile / FFT-radix variant of muser_image (half-width column strips, radix-8
+    stages, both) gives the default variant's dirty maps to 1e-6 of the peak and CLEAN lists that
+    follow the oracle; muser_autotune(MUSER_CALL_IMAGE) picks one of them on the caller's records."""
+    import torch
+    if N == 256:
+        wl = synth.small_workload(n_ant=31, N=256, n_frame=3, config_id=240, bmax=2000.0, max_iter=150)
+    else:
+        wl = synth.config3_muser2_uneven(n_frame=1, chans=[5, 250, 500])
+        wl.max_iter = 150
+    cell = m.pixel_size(wl.freq, wl.bmax, wl.N, wl.fov_min)
+    ro = oracle_records(wl)
+    assert_no_ties(ro, wl.G, wl.W)
+    maps, outs = {}, {}
+    try:
+        for v in range(4):
+            m.set_tuning(m.CALL_IMAGE, cfg_for(m, wl), v)
+            d = _image(m, wl, cfg_for(m, wl, max_iter=0))
+            maps[v] = _np(d.residual)
+            outs[v] = _image(m, wl, cfg_for(m, wl))
+        peak = np.abs(maps[0]).max()
+        for v in (1, 2, 3):
+            assert np.abs(maps[v] - maps[0]).max() <= 1e-6 * peak, v
+        jobs = []
+        for v in range(4):
+            for j in _jobs(wl, ro, outs[v], wl.max_iter, 0):
+                j["inst"] = (v, j["inst"])
+                jobs.append(j)
+        res = _pool_map(_oracle_jobs.check_image_instance, jobs)
+        assert len(res) == 4 * wl.n_inst
+        # the tuner, on the records muser_uvw writes for this batch
+        cfg = cfg_for(m, wl)
+        rec, _, _ = m.uvw(wl.ant_enu, wl.pairs, wl.ha, wl.dec, wl.freq, cell, wl.vis, cfg, flags=wl.flags)
+        choice = m.autotune(m.CALL_IMAGE, cfg, rec=rec, B=wl.n_inst)
+        assert 0 <= choice <= 3
+        tuned = _image(m, wl, cfg)
+        torch.cuda.synchronize()
+        assert np.array_equal(_np(tuned.comp_pos), _np(outs[choice].comp_pos))
+    finally:
+        m.set_tuning(m.CALL_IMAGE, cfg_for(m, wl), 0)
