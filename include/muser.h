@@ -65,7 +65,7 @@ enum {
   MUSER_ST_NO_DISK = 128        /* muser_center: no pixel above the mask level; offset 0 */
 };
 
-enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4 };
+enum { MUSER_FORWARD = 0, MUSER_ADJOINT = 1, MUSER_REUSE_PLAN = 4, MUSER_GRAD_CHAIN = 8, MUSER_GRAD_ROWS_READY = 16 };
 
 enum {
   MUSER_CALL_GRID = 1, MUSER_CALL_DIRTY = 2, MUSER_CALL_GMM = 3, MUSER_CALL_CLEAN = 4,
@@ -310,7 +310,11 @@ MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser
  * float, out), grad [N][N] (out, nullable).  flags: 0 builds the plan (as muser_degrid without
  * MUSER_REUSE_PLAN) in ws, MUSER_REUSE_PLAN reuses the plan a previous muser_degrid or
  * muser_grad_step built in the same ws for the same records.  ws: muser_workspace_size(
- * MUSER_CALL_GRAD, 1, n_vis, cfg) bytes (it holds the muser_degrid workspace at its start).  W <= 8. */
+ * MUSER_CALL_GRAD, 1, n_vis, cfg) bytes (it holds the muser_degrid workspace at its start).  W <= 8.
+ * Chained descent: MUSER_GRAD_CHAIN makes the call end with the next step's first transform pass
+ * (the forward rows of the updated image) left in ws; a following call on the same ws and image,
+ * with nothing else run on ws and the image unchanged in between, passes MUSER_GRAD_ROWS_READY
+ * (with MUSER_REUSE_PLAN) and skips that pass: one launch fewer per step of a descent loop. */
 MUSER_API int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_t n_vis, const float *obs,
                               float inv_sigma2, float eta, float *loss, float *grad, const muser_config_t *cfg,
                               void *ws, size_t ws_bytes, muser_stream_t stream);

@@ -12,7 +12,7 @@ from . import _build
 MUSER_OK, MUSER_ERR_ARG, MUSER_ERR_CUDA, MUSER_ERR_TIMEOUT, MUSER_ERR_UNSUPPORTED, MUSER_ERR_WORKSPACE = range(6)
 (ST_ALL_FLAGGED, ST_NONFINITE, ST_DROPPED, ST_GMM_DEGENERATE, ST_ITER_CAP, ST_BEAM_FIT, ST_TIMEOUT,
  ST_NO_DISK) = 1, 2, 4, 8, 16, 32, 64, 128
-FORWARD, ADJOINT, REUSE_PLAN = 0, 1, 4
+FORWARD, ADJOINT, REUSE_PLAN, GRAD_CHAIN, GRAD_ROWS_READY = 0, 1, 4, 8, 16
 (CALL_GRID, CALL_DIRTY, CALL_GMM, CALL_CLEAN, CALL_RESTORE, CALL_IMAGE, CALL_DEGRID, CALL_CHI2, CALL_CENTER,
  CALL_STEER, CALL_GRAD) = range(1, 12)
 

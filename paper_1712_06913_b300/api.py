@@ -582,10 +582,12 @@ class DegridPlan:
         self.cw, self.cwb = self.cws.get(workspace_size(CALL_CHI2, 1, self.n, None))
         self.planned = False
         self.lib = _lib.load()
+        self.rows_ready = None        # the image whose forward row pass a chained step left in ws
 
     def _flag(self, d):
         f = d | (_lib.REUSE_PLAN if self.planned else 0)
         self.planned = True
+        self.rows_ready = None
         return f
 
     def forward(self, img):
@@ -602,13 +604,20 @@ class DegridPlan:
                                     ctypes.byref(self.c), self.w, self.wb, _stream()))
         return out
 
-    def grad_step(self, img, obs, inv_sigma2: float, eta: float, loss, grad=None):
+    def grad_step(self, img, obs, inv_sigma2: float, eta: float, loss, grad=None, chain=False):
         """img -= eta grad chi2(img) in place (one library call, muser_grad_step); loss [1] (device)
-        receives chi2 at the incoming img, grad (optional [N, N]) the gradient."""
-        check(self.lib.muser_grad_step(_lib.REUSE_PLAN if self.planned else 0, _p(img), _p(self.rec), self.n,
-                                       _p(obs), float(inv_sigma2), float(eta), _p(loss), _p(grad),
-                                       ctypes.byref(self.c), self.w, self.wb, _stream()))
+        receives chi2 at the incoming img, grad (optional [N, N]) the gradient.  chain=True leaves
+        the next step's first pass in the workspace; a following chained step on the same image
+        tensor (changed by nothing else in between) then skips that pass."""
+        flags = _lib.REUSE_PLAN if self.planned else 0
+        if chain:
+            flags |= _lib.GRAD_CHAIN
+            if self.planned and self.rows_ready == img.data_ptr():
+                flags |= _lib.GRAD_ROWS_READY
+        check(self.lib.muser_grad_step(flags, _p(img), _p(self.rec), self.n, _p(obs), float(inv_sigma2), float(eta),
+                                       _p(loss), _p(grad), ctypes.byref(self.c), self.w, self.wb, _stream()))
         self.planned = True
+        self.rows_ready = img.data_ptr() if chain else None
 
     def normal_apply(self, v, inv_sigma2: float, out=None):
         """u = 2 Re A^H (w A v) / sigma^2, the chi-square Hessian applied to v (muser_normal_apply)."""
@@ -617,6 +626,7 @@ class DegridPlan:
         check(self.lib.muser_normal_apply(_lib.REUSE_PLAN if self.planned else 0, _p(v), _p(u), _p(self.rec), self.n,
                                           float(inv_sigma2), ctypes.byref(self.c), self.w, self.wb, _stream()))
         self.planned = True
+        self.rows_ready = None
         return u
 
     def lipschitz(self, v, inv_sigma2: float, iters: int, L=None):
@@ -627,6 +637,7 @@ class DegridPlan:
                                        float(inv_sigma2), int(iters), _p(L), ctypes.byref(self.c), self.w, self.wb,
                                        _stream()))
         self.planned = True
+        self.rows_ready = None
         return L
 
     def chi2(self, pred, obs, inv_sigma2: float):

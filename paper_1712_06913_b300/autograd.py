@@ -95,6 +95,11 @@ class GradientImaging:
                 api.normalize(u, v, L)
         return float(L[0])
 
+    def reset_chain(self):
+        """Forget the forward pass the last chained step left in the workspace (call it after
+        writing self.x outside step())."""
+        self.plan.rows_ready = None
+
     def _buffers(self):
         import torch
         if not hasattr(self, "_loss_buf"):
@@ -109,8 +114,8 @@ class GradientImaging:
         self._buffers()
         single = _dist.rank_world()[1] == 1
         with torch.no_grad():
-            if single:
-                self.plan.grad_step(self.x, self.obs, self.inv_s2, self.eta, self._loss_buf)
+            if single:                  # chained: each step leaves the next one's first pass done
+                self.plan.grad_step(self.x, self.obs, self.inv_s2, self.eta, self._loss_buf, chain=True)
             else:
                 self.plan.grad_step(self.x, self.obs, self.inv_s2, 0.0, self._loss_buf, self._grad_buf)
                 _dist.all_sum_(self._grad_buf)

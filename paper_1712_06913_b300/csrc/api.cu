@@ -721,7 +721,10 @@ int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_
                     float inv_sigma2, float eta, float *loss, float *grad, const muser_config_t *cfg, void *ws,
                     size_t ws_bytes, muser_stream_t stream) {
   MUSER_TRY(check_cfg(cfg, DEGRID));
-  if ((flags & ~MUSER_REUSE_PLAN) != 0) return fail(MUSER_ERR_ARG, "flags: 0 or MUSER_REUSE_PLAN");
+  if ((flags & ~(MUSER_REUSE_PLAN | MUSER_GRAD_CHAIN | MUSER_GRAD_ROWS_READY)) != 0)
+    return fail(MUSER_ERR_ARG, "flags: MUSER_REUSE_PLAN, MUSER_GRAD_CHAIN, MUSER_GRAD_ROWS_READY");
+  if ((flags & MUSER_GRAD_ROWS_READY) && !(flags & MUSER_REUSE_PLAN))
+    return fail(MUSER_ERR_ARG, "MUSER_GRAD_ROWS_READY needs MUSER_REUSE_PLAN (the workspace of the previous step)");
   if (n_vis < 1 || n_vis >= (int64_t)1 << 30) return fail(MUSER_ERR_ARG, "n_vis must be in [1, 2^30)");
   if (cfg->W > 8) return fail(MUSER_ERR_UNSUPPORTED, "muser_grad_step needs W <= 8");
   if (!img || !rec || !obs || !loss) return fail(MUSER_ERR_ARG, "muser_grad_step: required pointer is NULL");
@@ -734,7 +737,8 @@ int muser_grad_step(int flags, float *img, const muser_vis_record_t *rec, int64_
   cudaStream_t s = (cudaStream_t)stream;
   if (!(flags & MUSER_REUSE_PLAN)) plan_operator(w.d, (const Rec *)rec, *cfg, s);
   cudaMemsetAsync(w.ticket, 0, sizeof(unsigned), s);
-  launch_grad_step(img, w.d.p, (const float2 *)obs, inv_sigma2, w.resid, w.partial, w.ticket, loss, eta, grad, s);
+  launch_grad_step(img, w.d.p, (const float2 *)obs, inv_sigma2, w.resid, w.partial, w.ticket, loss, eta, grad,
+                   (flags & MUSER_GRAD_ROWS_READY) != 0, (flags & MUSER_GRAD_CHAIN) != 0, s);
   return check_launch("muser_grad_step");
 }
 

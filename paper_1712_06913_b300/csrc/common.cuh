@@ -254,8 +254,11 @@ int chi2_blocks(int64_t n_vis);
 // Hessian applied to v; y: n_vis scratch); norm = |u|, v = u / norm (one block);
 // y += alpha (alpha_dev ? *alpha_dev : 1) x.
 int grad_interp_blocks(int64_t n_vis);
+// rows_ready: the forward row pass of img is already in the plan's T (a previous step's chain);
+// chain: after the update, run the next step's forward row pass on the updated image into T.
 void launch_grad_step(float *img, const OpPlan &p, const float2 *obs, float inv_s2, float2 *resid, float *partial,
-                      unsigned *ticket, float *loss, float eta, float *grad, cudaStream_t s);
+                      unsigned *ticket, float *loss, float eta, float *grad, bool rows_ready, bool chain,
+                      cudaStream_t s);
 void launch_normal_apply(const float *v, float *u, const OpPlan &p, float2 *y, float inv_s2, cudaStream_t s);
 void launch_normalize(const float *u, int64_t n, float *v, float *norm, cudaStream_t s);
 void launch_axpy(float *y, const float *x, int64_t n, float alpha, const float *alpha_dev, cudaStream_t s);

@@ -36,14 +36,13 @@ using ColCfg = fft::ColCfg1<G>;
 template <int G>
 using RowCfg = fft::RowCfg1<G>;
 
-// FORWARD pass 1: rows of the padded image.
+// FORWARD pass 1: rows of the padded image, S rows from r0 (one block).
 template <int G>
-__global__ void __launch_bounds__(RowCfg<G>::NT) k_fwd_rows(const float *__restrict__ img, const float2 *__restrict__ tw,
-                                                           const float *__restrict__ gc, float2 *__restrict__ T1) {
+__device__ __forceinline__ void fwd_rows_strip(const float *__restrict__ img, const float2 *__restrict__ tw,
+                                               const float *__restrict__ gc, float2 *__restrict__ T1, int r0,
+                                               float2 *sm) {
   using C = RowCfg<G>;
   constexpr int N = G / 2, S = C::S, NT = C::NT, LO = G / 2 - N / 2;
-  __shared__ float2 sm[C::Layout::size];
-  const int r0 = blockIdx.x * S;       // image rows r0 .. r0 + S - 1
   struct Load {
     const float *img;
     const float *gc;
@@ -65,6 +64,13 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_fwd_rows(const float *__restr
     }
   } store{T1, r0};
   fft::run<G, S, NT, -1, false, typename C::Layout>(sm, tw, load, store);
+}
+
+template <int G>
+__global__ void __launch_bounds__(RowCfg<G>::NT) k_fwd_rows(const float *__restrict__ img, const float2 *__restrict__ tw,
+                                                           const float *__restrict__ gc, float2 *__restrict__ T1) {
+  __shared__ float2 sm[RowCfg<G>::Layout::size];
+  fwd_rows_strip<G>(img, tw, gc, T1, blockIdx.x * RowCfg<G>::S, sm);
 }
 
 // FORWARD pass 2: columns; inputs outside the central N rows are zero.
@@ -256,15 +262,15 @@ __global__ void __launch_bounds__(kInterpThreads) k_interp8_chi2(const float2 *_
 // thread per non-empty cell; longer lists are cut into pieces of kPiece taps.
 constexpr int kLongList = 32;
 constexpr int kPiece = 512;
-constexpr int kPieceBlocks = 592;
+constexpr int kPieceBlocks = 1184;
 constexpr int kItemBlocks = 1184;
 
 // One launch for both: the first kPieceBlocks blocks take one piece of a long list per warp
 // (lanes stride the piece, then a fixed shuffle tree) into partial[piece] -- they start first,
 // being the longest -- and the others gather the short lists (items {cell, first tap, end tap}
-// of the non-empty short cells in cell order, one thread per item, four gathers in flight,
-// added in list order).  A piece {cell, first tap, end tap, long-cell index} counts itself on
-// its cell's ticket; the warp that completes the cell adds its pieces' partial sums in a fixed
+// of the non-empty short cells in cell order, four lanes per item).  A piece {cell, first tap,
+// end tap, long-cell index} counts itself on its cell's ticket; the warp that completes the cell
+// adds its pieces' partial sums in a fixed
 // order (whichever warp comes last) and resets the ticket for the next call.  counts: {long
 // cells, pieces, short items, -}, then the tickets.
 __global__ void k_adj_gather(const int4 *__restrict__ items, const int2 *__restrict__ taps,
@@ -272,19 +278,24 @@ __global__ void k_adj_gather(const int4 *__restrict__ items, const int2 *__restr
                              int32_t *__restrict__ counts, float2 *__restrict__ partial,
                              const int4 *__restrict__ long_cells) {
   if ((int)blockIdx.x >= kPieceBlocks) {
+    // four lanes per short cell: lane q takes taps q, q + 4, ... (four loads in flight), then a
+    // fixed two-step shuffle tree; the warp sweeps eight cells at a time
     const int ns = counts[2];
-    for (int i = (blockIdx.x - kPieceBlocks) * blockDim.x + threadIdx.x; i < ns; i += kItemBlocks * blockDim.x) {
-      const int4 it = items[i];
-      const int e = it.z;
+    const int q = threadIdx.x & 3;
+    const int stride = kItemBlocks * blockDim.x / 4;
+    const int wbase = ((blockIdx.x - kPieceBlocks) * blockDim.x + (threadIdx.x & ~31)) / 4;   // the warp's first cell
+    for (int i0 = wbase; i0 < ns; i0 += stride) {                                          // uniform per warp
+      const int i = i0 + ((threadIdx.x & 31) >> 2);
+      int4 it = make_int4(0, 0, 0, 0);
+      if (i < ns) it = items[i];
       float2 z = make_float2(0.f, 0.f);
-      int j = it.y;
-      for (; j + 4 <= e; j += 4) {
+      for (int j = it.y + q; j < it.z; j += 16) {
         int2 t[4];
         float2 v[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) t[k] = __ldg(taps + j + k);
+        for (int k = 0; k < 4; k++) t[k] = j + 4 * k < it.z ? __ldg(taps + j + 4 * k) : make_int2(0, 0);
 #pragma unroll
-        for (int k = 0; k < 4; k++) v[k] = __ldg(vis + t[k].x);
+        for (int k = 0; k < 4; k++) v[k] = j + 4 * k < it.z ? __ldg(vis + t[k].x) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
           const float w = __int_as_float(t[k].y);
@@ -292,14 +303,11 @@ __global__ void k_adj_gather(const int4 *__restrict__ items, const int2 *__restr
           z.y += w * v[k].y;
         }
       }
-      for (; j < e; j++) {
-        const int2 t = __ldg(taps + j);
-        const float w = __int_as_float(t.y);
-        const float2 v = __ldg(vis + t.x);
-        z.x += w * v.x;
-        z.y += w * v.y;
-      }
-      Z[it.x] = z;
+      z.x += __shfl_xor_sync(0xffffffffu, z.x, 1);
+      z.y += __shfl_xor_sync(0xffffffffu, z.y, 1);
+      z.x += __shfl_xor_sync(0xffffffffu, z.x, 2);
+      z.y += __shfl_xor_sync(0xffffffffu, z.y, 2);
+      if (q == 0 && i < ns) Z[it.x] = z;
     }
     return;
   }
@@ -399,12 +407,14 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_adj_cols(const float2 *__rest
 }
 
 // ADJOINT pass 2: rows, central N columns, real part, grid correction and 1/K^2.
+// img = grad; or, in a gradient step (upd), img -= eta grad and grad (if given) = grad.  With
+// chain, the block then runs the next step's forward row pass on the image rows it has just
+// updated, into the same rows of T (the rows this block alone reads and writes).
 template <int G>
-// img = grad; or, in a gradient step (upd), img -= eta grad and grad (if given) = grad
-__global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
+__global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(float2 *__restrict__ T, const float2 *__restrict__ tw,
                                                            const float *__restrict__ gc, float invK2,
                                                            float *__restrict__ img, int upd, float eta,
-                                                           float *__restrict__ grad) {
+                                                           float *__restrict__ grad, int chain) {
   using C = RowCfg<G>;
   constexpr int N = G / 2, S = C::S, NT = C::NT, LO = G / 2 - N / 2;
   __shared__ float2 sm[C::Layout::size];
@@ -435,6 +445,10 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(const float2 *__rest
     }
   } store{gc, img, grad, r0, upd, invK2, eta};
   fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
+  if (chain) {
+    __syncthreads();                              // this block's image rows are written
+    fwd_rows_strip<G>(img, tw, gc, T, r0, sm);
+  }
 }
 
 // GradStep: the chi-square term of a gradient step fused into the interpolation (obs set)
@@ -443,6 +457,7 @@ struct GradStep {
   float inv_s2 = 0.f;
   float *partial = nullptr, *loss = nullptr;
   unsigned *ticket = nullptr;
+  bool rows_ready = false;      // the forward row pass of img is already in T (previous step's chain)
 };
 
 // FORWARD on the plan's sorted records: vis[order[i]] (caller order) or, with sorted_out,
@@ -453,8 +468,10 @@ void forward_G(const float *img, const OpPlan &p, float2 *vis, bool sorted_out, 
   using RC = RowCfg<G>;
   const int64_t n = p.n_vis;
   const int ntab = table_len(p.W, p.os);
-  k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, p.tw, p.gc, p.T);
-  note_launch();
+  if (!gs.rows_ready) {
+    k_fwd_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(img, p.tw, p.gc, p.T);
+    note_launch();
+  }
   cudaFuncSetAttribute(k_fwd_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_fwd_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(p.T, p.tw, p.X);
   note_launch();
@@ -480,7 +497,7 @@ void forward_G(const float *img, const OpPlan &p, float2 *vis, bool sorted_out, 
 // ADJOINT of sorted-order visibilities: gather into the plan's grid Zs, then the two passes.
 template <int G>
 void adjoint_G(const float2 *vis_sorted, const OpPlan &p, float *img, cudaStream_t s, int upd, float eta,
-               float *grad) {
+               float *grad, int chain = 0) {
   using CC = ColCfg<G>;
   using RC = RowCfg<G>;
   k_adj_gather<<<kPieceBlocks + kItemBlocks, 256, 0, s>>>(p.items, p.taps, vis_sorted, p.Zs, p.pieces, p.counts,
@@ -489,7 +506,7 @@ void adjoint_G(const float2 *vis_sorted, const OpPlan &p, float *img, cudaStream
   cudaFuncSetAttribute(k_adj_cols<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::smem);
   k_adj_cols<G><<<G / CC::S, CC::NT, CC::smem, s>>>(p.Zs, p.tw, p.T);
   note_launch();
-  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(p.T, p.tw, p.gc, 1.f / p.K2, img, upd, eta, grad);
+  k_adj_rows<G><<<(G / 2) / RC::S, RC::NT, 0, s>>>(p.T, p.tw, p.gc, 1.f / p.K2, img, upd, eta, grad, chain);
   note_launch();
 }
 
@@ -854,18 +871,20 @@ int grad_interp_blocks(int64_t n_vis) {
 }
 
 void launch_grad_step(float *img, const OpPlan &p, const float2 *obs, float inv_s2, float2 *resid, float *partial,
-                      unsigned *ticket, float *loss, float eta, float *grad, cudaStream_t s) {
+                      unsigned *ticket, float *loss, float eta, float *grad, bool rows_ready, bool chain,
+                      cudaStream_t s) {
   GradStep gs;
   gs.obs = obs;
   gs.inv_s2 = inv_s2;
   gs.partial = partial;
   gs.loss = loss;
   gs.ticket = ticket;
+  gs.rows_ready = rows_ready;
   switch (p.G) {
-#define MUSER_CASE(g)                                  \
-  case g:                                              \
-    forward_G<g>(img, p, resid, true, s, gs);          \
-    adjoint_G<g>(resid, p, img, s, 1, eta, grad);      \
+#define MUSER_CASE(g)                                              \
+  case g:                                                          \
+    forward_G<g>(img, p, resid, true, s, gs);                      \
+    adjoint_G<g>(resid, p, img, s, 1, eta, grad, chain ? 1 : 0);   \
     break;
     MUSER_DEGRID_CASES(MUSER_CASE)
 #undef MUSER_CASE

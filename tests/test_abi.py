@@ -105,6 +105,9 @@ def test_call_argument_errors_without_a_gpu():
     # muser_grad_step: bad flags, missing pointers
     cd = m.Config(N=64, G=128).c()
     assert lib.muser_grad_step(3, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
+    # a step that consumes a chained forward pass must reuse the plan's workspace
+    assert lib.muser_grad_step(m._lib.GRAD_ROWS_READY, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd),
+                               null, 0, null) == m._lib.MUSER_ERR_ARG
     assert lib.muser_grad_step(0, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
     # muser_set_tuning: band rows must divide G; column variant 0 or 1
     assert lib.muser_set_tuning(m.CALL_GRID, ctypes.byref(c), 3) != 0
