@@ -11,7 +11,7 @@ Reported (one JSON line on rank 0):
   value      CLEANed images/s, inputs resident on the device (muser_image per step)
   e2e        the same with the visibilities copied from pinned host memory every step and
              the restored images, component lists, counts and status read back (on a copy
-             stream, overlapping the next step)
+             stream, each chunk's as soon as muser_image_events announces it)
   roofline   the dominant kernel (CLEAN): its streaming-model bytes per second against the
              measured HBM copy bandwidth, with the DRAM and L2 fractions it actually reaches
   cpu_baseline  the FP64 oracle on a bounded sample on this host's cores
@@ -302,8 +302,9 @@ def main():
     gpu_launches = launches1 - launches0   # counted by the library as it enqueues its kernels
 
     # ---- end to end: pinned host visibilities in; restored images, CLEAN model and status out,
-    # every step.  Two output sets alternate, so that step k's results stream to the host on a
-    # copy stream while step k + 1 is imaged.
+    # every step.  Each chunk's results stream to the host on a copy stream as soon as the library
+    # announces them (muser_image_events), while the following chunks are imaged; two output sets
+    # alternate between steps.
     vis_host = torch.from_numpy(np.ascontiguousarray(vis.astype(np.complex64))).pin_memory()
     vis_dev = torch.empty_like(vis_host, device="cuda")
     outs = [out, imager.new_output()]
@@ -325,7 +326,8 @@ def main():
     h2d = vis_host.numel() * 8
     d2h = clean_host.numel() * 4 + pos_host.numel() * 4 + flux_host.numel() * 4 + 2 * B * 4
     copy_stream = torch.cuda.Stream()
-    imaged = [torch.cuda.Event() for _ in range(2)]
+    chunks = imager.chunks
+    done = [[torch.cuda.Event() for _ in chunks] for _ in range(2)]
     copied = [torch.cuda.Event() for _ in range(2)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -335,15 +337,17 @@ def main():
         if k >= 2:
             stream.wait_event(copied[j])    # this output set's copy from step k - 2 is done
         vis_dev.copy_(vis_host, non_blocking=True)
-        o = imager.run(vis_dev, out=outs[j])
-        imaged[j].record(stream)
+        o = imager.run(vis_dev, out=outs[j], chunk_done=done[j])
         with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(imaged[j])
-            clean_host.copy_(o.clean[:n_img], non_blocking=True)
-            pos_host.copy_(o.comp_pos, non_blocking=True)
-            flux_host.copy_(o.comp_flux, non_blocking=True)
-            nc_host.copy_(o.n_comp, non_blocking=True)
-            st_host.copy_(o.status, non_blocking=True)
+            for (c0, n), ev in zip(chunks, done[j]):
+                copy_stream.wait_event(ev)
+                c1 = min(c0 + n, n_img)
+                if c1 > c0:
+                    clean_host[c0:c1].copy_(o.clean[c0:c1], non_blocking=True)
+                pos_host[c0:c0 + n].copy_(o.comp_pos[c0:c0 + n], non_blocking=True)
+                flux_host[c0:c0 + n].copy_(o.comp_flux[c0:c0 + n], non_blocking=True)
+                nc_host[c0:c0 + n].copy_(o.n_comp[c0:c0 + n], non_blocking=True)
+                st_host[c0:c0 + n].copy_(o.status[c0:c0 + n], non_blocking=True)
             copied[j].record(copy_stream)
     stream.wait_stream(copy_stream)
     e1.record(stream)
@@ -494,7 +498,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "images/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h,
-                        "copies": "visibilities H2D; " + e2e_images + ", component lists, counts and status D2H"},
+                        "copies": "visibilities H2D; " + e2e_images + ", component lists, counts and status D2H, "
+                                  "each chunk's as soon as the library announces it (muser_image_events)"},
                 "gpu_launches": gpu_launches, "clocks": clk, "extra": extra}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -41,6 +41,7 @@ extern "C" {
 #endif
 
 typedef struct CUstream_st *muser_stream_t;   /* = cudaStream_t */
+typedef struct CUevent_st *muser_event_t;     /* = cudaEvent_t */
 
 /* return codes */
 enum {
@@ -241,6 +242,24 @@ MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pa
                 float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
                 float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
                 muser_stream_t stream);
+
+/* muser_image that announces each chunk's results as soon as they are complete, for pipelines
+ * that stream images out while the next ones are made (Sec. 6.3: real-time monitoring of the
+ * observation stream).  Same arguments, checks and results as muser_image, plus chunk_done:
+ * n_events events created by the caller (cudaEventCreate*).  Once chunk c (instances
+ * [c b, min(B, (c + 1) b)), b = cfg->batch_chunk, or B when that is 0 or >= B) has been restored,
+ * the call records chunk_done[c] on `stream` (cudaEventRecord), for c < n_events; later chunks
+ * are not announced.  A copy stream that waits on chunk_done[c] may then read chunk c's
+ * clean_img, residual, comp_pos, comp_flux, n_comp, thr_out, beam_params and status while the
+ * following chunks are imaged.  chunk_done may be NULL when n_events is 0; a NULL entry is
+ * skipped.  Returns MUSER_ERR_ARG when n_events < 0 or chunk_done is NULL with n_events > 0. */
+MUSER_API int muser_image_events(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl,
+                                 const double *ha, const double *dec, int n_frame, const double *freq_hz,
+                                 const double *cell_rad, int n_chan, const float *vis, const uint8_t *flags,
+                                 const double *dlm, const muser_config_t *cfg, float *clean_img, float *residual,
+                                 int32_t *comp_pos, float *comp_flux, int32_t *n_comp, float *thr_out,
+                                 float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
+                                 const muser_event_t *chunk_done, int n_events, muser_stream_t stream);
 
 /* Degridding measurement operator and its adjoint (the transpose of Alg. 1's gridding +
  * inverse FFT), for gradient-based imaging of one real sky image img[N][N], cfg->G = 2N:

@@ -53,6 +53,8 @@ SIGNATURES = {
     "muser_clean": (I32, [P, P, I32, CFG, P, P, P, P, P, SZ, P, P]),
     "muser_restore": (I32, [P, P, P, P, P, I32, CFG, P, P, P, SZ, P, P]),
     "muser_image": (I32, [P, I32, P, I32, P, P, I32, P, P, I32, P, P, P, CFG, P, P, P, P, P, P, P, P, SZ, P, P]),
+    "muser_image_events": (I32, [P, I32, P, I32, P, P, I32, P, P, I32, P, P, P, CFG, P, P, P, P, P, P, P, P, SZ, P,
+                                 P, I32, P]),
     "muser_degrid": (I32, [I32, P, P, I64, P, CFG, P, SZ, P]),
     "muser_chi2": (I32, [P, P, P, I64, F32, P, P, P, SZ, P]),
     "muser_center": (I32, [P, P, P, P, I32, CFG, P, P, P, P, SZ, P, P]),

@@ -294,17 +294,32 @@ class Imager:
             beam_params=torch.empty((B, 3), dtype=torch.float32, device=dev),
             status=torch.empty(B, dtype=torch.int32, device=dev))
 
-    def run(self, vis=None, out=None):
+    @property
+    def chunks(self):
+        """(first instance, instances) of each chunk muser_image images in turn."""
+        b = self.cfg.batch_chunk if 0 < self.cfg.batch_chunk < self.B else self.B
+        return [(c0, min(b, self.B - c0)) for c0 in range(0, self.B, b)]
+
+    def run(self, vis=None, out=None, chunk_done=None):
         """Launch the whole batch on the current stream (no host synchronisation), writing
-        `out` (default: self.out)."""
+        `out` (default: self.out).  chunk_done: torch.cuda.Event per chunk (see `chunks`), each
+        recorded on the current stream once its chunk's results are complete (muser_image_events),
+        so that another stream can copy them out while the next chunks are imaged."""
         V = self.vis if vis is None else vis
         o = self.out if out is None else out
         w, wb = self.ws.get(self.ws_bytes)
-        check(_lib.load().muser_image(
-            _p(self.ant), self.ant.shape[0], _p(self.pairs), self.nb, _p(self.ha), _p(self.dec), self.F,
-            _p(self.freq), _p(self.cell), self.C, _p(V), _p(self.flags), _p(self.dlm), ctypes.byref(self.c),
-            _p(o.clean), _p(o.residual), _p(o.comp_pos), _p(o.comp_flux), _p(o.n_comp), _p(o.thr),
-            _p(o.beam_params), w, wb, _p(o.status), _stream()))
+        args = (_p(self.ant), self.ant.shape[0], _p(self.pairs), self.nb, _p(self.ha), _p(self.dec), self.F,
+                _p(self.freq), _p(self.cell), self.C, _p(V), _p(self.flags), _p(self.dlm), ctypes.byref(self.c),
+                _p(o.clean), _p(o.residual), _p(o.comp_pos), _p(o.comp_flux), _p(o.n_comp), _p(o.thr),
+                _p(o.beam_params), w, wb, _p(o.status))
+        if chunk_done is None:
+            check(_lib.load().muser_image(*args, _stream()))
+            return o
+        for e in chunk_done:
+            if not e.cuda_event:            # torch creates the CUDA event at its first record
+                e.record()
+        ev = (ctypes.c_void_p * max(1, len(chunk_done)))(*[e.cuda_event for e in chunk_done])
+        check(_lib.load().muser_image_events(*args, ev, len(chunk_done), _stream()))
         return o
 
     def capture(self):

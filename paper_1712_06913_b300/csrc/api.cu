@@ -591,13 +591,15 @@ int muser_restore(const float *residual, const float *beam, const int32_t *comp_
   return check_launch("muser_restore");
 }
 
-int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+namespace {
+int image_batch(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
                 const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
                 const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
                 float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
                 float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
-                muser_stream_t stream) {
+                const muser_event_t *chunk_done, int n_events, muser_stream_t stream) {
   MUSER_TRY(check_cfg(cfg, IMAGING));
+  if (n_events < 0 || (n_events > 0 && !chunk_done)) return fail(MUSER_ERR_ARG, "muser_image_events: chunk_done");
   if (n_ant < 2 || n_bl < 0 || n_frame < 0 || n_chan < 0) return fail(MUSER_ERR_ARG, "negative sizes");
   const int64_t B64 = (int64_t)n_frame * n_chan;
   if (B64 > INT32_MAX) return fail(MUSER_ERR_ARG, "too many instances");
@@ -688,9 +690,34 @@ int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
     // restored, earlier on this stream), then this chunk's restore
     if (c + 1 < n_chunks) prepare(c + 1);
     restore(c);
+    if (c < n_events && chunk_done[c] && cudaEventRecord((cudaEvent_t)chunk_done[c], s) != cudaSuccess)
+      return fail(MUSER_ERR_CUDA, "muser_image_events: cudaEventRecord failed");
     MUSER_TRY(check_launch("muser_image"));
   }
   return check_launch("muser_image");
+}
+}  // namespace
+
+int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+                const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+                const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+                float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
+                float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
+                muser_stream_t stream) {
+  return image_batch(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_frame, freq_hz, cell_rad, n_chan, vis, flags, dlm,
+                     cfg, clean_img, residual, comp_pos, comp_flux, n_comp, thr_out, beam_params, ws, ws_bytes, status,
+                     nullptr, 0, stream);
+}
+
+int muser_image_events(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl, const double *ha,
+                       const double *dec, int n_frame, const double *freq_hz, const double *cell_rad, int n_chan,
+                       const float *vis, const uint8_t *flags, const double *dlm, const muser_config_t *cfg,
+                       float *clean_img, float *residual, int32_t *comp_pos, float *comp_flux, int32_t *n_comp,
+                       float *thr_out, float *beam_params, void *ws, size_t ws_bytes, int32_t *status,
+                       const muser_event_t *chunk_done, int n_events, muser_stream_t stream) {
+  return image_batch(ant_enu, n_ant, bl_pairs, n_bl, ha, dec, n_frame, freq_hz, cell_rad, n_chan, vis, flags, dlm,
+                     cfg, clean_img, residual, comp_pos, comp_flux, n_comp, thr_out, beam_params, ws, ws_bytes, status,
+                     chunk_done, n_events, stream);
 }
 
 int muser_degrid(int direction, float *img, const muser_vis_record_t *rec, int64_t n_vis, float *vis,

@@ -109,6 +109,13 @@ def test_call_argument_errors_without_a_gpu():
     assert lib.muser_grad_step(m._lib.GRAD_ROWS_READY, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd),
                                null, 0, null) == m._lib.MUSER_ERR_ARG
     assert lib.muser_grad_step(0, null, null, 10, null, 1.0, 0.1, null, null, ctypes.byref(cd), null, 0, null) != 0
+    # muser_image_events: a negative event count, or events missing while announced (checked
+    # before any device work)
+    args = [null, 2, null, 1, null, null, 1, null, null, 1, null, null, null, ctypes.byref(c), null, null, null, null,
+            null, null, null, null, 0, null]
+    assert lib.muser_image_events(*args, null, -1, null) == m._lib.MUSER_ERR_ARG
+    assert lib.muser_image_events(*args, null, 2, null) == m._lib.MUSER_ERR_ARG
+    assert b"chunk_done" in lib.muser_last_error()
     # muser_set_tuning: band rows must divide G; column variant 0 or 1
     assert lib.muser_set_tuning(m.CALL_GRID, ctypes.byref(c), 3) != 0
     assert lib.muser_set_tuning(m.CALL_DIRTY, ctypes.byref(c), 2) != 0
