@@ -599,6 +599,20 @@ class DegridPlan:
         self.lib = _lib.load()
         self.rows_ready = None        # the image whose forward row pass a chained step left in ws
 
+    def clone(self):
+        """A second operator over the same records that takes this one's plan (copied, not built
+        again) and has a workspace of its own: the plan's record order and tap lists fix the
+        order of every sum, so the two give identical results, while independently built plans
+        agree only to rounding."""
+        other = DegridPlan(self.rec, self.cfg)
+        if self.planned:
+            s0 = self.w.value - self.ws.buf.data_ptr()
+            d0 = other.w.value - other.ws.buf.data_ptr()
+            n = min(self.wb, other.wb)                   # both hold the whole workspace
+            other.ws.buf[d0:d0 + n].copy_(self.ws.buf[s0:s0 + n])
+            other.planned = True
+        return other
+
     def _flag(self, d):
         f = d | (_lib.REUSE_PLAN if self.planned else 0)
         self.planned = True

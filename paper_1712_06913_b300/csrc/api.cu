@@ -119,7 +119,7 @@ struct GridWs {
 
 template <class A>
 struct DirtyWs {
-  float *gc;
+  float *gc;            // (-1)^x / gc(x), the row pass's grid correction and modulation
   float2 *tw, *T;
   float *partial;
   void carve(A &a, int B, const muser_config_t &c) {
@@ -519,7 +519,7 @@ int muser_dirty(const float *Z, int B, const muser_config_t *cfg, float *dirty, 
   DirtyWs<Arena> w;
   w.carve(a, B, *cfg);
   cudaStream_t s = (cudaStream_t)stream;
-  launch_pswf_table(nullptr, cfg->W, cfg->os, w.gc, cfg->G, s);    // grid correction only
+  launch_pswf_table(nullptr, cfg->W, cfg->os, w.gc, cfg->G, s, 1);   // (-1)^x / gc(x) only
   fft::launch_twiddles(w.tw, cfg->G, s);
   launch_dirty((const float2 *)Z, B, cfg->N, cfg->G, w.tw, w.gc, w.T, w.partial, dirty, beam, status, s,
                tuned_dirty_variant(cfg->G));
@@ -626,7 +626,7 @@ int image_batch(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   const int n_chunks = (B + Bc - 1) / Bc;
   const int variant = tuned_image_variant(G);
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
-  launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s);
+  launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s, 1);
   if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
                           cfg->W, s);
   const WProj wp = make_wproj(w.wtab, *cfg);
@@ -919,7 +919,7 @@ int tune_image(const Rec *rec, int B, int n_bl, const muser_config_t &c0, cudaSt
     Arena a(ws, wsb);
     ImageWs<Arena> w;
     w.carve(a, B, n_bl, c);
-    launch_pswf_table(w.tab, c.W, c.os, w.d.gc, c.G, s);
+    launch_pswf_table(w.tab, c.W, c.os, w.d.gc, c.G, s, 1);
     if (w.wtab) launch_wtab(w.wtab, c.w_planes, table_len(c.w_support, c.os), c.os, c.w_support, c.w_max, c.W, s);
     fft::launch_twiddles(w.d.tw, c.G, s);
     float *D = (float *)out, *Bm = D + (size_t)B * c.N * c.N;

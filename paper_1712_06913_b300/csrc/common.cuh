@@ -129,7 +129,7 @@ struct Sizer {
 };
 
 // ---------------------------------------------------------------- launchers (one per .cu)
-void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t s);
+void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t s, int signed_recip = 0);
 void launch_uvw(const double *ant_enu, int n_ant, const int32_t *pairs, int n_bl, const double *ha, const double *dec,
                 int n_chan, const double *freq, const double *cell, const float2 *vis, const uint8_t *flags,
                 const double *dlm, int inst0, int n_inst, int G, int W, double lat, Rec *rec,
@@ -159,7 +159,8 @@ void launch_grid(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, i
 void launch_grid_sort(const Rec *rec, const int64_t *vis_off, int64_t dense_stride, int B, int G, int W, bool mirror,
                       int tr, int tc, int32_t *bin_off, int32_t *entries, int32_t *status, cudaStream_t s);
 
-// imaging FFT (dirty.cu)
+// imaging FFT (dirty.cu); gc here is the row pass's table (-1)^x / gc(x) (launch_pswf_table with
+// signed_recip)
 int dirty_strip_width(int G);
 // Gridding fused into the column pass (the G x G grid never reaches HBM): sorts the dense
 // records [B][stride] into per-strip lists (bin_off [B][G/S + 1], entries [B][stride][2][tiles],

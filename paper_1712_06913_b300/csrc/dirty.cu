@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(GridStrip<G, S_, MAXR>::NT) k_cols_grid(
 
 template <int G, int MAXR = 16>
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict__ T, const float2 *__restrict__ tw,
-                                                       const float *__restrict__ gc, const float *__restrict__ partial,
+                                                       const float *__restrict__ gcs, const float *__restrict__ partial,
                                                        int nstrip, int N, float *__restrict__ dirty,
                                                        float *__restrict__ beam, int32_t *__restrict__ status) {
   using C = RowCfg<G>;
@@ -195,20 +195,19 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_rows(const float2 *__restrict
     __device__ float2 operator()(int i, int s) const { return __ldcs(Ti + (size_t)(y0 + s) * G + i); }   // last use
   } load{Ti, y0};
   struct Store {
-    const float *gc;
+    const float *gcs;
     float *D, *Bm;
     int y0, N;
     float scale;
     __device__ void operator()(int x, int s, float2 v) const {
       if (x < G / 4 || x >= 3 * G / 4) return;
       const int y = y0 + s + G / 4;
-      float f = scale / (__ldg(gc + x) * __ldg(gc + y));
-      if ((x + y) & 1) f = -f;
+      const float f = scale * __ldg(gcs + y) * __ldg(gcs + x);   // (-1)^(x+y) scale / (gc(x) gc(y))
       Bm[(size_t)(y - G / 4) * (2 * N) + (x - G / 4)] = v.y * f;
       const int lo = G / 2 - N / 2;
       if (y >= lo && y < lo + N && x >= lo && x < lo + N) D[(size_t)(y - lo) * N + (x - lo)] = v.x * f;
     }
-  } store{gc, dirty + (size_t)inst * N * N, beam + (size_t)inst * 4 * N * N, y0, N, scale};
+  } store{gcs, dirty + (size_t)inst * N * N, beam + (size_t)inst * 4 * N * N, y0, N, scale};
   fft::run<G, S, NT, +1, false, typename C::Layout, false, MAXR>(sm, tw, load, store);
 }
 

@@ -137,14 +137,15 @@ __device__ double psi_dev(const Pswf &P, double eta) {
   return sum / P.psi00;
 }
 
-__global__ void k_pswf_fill(Pswf P, float *tab, int ntab, int W, int os, float *gc, int G) {
+__global__ void k_pswf_fill(Pswf P, float *tab, int ntab, int W, int os, float *gc, int G, int signed_recip) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < ntab) {
     double d = (double)i / os;
     tab[i] = (d <= 0.5 * W) ? (float)psi_dev(P, 2.0 * d / W) : 0.f;
   } else if (gc != nullptr && i < ntab + G) {
     int x = i - ntab;
-    gc[x] = (float)psi_dev(P, 2.0 * (x - G / 2) / (double)G);
+    const double g = psi_dev(P, 2.0 * (x - G / 2) / (double)G);
+    gc[x] = signed_recip ? (float)(((x & 1) ? -1.0 : 1.0) / g) : (float)g;
   }
 }
 
@@ -220,13 +221,14 @@ const Pswf &pswf_coefficients(int W) {
   return cache[W];
 }
 
-// tab (nullable) receives table_len(W, os) samples, gc (nullable) G grid-correction values.
-void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t s) {
+// tab (nullable) receives table_len(W, os) samples, gc (nullable) G grid-correction values:
+// gc(x), or with signed_recip (-1)^x / gc(x) (the factor the dirty transform's row pass applies).
+void launch_pswf_table(float *tab, int W, int os, float *gc, int G, cudaStream_t s, int signed_recip) {
   const Pswf &P = pswf_coefficients(W);
   int ntab = tab ? table_len(W, os) : 0;
   int total = ntab + (gc ? G : 0);
   if (total == 0) return;
-  k_pswf_fill<<<(total + 255) / 256, 256, 0, s>>>(P, tab, ntab, W, os, gc, G);
+  k_pswf_fill<<<(total + 255) / 256, 256, 0, s>>>(P, tab, ntab, W, os, gc, G, signed_recip);
   note_launch();
 }
 

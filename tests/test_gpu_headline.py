@@ -306,14 +306,16 @@ def test_image_variants_follow_oracle_and_autotune(m, name, N):
 
 def test_chained_gradient_steps_equal_separate_steps(m):
     """A descent loop whose steps chain (each leaves the next step's forward row pass in the
-    workspace, the next skips it) computes bit for bit what separate steps compute; a graph of one
-    chained step replays the same."""
+    workspace, the next skips it) computes bit for bit what separate steps compute with the same
+    plan (DegridPlan.clone); a graph of one chained step replays the same."""
     import torch
     from paper_1712_06913_b300.autograd import GradientImaging
     cfg, rec, ro = _small_operator(m, 64)
     obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
     a = GradientImaging(rec, obs, 0.5, cfg, eta=2e-5)
+    a.plan.forward(a.x.detach())                               # plans the operator once
     b = GradientImaging(rec, obs, 0.5, cfg, eta=2e-5)
+    b.plan = a.plan.clone()                                    # the same plan: the same sums
     lb = torch.zeros(1, device="cuda")
     for _ in range(6):
         la = float(a.step())                                   # chained
@@ -325,6 +327,7 @@ def test_chained_gradient_steps_equal_separate_steps(m):
         b.plan.grad_step(b.x.data, b.obs, b.inv_s2, b.eta, lb)
     x0 = a.x.detach().clone()
     c = GradientImaging(rec, obs, 0.5, cfg, x0=x0, eta=2e-5)
+    c.plan = b.plan.clone()
     a.replay(3)
     for _ in range(3):
         c.plan.grad_step(c.x.data, c.obs, c.inv_s2, c.eta, lb)
