@@ -335,7 +335,7 @@ int check_ws(void *ws, size_t ws_bytes, size_t need) {
 // adjoint's tap lists.
 template <class A>
 void plan_operator(DegridWs<A> &w, const Rec *rec, const muser_config_t &c, cudaStream_t s) {
-  launch_pswf_table(w.tab, c.W, c.os, w.gc, c.G, s);
+  launch_pswf_table(w.tab, c.W, c.os, w.gc, c.G, s, 1);   // gc as (-1)^x / gc(x) for the row passes
   fft::launch_twiddles(const_cast<float2 *>(w.p.tw), c.G, s);
   launch_degrid_plan(rec, w.p, s);
 }

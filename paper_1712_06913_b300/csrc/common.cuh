@@ -222,8 +222,9 @@ void launch_restore(const float *R, const float *beam, const int32_t *pos, const
 // {sorted record, weight}); short non-empty cells as items {cell, first tap, end tap}, long ones
 // ({cell, first piece, pieces}) cut into pieces ({cell, first tap, end tap, long-cell index});
 // counts {long cells, pieces, items, -} then one ticket per long cell.  Zs: the adjoint's grid,
-// zero where no tap falls.  Scratch: cnt [G*G], sums [degrid_plan_scan_blocks(G)], T (G/2 x G),
-// X (G x G), partial (pieces), vs (n_vis, the adjoint's input in sorted order).
+// zero where no tap falls.  gc: (-1)^x / gc(x), the row passes' grid correction and modulation.
+// Scratch: cnt [G*G], sums [degrid_plan_scan_blocks(G)], T (G/2 x G), X (G x G), partial
+// (pieces), vs (n_vis, the adjoint's input in sorted order).
 struct OpPlan {
   int N = 0, G = 0, W = 0, os = 0;
   float K2 = 1.f;

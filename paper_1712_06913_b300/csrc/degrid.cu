@@ -39,22 +39,20 @@ using RowCfg = fft::RowCfg1<G>;
 // FORWARD pass 1: rows of the padded image, S rows from r0 (one block).
 template <int G>
 __device__ __forceinline__ void fwd_rows_strip(const float *__restrict__ img, const float2 *__restrict__ tw,
-                                               const float *__restrict__ gc, float2 *__restrict__ T1, int r0,
+                                               const float *__restrict__ gcs, float2 *__restrict__ T1, int r0,
                                                float2 *sm) {
   using C = RowCfg<G>;
   constexpr int N = G / 2, S = C::S, NT = C::NT, LO = G / 2 - N / 2;
   struct Load {
     const float *img;
-    const float *gc;
+    const float *gcs;
     int r0;
     __device__ float2 operator()(int i, int s) const {
       if (i < LO || i >= LO + N) return make_float2(0.f, 0.f);
-      const int py = r0 + s + LO;
-      float v = img[(size_t)(r0 + s) * N + (i - LO)] / (__ldg(gc + i) * __ldg(gc + py));
-      if ((i + py) & 1) v = -v;
-      return make_float2(v, 0.f);
+      const int py = r0 + s + LO;   // gcs = (-1)^x / gc(x): x' = (-1)^(i+py) img / (gc(i) gc(py))
+      return make_float2(img[(size_t)(r0 + s) * N + (i - LO)] * __ldg(gcs + py) * __ldg(gcs + i), 0.f);
     }
-  } load{img, gc, r0};
+  } load{img, gcs, r0};
   struct Store {
     float2 *T1;
     int r0;
@@ -68,9 +66,9 @@ __device__ __forceinline__ void fwd_rows_strip(const float *__restrict__ img, co
 
 template <int G>
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_fwd_rows(const float *__restrict__ img, const float2 *__restrict__ tw,
-                                                           const float *__restrict__ gc, float2 *__restrict__ T1) {
+                                                           const float *__restrict__ gcs, float2 *__restrict__ T1) {
   __shared__ float2 sm[RowCfg<G>::Layout::size];
-  fwd_rows_strip<G>(img, tw, gc, T1, blockIdx.x * RowCfg<G>::S, sm);
+  fwd_rows_strip<G>(img, tw, gcs, T1, blockIdx.x * RowCfg<G>::S, sm);
 }
 
 // FORWARD pass 2: columns; inputs outside the central N rows are zero.
@@ -412,7 +410,7 @@ __global__ void __launch_bounds__(ColCfg<G>::NT) k_adj_cols(const float2 *__rest
 // updated, into the same rows of T (the rows this block alone reads and writes).
 template <int G>
 __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(float2 *__restrict__ T, const float2 *__restrict__ tw,
-                                                           const float *__restrict__ gc, float invK2,
+                                                           const float *__restrict__ gcs, float invK2,
                                                            float *__restrict__ img, int upd, float eta,
                                                            float *__restrict__ grad, int chain) {
   using C = RowCfg<G>;
@@ -425,15 +423,14 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(float2 *__restrict__
     __device__ float2 operator()(int i, int s) const { return T[(size_t)(r0 + s) * G + i]; }
   } load{T, r0};
   struct Store {
-    const float *gc;
+    const float *gcs;
     float *img, *grad;
     int r0, upd;
     float invK2, eta;
     __device__ void operator()(int x, int s, float2 v) const {
       if (x < LO || x >= LO + N) return;
       const int y = r0 + s + LO;
-      float f = invK2 / (__ldg(gc + x) * __ldg(gc + y));
-      if ((x + y) & 1) f = -f;
+      const float f = invK2 * __ldg(gcs + y) * __ldg(gcs + x);   // (-1)^(x+y) / (K^2 gc(x) gc(y))
       const size_t k = (size_t)(r0 + s) * N + (x - LO);
       const float g = v.x * f;
       if (!upd) {
@@ -443,11 +440,11 @@ __global__ void __launch_bounds__(RowCfg<G>::NT) k_adj_rows(float2 *__restrict__
       img[k] -= eta * g;
       if (grad) grad[k] = g;
     }
-  } store{gc, img, grad, r0, upd, invK2, eta};
+  } store{gcs, img, grad, r0, upd, invK2, eta};
   fft::run<G, S, NT, +1, false, typename C::Layout>(sm, tw, load, store);
   if (chain) {
     __syncthreads();                              // this block's image rows are written
-    fwd_rows_strip<G>(img, tw, gc, T, r0, sm);
+    fwd_rows_strip<G>(img, tw, gcs, T, r0, sm);
   }
 }
 
