@@ -429,9 +429,9 @@ def main():
             steer_ms = ec[0].elapsed_time(ec[1])
             steer_cycles = int(snc.sum())
         iters = nc.cpu().numpy().astype(np.float64)
-        # on-chip CLEAN: beam copies (read the 2N x 2N beam, write three shifted copies), residual
-        # read and written once, one N x N beam window read per iteration
-        clean_bytes.append(float(np.sum(64.0 * N * N + 8.0 * N * N + iters * 4.0 * N * N)))
+        # on-chip CLEAN: beam copy (read the 2N x 2N beam, write one shifted copy), residual read
+        # and written once, one N x N beam window read per iteration
+        clean_bytes.append(float(np.sum(32.0 * N * N + 8.0 * N * N + iters * 4.0 * N * N)))
         hbm_equiv_bytes.append(float(np.sum(4.0 * N * N + iters * 12.0 * N * N)))
         del D, Bm, R, img
     del Z, Zbuf, Dbuf, Bbuf
@@ -459,7 +459,7 @@ def main():
                 "dram_frac": traffic / (clean_ms / 1e3) / 1e9 / peak if tr else None,
                 "l2_frac": tr.get("lts_throughput") if tr else None,
                 "onchip_design_GBps": statistics.mean(clean_bytes) / (clean_ms / 1e3) / 1e9,
-                "onchip_design_bytes": "4 N^2 beam window per iteration + 8 N^2 residual in/out + 64 N^2 beam copies"}
+                "onchip_design_bytes": "4 N^2 beam window per iteration + 8 N^2 residual in/out + 32 N^2 beam copy"}
     grid_bytes = args.chunk * (32.0 * wl.n_bl + 8.0 * G * G)
     extra = {"phase_ms_per_chunk": {k: statistics.mean(v) for k, v in phase.items()},
              "gridding_GBps": grid_bytes / (statistics.mean(phase["grid"]) / 1e3) / 1e9,
@@ -493,8 +493,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "instances_per_gpu": B, "batch_chunk": args.chunk,
-                           "l2": "inputs larger than L2: per step 17 GB of residual, 68 GB of beams (+ 3 shifted "
-                                 "copies) and 283 GB of column-pass output stream through HBM"},
+                           "l2": "inputs larger than L2: per step 17 GB of residual, 68 GB of beams (+ 1 shifted "
+                                 "copy) and 283 GB of column-pass output stream through HBM"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": "images/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h,
@@ -673,7 +673,7 @@ def run_case(case, n_inst=0, iters=100, size=2560):
         e1.record()
         torch.cuda.synchronize()
         it_sum = float(nc.sum().item())
-        gb = (n_inst * 72.0 * N * N + it_sum * 4.0 * N * N) / 1e9   # same byte model as the roofline
+        gb = (n_inst * 40.0 * N * N + it_sum * 4.0 * N * N) / 1e9   # same byte model as the roofline
         print(json.dumps({"case": case, "instances": n_inst, "clean_ms": e0.elapsed_time(e1),
                           "GBps": gb / (e0.elapsed_time(e1) / 1e3), "algorithmic_GB": gb,
                           "iterations": it_sum, "n_comp_min": int(nc.min())}))

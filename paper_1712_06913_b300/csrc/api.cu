@@ -160,7 +160,7 @@ struct ImageWs {
     entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(w_footprint(c), c.G, S, c.G));
     d.carve(a, Bc, c);
     for (int k = 0; k < 2; k++) {
-      beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 4 : 1));
+      beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 2 : 1));
       mu_a[k] = (float *)a.template take<float>(Bc);
       mu_b[k] = (float *)a.template take<float>(Bc);
     }
@@ -440,7 +440,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_GMM: break;
     case MUSER_CALL_CLEAN:
       a.take<float>(2 * (size_t)B);
-      if (copies(*cfg)) a.take<float>((size_t)B * 16 * cfg->N * cfg->N);
+      if (copies(*cfg)) a.take<float>((size_t)B * 8 * cfg->N * cfg->N);
       a.take<int>(1);
       break;
     case MUSER_CALL_RESTORE: break;
@@ -559,7 +559,7 @@ int muser_clean(float *residual, const float *beam, int B, const muser_config_t 
   }
   const int N = cfg->N;
   if (copies(*cfg)) {
-    float *beam4 = a.take<float>((size_t)B * 16 * N * N);
+    float *beam4 = a.take<float>((size_t)B * 8 * N * N);
     int *next = a.take<int>(1);
     const size_t cstride = (size_t)B * 4 * N * N;
     launch_beam_copies(beam, B, N, 0, beam4, cstride, s);

@@ -336,9 +336,11 @@ struct Cand {
 // Band index of the thread's o-th pixel (o < 64: quad o / 4, element o mod 4).
 __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o >> 2) * kOnT) + (o & 3); }
 
-// beam4: four copies of every instance's beam, copy k at beam4 + k * cstride holding
+// beam4: two copies of every instance's beam, copy k at beam4 + k * cstride holding
 // Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
-// 16-byte aligned in copy (N - px) mod 4 and each residual quad takes one aligned 16-byte load.
+// 8-byte aligned in copy (N - px) mod 2 and each residual quad takes two aligned 8-byte loads
+// (four copies with one 16-byte load per quad move the same bytes with half the load
+// instructions, but put twice the window bytes in L2 and cost two more copies per instance).
 //
 // The kernel below is a persistent worker: its clusters draw instances from one atomic counter
 // (`next`) until the batch is exhausted.
@@ -465,19 +467,24 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       }
       const int py = p.idx / N, px = p.idx % N;
       // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]; its
-      // aligned copy (N - px) mod 4 starts each quad on a 16-byte boundary
+      // aligned copy (N - px) mod 2 starts each quad on an 8-byte boundary
       const int off = N - px;
-      const float *Wa = Bm + (size_t)(off & 3) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~3);
-      const float4 *bt = reinterpret_cast<const float4 *>(Wa + (size_t)qr * (2 * N) + qc);
+      const float *Wa = Bm + (size_t)(off & 1) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~1);
+      const float *bt = Wa + (size_t)qr * (2 * N) + qc;
       // beam quad of the thread's quad i: a fixed stride when a quad step spans whole rows, else
       // from the band pixel's row and column
-      auto beam_q = [&](int i) -> const float4 * {
+      auto beam_p = [&](int i) -> const float * {
         if constexpr (EXT) {
           const int b = 4 * (tid + i * kOnT), r = b / N, c = b - r * N;
-          return reinterpret_cast<const float4 *>(Wa + (size_t)r * (2 * N) + c);
+          return Wa + (size_t)r * (2 * N) + c;
         } else {
-          return bt + i * QSTEP * (2 * N / 4);
+          return bt + (size_t)i * QSTEP * (2 * N);
         }
+      };
+      auto beam_q = [&](int i) -> float4 {                 // two aligned 8-byte loads
+        const float2 *q = reinterpret_cast<const float2 *>(beam_p(i));
+        const float2 a = __ldg(q), b = __ldg(q + 1);
+        return make_float4(a.x, a.y, b.x, b.y);
       };
       cb = Cand<MODE>();
       // TB aligned beam loads in flight, then the residual read, updated and written back
@@ -486,7 +493,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       for (int i0 = 0; i0 < TQ; i0 += TB) {   // not unrolled: keeps the batches apart
         float4 bb[TB];
 #pragma unroll
-        for (int k = 0; k < TB; k++) bb[k] = __ldg(beam_q(i0 + k));
+        for (int k = 0; k < TB; k++) bb[k] = beam_q(i0 + k);
 #pragma unroll
         for (int k = 0; k < TB; k += 2) {
           const int i = i0 + k;
@@ -510,7 +517,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
         for (int i0 = kTmQuads; i0 < NQ; i0 += kSB) {
           float4 bb[kSB];
 #pragma unroll
-          for (int k = 0; k < kSB; k++) bb[k] = __ldg(beam_q(i0 + k));
+          for (int k = 0; k < kSB; k++) bb[k] = beam_q(i0 + k);
 #pragma unroll
           for (int k = 0; k < kSB; k++) {
             float4 v = xs4[(i0 + k - kTmQuads) * kOnT + tid];
@@ -806,7 +813,7 @@ bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, int *nex
               : launch_onchip_mode<N, CS, 0, NQ>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
 }
 
-// dst copy k (k = first..3) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
+// dst copy k (k = first..1) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
 __global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, float *__restrict__ beam4,
                              size_t cstride) {
   const int W = 2 * N;
@@ -814,7 +821,7 @@ __global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, f
   const float *src = beam + row * W;
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < 2; k++) {
       if (k < first) continue;
       __stcs(beam4 + k * cstride + row * W + x, x + k < W ? src[x + k] : 0.f);   // read by a later CLEAN
     }
