@@ -160,7 +160,7 @@ struct ImageWs {
     entries = (int32_t *)a.template take<int32_t>((size_t)Bc * n_bl * 2 * tiles_per_sample(w_footprint(c), c.G, S, c.G));
     d.carve(a, Bc, c);
     for (int k = 0; k < 2; k++) {
-      beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? 2 : 1));
+      beam[k] = (float *)a.template take<float>((size_t)Bc * 4 * c.N * c.N * (copies(c) ? beam_copies(Bc, c.N) : 1));
       mu_a[k] = (float *)a.template take<float>(Bc);
       mu_b[k] = (float *)a.template take<float>(Bc);
     }
@@ -440,7 +440,7 @@ size_t muser_workspace_size(int call_id, int B, int64_t n_vis_total, const muser
     case MUSER_CALL_GMM: break;
     case MUSER_CALL_CLEAN:
       a.take<float>(2 * (size_t)B);
-      if (copies(*cfg)) a.take<float>((size_t)B * 8 * cfg->N * cfg->N);
+      if (copies(*cfg)) a.take<float>((size_t)B * 4 * cfg->N * cfg->N * beam_copies(B, cfg->N));
       a.take<int>(1);
       break;
     case MUSER_CALL_RESTORE: break;
@@ -559,15 +559,16 @@ int muser_clean(float *residual, const float *beam, int B, const muser_config_t 
   }
   const int N = cfg->N;
   if (copies(*cfg)) {
-    float *beam4 = a.take<float>((size_t)B * 8 * N * N);
+    const int ncp = beam_copies(B, N);
+    float *beam4 = a.take<float>((size_t)B * 4 * N * N * ncp);
     int *next = a.take<int>(1);
     const size_t cstride = (size_t)B * 4 * N * N;
-    launch_beam_copies(beam, B, N, 0, beam4, cstride, s);
-    launch_hogbom(residual, beam, beam4, cstride, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
+    launch_beam_copies(beam, B, N, 0, ncp, beam4, cstride, s);
+    launch_hogbom(residual, beam, beam4, cstride, ncp, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
                   comp_flux, n_comp, status, s);
   } else if (!clean_uses_copies(N) && cfg->clean_kernel == 0) {   // no on-chip kernel: clusters stream
     int *next = a.take<int>(1);
-    launch_hogbom(residual, beam, nullptr, 0, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
+    launch_hogbom(residual, beam, nullptr, 0, 0, next, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos,
                   comp_flux, n_comp, status, s);
   } else {
     launch_hogbom_stream(residual, beam, B, N, t, cfg->gain, cfg->max_iter, cfg->peak_mode, comp_pos, comp_flux,
@@ -625,6 +626,7 @@ int image_batch(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
   const int N = cfg->N, G = cfg->G, cap = cfg->max_iter;
   const int n_chunks = (B + Bc - 1) / Bc;
   const int variant = tuned_image_variant(G);
+  const int ncp = beam_copies(Bc, N);                      // the on-chip CLEAN's beam copies
   cudaMemsetAsync(status, 0, sizeof(int32_t) * (size_t)B, s);
   launch_pswf_table(w.tab, cfg->W, cfg->os, w.d.gc, G, s, 1);
   if (w.wtab) launch_wtab(w.wtab, cfg->w_planes, table_len(cfg->w_support, cfg->os), cfg->os, cfg->w_support, cfg->w_max,
@@ -653,7 +655,7 @@ int image_batch(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
       k_fill<<<(n + 255) / 256, 256, 0, s>>>(thr_out + c0, n, -INFINITY);
       note_launch();
     }
-    if (copies(*cfg)) launch_beam_copies(w.beam[k], n, N, 1, w.beam[k], (size_t)Bc * 4 * N * N, s);
+    if (copies(*cfg)) launch_beam_copies(w.beam[k], n, N, 1, ncp, w.beam[k], (size_t)Bc * 4 * N * N, s);
     cudaEventRecord(pp->prepped[k], s);
   };
   auto restore = [&](int c) {
@@ -680,7 +682,7 @@ int image_batch(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n
                    w.sFB[k], w.sF[k], w.sU[k], w.sY[k], w.sstate[k], status + c0, hs);
     } else {
       launch_hogbom(residual + (size_t)c0 * N * N, w.beam[k], copies(*cfg) ? w.beam[k] : nullptr,
-                    (size_t)Bc * 4 * N * N, cfg->clean_kernel == 0 ? w.next[k] : nullptr, n, N,
+                    (size_t)Bc * 4 * N * N, ncp, cfg->clean_kernel == 0 ? w.next[k] : nullptr, n, N,
                     cfg->thr_mode == 1 ? w.mu_a[k] : nullptr, cfg->gain, cap, cfg->peak_mode,
                     comp_pos ? comp_pos + (size_t)c0 * cap : nullptr,
                     comp_flux ? comp_flux + (size_t)c0 * cap : nullptr, n_comp + c0, status + c0, hs);

@@ -336,11 +336,13 @@ struct Cand {
 // Band index of the thread's o-th pixel (o < 64: quad o / 4, element o mod 4).
 __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o >> 2) * kOnT) + (o & 3); }
 
-// beam4: two copies of every instance's beam, copy k at beam4 + k * cstride holding
-// Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window row of any peak starts
-// 8-byte aligned in copy (N - px) mod 2 and each residual quad takes two aligned 8-byte loads
-// (four copies with one 16-byte load per quad move the same bytes with half the load
-// instructions, but put twice the window bytes in L2 and cost two more copies per instance).
+// beam4: CP copies of every instance's beam (beam_copies(B, N): 4 or 2), copy k at
+// beam4 + k * cstride holding Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window
+// row of any peak starts 4 CP-byte aligned in copy (N - px) mod CP: each residual quad takes one
+// aligned 16-byte load from four copies, or two aligned 8-byte loads from two.  Two copies put
+// half the window bytes in L2 (with many instances in flight the windows of four copies overflow
+// it and half the window reads go to DRAM); four copies halve the load instructions, which is
+// the better trade when a batch's beams fit in L2.
 //
 // The kernel below is a persistent worker: its clusters draw instances from one atomic counter
 // (`next`) until the batch is exhausted.
@@ -348,7 +350,7 @@ __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o
 // Per block, a band of kTmPix / N rows of the residual (CS blocks per instance).
 // NQ quads per thread: the first kTmQuads in tensor memory, the rest (EXT: the 320, 640 and 1280
 // pixel images, 25 quads = 102400 pixels per block) in shared memory, [quad - kTmQuads][thread].
-template <int N, int CS, int MODE, int NQ = kTmQuads>
+template <int N, int CS, int MODE, int NQ = kTmQuads, int CP = 2>
 __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ Rall, const float *__restrict__ beam4,
                                                            size_t cstride, int B, int *__restrict__ next,
                                                            const float *__restrict__ thr, float gain, int cap,
@@ -467,9 +469,9 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
       }
       const int py = p.idx / N, px = p.idx % N;
       // beam element of band pixel (r, c): Bm[(row0 + r - py + N) * 2N + (c - px + N)]; its
-      // aligned copy (N - px) mod 2 starts each quad on an 8-byte boundary
+      // aligned copy (N - px) mod CP starts each quad on a 4 CP-byte boundary
       const int off = N - px;
-      const float *Wa = Bm + (size_t)(off & 1) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & ~1);
+      const float *Wa = Bm + (size_t)(off & (CP - 1)) * cstride + (size_t)(row0 - py + N) * (2 * N) + (off & -CP);
       const float *bt = Wa + (size_t)qr * (2 * N) + qc;
       // beam quad of the thread's quad i: a fixed stride when a quad step spans whole rows, else
       // from the band pixel's row and column
@@ -481,10 +483,14 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
           return bt + (size_t)i * QSTEP * (2 * N);
         }
       };
-      auto beam_q = [&](int i) -> float4 {                 // two aligned 8-byte loads
-        const float2 *q = reinterpret_cast<const float2 *>(beam_p(i));
-        const float2 a = __ldg(q), b = __ldg(q + 1);
-        return make_float4(a.x, a.y, b.x, b.y);
+      auto beam_q = [&](int i) -> float4 {   // one aligned 16-byte load (4 copies) or two 8-byte loads
+        if constexpr (CP == 4) {
+          return __ldg(reinterpret_cast<const float4 *>(beam_p(i)));
+        } else {
+          const float2 *q = reinterpret_cast<const float2 *>(beam_p(i));
+          const float2 a = __ldg(q), b = __ldg(q + 1);
+          return make_float4(a.x, a.y, b.x, b.y);
+        }
       };
       cb = Cand<MODE>();
       // TB aligned beam loads in flight, then the residual read, updated and written back
@@ -763,12 +769,12 @@ struct OnchipPlan {
 };
 
 // Launch the persistent clusters if the device can host them; false -> fallback.
-template <int N, int CS, int MODE, int NQ = kTmQuads>
+template <int N, int CS, int MODE, int NQ, int CP>
 bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
                         int cap, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
   static OnchipPlan plan;          // per process: the library runs on one device model
   constexpr bool EXT = NQ > kTmQuads;
-  auto k = k_hogbom_onchip<N, CS, MODE, NQ>;
+  auto k = k_hogbom_onchip<N, CS, MODE, NQ, CP>;
   // the residual lives in tensor memory (and, EXT, partly in shared memory); the kernel asks for
   // more than half of an SM's shared memory so that no two of its blocks (each allocating all
   // 512 columns) share an SM
@@ -807,22 +813,31 @@ bool launch_onchip_mode(float *R, const float *beam4, size_t cstride, int B, int
 }
 
 template <int N, int CS, int NQ = kTmQuads>
-bool launch_onchip(float *R, const float *beam4, size_t cstride, int B, int *next, const float *thr, float gain,
-                   int cap, int mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s) {
-  return mode ? launch_onchip_mode<N, CS, 1, NQ>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s)
-              : launch_onchip_mode<N, CS, 0, NQ>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp, status, s);
+bool launch_onchip(float *R, const float *beam4, size_t cstride, int copies, int B, int *next, const float *thr,
+                   float gain, int cap, int mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status,
+                   cudaStream_t s) {
+  if (copies == 4)
+    return mode ? launch_onchip_mode<N, CS, 1, NQ, 4>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp,
+                                                      status, s)
+                : launch_onchip_mode<N, CS, 0, NQ, 4>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp,
+                                                      status, s);
+  return mode ? launch_onchip_mode<N, CS, 1, NQ, 2>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp,
+                                                    status, s)
+              : launch_onchip_mode<N, CS, 0, NQ, 2>(R, beam4, cstride, B, next, thr, gain, cap, pos, flux, n_comp,
+                                                    status, s);
 }
 
-// dst copy k (k = first..1) of every instance: Bk[y][x] = Bm[y][x + k], zero past the row end.
-__global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, float *__restrict__ beam4,
+// dst copy k (k = first..copies-1) of every instance: Bk[y][x] = Bm[y][x + k], zero past the
+// row end.
+__global__ void k_beam_shift(const float *__restrict__ beam, int N, int first, int copies, float *__restrict__ beam4,
                              size_t cstride) {
   const int W = 2 * N;
   const size_t row = (size_t)blockIdx.y * W + blockIdx.x;    // (instance, y) flattened
   const float *src = beam + row * W;
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-      if (k < first) continue;
+    for (int k = 0; k < 4; k++) {
+      if (k < first || k >= copies) continue;
       __stcs(beam4 + k * cstride + row * W + x, x + k < W ? src[x + k] : 0.f);   // read by a later CLEAN
     }
   }
@@ -842,43 +857,44 @@ int hogbom_onchip_clusters(int N) {
   }
 }
 
-void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4, size_t cstride, cudaStream_t s) {
+void launch_beam_copies(const float *beam, int B, int N, int first, int copies, float *beam4, size_t cstride,
+                        cudaStream_t s) {
   for (int i = 0; i < B; i += 32768) {
     const int n = B - i < 32768 ? B - i : 32768;
-    k_beam_shift<<<dim3(2 * N, n), 256, 0, s>>>(beam + (size_t)i * 4 * N * N, N, first,
+    k_beam_shift<<<dim3(2 * N, n), 256, 0, s>>>(beam + (size_t)i * 4 * N * N, N, first, copies,
                                                  beam4 + (size_t)i * 4 * N * N, cstride);
     note_launch();
   }
 }
 
-void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int *next, int B, int N,
-                   const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp,
-                   int32_t *status, cudaStream_t s) {
+void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int copies, int *next, int B,
+                   int N, const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux,
+                   int32_t *n_comp, int32_t *status, cudaStream_t s) {
   if (B <= 0) return;
   bool done = false;
   if (beam4 && next) {
     // 256^2: one block per instance fills the SMs with many instances; a batch of a few
     // instances runs faster in clusters of 4 blocks (16384-pixel bands, 4 quads per thread)
     if (N == 256 && B <= 32)
-      done = launch_onchip<256, 4, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+      done = launch_onchip<256, 4, 4>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
                                        s);
     if (N == 256 && !done)
-      done = launch_onchip<256, 1>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<256, 1>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     // 512^2: clusters of 4 blocks; a batch of a few instances in clusters of 16 (4 quads per thread)
     if (N == 512 && B <= 7)
-      done = launch_onchip<512, 16, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+      done = launch_onchip<512, 16, 4>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
                                         s);
     if (N == 512 && !done)
-      done = launch_onchip<512, 4>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<512, 4>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 1024)
-      done = launch_onchip<1024, 16>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<1024, 16>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     // 102400-pixel bands: 65536 pixels in tensor memory, 36864 in shared memory
     if (N == 320)
-      done = launch_onchip<320, 1, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<320, 1, 25>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 640)
-      done = launch_onchip<640, 4, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+      done = launch_onchip<640, 4, 25>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (N == 1280)
-      done = launch_onchip<1280, 16, 25>(R, beam4, cstride, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
+      done = launch_onchip<1280, 16, 25>(R, beam4, cstride, copies, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status,
                                          s);
   }
   if (done) return;

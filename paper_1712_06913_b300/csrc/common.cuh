@@ -191,19 +191,26 @@ void launch_twiddles(float2 *tw, int L, cudaStream_t s);   // tw[m] = exp(+2 pi 
 }
 
 // CLEAN, GMM, restore (clean.cu, gmm.cu, restore.cu)
-// CLEAN: on-chip residual kernel for N = 256, 512, 1024 when beam4 (four column-shifted beam
-// copies, copy k at beam4 + k * cstride, built by launch_beam_copies) is given and the device can
-// host it; otherwise the streaming kernel on `beam`.  launch_hogbom_stream forces streaming.
-// `next` is a device int the launch resets: the on-chip clusters (and, on SMs that cannot host a
-// whole cluster, streaming workers on a second stream) claim instances from it.
-void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int *next, int B, int N,
-                   const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux, int32_t *n_comp,
-                   int32_t *status, cudaStream_t s);
+// CLEAN: on-chip residual kernel for N = 256, 320, 512, 640, 1024, 1280 when beam4 (`copies`
+// column-shifted beam copies, copy k at beam4 + k * cstride, built by launch_beam_copies) is
+// given and the device can host it; otherwise the streaming kernel on `beam`.
+// launch_hogbom_stream forces streaming.  `next` is a device int the launch resets: the on-chip
+// clusters (and, on SMs that cannot host a whole cluster, streaming workers on a second stream)
+// claim instances from it.
+void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstride, int copies, int *next, int B,
+                   int N, const float *thr, float gain, int cap, int peak_mode, int32_t *pos, float *flux,
+                   int32_t *n_comp, int32_t *status, cudaStream_t s);
 // bounded-wait self-test (clean.cu): status[0] = MUSER_ST_TIMEOUT once limit_cycles pass
 void launch_wait_selftest(long long limit_cycles, int32_t *status, cudaStream_t s);
-// copies k = first..3 of beam [B][2N][2N] into beam4 (copy 0 at beam4 is written only if first == 0)
-void launch_beam_copies(const float *beam, int B, int N, int first, float *beam4, size_t cstride, cudaStream_t s);
+// copies k = first..copies-1 of beam [B][2N][2N] into beam4 (copy 0 at beam4 is written only if
+// first == 0)
+void launch_beam_copies(const float *beam, int B, int N, int first, int copies, float *beam4, size_t cstride,
+                        cudaStream_t s);
 inline bool clean_uses_copies(int N) { return N == 256 || N == 512 || N == 1024 || N == 320 || N == 640 || N == 1280; }
+// Beam copies of the on-chip CLEAN for a batch of B instances of side N: four (one 16-byte
+// window load per quad) while the four copies' windows of the whole batch fit in L2 with room to
+// spare (B N^2 <= 2^21), else two (two 8-byte loads per quad, half the L2 footprint).
+inline int beam_copies(int B, int N) { return (int64_t)B * N * N <= ((int64_t)1 << 21) ? 4 : 2; }
 void launch_hogbom_stream(float *R, const float *beam, int B, int N, const float *thr, float gain, int cap,
                           int peak_mode, int32_t *pos, float *flux, int32_t *n_comp, int32_t *status, cudaStream_t s);
 int hogbom_onchip_clusters(int N);   // blocks per instance of the on-chip kernel (0: not available)
