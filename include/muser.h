@@ -80,11 +80,14 @@ typedef struct muser_config {
   int32_t G;            /* uv-grid side: 4N for imaging (beam of 2N, Sec. 3.2.1), 2N for degrid */
   int32_t W;            /* spheroidal support in cells, odd, 3..9 (7 in every workload) */
   int32_t os;           /* kernel table samples per cell, 16..4096 (1024) */
-  int32_t weight_mode;  /* 0 natural; 1 uniform (Alg. 1 weighting mode), imaging calls only: each
-                           kept sample weighted by 1 / cnt, cnt = samples (with their -uv mirrors)
-                           in its cell of the unpadded N x N grid, the cell decided in FP32 as
+  int32_t weight_mode;  /* 0 natural; 1 uniform (Alg. 1 weighting mode): each kept sample weighted
+                           by 1 / cnt, cnt = samples (with their -uv mirrors) in its cell of the
+                           unpadded N x N grid, the cell decided in FP32 as
                            floor((float(k - G/2) - f) / (G/N) + N/2 + 1/2) per axis, the mirror's
-                           as N - cell; muser_grid applies it to a copy of the records */
+                           as N - cell; muser_grid applies it to a copy of the records; for the
+                           degridding operator's plan it sets the chi-square weights w_k of
+                           muser_grad_step, muser_normal_apply and muser_lipschitz (muser_degrid's
+                           forward and adjoint carry no weights; muser_chi2 uses its records' own) */
   int32_t peak_mode;    /* CLEAN peak: 0 largest signed value, 1 largest |value| */
   int32_t thr_mode;     /* CLEAN threshold: 0 fixed thr[] (or -inf), 1 GMM sky level mu_a (Sec. 4.3) */
   int32_t max_iter;     /* CLEAN iteration cap (>= 0) */
@@ -323,6 +326,8 @@ MUSER_API int muser_steer(float *residual, const float *beam, int B, const muser
  * muser_degrid; its gradient as for muser_chi2 + MUSER_ADJOINT):
  *   v = A img;  loss = sum_k w_k |v_k - obs_k|^2 / sigma^2;  grad = Re A^H (2 w (v - obs) / sigma^2);
  *   img -= eta grad.
+ * w_k: the records' weights, or with cfg->weight_mode 1 the uniform weights the plan computes
+ * from them (records with w_k = 0 stay out).
  * One call: the two forward transform passes, the interpolation with the chi-square term fused
  * (the predicted visibilities are not stored), the adjoint's tap gathers and transform passes, and
  * the update in the last pass's epilogue.  img [N][N] (in/out), obs [n_vis] complex64, loss (device
@@ -343,7 +348,8 @@ MUSER_API int muser_grad_step(int flags, float *img, const muser_vis_record_t *r
  * W = diag(w_k), found by power iteration.
  *
  * muser_normal_apply:  u = H v for one real image v[N][N] (device, read) into u[N][N] (device, written;
- *   may alias v).  A is muser_degrid's operator on rec[n_vis]; the weights w_k are the records'.
+ *   may alias v).  A is muser_degrid's operator on rec[n_vis]; the weights w_k are the records' (uniform,
+ *   computed by the plan, with cfg->weight_mode 1).
  * muser_normalize:  norm[0] = ||u||_2 over n floats, v = u / norm[0] (v = 0 if u = 0); v may alias u;
  *   all device.  One block: meant for the power iteration's N x N directions, not for bulk data.
  * muser_lipschitz:  v[N][N] (device, in: any non-zero start vector, out: the last unit direction);

@@ -91,9 +91,9 @@ def direct(x, rec, N, cell):
 def chi2_grad(x, rec, V, sigma, N, G, ker, K=None):
     """(chi2, grad) of chi2(x) = sum_k w_k |A x - V|^2 / sigma^2."""
     w = rec["w"]
-    r = (forward(x, rec, N, G, ker, K) - V) * w
-    chi2 = float((np.abs(r) ** 2).sum() / sigma ** 2)
-    grad = 2.0 * adjoint(r, rec, N, G, ker, K).real / sigma ** 2
+    d = forward(x, rec, N, G, ker, K) - V
+    chi2 = float((w * np.abs(d) ** 2).sum() / sigma ** 2)
+    grad = 2.0 * adjoint(w * d, rec, N, G, ker, K).real / sigma ** 2
     return chi2, grad
 
 

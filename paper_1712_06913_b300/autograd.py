@@ -47,7 +47,12 @@ class Chi2(torch.autograd.Function):
 
 
 def chi2_loss(img, plan, obs, inv_sigma2):
-    """chi2(img) through both autograd functions (plan: api.DegridPlan of the records)."""
+    """chi2(img) through both autograd functions (plan: api.DegridPlan of the records).  Chi2 weighs
+    the visibilities by the records' own weights, so a plan with uniform weighting (weight_mode 1,
+    whose weights only the library's fused calls apply) is refused here."""
+    if plan.cfg.weight_mode != 0:
+        raise ValueError("chi2_loss uses the records' own weights: with weight_mode 1 use "
+                         "GradientImaging.step (muser_grad_step), which applies the uniform weights")
     return Chi2.apply(Degrid.apply(img, plan), obs, plan, inv_sigma2)
 
 

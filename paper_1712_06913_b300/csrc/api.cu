@@ -56,8 +56,6 @@ int check_cfg(const muser_config_t *cfg, Mode mode) {
   if (cfg->W < 3 || cfg->W > 9 || (cfg->W & 1) == 0) return fail(MUSER_ERR_ARG, "W must be odd in [3, 9]");
   if (cfg->os < 16 || cfg->os > 4096) return fail(MUSER_ERR_ARG, "os must be in [16, 4096]");
   if (cfg->weight_mode != 0 && cfg->weight_mode != 1) return fail(MUSER_ERR_ARG, "weight_mode must be 0 or 1");
-  if (cfg->weight_mode != 0 && mode == DEGRID)
-    return fail(MUSER_ERR_UNSUPPORTED, "the degridding operator uses natural weights (weight_mode 0)");
   if (cfg->peak_mode != 0 && cfg->peak_mode != 1) return fail(MUSER_ERR_ARG, "peak_mode must be 0 or 1");
   if (cfg->thr_mode != 0 && cfg->thr_mode != 1) return fail(MUSER_ERR_ARG, "thr_mode must be 0 or 1");
   if (cfg->max_iter < 0) return fail(MUSER_ERR_ARG, "max_iter must be >= 0");
@@ -219,6 +217,7 @@ ImagePipe *image_pipe() {
 template <class A>
 struct DegridWs {
   float *tab, *gc;
+  int32_t *ucnt = nullptr;      // uniform weighting: the N-grid cell counts of the records
   OpPlan p;
   void carve(A &a, int64_t n_vis, const muser_config_t &c) {
     const int G = c.G;
@@ -248,6 +247,7 @@ struct DegridWs {
     p.order = (int32_t *)a.template take<int32_t>((size_t)n_vis);
     p.srec = (Rec *)a.template take<Rec>((size_t)n_vis);
     p.vs = (float2 *)a.template take<float2>((size_t)n_vis);
+    if (c.weight_mode == 1) ucnt = (int32_t *)a.template take<int32_t>(uniform_count_len(c.N));
     const Pswf &P = pswf_coefficients(c.W);
     p.K2 = (float)(P.K * P.K);
   }
@@ -338,6 +338,8 @@ void plan_operator(DegridWs<A> &w, const Rec *rec, const muser_config_t &c, cuda
   launch_pswf_table(w.tab, c.W, c.os, w.gc, c.G, s, 1);   // gc as (-1)^x / gc(x) for the row passes
   fft::launch_twiddles(const_cast<float2 *>(w.p.tw), c.G, s);
   launch_degrid_plan(rec, w.p, s);
+  // uniform weighting: the chi-square weights of the plan's (sorted) records become 1 / cnt
+  if (c.weight_mode == 1) launch_uniform_weights(w.p.srec, nullptr, w.p.n_vis, 1, c.N, c.G, w.ucnt, s);
 }
 
 __global__ void k_fill(float *p, int n, float v) {

@@ -76,8 +76,10 @@ def test_config_validation_of_the_widened_calls():
         m.workspace_size(m.CALL_IMAGE, 2, 100, m.Config(N=64, G=256))
     with pytest.raises(m.MuserError):
         m.workspace_size(m.CALL_GRID, 1, 10, m.Config(N=64, G=256, weight_mode=2))
-    with pytest.raises(m.MuserError):
-        m.workspace_size(m.CALL_DEGRID, 1, 10, m.Config(N=64, G=128, weight_mode=1))
+    # uniform weighting in the degridding operator's plan: the cell counts on top
+    assert m.workspace_size(m.CALL_GRAD, 1, 10, m.Config(N=64, G=128, weight_mode=1)) == \
+        m.workspace_size(m.CALL_GRAD, 1, 10, m.Config(N=64, G=128)) + \
+        (((64 * 64 + 64 + 1) * 4 + 255) // 256) * 256
     # CLEAN variant
     assert m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256, clean_variant=1)) > \
         m.workspace_size(m.CALL_IMAGE, 4, 100, m.Config(N=64, G=256))

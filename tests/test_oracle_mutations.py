@@ -192,3 +192,13 @@ def test_uniform_weights_without_mirror_count_is_caught(monkeypatch):
         return w
     monkeypatch.setattr(imaging, "uniform_weights", bad)
     _fails(pins.test_uniform_weights_from_fp64_uv_cells)
+
+
+def test_chi2_with_squared_weights_is_caught(monkeypatch):
+    def bad(x, rec, V, sigma, N, G, ker, K=None):
+        r = (operator.forward(x, rec, N, G, ker, K) - V) * rec["w"]
+        chi2 = float((np.abs(r) ** 2).sum() / sigma ** 2)      # w^2 |r|^2: fine for 0/1 weights only
+        grad = 2.0 * operator.adjoint(r, rec, N, G, ker, K).real / sigma ** 2
+        return chi2, grad
+    monkeypatch.setattr(operator, "chi2_grad", bad)
+    _fails(pins.test_chi2_with_fractional_weights)

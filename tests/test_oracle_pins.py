@@ -475,6 +475,31 @@ def test_chi2_gradient_finite_differences():
         assert fd == pytest.approx(g.ravel()[p], rel=1e-6, abs=1e-9 * np.abs(g).max())
 
 
+def test_chi2_with_fractional_weights():
+    """The chi-square is linear in the weights, sum_k w_k |A x - V_k|^2 / sigma^2, for any weights
+    (uniform weighting makes them fractional): at x = 0 it is sum_k w_k |V_k|^2 / sigma^2, and its
+    gradient is the central finite difference of the loss with those weights."""
+    N = 32
+    wl, rec, G, cell = _op_case(N)
+    rng = np.random.default_rng(5)
+    r = dict(rec)
+    r["w"] = np.where(rec["w"] > 0, rng.uniform(0.1, 1.0, size=len(rec["w"])), 0.0)
+    V = rec["vis"]
+    sigma = 0.7
+    c0, _ = operator.chi2_grad(np.zeros((N, N)), r, V, sigma, N, G, KER)
+    assert c0 == pytest.approx(float((r["w"] * np.abs(V) ** 2).sum()) / sigma ** 2, rel=1e-12)
+    x = rng.uniform(size=(N, N)) * 0.01
+    _, g = operator.chi2_grad(x, r, V, sigma, N, G, KER)
+    h = 1e-3
+    for p in rng.choice(N * N, 8, replace=False):
+        e = np.zeros(N * N)
+        e[p] = h
+        e = e.reshape(N, N)
+        cp, _ = operator.chi2_grad(x + e, r, V, sigma, N, G, KER)
+        cm, _ = operator.chi2_grad(x - e, r, V, sigma, N, G, KER)
+        assert (cp - cm) / (2 * h) == pytest.approx(g.ravel()[p], rel=1e-6, abs=1e-9 * np.abs(g).max())
+
+
 def test_gradient_at_zero_is_scaled_dirty_image():
     """grad chi2(0) = -(2 sum w / sigma^2) D_dft (the dirty image is the adjoint)."""
     N = 32
