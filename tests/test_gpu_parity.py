@@ -565,6 +565,35 @@ def test_fused_gradient_step_equals_autograd_step(m, N):
     assert np.linalg.norm(_np(grad) - g_o) <= 1e-4 * np.linalg.norm(g_o)
 
 
+@pytest.mark.parametrize("N", [32, 64])
+def test_grad_step_uniform_weights_vs_oracle(m, N):
+    """weight_mode 1 in the operator's plan: the chi-square weighs each record by Alg. 1's uniform
+    weight (1 / samples in its cell of the N x N grid, G/N = 2 uv cells wide), computed by the
+    plan from the records.  Loss and gradient of muser_grad_step against the FP64 oracle with
+    oracle.imaging.uniform_weights; the autograd loss (the records' own weights) refuses it."""
+    import torch
+    from paper_1712_06913_b300.autograd import chi2_loss
+    wl, cfg, rec, ro = _op_case(m, N, n_chan=4)
+    cfg_u = m.Config(N=N, G=cfg.G, lat_rad=wl.lat, weight_mode=1)
+    ro_u = dict(ro)
+    ro_u["w"] = imaging.uniform_weights(ro, cfg.G, N)
+    assert (ro_u["w"][ro["w"] > 0] < 1.0).any()          # some cells hold several samples
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    x0 = np.random.default_rng(N + 7).normal(size=(N, N))
+    plan = m.DegridPlan(rec, cfg_u)
+    x = torch.tensor(x0, dtype=torch.float32, device="cuda")
+    grad = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    plan.grad_step(x, obs, 1.0 / 0.25, 0.0, loss, grad)
+    c_o, g_o = oop.chi2_grad(x0, ro_u, ro["vis"], 0.5, N, cfg.G, KER)
+    c_n, g_n = oop.chi2_grad(x0, ro, ro["vis"], 0.5, N, cfg.G, KER)
+    assert float(loss[0]) == pytest.approx(c_o, rel=1e-4)
+    assert np.linalg.norm(_np(grad) - g_o) <= 1e-4 * np.linalg.norm(g_o)
+    assert np.linalg.norm(g_n - g_o) > 1e-2 * np.linalg.norm(g_o)   # the weights matter here
+    with pytest.raises(ValueError):
+        chi2_loss(x, plan, obs, 4.0)
+
+
 # ------------------------------------------------------------------------------ disk centring (Sec. 4.2)
 def _centring_case(off_px, N=128, seed=110):
     wl0 = synth.small_workload(n_ant=31, N=N, config_id=seed, bmax=600.0, snr=0)
