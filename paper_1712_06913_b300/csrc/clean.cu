@@ -339,7 +339,8 @@ __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o
 // beam4: CP copies of every instance's beam (beam_copies(B, N): 4 or 2), copy k at
 // beam4 + k * cstride holding Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window
 // row of any peak starts 4 CP-byte aligned in copy (N - px) mod CP: each residual quad takes one
-// aligned 16-byte load from four copies, or two aligned 8-byte loads from two.  Two copies put
+// aligned 16-byte load from four copies, or from two copies one 16-byte load when the row happens
+// to start 16-byte aligned and two 8-byte loads otherwise.  Two copies put
 // half the window bytes in L2 (with many instances in flight the windows of four copies overflow
 // it and half the window reads go to DRAM); four copies halve the load instructions, which is
 // the better trade when a batch's beams fit in L2.
@@ -483,14 +484,15 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
           return bt + (size_t)i * QSTEP * (2 * N);
         }
       };
-      auto beam_q = [&](int i) -> float4 {   // one aligned 16-byte load (4 copies) or two 8-byte loads
-        if constexpr (CP == 4) {
-          return __ldg(reinterpret_cast<const float4 *>(beam_p(i)));
-        } else {
-          const float2 *q = reinterpret_cast<const float2 *>(beam_p(i));
-          const float2 a = __ldg(q), b = __ldg(q + 1);
-          return make_float4(a.x, a.y, b.x, b.y);
-        }
+      // one aligned 16-byte load per quad from four copies; from two, one 16-byte load when the
+      // window row starts on a 16-byte boundary of its copy ((N - px) mod 4 < 2, the same for
+      // every thread of the cluster), else two 8-byte loads
+      const bool a16 = CP == 4 || (off & 2) == 0;
+      auto beam_q = [&](int i) -> float4 {
+        if (a16) return __ldg(reinterpret_cast<const float4 *>(beam_p(i)));
+        const float2 *q = reinterpret_cast<const float2 *>(beam_p(i));
+        const float2 a = __ldg(q), b = __ldg(q + 1);
+        return make_float4(a.x, a.y, b.x, b.y);
       };
       cb = Cand<MODE>();
       // TB aligned beam loads in flight, then the residual read, updated and written back
