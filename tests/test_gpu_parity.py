@@ -405,6 +405,32 @@ def _op_case(m, N=32, n_chan=3, seed=220):
     return wl, cfg, rec, ro
 
 
+def test_degrid_degenerate_record_sets(m):
+    """No records, or only records with w = 0 (every baseline flagged): the forward operator gives
+    zeros (or nothing), the adjoint an all-zero image, and a gradient step a zero loss and
+    gradient that leaves the image unchanged."""
+    import torch
+    wl, cfg, rec, ro = _op_case(m, 32)
+    N = cfg.N
+    x = torch.tensor(np.random.default_rng(3).normal(size=(N, N)), dtype=torch.float32, device="cuda")
+    empty = rec[:0]
+    plan0 = m.DegridPlan(empty, cfg)
+    assert plan0.forward(x).numel() == 0
+    assert float(plan0.adjoint(torch.zeros(0, dtype=torch.complex64, device="cuda")).abs().max()) == 0.0
+    flagged = rec.clone()
+    m.record_fields(flagged)[5].zero_()                          # w = 0: every record weighted out
+    plan = m.DegridPlan(flagged, cfg)
+    assert float(plan.forward(x).abs().max()) == 0.0
+    obs = torch.tensor(ro["vis"], dtype=torch.complex64, device="cuda")
+    assert float(plan.adjoint(obs).abs().max()) == 0.0
+    x1 = x.clone()
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    grad = torch.empty((N, N), dtype=torch.float32, device="cuda")
+    plan.grad_step(x1, obs, 4.0, 0.1, loss, grad)
+    assert float(loss[0]) == 0.0 and float(grad.abs().max()) == 0.0
+    assert torch.equal(x1, x)
+
+
 def _cfg4(m):
     wl = synth.config4_operator()
     N, G = wl.N, wl.G
