@@ -340,10 +340,10 @@ __device__ __forceinline__ int band_index(int o, int tid) { return 4 * (tid + (o
 // beam4 + k * cstride holding Bk[y][x] = Bm[y][x + k] (zero past the row end), so that the window
 // row of any peak starts 4 CP-byte aligned in copy (N - px) mod CP: each residual quad takes one
 // aligned 16-byte load from four copies, or from two copies one 16-byte load when the row happens
-// to start 16-byte aligned and two 8-byte loads otherwise.  Two copies put
-// half the window bytes in L2 (with many instances in flight the windows of four copies overflow
-// it and half the window reads go to DRAM); four copies halve the load instructions, which is
-// the better trade when a batch's beams fit in L2.
+// to start 16-byte aligned and two 8-byte loads otherwise.  Two copies put half the window
+// bytes in L2 (with many instances in flight the windows of four copies overflow it and half the
+// window reads go to DRAM); four copies take a third fewer load instructions, the better trade
+// when a batch's beams fit in L2.
 //
 // The kernel below is a persistent worker: its clusters draw instances from one atomic counter
 // (`next`) until the batch is exhausted.
