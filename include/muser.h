@@ -255,7 +255,9 @@ MUSER_API int muser_image(const double *ant_enu, int n_ant, const int32_t *bl_pa
  * are not announced.  A copy stream that waits on chunk_done[c] may then read chunk c's
  * clean_img, residual, comp_pos, comp_flux, n_comp, thr_out, beam_params and status while the
  * following chunks are imaged.  chunk_done may be NULL when n_events is 0; a NULL entry is
- * skipped.  Returns MUSER_ERR_ARG when n_events < 0 or chunk_done is NULL with n_events > 0. */
+ * skipped.  Meant for eager launches: under stream capture the records become nodes of the
+ * captured graph, which a stream outside that graph cannot wait on (capture muser_image instead).
+ * Returns MUSER_ERR_ARG when n_events < 0 or chunk_done is NULL with n_events > 0. */
 MUSER_API int muser_image_events(const double *ant_enu, int n_ant, const int32_t *bl_pairs, int n_bl,
                                  const double *ha, const double *dec, int n_frame, const double *freq_hz,
                                  const double *cell_rad, int n_chan, const float *vis, const uint8_t *flags,
