@@ -208,6 +208,8 @@ ONCHIP_CASES = {
     "N512x2": lambda: synth.config2_muser1_band(n_frame=1, chans=[10, 50]),
     "N512x12": lambda: synth.config2_muser1_band(n_frame=1, chans=list(range(4, 64, 5))),
     "N1024x2": lambda: synth.config3_muser2_uneven(n_frame=1, chans=[7, 400]),
+    # four beam copies up to B N^2 = 2^21 (the cases above), two beyond: 3 instances at 1024^2
+    "N1024x3": lambda: synth.config3_muser2_uneven(n_frame=1, chans=[7, 200, 400]),
 }
 
 
