@@ -144,8 +144,9 @@ class GradientImaging:
         self.loss = loss
         return self.loss
 
-    def capture(self, warmup=3):
-        """Record one step in a CUDA graph (after `warmup` eager steps on a side stream)."""
+    def capture(self, warmup=3, steps=1):
+        """Record `steps` consecutive steps in one CUDA graph (after `warmup` eager steps on a side
+        stream): a descent loop of many steps replays it and pays one graph launch per `steps`."""
         import torch
         if self.eta is None:
             self.eta = 1.0 / self.lipschitz()
@@ -157,10 +158,13 @@ class GradientImaging:
         torch.cuda.current_stream().wait_stream(s)
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.static_loss = self.step()
+            for _ in range(steps):
+                self.static_loss = self.step()
+        self.graph_steps = steps
         return self
 
     def replay(self, n=1):
+        """Replay the captured graph n times (n * `steps` steps); returns the last step's loss."""
         for _ in range(n):
             self.graph.replay()
         return self.static_loss

@@ -333,6 +333,17 @@ def test_chained_gradient_steps_equal_separate_steps(m):
         c.plan.grad_step(c.x.data, c.obs, c.inv_s2, c.eta, lb)
     torch.cuda.synchronize()
     assert torch.equal(a.x.detach(), c.x.detach())
+    # a graph of four chained steps, replayed twice after one eager step: nine steps
+    d = GradientImaging(rec, obs, 0.5, cfg, x0=x0, eta=2e-5)
+    e = GradientImaging(rec, obs, 0.5, cfg, x0=x0, eta=2e-5)
+    d.plan, e.plan = a.plan.clone(), a.plan.clone()
+    d.capture(warmup=1, steps=4)
+    d.replay(2)
+    for _ in range(9):
+        e.plan.grad_step(e.x.data, e.obs, e.inv_s2, e.eta, lb)
+    torch.cuda.synchronize()
+    assert torch.equal(d.x.detach(), e.x.detach())
+    assert float(d.static_loss) == float(lb[0])
 
 
 # ------------------------------------------------------------------------------ results streamed per chunk
