@@ -180,6 +180,12 @@ def test_dirty_full_size_instance(m):
     for i, (Zo, Do, Bo, norm) in enumerate(ref):
         assert np.abs(Dg[i] - Do).max() <= 1e-4 * np.abs(Do).max()
         assert np.abs(Bg[i] - Bo).max() <= 1e-4
+        # the beam is even about (N, N) (both uv signs gridded): each side within 1e-4 of the
+        # oracle's, whose mirror pairs agree to 1e-12
+        A = Bg[i][1:, 1:]
+        assert np.abs(A - A[::-1, ::-1]).max() <= 2e-4
+        N = cfg.N
+        assert np.unravel_index(np.argmax(Bg[i]), Bg[i].shape) == (N, N)
 
 
 # ------------------------------------------------------------------------------ CLEAN

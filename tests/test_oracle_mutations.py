@@ -202,3 +202,18 @@ def test_chi2_with_squared_weights_is_caught(monkeypatch):
         return chi2, grad
     monkeypatch.setattr(operator, "chi2_grad", bad)
     _fails(pins.test_chi2_with_fractional_weights)
+
+
+def test_beam_window_off_by_one_is_caught(monkeypatch):
+    def bad(Z, N, ker):
+        G = Z.shape[0]
+        I = imaging.centred_inverse_dft2(Z)
+        gc = ker.grid_correction(G)
+        corr = np.outer(gc, gc)
+        lo_d, lo_b = G // 2 - N // 2, G // 2 - N + 1          # beam window one pixel off centre
+        D = (I.real / corr)[lo_d:lo_d + N, lo_d:lo_d + N]
+        Bm = (I.imag / corr)[lo_b:lo_b + 2 * N, lo_b:lo_b + 2 * N]
+        norm = Bm[N, N]
+        return D / norm, Bm / norm, norm
+    monkeypatch.setattr(imaging, "dirty_and_beam", bad)
+    _fails(pins.test_dirty_beam_is_point_symmetric_about_its_centre)

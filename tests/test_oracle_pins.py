@@ -164,6 +164,21 @@ def test_phase_centre_point_source():
     np.testing.assert_allclose(D, 2.5 * Bm[N // 2:N // 2 + N, N // 2:N // 2 + N], rtol=0, atol=1e-14 * 2.5)
 
 
+def test_dirty_beam_is_point_symmetric_about_its_centre():
+    """Every sample is gridded at +uv and at -uv with the same weight (Sec. 3.2.3), so the beam
+    part of the grid is real and even about the grid centre and so is its transform: over the
+    2N x 2N beam, Bm(N + dy, N + dx) = Bm(N - dy, N - dx) (row and column 0 have no mirror
+    inside the beam), and the largest value is the unit centre."""
+    for N in (32, 40):
+        wl, rec = _tiny(N=N, n_ant=9, seed_cfg=107)
+        Z = imaging.grid(rec, wl.G, KER)
+        _, Bm, _ = imaging.dirty_and_beam(Z, N, KER)
+        A = Bm[1:, 1:]
+        np.testing.assert_allclose(A, A[::-1, ::-1], rtol=0, atol=1e-12)
+        assert Bm[N, N] == 1.0
+        assert np.unravel_index(np.argmax(Bm), Bm.shape) == (N, N)
+
+
 @pytest.mark.parametrize("N,n_ant,cfg", [(32, 7, 102), (64, 10, 103)])
 def test_gridded_image_matches_direct_dft(N, n_ant, cfg):
     """Gridding + FFT + correction approximates the direct transform (reading A6 bound)."""
