@@ -2,7 +2,12 @@
 // Alg. 1 pre_clean, first step).
 //
 // One block per instance: min/max, a `bins`-range histogram in shared memory, then EM on the
-// bins (K = 3, weighted by the counts) in FP32 with log-space responsibilities.  Start:
+// bins (K = 3, weighted by the counts) in FP32 with log-space (base 2) responsibilities.  The
+// M step takes, in the same pass as the responsibilities r, the sums n = sum h r,
+// s1 = sum h r d and s2 = sum h r d^2 about the current mean (d = x - mu_k), so that
+// mu' = mu_k + s1 / n and var' = s2 / n - (s1 / n)^2: the weighted mean and the weighted
+// variance about the new mean, without storing r or a second pass (and without cancellation
+// near the fixed point, where s1 / n is small).  Start:
 // means at the bins where the count CDF first reaches 0.25, 0.85 and 0.995 (decided in
 // FP64 on exact integer counts), variances var/3 (var of the histogram), equal weights;
 // variance floor (bin width)^2.  Stopping: the FP64 rule |dlogL| < 1e-12 |logL| cannot be
@@ -16,9 +21,9 @@ namespace muser {
 
 namespace {
 
-constexpr int kGmmThreads = 256;
-constexpr int kMaxBinsPerThread = 16;    // bins <= 4096
+constexpr int kGmmThreads = 256;          // bins per thread: 8 (bins <= 2048) or 16 (<= 4096)
 constexpr int K = 3;
+constexpr float kHalfLog2e = 0.7213475204444817f;   // log2(e) / 2
 
 template <int NV>
 __device__ void block_sum(float (&v)[NV], float (*sh)[kGmmThreads / 32]) {
@@ -40,11 +45,12 @@ __device__ void block_sum(float (&v)[NV], float (*sh)[kGmmThreads / 32]) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ Dall, int N, int bins,
-                                                     float *__restrict__ mu_a, float *__restrict__ mu_b,
-                                                     int32_t *__restrict__ status) {
+template <int BPT>
+__global__ void __launch_bounds__(kGmmThreads, BPT <= 8 ? 4 : 2) k_gmm(const float *__restrict__ Dall, int N, int bins,
+                                                                     float *__restrict__ mu_a, float *__restrict__ mu_b,
+                                                                     int32_t *__restrict__ status) {
   extern __shared__ int hist[];      // bins ints
-  __shared__ float red[8][kGmmThreads / 32];
+  __shared__ float red[3 * K][kGmmThreads / 32];
   __shared__ float mm[2][kGmmThreads / 32];
   __shared__ int qbin[K];
   const int inst = blockIdx.x;
@@ -97,10 +103,10 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
     while (k < K) qbin[k++] = bins - 1;
   }
   // per-thread bins
-  float xb[kMaxBinsPerThread], hb[kMaxBinsPerThread];
+  float xb[BPT], hb[BPT];
   int nb = 0;
 #pragma unroll
-  for (int j = 0; j < kMaxBinsPerThread; j++) {
+  for (int j = 0; j < BPT; j++) {
     const int b = threadIdx.x + j * kGmmThreads;
     xb[j] = lo + ((float)b + 0.5f) * width;
     hb[j] = b < bins ? (float)hist[b] : 0.f;
@@ -131,66 +137,52 @@ __global__ void __launch_bounds__(kGmmThreads) k_gmm(const float *__restrict__ D
     float prev[3 * K];
 #pragma unroll
     for (int k = 0; k < K; k++) { prev[k] = mu[k]; prev[K + k] = var[k]; prev[2 * K + k] = pi[k]; }
+    // log2 of pi_k N(x; mu_k, var_k) = lpi + c2 (x - mu)^2 + ln, in base 2 so that each
+    // responsibility takes one exp2f
     float lpi[K], c2[K], ln[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      lpi[k] = logf(pi[k]);
-      c2[k] = -0.5f / var[k];
-      ln[k] = -0.5f * logf(2.f * CUDART_PI_F * var[k]);
+      lpi[k] = log2f(pi[k]);
+      c2[k] = -kHalfLog2e / var[k];
+      ln[k] = -0.5f * log2f(2.f * CUDART_PI_F * var[k]);
     }
-    float acc[2 * K];
+    float acc[3 * K];       // per component: n, s1, s2 about the current mean
 #pragma unroll
-    for (int a = 0; a < 2 * K; a++) acc[a] = 0.f;
-    float rr[kMaxBinsPerThread][K];
+    for (int a = 0; a < 3 * K; a++) acc[a] = 0.f;
 #pragma unroll
-    for (int j = 0; j < kMaxBinsPerThread; j++) {
+    for (int j = 0; j < BPT; j++) {
       if (j < nb) {
-        float lp[K], m = -CUDART_INF_F;
+        float d[K], lp[K], m = -CUDART_INF_F;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-          const float d = xb[j] - mu[k];
-          lp[k] = lpi[k] + c2[k] * d * d + ln[k];
+          d[k] = xb[j] - mu[k];
+          lp[k] = lpi[k] + c2[k] * d[k] * d[k] + ln[k];
           m = fmaxf(m, lp[k]);
         }
         float e[K], s = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; k++) { e[k] = expf(lp[k] - m); s += e[k]; }
+        for (int k = 0; k < K; k++) { e[k] = exp2f(lp[k] - m); s += e[k]; }
         const float invs = 1.f / s;
 #pragma unroll
         for (int k = 0; k < K; k++) {
-          rr[j][k] = e[k] * invs;
-          const float hr = hb[j] * rr[j][k];
+          const float hr = hb[j] * (e[k] * invs);
           acc[k] += hr;
-          acc[K + k] += hr * xb[j];
+          acc[K + k] += hr * d[k];
+          acc[2 * K + k] += hr * d[k] * d[k];
         }
       }
     }
-    block_sum<2 * K>(acc, red);
-    float nk[K];
+    block_sum<3 * K>(acc, red);
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      nk[k] = acc[k];
-      if (nk[k] > 0.f) mu[k] = acc[K + k] / nk[k];
-    }
-    float sv[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) sv[k] = 0.f;
-#pragma unroll
-    for (int j = 0; j < kMaxBinsPerThread; j++) {
-      if (j < nb) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-          const float d = xb[j] - mu[k];
-          sv[k] += hb[j] * rr[j][k] * d * d;
-        }
+      const float nk = acc[k];
+      if (nk > 0.f) {
+        const float dm = acc[K + k] / nk;
+        mu[k] += dm;
+        var[k] = acc[2 * K + k] / nk - dm * dm;
       }
-    }
-    block_sum<K>(sv, red);
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      if (nk[k] > 0.f) var[k] = sv[k] / nk[k];
       var[k] = fmaxf(var[k], floor_v);
-      pi[k] = nk[k] / total;
+      pi[k] = nk / total;
     }
     bool same = true;
 #pragma unroll
@@ -217,8 +209,12 @@ void launch_gmm(const float *dirty, int B, int N, int bins, float *mu_a, float *
   if (B <= 0) return;
   for (int i = 0; i < B; i += 65535) {
     const int n = B - i < 65535 ? B - i : 65535;
-    k_gmm<<<n, kGmmThreads, bins * sizeof(int), s>>>(dirty + (size_t)i * N * N, N, bins, mu_a + i, mu_b + i,
-                                                      status ? status + i : nullptr);
+    if (bins <= 8 * kGmmThreads)
+      k_gmm<8><<<n, kGmmThreads, bins * sizeof(int), s>>>(dirty + (size_t)i * N * N, N, bins, mu_a + i, mu_b + i,
+                                                           status ? status + i : nullptr);
+    else
+      k_gmm<16><<<n, kGmmThreads, bins * sizeof(int), s>>>(dirty + (size_t)i * N * N, N, bins, mu_a + i, mu_b + i,
+                                                            status ? status + i : nullptr);
     note_launch();
   }
 }

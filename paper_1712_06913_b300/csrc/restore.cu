@@ -6,7 +6,10 @@
 // MUSER_ST_BEAM_FIT).  Its second moments about the centre (integer sums, then FP64),
 // with 1/12 added on the diagonal for the unit pixel area, give Sigma = (2 / ln 2) M.
 // k_restore (one block per 32 x 32 tile): residual + sum_c f_c exp(-q' Sigma^-1 q / 2) over
-// the components whose Gaussian exceeds 1e-7 on the tile, in component order.
+// the components whose Gaussian exceeds 1e-7 on the tile, in component order.  The exponent is
+// taken in base 2 (the inverse covariance scaled by -log2(e) / 2 once per instance, exp2f per
+// pixel), with the component's coordinates kept as floats next to its flux: the four pixels
+// of a thread cost two multiplies, two FMAs and one exp2f each per component.
 #include "common.cuh"
 
 namespace muser {
@@ -17,6 +20,34 @@ constexpr int kFitThreads = 1024;
 constexpr int kWin = 63;                   // half window
 constexpr int kSide = 2 * kWin + 1;
 constexpr float kTrunc = 32.2361913f;      // 2 ln(1e7): Gaussian below 1e-7 outside q' S^-1 q > kTrunc
+constexpr float kHalfLog2e = 0.7213475204444817f;   // log2(e) / 2
+
+// The clean beam's exponent in base 2: exp(-q' S^-1 q / 2) = 2^e with
+// e = a dx^2 + b dx dy + c dy^2 (a = -log2(e)/2 Sxx', b = -log2(e) Sxy', c = -log2(e)/2 Syy' for
+// S^-1 = [[Sxx', Sxy'], [Sxy', Syy']]); the Gaussian is below 1e-7 where e < emin.
+struct BeamExp {
+  float a, b, c, emin;
+};
+
+__device__ __forceinline__ BeamExp beam_exp(float ixx, float ixy, float iyy) {
+  return BeamExp{-kHalfLog2e * ixx, -2.f * kHalfLog2e * ixy, -kHalfLog2e * iyy, -kHalfLog2e * kTrunc};
+}
+
+// acc[k] += f_j 2^e(pixel k - component j) for the m components j of the shared lists, in list
+// order, for a thread's four pixels (fx[k], fy[k]).
+__device__ __forceinline__ void add_components(const float *cx, const float *cy, const float *cf, int m,
+                                               const BeamExp &g, const float (&fx)[4], const float (&fy)[4],
+                                               float (&acc)[4]) {
+  for (int j = 0; j < m; j++) {
+    const float x = cx[j], y = cy[j], f = cf[j];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float dx = fx[k] - x, dy = fy[k] - y;
+      const float e = fmaf(fmaf(g.a, dx, g.b * dy), dx, g.c * (dy * dy));
+      if (e >= g.emin) acc[k] = fmaf(f, exp2f(e), acc[k]);
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kFitThreads) k_beam_fit(const float *__restrict__ Ball, int N,
                                                           float *__restrict__ params,
@@ -94,8 +125,7 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
                                                  const float *__restrict__ flux, const int32_t *__restrict__ n_comp,
                                                  int N, int cap, const float *__restrict__ params,
                                                  float *__restrict__ clean) {
-  __shared__ int cp[256];
-  __shared__ float cf[256];
+  __shared__ float cxs[256], cys[256], cf[256];
   const int inst = blockIdx.y;
   const int tiles_x = N / 32 > 0 ? N / 32 : 1;
   const int tw = N < 32 ? N : 32;
@@ -107,8 +137,9 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
   const bool ok = det > 0.f;
   const float ixx = ok ? syy / det : 0.f, ixy = ok ? -sxy / det : 0.f, iyy = ok ? sxx / det : 0.f;
   const float ex = ok ? sqrtf(kTrunc * sxx) : 0.f, ey = ok ? sqrtf(kTrunc * syy) : 0.f;
+  const BeamExp g = beam_exp(ixx, ixy, iyy);
   // 4 pixels per thread (tile of tw x tw <= 1024 pixels)
-  float acc[4];
+  float acc[4], fx[4], fy[4];
   int py[4], px[4];
   const int npx = tw * tw;
 #pragma unroll
@@ -116,6 +147,8 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
     const int p = threadIdx.x + k * 256;
     py[k] = ty0 + (p < npx ? p / tw : 0);
     px[k] = tx0 + (p < npx ? p % tw : 0);
+    fx[k] = (float)px[k];
+    fy[k] = (float)py[k];
     acc[k] = 0.f;
   }
   // components whose truncated Gaussian reaches this tile: each thread tests a share of the
@@ -128,12 +161,13 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
     __syncthreads();
     const int c = c0 + threadIdx.x;
     bool hit = false;
-    int cpos = 0;
+    int cy = 0, cx = 0;
     float cflux = 0.f;
     if (c < nc) {
-      cpos = pos[(size_t)inst * cap + c];
+      const int cpos = pos[(size_t)inst * cap + c];
       cflux = flux[(size_t)inst * cap + c];
-      const int cy = cpos / N, cx = cpos % N;
+      cy = cpos / N;
+      cx = cpos - cy * N;
       hit = !(cx + ex < tx0 || cx - ex > tx0 + tw - 1 || cy + ey < ty0 || cy - ey > ty0 + tw - 1);
     }
     // order-preserving compaction: warp ballots, then a prefix over the 8 warps
@@ -146,7 +180,8 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
     for (int w = 0; w < wid; w++) base += wcount[w];
     if (hit) {
       const int slot = base + __popc(mask & ((1u << lane) - 1u));
-      cp[slot] = cpos;
+      cxs[slot] = (float)cx;
+      cys[slot] = (float)cy;
       cf[slot] = cflux;
     }
     if (threadIdx.x == 255) {
@@ -155,17 +190,7 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
       nsurv = tot;
     }
     __syncthreads();
-    const int m = nsurv;
-    for (int k2 = 0; k2 < m; k2++) {
-      const int cy = cp[k2] / N, cx = cp[k2] % N;
-      const float f = cf[k2];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const float dx = (float)(px[k] - cx), dy = (float)(py[k] - cy);
-        const float qq = ixx * dx * dx + 2.f * ixy * dx * dy + iyy * dy * dy;
-        if (qq <= kTrunc) acc[k] += f * expf(-0.5f * qq);
-      }
-    }
+    add_components(cxs, cys, cf, nsurv, g, fx, fy, acc);
   }
 #pragma unroll
   for (int k = 0; k < 4; k++) {
@@ -182,8 +207,7 @@ __global__ void __launch_bounds__(256) k_restore(const float *__restrict__ Rall,
 // in row-major order, a chunk of 256 at a time, and added as in k_restore.
 __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ Rall, const float *__restrict__ model,
                                                      int N, const float *__restrict__ params, float *__restrict__ clean) {
-  __shared__ int cp[256];
-  __shared__ float cf[256];
+  __shared__ float cxs[256], cys[256], cf[256];
   __shared__ int wcount[8];
   __shared__ int nsurv;
   const int inst = blockIdx.y;
@@ -198,7 +222,8 @@ __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ R
   const bool ok = det > 0.f;
   const float ixx = ok ? syy / det : 0.f, ixy = ok ? -sxy / det : 0.f, iyy = ok ? sxx / det : 0.f;
   const int rx = ok ? (int)ceilf(sqrtf(kTrunc * sxx)) : 0, ry = ok ? (int)ceilf(sqrtf(kTrunc * syy)) : 0;
-  float acc[4];
+  const BeamExp g = beam_exp(ixx, ixy, iyy);
+  float acc[4], fx[4], fy[4];
   int py[4], px[4];
   const int npx = tw * tw;
 #pragma unroll
@@ -206,6 +231,8 @@ __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ R
     const int p = threadIdx.x + k * 256;
     py[k] = ty0 + (p < npx ? p / tw : 0);
     px[k] = tx0 + (p < npx ? p % tw : 0);
+    fx[k] = (float)px[k];
+    fy[k] = (float)py[k];
     acc[k] = 0.f;
   }
   const int hy0 = max(0, ty0 - ry), hy1 = min(N - 1, ty0 + tw - 1 + ry);
@@ -215,11 +242,12 @@ __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ R
   for (int h0 = 0; h0 < nh; h0 += 256) {
     __syncthreads();
     const int h = h0 + threadIdx.x;
-    int cpos = 0;
+    int cy = 0, cx = 0;
     float cflux = 0.f;
     if (h < nh) {
-      cpos = (hy0 + h / hw) * N + hx0 + h % hw;
-      cflux = M[cpos];
+      cy = hy0 + h / hw;
+      cx = hx0 + h % hw;
+      cflux = M[(size_t)cy * N + cx];
     }
     const bool hit = cflux != 0.f;
     const unsigned mask = __ballot_sync(0xffffffffu, hit);
@@ -229,7 +257,8 @@ __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ R
     for (int w = 0; w < wid; w++) base += wcount[w];
     if (hit) {
       const int slot = base + __popc(mask & ((1u << lane) - 1u));
-      cp[slot] = cpos;
+      cxs[slot] = (float)cx;
+      cys[slot] = (float)cy;
       cf[slot] = cflux;
     }
     if (threadIdx.x == 255) {
@@ -238,17 +267,7 @@ __global__ void __launch_bounds__(256) k_restore_map(const float *__restrict__ R
       nsurv = tot;
     }
     __syncthreads();
-    const int m = nsurv;
-    for (int k2 = 0; k2 < m; k2++) {
-      const int cy = cp[k2] / N, cx = cp[k2] % N;
-      const float f = cf[k2];
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const float dx = (float)(px[k] - cx), dy = (float)(py[k] - cy);
-        const float qq = ixx * dx * dx + 2.f * ixy * dx * dy + iyy * dy * dy;
-        if (qq <= kTrunc) acc[k] += f * expf(-0.5f * qq);
-      }
-    }
+    add_components(cxs, cys, cf, nsurv, g, fx, fy, acc);
   }
 #pragma unroll
   for (int k = 0; k < 4; k++) {
