@@ -61,8 +61,8 @@ class GradientImaging:
 
     Each step evaluates chi2 and its gradient through Degrid/Chi2 (forward operator,
     chi-square seed and adjoint are library kernels) and applies x <- x - eta * grad.
-    `capture()` records one step in a CUDA graph so that `replay()` runs it without host
-    work; the image, loss and gradient live in fixed device tensors.
+    `capture()` records one step (or several chained steps) in a CUDA graph so that `replay()`
+    runs them without host work; the image, loss and gradient live in fixed device tensors.
 
     Under torch.distributed each rank passes the records and visibilities of its own block of
     channels (`dist.block`); the loss and the gradient are summed over ranks every step, so
