@@ -265,6 +265,21 @@ def test_gmm(m, name):
         assert abs(float(_np(mu_b)[i]) - b) <= 1e-4 * rng
 
 
+@pytest.mark.parametrize("bins", [4096, 300])
+def test_gmm_bin_counts(m, bins):
+    """The histogram has gmm_bins ranges (2..4096): 4096 takes the kernel's instance with sixteen
+    bins per thread, 300 the eight-bin one with most threads holding fewer than eight."""
+    wl = WORKLOADS["plain-N256"]()
+    cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
+    cfg.gmm_bins = bins
+    mu_a, mu_b, _ = m.gmm(D, cfg)
+    for i, (_, Do, _, _) in enumerate(ref):
+        a, b, _ = ogmm.sky_and_disk(Do, bins)
+        rng = Do.max() - Do.min()
+        assert abs(float(_np(mu_a)[i]) - a) <= 1e-4 * rng
+        assert abs(float(_np(mu_b)[i]) - b) <= 1e-4 * rng
+
+
 # ------------------------------------------------------------------------------ restore
 def test_restore(m):
     wl = WORKLOADS["plain-N256"]()
