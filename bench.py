@@ -445,9 +445,11 @@ def main():
     achieved = stream_model / (clean_ms / 1e3) / 1e9
     traffic = statistics.mean(clean_bytes) * tr["dram_per_algorithmic"] if tr else None
     roofline = {"kernel": "muser_clean: k_beam_shift + k_hogbom_onchip", "bound": "latency",
-                "bound_detail": ("the residual stays on chip, so DRAM is not the limit: an iteration is the "
-                                 "beam-window loads, the tensor-memory pass and the 16-block cluster exchange "
-                                 "one after the other (SM time and exchange latency)"),
+                "bound_detail": ("the residual stays on chip, so DRAM is not the limit: an iteration is each "
+                                 "SM's pass over its 256 KB band of L2-resident beam window (loads at the L2 "
+                                 "latency of a fully loaded GPU, tensor-memory reads and writes) and then the "
+                                 "16-block cluster exchange; a 256^2 kernel with no exchange iterates no faster "
+                                 "under load, so the pass's latency sets the time"),
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": peak_kind,
                 "bytes_model": "12 N^2 per iteration (residual read + beam window read + residual write) + 4 N^2",
