@@ -4,11 +4,13 @@ Each case swaps one oracle function for a subtly wrong copy -- a dropped term, a
 wrong sign, a transposed operand, an off-by-one index -- and runs the pin that is
 meant to catch it.
 """
+import math
+
 import numpy as np
 import pytest
 
 import test_oracle_pins as pins
-from oracle import clean, geometry, gmm, imaging, operator, pswf, steer
+from oracle import clean, geometry, gmm, imaging, operator, pswf, restore, steer
 
 
 def _fails(fn, *args):
@@ -217,3 +219,49 @@ def test_beam_window_off_by_one_is_caught(monkeypatch):
         return D / norm, Bm / norm, norm
     monkeypatch.setattr(imaging, "dirty_and_beam", bad)
     _fails(pins.test_dirty_beam_is_point_symmetric_about_its_centre)
+
+
+def test_hogbom_component_without_gain_is_caught(monkeypatch):
+    def bad(D, Bm, gain, thr, cap, peak_mode=0):
+        R = np.array(D, dtype=np.float64, copy=True)
+        N = R.shape[0]
+        pos, flux = [], []
+        val, p = clean.peak(R, peak_mode)
+        while (val if peak_mode == 0 else abs(val)) > thr and len(pos) < cap:
+            py, px = divmod(p, N)
+            R -= gain * val * Bm[N - py:2 * N - py, N - px:2 * N - px]
+            pos.append(p)
+            flux.append(val)                       # the component's flux without the loop gain
+            val, p = clean.peak(R, peak_mode)
+        return R, np.asarray(pos, np.int64), np.asarray(flux, float)
+    monkeypatch.setattr(clean, "hogbom", bad)
+    _fails(pins.test_hogbom_isolated_point_source_closed_form)
+
+
+def test_hogbom_last_of_equal_peaks_is_caught(monkeypatch):
+    def bad(R, peak_mode=0):
+        key = np.abs(R) if peak_mode else R
+        flat = key.ravel()
+        p = flat.size - 1 - int(np.argmax(flat[::-1]))   # the highest index among equal keys
+        return float(R.flat[p]), p
+    monkeypatch.setattr(clean, "peak", bad)
+    _fails(pins.test_hogbom_tie_break_and_abs_mode)
+
+
+def test_clean_beam_without_half_width_factor_is_caught(monkeypatch):
+    orig = restore.clean_beam
+
+    def bad(Bm):
+        return tuple(math.log(2.0) * s for s in orig(Bm))   # covariance 2 M instead of (2 / ln 2) M
+    monkeypatch.setattr(restore, "clean_beam", bad)
+    _fails(pins.test_clean_beam_of_exact_gaussian)
+
+
+def test_restore_gaussian_with_swapped_axes_is_caught(monkeypatch):
+    def bad(S, dx, dy):
+        sxx, sxy, syy = S
+        det = sxx * syy - sxy * sxy
+        ixx, ixy, iyy = syy / det, -sxy / det, sxx / det
+        return np.exp(-0.5 * (ixx * dy * dy + 2 * ixy * dx * dy + iyy * dx * dx))   # x and y exchanged
+    monkeypatch.setattr(restore, "gaussian", bad)
+    _fails(pins.test_restore_point_component)
