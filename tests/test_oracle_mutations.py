@@ -265,3 +265,12 @@ def test_restore_gaussian_with_swapped_axes_is_caught(monkeypatch):
         return np.exp(-0.5 * (ixx * dy * dy + 2 * ixy * dx * dy + iyy * dx * dx))   # x and y exchanged
     monkeypatch.setattr(restore, "gaussian", bad)
     _fails(pins.test_restore_point_component)
+
+
+def test_phase_rotation_sign_flipped_is_caught(monkeypatch):
+    orig = geometry.grid_records
+
+    def bad(uvw, vis, flags, cell, G, W, dlm=None):
+        return orig(uvw, vis, flags, cell, G, W, None if dlm is None else -np.asarray(dlm))   # exp(-2 pi i ...)
+    monkeypatch.setattr(geometry, "grid_records", bad)
+    _fails(pins.test_phase_rotation_moves_a_point_source_to_the_centre)

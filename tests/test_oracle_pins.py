@@ -164,6 +164,30 @@ def test_phase_centre_point_source():
     np.testing.assert_allclose(D, 2.5 * Bm[N // 2:N // 2 + N, N // 2:N // 2 + N], rtol=0, atol=1e-14 * 2.5)
 
 
+def test_phase_rotation_moves_a_point_source_to_the_centre():
+    """A unit point source (a, b) pixels from the phase centre has V = exp(-2 pi i (u l0 + v m0))
+    with l0 = a cell, m0 = b cell; since l = (x - N/2) cell and m = (y - N/2) cell (the direct
+    transform of the definition), its dirty map peaks at row N/2 + b, column N/2 + a.  Rotating
+    each visibility by exp(+2 pi i (u l0 + v m0)) (Sec. 4.2, the phase correction of Alg. 1) makes
+    it a source at the centre: the peak moves to (N/2, N/2) and the map is the beam's central
+    N x N (V' = 1)."""
+    wl, _ = _tiny(N=32, snr=0)
+    N, G = wl.N, wl.G
+    cell = pipeline.cell_sizes(wl)
+    uvw = geometry.uvw(wl.ant_enu, wl.pairs, wl.lat, wl.ha, wl.dec, wl.freq)
+    a, b = 5, -3
+    l0, m0 = a * cell[None, :, None], b * cell[None, :, None]
+    V = np.exp(-2j * math.pi * (uvw[..., 0] * l0 + uvw[..., 1] * m0))
+    flags = np.zeros(V.shape, np.uint8)
+    F, C = V.shape[:2]
+    dlm = np.stack([np.broadcast_to(a * cell, (F, C)), np.broadcast_to(b * cell, (F, C))], -1).reshape(F * C, 2)
+    for rot, centre in ((None, (N // 2 + b, N // 2 + a)), (dlm, (N // 2, N // 2))):
+        rec = geometry.grid_records(uvw, V, flags, cell, G, wl.W, rot)
+        _, D, Bm, _ = pipeline.dirty(geometry.instance_slice(rec, 0, wl.n_bl), N, G, KER)
+        assert np.unravel_index(np.argmax(D), D.shape) == centre
+    np.testing.assert_allclose(D, Bm[N // 2:N // 2 + N, N // 2:N // 2 + N], rtol=0, atol=1e-12)
+
+
 def test_dirty_beam_is_point_symmetric_about_its_centre():
     """Every sample is gridded at +uv and at -uv with the same weight (Sec. 3.2.3), so the beam
     part of the grid is real and even about the grid centre and so is its transform: over the
