@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import test_oracle_pins as pins
-from oracle import clean, geometry, gmm, imaging, operator, pswf, restore, steer
+from oracle import centering, clean, geometry, gmm, imaging, operator, pswf, restore, steer
 
 
 def _fails(fn, *args):
@@ -274,3 +274,12 @@ def test_phase_rotation_sign_flipped_is_caught(monkeypatch):
         return orig(uvw, vis, flags, cell, G, W, None if dlm is None else -np.asarray(dlm))   # exp(-2 pi i ...)
     monkeypatch.setattr(geometry, "grid_records", bad)
     _fails(pins.test_phase_rotation_moves_a_point_source_to_the_centre)
+
+
+def test_centering_correlation_sign_flipped_is_caught(monkeypatch):
+    orig = centering.correlation
+
+    def bad(M, S, smax):
+        return orig(M, S, smax)[::-1, ::-1]      # sum_p M(p) S(p + s)
+    monkeypatch.setattr(centering, "correlation", bad)
+    _fails(pins.test_centering_shift_of_a_displaced_disk_and_parabolic_peak)

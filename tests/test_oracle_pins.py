@@ -434,6 +434,20 @@ def test_correlation_fft_equals_bruteforce():
     np.testing.assert_allclose(centering.correlation(M, S, 6), centering.correlation_bruteforce(M, S, 6), atol=1e-10)
 
 
+def test_centering_shift_of_a_displaced_disk_and_parabolic_peak():
+    """Cc(s) = sum_p M(p) S(p - s) is largest where the mask's disk sits (Sec. 4.2 step 2): a model
+    disk moved by 4 columns and -3 rows gives the shift (4, -3) (x along columns, y along rows),
+    the parabolic refinement adding nothing at the symmetric peak; on samples of a quadratic bowl
+    whose top is at (2.3, -1.4) the three-point parabolas recover the fractional parts exactly."""
+    N, smax = 48, 12
+    S = centering.disk_model(N, 9.0)
+    M = np.roll(np.roll(S, -3, axis=0), 4, axis=1)
+    assert centering.best_shift(centering.correlation(M, S, smax), smax) == (4.0, -3.0)
+    yy, xx = np.mgrid[0:2 * smax + 1, 0:2 * smax + 1] - smax
+    sx, sy = centering.best_shift(-((xx - 2.3) ** 2) - 0.5 * (yy + 1.4) ** 2, smax)
+    assert sx == pytest.approx(2.3, abs=1e-12) and sy == pytest.approx(-1.4, abs=1e-12)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("off_px", [(0, 0), (9.0, -6.0), (-15.0, 12.0), (3.4, -7.7)])
 def test_centering_recovers_known_disk_offset(off_px):
