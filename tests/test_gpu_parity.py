@@ -265,6 +265,28 @@ def test_gmm(m, name):
         assert abs(float(_np(mu_b)[i]) - b) <= 1e-4 * rng
 
 
+def test_gmm_degenerate_and_few_valued_maps(m):
+    """A constant map has no histogram range: both levels are its value and the instance is marked
+    GMM_DEGENERATE; a zero map with three bright pixels collapses the three components onto one
+    level (no weight below 1e-4, so not marked); a two-valued noisy map splits cleanly.  Levels
+    and marks as in the oracle on the same FP32 maps."""
+    import torch
+    N = 64
+    rng = np.random.default_rng(5)
+    maps = [np.full((N, N), 0.25), np.zeros((N, N)),
+            np.where(rng.uniform(size=(N, N)) < 0.5, 0.0, 1.0) + 1e-3 * rng.normal(size=(N, N))]
+    maps[1][5, 7], maps[1][9, 9], maps[1][30, 2] = 1.0, 0.5, -0.2
+    maps = [d.astype(np.float32) for d in maps]
+    D = torch.tensor(np.stack(maps), device="cuda")
+    mu_a, mu_b, st = m.gmm(D, m.Config(N=N, G=4 * N))
+    ga, gb, st = _np(mu_a), _np(mu_b), _np(st)
+    for i, Dm in enumerate(maps):
+        a, b, deg = ogmm.sky_and_disk(Dm.astype(float))
+        tol = 1e-4 * max(float(Dm.max() - Dm.min()), 1.0)
+        assert abs(float(ga[i]) - a) <= tol and abs(float(gb[i]) - b) <= tol, i
+        assert bool(st[i] & m.ST_GMM_DEGENERATE) == deg, i
+
+
 @pytest.mark.parametrize("bins", [4096, 300])
 def test_gmm_bin_counts(m, bins):
     """The histogram has gmm_bins ranges (2..4096): 4096 takes the kernel's instance with sixteen
