@@ -252,6 +252,25 @@ def test_clean_threshold_and_abs_mode(m):
     lockstep(Do, Bo, _np(pos)[0], _np(flux)[0], cfg.gain, peak_mode=1)
 
 
+@pytest.mark.parametrize("name", ["N256x6", "N256x40", "N512x2", "N512x12", "N1024x2", "N1024x3"])
+def test_clean_onchip_abs_peaks_equal_streaming_and_oracle(m, name):
+    """The same on-chip shapes with the peak of |R| (peak_mode 1: keys |v|, the sign carried with
+    the index): components identical to the streaming kernel's, both following the oracle."""
+    import torch
+    wl = ONCHIP_CASES[name]()
+    cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
+    cfg.max_iter, cfg.thr_mode, cfg.peak_mode = 150, 0, 1
+    R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
+    cfg.clean_kernel = 1
+    R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
+    assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
+    assert float((R1 - R2).abs().max()) == 0.0
+    pg, fg = _np(p1), _np(f1)
+    for i, (Zo, Do, Bo, _) in enumerate(ref):
+        lockstep(Do, Bo, pg[i], fg[i], cfg.gain, peak_mode=1)
+        identical_positions_unless_near_tie(Do, Bo, pg[i], cfg.gain, cfg.max_iter, peak_mode=1)
+
+
 # ------------------------------------------------------------------------------ GMM
 @pytest.mark.parametrize("name", ["small-N64", "plain-N256"])
 def test_gmm(m, name):
