@@ -1237,22 +1237,24 @@ def test_autotune_grid_and_dirty_shapes(m):
         m.set_tuning(m.CALL_DIRTY, cfg, 0)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("name", ["N320x2", "N640", "N1280"])
-def test_clean_extended_onchip_equals_single_block(m, name):
+def test_clean_extended_onchip_equals_single_block(m, name, mode):
     """320, 640 and 1280 pixel images: bands of 102400 pixels on chip (65536 in tensor memory,
     36864 in shared memory; clusters of 1, 4 and 16 blocks) give the components and residuals of
-    one streaming block per instance (the same operations), and follow the oracle."""
+    one streaming block per instance (the same operations), and follow the oracle; for the
+    signed peak and for the peak of |R| (peak_mode 1)."""
     import torch
     wl = FIVE_CASES[name]()
     cfg, Z, D, Bm, st, ref = _dirty_both(m, wl)
-    cfg.max_iter = 120
+    cfg.max_iter, cfg.peak_mode = 120, mode
     R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
     cfg.clean_kernel = 1
     R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
     assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
     assert float((R1 - R2).abs().max()) == 0.0
     Do, Bo = ref[0][1], ref[0][2]
-    lockstep(Do, Bo, _np(p1)[0], _np(f1)[0], cfg.gain)
+    lockstep(Do, Bo, _np(p1)[0], _np(f1)[0], cfg.gain, peak_mode=mode)
 
 
 # ------------------------------------------------------------------------------ failure detection
