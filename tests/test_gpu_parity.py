@@ -1045,9 +1045,12 @@ def test_image_five_end_to_end(m, name, cap):
             assert np.abs(_np(out.residual)[i] - o["R"]).max() <= 1e-4 * np.abs(o["D"]).max()
 
 
-def test_clean_clustered_streaming_2560_equals_single_block(m):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_clean_clustered_streaming_2560_equals_single_block(m, mode):
     """2560^2 in a batch smaller than half the SMs: clusters of 16 blocks stream one instance and
-    give the components and residuals of one streaming block per instance, bit for bit."""
+    give the components and residuals of one streaming block per instance, bit for bit; for the
+    signed peak and for the peak of |R| (which takes the strong negative source first, followed
+    against the oracle)."""
     import torch
     N = 2560
     rng = np.random.default_rng(2560)
@@ -1059,14 +1062,18 @@ def test_clean_clustered_streaming_2560_equals_single_block(m):
     Do = rng.normal(size=(2, N, N)).astype(np.float32)
     Do[0, 100, 2000] += 30.0
     Do[1, 1500, 7] += 20.0
+    Do[1, 700, 2400] -= 35.0
     D = torch.tensor(Do, device="cuda")
     Bm = torch.tensor(np.stack([Bo, Bo]), device="cuda")
-    cfg = m.Config(N=N, G=4 * N, max_iter=30)
+    cfg = m.Config(N=N, G=4 * N, max_iter=30, peak_mode=mode)
     R1, p1, f1, n1, _ = m.clean(D, Bm, cfg)
     cfg.clean_kernel = 1
     R2, p2, f2, n2, _ = m.clean(D, Bm, cfg)
     assert torch.equal(n1, n2) and torch.equal(p1, p2) and torch.equal(f1, f2)
     assert float((R1 - R2).abs().max()) == 0.0
+    if mode == 1:
+        assert int(_np(p1)[1][0]) == 700 * N + 2400
+        lockstep(Do[1], Bo, _np(p1)[1], _np(f1)[1], cfg.gain, peak_mode=1)
 
 
 def test_clean_5120_streaming(m):
