@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kOnT, 1) k_hogbom_onchip(float *__restrict__ R
   }
 }
 
-// k_hogbom_cstream (images whose residual does not fit on chip, N >= 640): clusters of CS
+// k_hogbom_cstream (images whose residual does not fit on chip: 2560 and 5120): clusters of CS
 // blocks share an instance; block `rank` streams rows [rank ceil(N/CS), ...) of the residual from
 // memory every iteration (16-byte residual accesses, 4-byte beam loads) and the block maxima meet
 // in the cluster exchange of k_hogbom_onchip.  Instances are claimed from a counter, so a batch of
@@ -900,18 +900,17 @@ void launch_hogbom(float *R, const float *beam, const float *beam4, size_t cstri
                                          s);
   }
   if (done) return;
-  // images too large for the chip: one streaming block per instance fills the SMs when the batch
-  // has at least half as many instances as SMs (two chunks of muser_image overlap); smaller
-  // batches stream in clusters of blocks instead
+  // images too large for the chip (2560 and 5120 pixels): one streaming block per instance fills
+  // the SMs when the batch has at least half as many instances as SMs (two chunks of muser_image
+  // overlap); smaller batches stream in clusters of 16 blocks instead
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       sms = 1;
   }
-  if (next && !clean_uses_copies(N) && N >= 640 && N % 4 == 0 && 2 * B < sms) {
-    done = N >= 2560 ? launch_cstream<16>(R, beam, N, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s)
-                     : launch_cstream<8>(R, beam, N, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
+  if (next && !clean_uses_copies(N) && N >= 2560 && N % 4 == 0 && 2 * B < sms) {
+    done = launch_cstream<16>(R, beam, N, B, next, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
     if (done) return;
   }
   launch_hogbom_stream(R, beam, B, N, thr, gain, cap, peak_mode, pos, flux, n_comp, status, s);
