@@ -304,6 +304,24 @@ def test_image_variants_follow_oracle_and_autotune(m, name, N):
         m.set_tuning(m.CALL_IMAGE, cfg_for(m, wl), 0)
 
 
+@pytest.mark.parametrize("N", [256, 1024])
+def test_image_with_streaming_clean_vs_oracle(m, N):
+    """muser_image with the streaming CLEAN kernel chosen (clean_kernel 1: no beam copies, no
+    instance counter, one block per instance), over several chunks: every instance follows the
+    oracle, one restored image included."""
+    if N == 256:
+        wl, cap, chunk = synth.small_workload(n_ant=31, N=256, n_frame=6, config_id=232, bmax=2000.0), 200, 4
+    else:
+        wl, cap, chunk = synth.config3_muser2_uneven(n_frame=1, chans=[9, 250]), 300, 1
+    cfg = cfg_for(m, wl, batch_chunk=chunk, max_iter=cap)
+    cfg.clean_kernel = 1
+    out = _image(m, wl, cfg)
+    ro = oracle_records(wl)
+    assert_no_ties(ro, wl.G, wl.W)
+    res = _pool_map(_oracle_jobs.check_image_instance, _jobs(wl, ro, out, cap, 0, restore_for=(0,)))
+    assert len(res) == wl.n_inst and all(r["residual_err"] <= 1e-4 for r in res)
+
+
 def test_chained_gradient_steps_equal_separate_steps(m):
     """A descent loop whose steps chain (each leaves the next step's forward row pass in the
     workspace, the next skips it) computes bit for bit what separate steps compute with the same
